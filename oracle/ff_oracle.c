@@ -1,0 +1,370 @@
+/*
+ * ff_oracle.c -- plain CPU oracle of the Flow Fields dense-matching stage of FlowFields++
+ * (arXiv 1805.03517, Sec. 3 "Method" and Sec. 3.1 "Matches").
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the CPU-baseline leg of the benchmark.
+ * The product path never calls it.  It shares no code with the CUDA library.
+ *
+ * What it computes, step by step in the paper's order (Sec. 3.1):
+ *   1. an image pyramid of both frames, matched from the coarsest level to the finest (Sec. 3);
+ *   2. Walsh-Hadamard patch descriptors at every level (Sec. 3.1);
+ *   3. initial matches at the lowest resolution (Sec. 3.1: kD-tree matching of the WHT descriptors; here an
+ *      exact nearest-neighbour search, which the kD-tree approximates);
+ *   4. per scale: i iterations of propagation towards the four quadrants; in every iteration, the last
+ *      three propagation steps are each followed by a random search that perturbs both flow components by a
+ *      small random amount (Sec. 3.1);
+ *   5. an inverse flow field, and the consistency check that removes a match whose consistency error exceeds
+ *      the threshold eps (Sec. 3.1; eps in Table 3).
+ * The paper leaves the cost, descriptor size, filter, schedule and tie rules to cited work that is not
+ * restated here; the readings taken are listed beside each function.  Parity of the end-to-end schedule is
+ * pinned only through invariants (monotone cost, exact seed, exact translation recovery), since the paper
+ * prints no matching output to compare with.
+ */
+#include "ff_oracle.h"
+
+#include <limits.h>
+#include <stdlib.h>
+#include <string.h>
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+static int mini(int a, int b) { return a < b ? a : b; }
+
+/* Level sizes of the image pyramid (Sec. 3): each level halves the previous one, rounding down,
+ * never below 1 pixel.  Reading: the paper does not give the filter or odd-size rule. */
+int ffo_level_dims(int w, int h, int n_scales, int* ws, int* hs) {
+    if (w < 1 || h < 1 || n_scales < 1) return -1;
+    ws[0] = w;
+    hs[0] = h;
+    for (int s = 1; s < n_scales; s++) {
+        ws[s] = ws[s - 1] / 2 > 0 ? ws[s - 1] / 2 : 1;
+        hs[s] = hs[s - 1] / 2 > 0 ? hs[s - 1] / 2 : 1;
+    }
+    return 0;
+}
+
+/* One pyramid step (Sec. 3).  Reading: 2x2 box average per channel, rounded half up,
+ * source coordinates clamped to the image (only matters for a 1-pixel-wide or -high level). */
+void ffo_downsample(const uint8_t* src, int w, int h, uint8_t* dst) {
+    int w2 = w / 2 > 0 ? w / 2 : 1;
+    int h2 = h / 2 > 0 ? h / 2 : 1;
+    for (int y = 0; y < h2; y++) {
+        for (int x = 0; x < w2; x++) {
+            int x0 = mini(2 * x, w - 1), x1 = mini(2 * x + 1, w - 1);
+            int y0 = mini(2 * y, h - 1), y1 = mini(2 * y + 1, h - 1);
+            for (int c = 0; c < 3; c++) {
+                int a = src[(y0 * w + x0) * 3 + c];
+                int b = src[(y0 * w + x1) * 3 + c];
+                int d = src[(y1 * w + x0) * 3 + c];
+                int e = src[(y1 * w + x1) * 3 + c];
+                dst[(y * w2 + x) * 3 + c] = (uint8_t)((a + b + d + e + 2) / 4);
+            }
+        }
+    }
+}
+
+/* The four lowest-sequency Walsh functions of length 8, in sequency order (0, 1, 2, 3 sign changes). */
+static const int WALSH8[4][8] = {
+    {1, 1, 1, 1, 1, 1, 1, 1},
+    {1, 1, 1, 1, -1, -1, -1, -1},
+    {1, 1, -1, -1, -1, -1, 1, 1},
+    {1, 1, -1, -1, 1, 1, -1, -1},
+};
+
+/* Walsh-Hadamard patch descriptor (Sec. 3.1).  Reading: for every pixel and colour channel, the 4x4
+ * lowest-sequency coefficients of the 8x8 patch covering rows y-3..y+4 and columns x-3..x+4 (edge pixels
+ * repeated), unnormalised:
+ *     C_c[u][v](x, y) = sum_i sum_j W_u(i) W_v(j) I_c(clamp(x-3+j), clamp(y-3+i)),
+ * u indexing the vertical (row) Walsh function and v the horizontal one. |C| <= 64*255 fits int16. */
+void ffo_wht(const uint8_t* img, int w, int h, int16_t* feat) {
+    for (int y = 0; y < h; y++) {
+        for (int x = 0; x < w; x++) {
+            int16_t* out = feat + ((long)y * w + x) * FFO_NF;
+            for (int c = 0; c < 3; c++) {
+                for (int u = 0; u < 4; u++) {
+                    for (int v = 0; v < 4; v++) {
+                        int acc = 0;
+                        for (int i = 0; i < 8; i++) {
+                            int yy = clampi(y - 3 + i, 0, h - 1);
+                            for (int j = 0; j < 8; j++) {
+                                int xx = clampi(x - 3 + j, 0, w - 1);
+                                acc += WALSH8[u][i] * WALSH8[v][j] * img[((long)yy * w + xx) * 3 + c];
+                            }
+                        }
+                        out[c * 16 + u * 4 + v] = (int16_t)acc;
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* 32-bit integer finaliser "lowbias32" (C. Wellons, hash-prospector, 2018): the counter-based generator
+ * behind the random search.  The paper only asks for small random offsets (Sec. 3.1); a counter-based
+ * hash makes the offsets independent of execution order. */
+uint32_t ffo_mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+/* Random-search draw for pixel (x, y) at level `level`, iteration t, propagation direction d, flow
+ * component comp, matching direction dir (0 = frame 1 -> frame 2, 1 = inverse). */
+uint32_t ffo_hash(uint32_t seed, int dir, int level, int t, int d, int x, int y, int comp) {
+    uint32_t k0 = ffo_mix32((uint32_t)dir * 65536u + (uint32_t)level * 256u + (uint32_t)t);
+    uint32_t k1 = ffo_mix32(seed ^ k0);
+    uint32_t k2 = ffo_mix32(k1 ^ ((uint32_t)y * 65536u + (uint32_t)x));
+    return ffo_mix32(k2 ^ (uint32_t)(d * 2 + comp));
+}
+
+/* Matching cost (Sec. 3.1 defines it as a distance between feature descriptors).  Reading: sum of absolute
+ * differences over the 48 WHT coefficients of pixel (x, y) in frame A and pixel (x+fx, y+fy) in frame B.
+ * Returns -1 when the target lies outside the level (the candidate is rejected). */
+int32_t ffo_sad(const int16_t* fa, const int16_t* fb, int w, int h, int x, int y, int fx, int fy) {
+    int qx = x + fx, qy = y + fy;
+    if (qx < 0 || qx >= w || qy < 0 || qy >= h) return -1;
+    const int16_t* a = fa + ((long)y * w + x) * FFO_NF;
+    const int16_t* b = fb + ((long)qy * w + qx) * FFO_NF;
+    int32_t s = 0;
+    for (int k = 0; k < FFO_NF; k++) s += abs((int)a[k] - (int)b[k]);
+    return s;
+}
+
+/* floor(c / 128), the arithmetic shift C >> 7 written without relying on signed shifts. */
+static int quant7(int c) { return c >= 0 ? c / 128 : -((-c + 127) / 128); }
+
+/* Initial matches at the coarsest level (Sec. 3.1: WHT descriptors matched with kD-trees).  Reading: the
+ * exact nearest neighbour that a kD-tree approximates.  The descriptor is quantised to 8 bits (C >> 7,
+ * in [-128, 127]); distance = squared Euclidean; ties go to the smallest row-major index of frame B.
+ * flow = q - p; dist = the winning squared distance. */
+void ffo_seed(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* flow, int32_t* dist) {
+    long n = (long)w * h;
+    for (long p = 0; p < n; p++) {
+        long best_q = 0;
+        int32_t best = INT32_MAX;
+        for (long q = 0; q < n; q++) {
+            int32_t d2 = 0;
+            for (int k = 0; k < FFO_NF; k++) {
+                int e = quant7(fa[p * FFO_NF + k]) - quant7(fb[q * FFO_NF + k]);
+                d2 += e * e;
+            }
+            if (d2 < best) {
+                best = d2;
+                best_q = q;
+            }
+        }
+        flow[p * 2 + 0] = (int16_t)(best_q % w - p % w);
+        flow[p * 2 + 1] = (int16_t)(best_q / w - p / w);
+        dist[p] = best;
+    }
+}
+
+/* cost(p) = SAD of p's current flow; every flow handed in must point inside the level. */
+void ffo_init_cost(const int16_t* fa, const int16_t* fb, int w, int h, const int16_t* flow, int32_t* cost) {
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            long p = (long)y * w + x;
+            cost[p] = ffo_sad(fa, fb, w, h, x, y, flow[2 * p], flow[2 * p + 1]);
+        }
+}
+
+/* Coarse-to-fine hand-over (Sec. 3): a pixel starts from twice the flow of its parent pixel one level up,
+ * parent = (min(x/2, wc-1), min(y/2, hc-1)), and its cost is recomputed at the finer level.  Such a flow
+ * always lands inside the finer level; returns -2 if one does not (a broken assertion). */
+int ffo_upsample(const int16_t* fa, const int16_t* fb, int w, int h, const int16_t* flow_coarse, int wc, int hc,
+                 int16_t* flow, int32_t* cost) {
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            int px = mini(x / 2, wc - 1), py = mini(y / 2, hc - 1);
+            long pc = (long)py * wc + px, p = (long)y * w + x;
+            int fx = 2 * flow_coarse[2 * pc], fy = 2 * flow_coarse[2 * pc + 1];
+            flow[2 * p] = (int16_t)fx;
+            flow[2 * p + 1] = (int16_t)fy;
+            cost[p] = ffo_sad(fa, fb, w, h, x, y, fx, fy);
+            if (cost[p] < 0) return -2;
+        }
+    return 0;
+}
+
+/* The two neighbours a pixel looks at in propagation direction d (one direction per quadrant, Sec. 3.1).
+ * Reading: one sweep direction per quadrant -- d=0 from the left/top, d=1 right/top, d=2 left/bottom,
+ * d=3 right/bottom -- with the horizontal neighbour tried first. */
+static void neighbours(int d, int x, int y, int* n1x, int* n1y, int* n2x, int* n2y) {
+    *n1x = (d == 0 || d == 2) ? x - 1 : x + 1;
+    *n1y = y;
+    *n2x = x;
+    *n2y = (d == 0 || d == 1) ? y - 1 : y + 1;
+}
+
+/* Propagation with random search at one level (Sec. 3.1).  For t = 0..iters-1, for each direction d = 0..3,
+ * two half-sweeps (pixels with (x+y) even, then odd); within a half-sweep every pixel of that colour is
+ * updated from the state at the start of the half-sweep, so their order does not matter.
+ * A pixel tries, in order: the flow of neighbour 1, the flow of neighbour 2 (neighbours outside the level
+ * are skipped), and for d >= 1 (the last three propagation steps of the iteration) its current flow plus a
+ * random offset (ox, oy), each component uniform in [-R, R] from the hash, skipped if (0, 0).  A candidate
+ * replaces the current flow iff its cost is strictly lower; candidates outside the level are rejected.
+ * Stops after max_halfsweeps half-sweeps if max_halfsweeps >= 0; returns the number run. */
+long ffo_propagate(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* flow, int32_t* cost, int iters,
+                   int rs_radius, uint32_t seed, int dir, int level, long max_halfsweeps) {
+    long n = (long)w * h, done = 0;
+    int16_t* prev = (int16_t*)malloc(sizeof(int16_t) * 2 * (size_t)n);
+    if (!prev) return -1;
+    int span = 2 * rs_radius + 1;
+    for (int t = 0; t < iters; t++) {
+        for (int d = 0; d < 4; d++) {
+            for (int colour = 0; colour < 2; colour++) {
+                if (max_halfsweeps >= 0 && done >= max_halfsweeps) {
+                    free(prev);
+                    return done;
+                }
+                memcpy(prev, flow, sizeof(int16_t) * 2 * (size_t)n);
+                for (int y = 0; y < h; y++) {
+                    for (int x = 0; x < w; x++) {
+                        if ((x + y) % 2 != colour) continue;
+                        long p = (long)y * w + x;
+                        int fx = flow[2 * p], fy = flow[2 * p + 1];
+                        int32_t c = cost[p];
+                        int nx[2], ny[2];
+                        neighbours(d, x, y, &nx[0], &ny[0], &nx[1], &ny[1]);
+                        for (int k = 0; k < 2; k++) {
+                            if (nx[k] < 0 || nx[k] >= w || ny[k] < 0 || ny[k] >= h) continue;
+                            long q = (long)ny[k] * w + nx[k];
+                            int cx = prev[2 * q], cy = prev[2 * q + 1];
+                            int32_t cc = ffo_sad(fa, fb, w, h, x, y, cx, cy);
+                            if (cc >= 0 && cc < c) {
+                                fx = cx;
+                                fy = cy;
+                                c = cc;
+                            }
+                        }
+                        if (d >= 1) {
+                            int ox = (int)(ffo_hash(seed, dir, level, t, d, x, y, 0) % (uint32_t)span) - rs_radius;
+                            int oy = (int)(ffo_hash(seed, dir, level, t, d, x, y, 1) % (uint32_t)span) - rs_radius;
+                            if (ox != 0 || oy != 0) {
+                                int32_t cc = ffo_sad(fa, fb, w, h, x, y, fx + ox, fy + oy);
+                                if (cc >= 0 && cc < c) {
+                                    fx += ox;
+                                    fy += oy;
+                                    c = cc;
+                                }
+                            }
+                        }
+                        flow[2 * p] = (int16_t)fx;
+                        flow[2 * p + 1] = (int16_t)fy;
+                        cost[p] = c;
+                    }
+                }
+                done++;
+            }
+        }
+    }
+    free(prev);
+    return done;
+}
+
+/* One matching direction over a prepared pyramid of features (Sec. 3.1): exact seed at the coarsest level,
+ * then for every level from coarse to fine: hand-over from the level above (except the coarsest), cost,
+ * propagation with random search.  Writes the level-0 flow and cost.  feat_a/feat_b[s] are the level-s
+ * feature maps of the source and target frames; both frames have the sizes ws[s] x hs[s]. */
+int ffo_match_dir(const int16_t* const* feat_a, const int16_t* const* feat_b, const int* ws, const int* hs,
+                  const ffo_params* prm, int dir, int16_t* flow, int32_t* cost) {
+    int L = prm->n_scales;
+    int16_t* f_prev = NULL;
+    int w_prev = 0, h_prev = 0;
+    for (int s = L - 1; s >= 0; s--) {
+        int w = ws[s], h = hs[s];
+        long n = (long)w * h;
+        int16_t* f = (int16_t*)malloc(sizeof(int16_t) * 2 * (size_t)n);
+        int32_t* c = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+        if (!f || !c) {
+            free(f);
+            free(c);
+            free(f_prev);
+            return -1;
+        }
+        if (s == L - 1) {
+            ffo_seed(feat_a[s], feat_b[s], w, h, f, c);
+            ffo_init_cost(feat_a[s], feat_b[s], w, h, f, c);
+        } else if (ffo_upsample(feat_a[s], feat_b[s], w, h, f_prev, w_prev, h_prev, f, c) != 0) {
+            free(f);
+            free(c);
+            free(f_prev);
+            return -2;
+        }
+        ffo_propagate(feat_a[s], feat_b[s], w, h, f, c, prm->iters, prm->rs_radius, prm->seed, dir, s, -1);
+        free(f_prev);
+        f_prev = f;
+        w_prev = w;
+        h_prev = h;
+        if (s == 0) {
+            memcpy(flow, f, sizeof(int16_t) * 2 * (size_t)n);
+            memcpy(cost, c, sizeof(int32_t) * (size_t)n);
+        }
+        free(c);
+    }
+    free(f_prev);
+    return 0;
+}
+
+/* Forward/backward consistency check (Sec. 3.1; eps in Table 3).  p is kept iff q = p + f(p) lies in the
+ * image and the consistency error |f(p) + b(q)| (Euclidean) does not exceed eps; compared as squares. */
+void ffo_consistency(const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, uint8_t* mask) {
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            long p = (long)y * w + x;
+            int fx = fwd[2 * p], fy = fwd[2 * p + 1];
+            int qx = x + fx, qy = y + fy;
+            if (qx < 0 || qx >= w || qy < 0 || qy >= h) {
+                mask[p] = 0;
+                continue;
+            }
+            long q = (long)qy * w + qx;
+            long ex = fx + bwd[2 * q], ey = fy + bwd[2 * q + 1];
+            mask[p] = (uint8_t)(ex * ex + ey * ey <= (long)eps * eps);
+        }
+}
+
+/* The whole stage for one frame pair: pyramids and features of both frames, matching frame 1 -> 2
+ * (dir 0) and the inverse field 2 -> 1 (dir 1), then the consistency mask of the forward field. */
+int ffo_match_bidir(const uint8_t* rgb_a, const uint8_t* rgb_b, int w, int h, const ffo_params* prm,
+                    int16_t* flow_fwd, int16_t* flow_bwd, int32_t* cost_fwd, int32_t* cost_bwd, uint8_t* mask) {
+    int L = prm->n_scales;
+    if (L < 1 || L > 16) return -1;
+    int ws[16], hs[16];
+    if (ffo_level_dims(w, h, L, ws, hs) != 0) return -1;
+    uint8_t* img[2][16];
+    int16_t* feat[2][16];
+    memset(img, 0, sizeof img);
+    memset(feat, 0, sizeof feat);
+    int rc = 0;
+    for (int f = 0; f < 2 && rc == 0; f++) {
+        const uint8_t* src = f == 0 ? rgb_a : rgb_b;
+        for (int s = 0; s < L; s++) {
+            long n = (long)ws[s] * hs[s];
+            img[f][s] = (uint8_t*)malloc((size_t)n * 3);
+            feat[f][s] = (int16_t*)malloc((size_t)n * FFO_NF * sizeof(int16_t));
+            if (!img[f][s] || !feat[f][s]) {
+                rc = -1;
+                break;
+            }
+            if (s == 0)
+                memcpy(img[f][s], src, (size_t)n * 3);
+            else
+                ffo_downsample(img[f][s - 1], ws[s - 1], hs[s - 1], img[f][s]);
+            ffo_wht(img[f][s], ws[s], hs[s], feat[f][s]);
+        }
+    }
+    if (rc == 0) rc = ffo_match_dir((const int16_t* const*)feat[0], (const int16_t* const*)feat[1], ws, hs, prm, 0,
+                                    flow_fwd, cost_fwd);
+    if (rc == 0) rc = ffo_match_dir((const int16_t* const*)feat[1], (const int16_t* const*)feat[0], ws, hs, prm, 1,
+                                    flow_bwd, cost_bwd);
+    if (rc == 0) ffo_consistency(flow_fwd, flow_bwd, w, h, prm->eps, mask);
+    for (int f = 0; f < 2; f++)
+        for (int s = 0; s < L; s++) {
+            free(img[f][s]);
+            free(feat[f][s]);
+        }
+    return rc;
+}

@@ -1,0 +1,97 @@
+"""The five matching workloads and their parameters.
+
+Matching parameters follow FlowFields++ (arXiv 1805.03517) where it gives them -- the consistency threshold
+eps is 1 px for KITTI-style data and 7 px for Sintel-style data (Table 3) -- and otherwise the readings listed
+in the design notes: 8x8 patches with 16 Walsh-Hadamard coefficients per channel, a random-search radius of 2,
+3 scales / 4 iterations for the small case and 5 scales / 6 iterations for the rest (the paper itself uses
+i = 12 iterations, Sec. 3.1).
+
+Input seeds are 1000 * workload + pair index.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+__all__ = ["MatchParams", "PairSpec", "Workload", "WORKLOADS", "workload"]
+
+HASH_SEED = 0x2018_0503
+
+
+@dataclass(frozen=True)
+class MatchParams:
+    n_scales: int = 5
+    iters: int = 6
+    patch: int = 8
+    n_coef: int = 16
+    rs_radius: int = 2
+    eps: int = 1
+    seed: int = HASH_SEED
+
+
+@dataclass(frozen=True)
+class PairSpec:
+    kind: str  # 'rects' | 'kitti' | 'sintel'
+    w: int
+    h: int
+    seed: int
+    params: MatchParams
+
+    @property
+    def pixels(self) -> int:
+        return self.w * self.h
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    pairs: tuple = field(default_factory=tuple)
+    description: str = ""
+
+    @property
+    def pixels(self) -> int:
+        return sum(p.pixels for p in self.pairs)
+
+
+SMALL = MatchParams(n_scales=3, iters=4, eps=1)
+KITTI = MatchParams(n_scales=5, iters=6, eps=1)
+SINTEL = MatchParams(n_scales=5, iters=6, eps=7)
+
+SERVE_SIZES = ((320, 240, "rects"), (640, 480, "rects"), (1024, 436, "sintel"), (1242, 375, "kitti"))
+
+
+def _batch48():
+    pairs = []
+    for i in range(16):
+        pairs.append(PairSpec("kitti", 1242, 375, 4000 + i, KITTI))
+    for i in range(16):
+        pairs.append(PairSpec("sintel", 1024, 436, 4016 + i, SINTEL))
+    for i in range(16):
+        pairs.append(PairSpec("rects", 640, 480, 4032 + i, KITTI))
+    return tuple(pairs)
+
+
+WORKLOADS = {
+    "small_128x96": Workload("small_128x96", (PairSpec("rects", 128, 96, 1000, SMALL),),
+                             "128x96 value noise, two translated rectangles, L=3, T=4, eps=1"),
+    "kitti_1242x375": Workload("kitti_1242x375", (PairSpec("kitti", 1242, 375, 2000, KITTI),),
+                               "KITTI-shaped 1242x375 pair, L=5, T=6, eps=1"),
+    "sintel_1024x436": Workload("sintel_1024x436", (PairSpec("sintel", 1024, 436, 3000, SINTEL),),
+                                "Sintel-shaped 1024x436 pair, L=5, T=6, eps=7"),
+    "batch48_mixed": Workload("batch48_mixed", _batch48(),
+                              "48 pairs: 16x 1242x375, 16x 1024x436, 16x 640x480"),
+}
+
+
+def workload(name: str) -> Workload:
+    return WORKLOADS[name]
+
+
+def serve_pair(i: int) -> PairSpec:
+    """The i-th pair of the served stream: size drawn uniformly from SERVE_SIZES (seeded by i)."""
+    import numpy as np
+
+    rng = np.random.Generator(np.random.PCG64(5000))
+    choices = rng.integers(0, len(SERVE_SIZES), size=i + 1)
+    w, h, kind = SERVE_SIZES[int(choices[i])]
+    prm = SINTEL if kind == "sintel" else KITTI
+    return PairSpec(kind, w, h, 5000 + i, prm)

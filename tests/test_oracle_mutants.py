@@ -1,0 +1,68 @@
+"""Planted mistakes in the oracle must be caught by its pins.
+
+Each case copies oracle/ff_oracle.c, plants one plausible mistake (a dropped term, a wrong sign, index or
+operand, a wrong tie rule, wrong wiring of level or direction), compiles the copy with gcc and runs every pin
+of tests/oracle_pins.py against it: at least one must fail.  Mistakes are chosen so that the copy stays in
+bounds (every access the oracle makes is range-checked or clamped).
+"""
+import os
+
+import pytest
+
+import oracle
+from tests import oracle_pins as P
+
+MUTANTS = {
+    "pyr_round_down": ("(a + b + d + e + 2) / 4", "(a + b + d + e + 1) / 4"),
+    "pyr_wrong_column": ("x1 = mini(2 * x + 1, w - 1)", "x1 = mini(2 * x, w - 1)"),
+    "wht_transposed_basis": ("WALSH8[u][i] * WALSH8[v][j]", "WALSH8[u][j] * WALSH8[v][i]"),
+    "wht_anchor_off_by_one": ("int xx = clampi(x - 3 + j, 0, w - 1)", "int xx = clampi(x - 4 + j, 0, w - 1)"),
+    "wht_store_transposed": ("out[c * 16 + u * 4 + v]", "out[c * 16 + v * 4 + u]"),
+    "wht_wrong_walsh_row": ("{1, 1, -1, -1, -1, -1, 1, 1}", "{1, -1, -1, 1, 1, -1, -1, 1}"),
+    "mix_wrong_shift": ("x ^= x >> 15;", "x ^= x >> 14;"),
+    "hash_xy_swapped": ("(uint32_t)y * 65536u + (uint32_t)x", "(uint32_t)x * 65536u + (uint32_t)y"),
+    "hash_drops_direction_step": ("(uint32_t)(d * 2 + comp)", "(uint32_t)(2 + comp)"),
+    "sad_drops_last_coef": ("for (int k = 0; k < FFO_NF; k++) s += abs", "for (int k = 0; k < FFO_NF - 1; k++) s += abs"),
+    "sad_wrong_target_column": ("fb + ((long)qy * w + qx)", "fb + ((long)qy * w + x)"),
+    "quant_truncates": ("return c >= 0 ? c / 128 : -((-c + 127) / 128);", "return c / 128;"),
+    "seed_last_tie_wins": ("if (d2 < best) {", "if (d2 <= best) {"),
+    "seed_flow_sign": ("(int16_t)(best_q % w - p % w)", "(int16_t)(p % w - best_q % w)"),
+    "upsample_not_doubled": ("int fx = 2 * flow_coarse[2 * pc]", "int fx = flow_coarse[2 * pc]"),
+    "neighbour_wrong_quadrant": ("*n1x = (d == 0 || d == 2) ? x - 1 : x + 1;", "*n1x = (d == 0 || d == 1) ? x - 1 : x + 1;"),
+    "colour_order_swapped": ("if ((x + y) % 2 != colour) continue;", "if ((x + y) % 2 == colour) continue;"),
+    "accept_ties": ("if (cc >= 0 && cc < c) {\n                                fx = cx;", "if (cc >= 0 && cc <= c) {\n                                fx = cx;"),
+    "random_accept_ties": ("if (cc >= 0 && cc < c) {\n                                    fx += ox;",
+                           "if (cc >= 0 && cc <= c) {\n                                    fx += ox;"),
+    "random_search_on_all_steps": ("if (d >= 1) {", "if (d >= 0) {"),
+    "random_offset_not_centred": ("% (uint32_t)span) - rs_radius;\n                            int oy",
+                                  "% (uint32_t)span);\n                            int oy"),
+    "random_cost_wrong_component": ("x, y, fx + ox, fy + oy);", "x, y, fx + ox, fy + ox);"),
+    "level_not_in_hash": ("prm->rs_radius, prm->seed, dir, s, -1)", "prm->rs_radius, prm->seed, dir, 0, -1)"),
+    "inverse_same_direction_key": ("ws, hs, prm, 1,", "ws, hs, prm, 0,"),
+    "consistency_strict": ("<= (long)eps * eps", "< (long)eps * eps"),
+    "consistency_sign": ("long ex = fx + bwd[2 * q]", "long ex = fx - bwd[2 * q]"),
+}
+
+
+@pytest.fixture(scope="module")
+def source():
+    with open(os.path.join(os.path.dirname(oracle.__file__), "ff_oracle.c")) as f:
+        return f.read()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, source, tmp_path):
+    old, new = MUTANTS[name]
+    assert source.count(old) == 1, f"mutation site not unique: {old!r}"
+    src = tmp_path / "ff_oracle_mutant.c"
+    src.write_text(source.replace(old, new))
+    lib = oracle.load_library(oracle.compile_library(str(src), str(tmp_path / f"libffo_{name}.so")))
+    mutant = oracle.Oracle(lib)
+    caught = []
+    for check in P.ALL_CHECKS:
+        try:
+            check(mutant)
+        except Exception as e:  # an assertion, or the oracle reporting a broken internal assertion
+            caught.append((check.__name__, type(e).__name__))
+            break
+    assert caught, f"no pin catches the planted mistake {name}"
