@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the Flow Fields dense-matching stage (FlowFields++, arXiv 1805.03517, Sec. 3.1) on GB300.
+
+One step = the whole stage for one frame pair: features (pyramid + Walsh-Hadamard descriptors) of both frames,
+exact initial matches, per-level propagation with random search in both directions, and the forward/backward
+consistency check.  Metric: Mpx/s = level-0 pixels of frame 1 matched per second (bidirectional).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica of the workload (the path has no exchange between pairs; weak
+scaling); rank 0 prints one JSON line with the max-over-ranks step time.  ``--impl reference`` times the CPU
+oracle (the reference arm of this benchmark) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpx/s bidirectional FF matching, batched/served vs single-pair; p50/p99 latency"
+UNIT = "Mpx/s"
+L2_FLUSH_BYTES = 512 << 20
+ALG_BYTES_PER_PIXEL_ITER = 11 * 96 + 96 + 8  # candidate gathers + own descriptor + flow/cost, per direction
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="kitti_1242x375")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled in the background during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        self.index = vis.split(",")[local_rank].strip() if vis else str(local_rank)
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(workload):
+    from paper_1805_03517_gb300 import synth
+
+    return [synth.make_pair(p.kind, p.seed, p.w, p.h)[:2] for p in workload.pairs]
+
+
+def cpu_baseline(workload, imgs):
+    """The oracle as it stands, single-threaded, on one pair of the workload (a bounded sample)."""
+    import oracle
+
+    spec = workload.pairs[0]
+    a, b = imgs[0]
+    p = spec.params
+    o = oracle.default()
+    t = time.perf_counter()
+    o.match_bidir(a, b, oracle.params(p.n_scales, p.iters, p.rs_radius, p.eps, p.seed))
+    dt = time.perf_counter() - t
+    return {"value": spec.pixels / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one {spec.w}x{spec.h} pair of the workload, full bidirectional matching, "
+                      f"{dt:.2f} s on 1 host thread"}
+
+
+def _oracle_task(args):
+    import oracle
+
+    a, b, prm = args
+    o = oracle.default()
+    o.match_bidir(a, b, oracle.params(*prm))
+    return a.shape[0] * a.shape[1]
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle, as it stands, on the host cores; one pair per step, steps spread over a
+    process pool (one single-threaded oracle per core)."""
+    if rank != 0:
+        return
+    import multiprocessing as mp
+
+    from paper_1805_03517_gb300 import configs
+
+    workload = configs.workload(args.workload)
+    imgs = make_inputs(workload)
+    import oracle
+
+    oracle.build()
+    spec = workload.pairs[0]
+    p = spec.params
+    task = (imgs[0][0], imgs[0][1], (p.n_scales, p.iters, p.rs_radius, p.eps, p.seed))
+    cores = max(1, min(os.cpu_count() or 1, args.steps))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        if args.warmup:
+            pool.map(_oracle_task, [task] * min(args.warmup, cores))
+        t = time.perf_counter()
+        px = sum(pool.map(_oracle_task, [task] * args.steps))
+        dt = time.perf_counter() - t
+    value = px / dt / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1000 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload.name, "pairs_per_step": 1, "n_scales": p.n_scales, "iters": p.iters},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full {spec.w}x{spec.h} pairs over {cores} single-threaded "
+                                       "oracle processes"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    from paper_1805_03517_gb300 import build as B
+    from paper_1805_03517_gb300 import configs, ff
+
+    B.build()
+    workload = configs.workload(args.workload)
+    imgs = make_inputs(workload)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    prm = workload.pairs[0].params
+    M = ff.Matcher(prm, local_rank, stream)
+    with torch.cuda.stream(stream):
+        dev_imgs = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in imgs]
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream.synchronize()
+    px_per_step = workload.pixels
+    outs = None
+
+    def step():
+        nonlocal outs
+        pyrs = [(M.features(a), M.features(b)) for a, b in dev_imgs]
+        outs = M.match_batch(pyrs, outs=outs, with_cost=False)
+        for pa, pb in pyrs:
+            M.release(pa)
+            M.release(pb)
+
+    def timed(n, body, pre=None):
+        ms = []
+        for _ in range(n):
+            if pre:
+                pre()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            body()
+            e1.record(stream)
+            ms.append((e0, e1))
+        stream.synchronize()
+        return [a.elapsed_time(b) for a, b in ms]
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+
+    for _ in range(args.warmup):
+        flush_l2()
+        step()
+    stream.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    s0 = M.stats()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    times = timed(args.steps, step, pre=flush_l2)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    s1 = M.stats()
+    if dist:
+        dist.barrier()
+    ms = sum(times) / len(times)
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    value = px_per_step * world / (ms / 1000.0) / 1e6
+    launches = int(s1["kernel_launches"] - s0["kernel_launches"])
+
+    # end to end through the public API: pinned host frames in, flows and mask out, copies inside the timing
+    host_in = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in imgs]
+    host_out = None
+
+    def e2e_step():
+        nonlocal host_out
+        with torch.cuda.stream(stream):
+            for (ha, hb), (da, db) in zip(host_in, dev_imgs):
+                da.copy_(ha, non_blocking=True)
+                db.copy_(hb, non_blocking=True)
+        step()
+        with torch.cuda.stream(stream):
+            if host_out is None:
+                host_out = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items()}
+                            for o in outs]
+            for ho, o in zip(host_out, outs):
+                for k in ("flow_fwd", "flow_bwd", "mask"):
+                    ho[k].copy_(o[k], non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    e2e_times = timed(max(10, args.steps // 4), e2e_step, pre=flush_l2)
+    e2e_ms = sum(e2e_times) / len(e2e_times)
+    h2d = sum(a.numel() + b.numel() for a, b in host_in)
+    d2h = sum(o[k].numel() * o[k].element_size() for o in outs for k in ("flow_fwd", "flow_bwd", "mask"))
+
+    # per-phase device time (profiling context: same kernels and launch shapes, phases bracketed by events)
+    P = ff.Matcher(prm, local_rank, stream)
+    ff.ff_profile_enable(P.ctx, True)
+    prof_outs = None
+
+    def prof_step():
+        nonlocal prof_outs
+        pyrs = [(P.features(a), P.features(b)) for a, b in dev_imgs]
+        prof_outs = P.match_batch(pyrs, outs=prof_outs, with_cost=False)
+        for pa, pb in pyrs:
+            P.release(pa)
+            P.release(pb)
+
+    for _ in range(3):
+        prof_step()
+    ff.ff_profile_read(P.ctx)
+    n_prof = max(5, min(50, args.steps))
+    for _ in range(n_prof):
+        flush_l2()
+        prof_step()
+    phases = ff.ff_profile_read(P.ctx)
+    P.close()
+    pix_iters = sum(ff.ff_work_counts(M.ctx, p.w, p.h)[0] for p in workload.pairs)
+    prop_ms, prop_launches = phases["propagate"]
+    alg_bytes_per_step = pix_iters * 2 * ALG_BYTES_PER_PIXEL_ITER
+    launches_per_step = prop_launches / n_prof
+    avg_launch_ms = prop_ms / prop_launches
+    bytes_per_launch = alg_bytes_per_step / launches_per_step
+    achieved = bytes_per_launch / (avg_launch_ms / 1000.0) / 1e9
+    peak, peak_kind = load_peaks()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int16", "data": "synthetic",
+            "config": {"workload": workload.name, "pairs_per_step": len(workload.pairs),
+                       "px_per_step": px_per_step, "n_scales": prm.n_scales, "iters": prm.iters,
+                       "rs_radius": prm.rs_radius, "eps": prm.eps, "parallelism": f"replicas x{world}",
+                       "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write, outside the events)"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": {"value": px_per_step * world / (e2e_ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": {"bound": "hbm", "kernel": "k_propagate", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
+                         "launches_per_step": launches_per_step},
+            "phases_ms_per_step": {k: v[0] / n_prof for k, v in phases.items()},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(workload, imgs)
+        print(json.dumps(line), flush=True)
+    M.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

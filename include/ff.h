@@ -1,0 +1,164 @@
+/*
+ * ff.h -- C-ABI of the GB300 (sm_103a) Flow Fields dense-matching library (libff.so).
+ *
+ * The library computes the matching stage of FlowFields++ (Schuster, Bailer, Wasenmueller, Stricker,
+ * arXiv 1805.03517), Sec. 3.1 "Matches": for a pair of RGB frames it builds an image pyramid and per-level
+ * Walsh-Hadamard patch descriptors, finds initial matches at the coarsest level, refines them level by level
+ * with propagation towards the four quadrants plus random search, computes the inverse flow field and rejects
+ * matches whose forward/backward consistency error exceeds eps (Table 3 gives eps).  Interpolation (Sec. 3.2)
+ * and variational refinement (Sec. 3.3) are not part of this library.
+ *
+ * Conventions shared by every call:
+ *   - All arithmetic is integer and the result of every call is deterministic, independent of batching,
+ *     tiling and launch order.
+ *   - Image     uint8 [h][w][3] (RGB), rows `pitch_bytes` apart (pitch_bytes >= 3*w).
+ *   - Flow      int16 [h][w][2] row-major, (dx, dy) in whole pixels; pixel (x, y) of the source frame
+ *               matches pixel (x+dx, y+dy) of the target frame.  4-byte aligned.
+ *   - Cost      int32 [h][w]: sum of absolute differences of the 48 int16 descriptor coefficients.
+ *   - Mask      uint8 [h][w]: 1 = the match passed the consistency check, 0 = rejected.
+ *   - Pointers marked "device" must point to memory of the context's device; the caller owns them.
+ *     Calls only enqueue work on the context's stream and return; a device buffer handed in must stay
+ *     valid until that work has run (ff_sync waits for it).
+ *   - Sizes: 1 <= w, h <= 8192; n_scales 1..8 (every level is at least 1x1).  A violation returns
+ *     FF_ERR_ARG and launches nothing.
+ *   - Errors: every call returns an ff_status; ff_last_error() gives a message for the last failure.  A
+ *     CUDA failure (including one from earlier asynchronous work) returns FF_ERR_CUDA.
+ *   - A context is not thread-safe: use one context per host thread (or serialise calls).
+ */
+#ifndef FF_H
+#define FF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FF_API __attribute__((visibility("default")))
+#else
+#define FF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ff_ctx ff_ctx; /* matching context: device, stream, parameters, scratch and plan caches */
+typedef struct ff_pyr ff_pyr; /* one frame's feature pyramid, owned by the context that made it */
+
+typedef enum {
+    FF_OK = 0,
+    FF_ERR_ARG = 1,     /* invalid argument (nothing was launched) */
+    FF_ERR_OOM = 2,     /* device or host allocation failed */
+    FF_ERR_CUDA = 3,    /* a CUDA call failed, or earlier asynchronous work failed */
+    FF_ERR_TIMEOUT = 4, /* a bounded device-side wait gave up */
+    FF_ERR_BUSY = 5     /* resource in use (e.g. a pyramid released while a plan still refers to it) */
+} ff_status;
+
+/* Matching parameters (Sec. 3.1; eps from Table 3).
+ *   n_scales  pyramid levels L (1..8); level 0 is full resolution, each level halves the previous one.
+ *   iters     propagation iterations per level (1..255); the paper uses 12.
+ *   patch     patch size; must be 8.
+ *   n_coef    Walsh-Hadamard coefficients per channel; must be 16 (the 4x4 lowest sequencies).
+ *   rs_radius random-search radius R (0..16): each random candidate moves both flow components by an
+ *             integer in [-R, R].
+ *   eps       consistency threshold in pixels (>= 0); a match is kept iff |f(p) + b(p + f(p))| <= eps.
+ *   seed      seed of the counter-based random-search hash. */
+typedef struct {
+    int n_scales;
+    int iters;
+    int patch;
+    int n_coef;
+    int rs_radius;
+    int eps;
+    uint32_t seed;
+} ff_params;
+
+/* Default parameters: L=5, iters=6, patch=8, n_coef=16, rs_radius=2, eps=1, seed=0x20180503. */
+FF_API void ff_default_params(ff_params* p);
+
+/* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a cudaStream_t; NULL
+ * means the legacy default stream).  The parameters are copied.  *out receives the context. */
+FF_API ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* cuda_stream);
+
+/* Build the feature pyramid of one frame (Sec. 3 and 3.1): L pyramid levels (2x2 box average, rounded half
+ * up, sizes halved rounding down, at least 1), the 48 int16 Walsh-Hadamard coefficients of the 8x8 patch
+ * around every pixel of every level (edge pixels repeated), and the packed 8-bit descriptors of the coarsest
+ * level used by the initial matching.  `rgb_dev` is a device image [h][w][3] with rows pitch_bytes apart.
+ * *out receives a pyramid owned by the context; it stays valid until ff_pyr_release or ff_destroy.
+ * Released pyramids of the same size are recycled, so steady-state calls allocate nothing. */
+FF_API ff_status ff_features(ff_ctx* ctx, const uint8_t* rgb_dev, int w, int h, int pitch_bytes, ff_pyr** out);
+
+/* Match one direction (Sec. 3.1): dir 0 matches frame a to frame b, dir 1 computes the inverse field (the
+ * caller passes the pyramids swapped; dir only selects the random-search stream).  Exact nearest-neighbour
+ * initial matches at the coarsest level, then per level, coarse to fine: hand-over of twice the parent
+ * pixel's flow, `iters` iterations of propagation with random search.  Writes the level-0 flow to flow_dev
+ * (device, int16 [h][w][2]) and, if cost_dev is not NULL, the level-0 cost to cost_dev (device, int32
+ * [h][w]).  Both pyramids must have the same size. */
+FF_API ff_status ff_match_pair(ff_ctx* ctx, const ff_pyr* a, const ff_pyr* b, int dir, int16_t* flow_dev,
+                        int32_t* cost_dev);
+
+/* One frame pair of a batch: forward field a -> b, inverse field b -> a and the consistency mask of the
+ * forward field.  All outputs are device buffers of the pair's level-0 size; cost_fwd/cost_bwd may be NULL. */
+typedef struct {
+    const ff_pyr* a;
+    const ff_pyr* b;
+    int16_t* flow_fwd;
+    int16_t* flow_bwd;
+    int32_t* cost_fwd;
+    int32_t* cost_bwd;
+    uint8_t* mask;
+} ff_pair_job;
+
+/* Match n pairs of possibly different sizes in merged launches: for every job, the forward field, the
+ * inverse field and the consistency mask (Sec. 3.1).  Each job's results are identical to matching it alone.
+ * The launch sequence of a batch is recorded once into a CUDA graph and replayed when the same jobs (same
+ * pyramids and output buffers) are matched again. */
+FF_API ff_status ff_match_batch(ff_ctx* ctx, int n, const ff_pair_job* jobs);
+
+/* Forward/backward consistency check (Sec. 3.1, eps as in Table 3): mask[p] = 1 iff q = p + fwd(p) lies in
+ * the image and (fwd_x(p) + bwd_x(q))^2 + (fwd_y(p) + bwd_y(q))^2 <= eps^2.  All pointers are device
+ * buffers of size w x h. */
+FF_API ff_status ff_consistency(ff_ctx* ctx, const int16_t* fwd, const int16_t* bwd, int w, int h, int eps,
+                         uint8_t* mask_dev);
+
+/* Return a pyramid to the context's pool (its memory is reused by a later ff_features of the same size). */
+FF_API ff_status ff_pyr_release(ff_ctx* ctx, ff_pyr* pyr);
+
+/* Sizes of level `level` of a pyramid; FF_ERR_ARG if the level does not exist. */
+FF_API ff_status ff_pyr_level_dims(const ff_pyr* pyr, int level, int* w, int* h);
+
+/* Device pointer to the int16 [h][w][48] features of `level` (read-only view owned by the pyramid). */
+FF_API const int16_t* ff_pyr_features(const ff_pyr* pyr, int level);
+
+/* Message of the last failure on this context ("" if none).  Valid until the next call on the context. */
+FF_API const char* ff_last_error(ff_ctx* ctx);
+
+/* Wait for all work enqueued by this context; reports failures of asynchronous work as FF_ERR_CUDA. */
+FF_API ff_status ff_sync(ff_ctx* ctx);
+
+/* Counters of the most recent ff_match_pair / ff_match_batch / ff_features calls. */
+typedef struct {
+    int64_t kernel_launches;   /* kernels enqueued by this context since creation (graph nodes counted) */
+    int64_t graph_replays;     /* CUDA-graph launches since creation */
+    int64_t plans_built;       /* distinct match plans built (each may be captured into a graph) */
+    int64_t scratch_bytes;     /* device bytes currently held for plans, pyramids and staging */
+} ff_stats;
+FF_API ff_status ff_get_stats(ff_ctx* ctx, ff_stats* out);
+
+/* Per-phase device time.  When enabled, the context brackets each phase of the matching calls with CUDA
+ * events (and does not use graphs); ff_profile_read waits for the work and returns, per phase, the summed
+ * duration in milliseconds and the number of kernel launches since the last read.  Phases: */
+enum { FF_PHASE_FEATURES = 0, FF_PHASE_SEED = 1, FF_PHASE_HANDOVER = 2, FF_PHASE_PROPAGATE = 3,
+       FF_PHASE_CONSISTENCY = 4, FF_N_PHASES = 5 };
+FF_API ff_status ff_profile_enable(ff_ctx* ctx, int on);
+FF_API ff_status ff_profile_read(ff_ctx* ctx, double* ms /* [FF_N_PHASES] */, int64_t* launches /* [FF_N_PHASES] */);
+
+/* Algorithmic work of a plan for pyramids of size w x h with the context's parameters: per direction, the
+ * number of (pixel, iteration) updates summed over all levels, and the number of level-0 pixels. */
+FF_API ff_status ff_work_counts(ff_ctx* ctx, int w, int h, int64_t* pixel_iters, int64_t* pixels);
+
+/* Release every resource of the context (pyramids, plans, graphs); ctx must not be used afterwards. */
+FF_API ff_status ff_destroy(ff_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FF_H */

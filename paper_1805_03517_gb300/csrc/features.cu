@@ -1,0 +1,140 @@
+// features.cu -- image pyramid and Walsh-Hadamard patch descriptors (FlowFields++, arXiv 1805.03517, Sec. 3
+// and Sec. 3.1), plus the packed 8-bit descriptors of the coarsest level used by the initial matching.
+#include "ff_internal.h"
+
+namespace ff {
+
+// One pyramid step (Sec. 3): 2x2 box average per channel, rounded half up; source coordinates clamped so
+// that a 1-pixel-wide or -high level averages its only column/row.  One thread per output pixel.
+__global__ void k_downsample(const uint8_t* __restrict__ src, int sw, int sh, int spitch, uint8_t* __restrict__ dst,
+                             int dw, int dh) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y;
+    if (x >= dw || y >= dh) return;
+    int x0 = min(2 * x, sw - 1), x1 = min(2 * x + 1, sw - 1);
+    int y0 = min(2 * y, sh - 1), y1 = min(2 * y + 1, sh - 1);
+    const uint8_t* r0 = src + (size_t)y0 * spitch;
+    const uint8_t* r1 = src + (size_t)y1 * spitch;
+    uint8_t* o = dst + ((size_t)y * dw + x) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        int s = r0[x0 * 3 + c] + r0[x1 * 3 + c] + r1[x0 * 3 + c] + r1[x1 * 3 + c];
+        o[c] = (uint8_t)((s + 2) >> 2);
+    }
+}
+
+void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* dst, int dw, int dh,
+                       cudaStream_t st) {
+    dim3 grid((dw + 127) / 128, dh);
+    k_downsample<<<grid, 128, 0, st>>>(src, sw, sh, spitch, dst, dw, dh);
+}
+
+// Walsh-Hadamard descriptor (Sec. 3.1): for every pixel and channel, the 4x4 lowest-sequency coefficients of
+// the 8x8 patch over rows y-3..y+4, columns x-3..x+4 (edge pixels repeated), unnormalised.  The length-8
+// sequency-ordered Walsh functions are sums of the pair sums s01, s23, s45, s67 with signs
+//   W0 = + + + +,  W1 = + + - -,  W2 = + - - +,  W3 = + - + -
+// so the transform is separable: a row pass (4 outputs per patch row) then a column pass.
+// CTA = 32x8 output pixels; its 39x15 input window (with the clamped halo) is staged in shared memory.
+constexpr int kWtx = 32, kWty = 8;
+constexpr int kWinX = kWtx + 7, kWinY = kWty + 7;
+
+__device__ __forceinline__ void walsh4(int a0, int a1, int a2, int a3, int a4, int a5, int a6, int a7, int& c0,
+                                       int& c1, int& c2, int& c3) {
+    int s01 = a0 + a1, s23 = a2 + a3, s45 = a4 + a5, s67 = a6 + a7;
+    int p = s01 + s23, q = s45 + s67, r = s01 - s23, t = s45 - s67;
+    c0 = p + q;  // + + + + + + + +
+    c1 = p - q;  // + + + + - - - -
+    c2 = r - t;  // + + - - - - + +
+    c3 = r + t;  // + + - - + + - -
+}
+
+__global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
+    __shared__ uint8_t win[3][kWinY][kWinX];
+    int b = blockIdx.x, li = 0;
+    while (li + 1 < args.n && b >= args.lv[li + 1].tile_base) li++;
+    const WhtLevel L = args.lv[li];
+    int t = b - L.tile_base;
+    int tx0 = (t % L.tiles_x) * kWtx, ty0 = (t / L.tiles_x) * kWty;
+    for (int i = threadIdx.x; i < kWinX * kWinY; i += blockDim.x) {
+        int r = i / kWinX, c = i - r * kWinX;
+        int gy = min(max(ty0 - 3 + r, 0), L.h - 1);
+        int gx = min(max(tx0 - 3 + c, 0), L.w - 1);
+        const uint8_t* px = L.img + (size_t)gy * L.pitch + gx * 3;
+        win[0][r][c] = px[0];
+        win[1][r][c] = px[1];
+        win[2][r][c] = px[2];
+    }
+    __syncthreads();
+    int lx = threadIdx.x % kWtx, ly = threadIdx.x / kWtx;
+    int x = tx0 + lx, y = ty0 + ly;
+    if (x >= L.w || y >= L.h) return;
+    uint32_t out[24];
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        int R[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const uint8_t* row = &win[ch][ly + i][lx];
+            walsh4(row[0], row[1], row[2], row[3], row[4], row[5], row[6], row[7], R[i][0], R[i][1], R[i][2],
+                   R[i][3]);
+        }
+        int C[4][4];
+#pragma unroll
+        for (int v = 0; v < 4; v++)
+            walsh4(R[0][v], R[1][v], R[2][v], R[3][v], R[4][v], R[5][v], R[6][v], R[7][v], C[0][v], C[1][v],
+                   C[2][v], C[3][v]);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+            for (int v = 0; v < 4; v += 2)
+                out[ch * 8 + u * 2 + v / 2] = (uint32_t)(C[u][v] & 0xffff) | ((uint32_t)C[u][v + 1] << 16);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(L.feat + ((size_t)y * L.w + x) * kNF);
+#pragma unroll
+    for (int k = 0; k < 6; k++) dst[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+}
+
+int wht_tiles(int w, int h) { return ((w + kWtx - 1) / kWtx) * ((h + kWty - 1) / kWty); }
+
+void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st) {
+    k_wht<<<total_tiles, kWtx * kWty, 0, st>>>(a);
+}
+
+// 8-bit descriptor of the coarsest level: C >> 7 (arithmetic, i.e. floor(C / 128), in [-128, 127]) for the 48
+// coefficients, zero for the 16 padding lanes and for padding rows n..n8-1; norm = sum of squares.
+__global__ void k_seed_pack(const int16_t* __restrict__ feat, int n, int n8, int8_t* __restrict__ desc,
+                            int32_t* __restrict__ norm) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n8) return;
+    uint32_t words[16];
+    int s = 0;
+    if (p < n) {
+        const int16_t* f = feat + (size_t)p * kNF;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            uint32_t wv = 0;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                int q = ((int)f[4 * k + j]) >> 7;
+                s += q * q;
+                wv |= ((uint32_t)(q & 0xff)) << (8 * j);
+            }
+            words[k] = wv;
+        }
+        norm[p] = s;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 12; k++) words[k] = 0;
+    }
+#pragma unroll
+    for (int k = 12; k < 16; k++) words[k] = 0;
+    uint4* dst = reinterpret_cast<uint4*>(desc + (size_t)p * kSeedK);
+#pragma unroll
+    for (int k = 0; k < 4; k++) dst[k] = make_uint4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
+}
+
+void launch_seed_pack(const int16_t* feat, int n, int n8, int8_t* desc, int32_t* norm, cudaStream_t st) {
+    k_seed_pack<<<(n8 + 127) / 128, 128, 0, st>>>(feat, n, n8, desc, norm);
+}
+
+}  // namespace ff

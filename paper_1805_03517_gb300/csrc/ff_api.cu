@@ -1,0 +1,826 @@
+// ff_api.cu -- C-ABI of libff: contexts, feature pyramids, match plans (merged launches over many pairs, CUDA-graph
+// capture and replay), profiling.  The operations follow FlowFields++ (arXiv 1805.03517), Sec. 3.1.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ff.h"
+#include "ff_internal.h"
+
+using namespace ff;
+
+namespace {
+
+constexpr int kMaxDim = 8192;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
+int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+void level_dims(int w, int h, int L, int* ws, int* hs) {
+    ws[0] = w;
+    hs[0] = h;
+    for (int s = 1; s < L; s++) {
+        ws[s] = std::max(1, ws[s - 1] / 2);
+        hs[s] = std::max(1, hs[s - 1] / 2);
+    }
+}
+
+// A device allocation owned by a context.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct ff_pyr {
+    int w = 0, h = 0, L = 0;
+    int ws[kMaxLevels] = {}, hs[kMaxLevels] = {};
+    uint8_t* img[kMaxLevels] = {};   // levels 1..L-1 (level 0 is the caller's image, read only by ff_features)
+    int16_t* feat[kMaxLevels] = {};
+    int8_t* seed_desc = nullptr;     // [n_pad][64]
+    int32_t* seed_norm = nullptr;    // [n_coarse]
+    int n_coarse = 0, n_pad = 0;
+    DevBuf mem;
+    bool in_use = false;
+};
+
+namespace {
+
+enum class Kind { Seed, Handover, Propagate, Consistency };
+
+struct Launch {
+    Kind kind;
+    int phase;
+    // seed / handover / propagate: problem arrays in the plan's device table
+    const void* probs = nullptr;
+    const int* tile_prob = nullptr;
+    int n_probs = 0;
+    int total = 0;           // row tiles (seed) / CTAs (propagate)
+    int64_t total_pix = 0;   // handover
+    PropLaunch prop{};
+    // consistency
+    const uint32_t* fwd = nullptr;
+    const uint32_t* bwd = nullptr;
+    int w = 0, h = 0, eps = 0;
+    uint8_t* mask = nullptr;
+};
+
+// One direction of one pair.
+struct DirJob {
+    const ff_pyr* a;
+    const ff_pyr* b;
+    int dir;
+    uint32_t* flow_out;
+    int32_t* cost_out;  // may be null
+};
+struct ConsJob {
+    int dj_fwd, dj_bwd;  // indices into the plan's DirJobs
+    uint8_t* mask;
+};
+
+struct Plan {
+    std::vector<uintptr_t> key;
+    std::vector<Launch> launches;
+    std::vector<DevBuf> bufs;
+    cudaGraphExec_t exec = nullptr;
+    int graph_nodes = 0;
+    int64_t pixel_iters = 0;
+};
+
+struct TileCfg {
+    int tw, th, k;
+};
+
+}  // namespace
+
+struct ff_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    ff_params prm{};
+    std::vector<std::unique_ptr<ff_pyr>> pyrs;
+    std::map<std::vector<uintptr_t>, std::unique_ptr<Plan>> plans;
+    std::string err;
+    int64_t launches = 0, replays = 0, plans_built = 0, bytes = 0;
+    bool profiling = false;
+    struct Ev {
+        int phase;
+        cudaEvent_t a, b;
+        int n;
+    };
+    std::vector<Ev> events;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+ff_status fail(ff_ctx* c, ff_status s, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+ff_status fail(ff_ctx* c, ff_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define FF_CUDA(ctx, call)                                                                             \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail((ctx), FF_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));           \
+    } while (0)
+
+ff_status dev_alloc(ff_ctx* c, DevBuf& b, size_t bytes) {
+    b.bytes = bytes;
+    if (bytes == 0) {
+        b.p = nullptr;
+        return FF_OK;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(c, e == cudaErrorMemoryAllocation ? FF_ERR_OOM : FF_ERR_CUDA, "cudaMalloc(%zu) failed: %s",
+                    bytes, cudaGetErrorString(e));
+    }
+    c->bytes += (int64_t)bytes;
+    return FF_OK;
+}
+
+void dev_free(ff_ctx* c, DevBuf& b) {
+    if (b.p) {
+        cudaFree(b.p);
+        c->bytes -= (int64_t)b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+ff_status check_params(const ff_params* p, ff_ctx* c) {
+    if (!p) return fail(c, FF_ERR_ARG, "params is NULL");
+    if (p->n_scales < 1 || p->n_scales > kMaxLevels) return fail(c, FF_ERR_ARG, "n_scales must be 1..%d", kMaxLevels);
+    if (p->iters < 1 || p->iters > 255) return fail(c, FF_ERR_ARG, "iters must be 1..255");
+    if (p->patch != 8) return fail(c, FF_ERR_ARG, "patch must be 8");
+    if (p->n_coef != 16) return fail(c, FF_ERR_ARG, "n_coef must be 16");
+    if (p->rs_radius < 0 || p->rs_radius > 16) return fail(c, FF_ERR_ARG, "rs_radius must be 0..16");
+    if (p->eps < 0 || p->eps > 32767) return fail(c, FF_ERR_ARG, "eps must be 0..32767");
+    return FF_OK;
+}
+
+// Tile shape and iterations fused per launch for one level, from the total work of the launch.
+TileCfg choose_tiles(int64_t level_pixels_all_jobs, int T) {
+    // enough CTAs to cover the GPU a few times over, tiles no smaller than 16x16
+    static const TileCfg cands[] = {{64, 32, 1}, {32, 32, 1}, {32, 16, 1}, {16, 16, 1}};
+    for (const TileCfg& c : cands)
+        if (level_pixels_all_jobs / (c.tw * c.th) >= 2 * 152) return c;
+    (void)T;
+    return {16, 16, 1};
+}
+
+ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
+    cudaStream_t st = c->stream;
+    switch (L.kind) {
+        case Kind::Seed:
+            launch_seed(static_cast<const SeedProblem*>(L.probs), L.n_probs, L.total, st);
+            break;
+        case Kind::Handover:
+            launch_handover(static_cast<const HandoverProblem*>(L.probs), L.n_probs, L.total_pix, st);
+            break;
+        case Kind::Propagate:
+            launch_propagate(static_cast<const PropProblem*>(L.probs), L.tile_prob, L.total, L.prop, st);
+            break;
+        case Kind::Consistency:
+            launch_consistency(L.fwd, L.bwd, L.w, L.h, L.eps, L.mask, st);
+            break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, FF_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return FF_OK;
+}
+
+cudaEvent_t get_event(ff_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Enqueue a sequence of launches; with profiling on, each phase group is bracketed by events.
+ff_status run_launches(ff_ctx* c, const std::vector<Launch>& ls) {
+    size_t i = 0;
+    while (i < ls.size()) {
+        size_t j = i;
+        while (j < ls.size() && ls[j].phase == ls[i].phase) j++;
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (c->profiling) {
+            ea = get_event(c);
+            eb = get_event(c);
+            FF_CUDA(c, cudaEventRecord(ea, c->stream));
+        }
+        for (size_t k = i; k < j; k++) {
+            ff_status s = enqueue_launch(c, ls[k]);
+            if (s != FF_OK) return s;
+            c->launches += 1;
+        }
+        if (c->profiling) {
+            FF_CUDA(c, cudaEventRecord(eb, c->stream));
+            c->events.push_back({ls[i].phase, ea, eb, (int)(j - i)});
+        }
+        i = j;
+    }
+    return FF_OK;
+}
+
+// Build the launch sequence of a set of matching directions (+ consistency checks).
+ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons, Plan& P) {
+    const int L = c->prm.n_scales, T = c->prm.iters;
+    const int nj = (int)jobs.size();
+    // per job and level: two flow and two cost buffers (ping-pong) + seed distances
+    struct LevelBufs {
+        uint32_t* flow[2];
+        int32_t* cost[2];
+    };
+    std::vector<std::vector<LevelBufs>> lb(nj, std::vector<LevelBufs>(L));
+    std::vector<int32_t*> seed_dist(nj);
+    size_t scratch = 0;
+    for (int j = 0; j < nj; j++) {
+        for (int s = 0; s < L; s++) scratch += 4 * align_up((size_t)jobs[j].a->ws[s] * jobs[j].a->hs[s] * 4);
+        scratch += align_up((size_t)jobs[j].a->n_coarse * 4);
+    }
+    // problem tables
+    std::vector<SeedProblem> seeds;
+    std::vector<HandoverProblem> hos;
+    std::vector<PropProblem> props;
+    std::vector<int> tile_prob;
+    // record table offsets per launch, patched to device pointers after upload
+    struct Pending {
+        Launch l;
+        size_t off_probs, off_tiles;
+    };
+    std::vector<Pending> pend;
+
+    P.bufs.emplace_back();
+    ff_status st = dev_alloc(c, P.bufs.back(), scratch);
+    if (st != FF_OK) return st;
+    char* base = static_cast<char*>(P.bufs.back().p);
+    size_t off = 0;
+    for (int j = 0; j < nj; j++) {
+        for (int s = 0; s < L; s++) {
+            size_t n = (size_t)jobs[j].a->ws[s] * jobs[j].a->hs[s];
+            for (int k = 0; k < 2; k++) {
+                lb[j][s].flow[k] = reinterpret_cast<uint32_t*>(base + off);
+                off += align_up(n * 4);
+                lb[j][s].cost[k] = reinterpret_cast<int32_t*>(base + off);
+                off += align_up(n * 4);
+            }
+        }
+        seed_dist[j] = reinterpret_cast<int32_t*>(base + off);
+        off += align_up((size_t)jobs[j].a->n_coarse * 4);
+    }
+
+    // 1. exact initial matches at the coarsest level
+    {
+        Launch l{};
+        l.kind = Kind::Seed;
+        l.phase = FF_PHASE_SEED;
+        int tiles = 0;
+        size_t o = seeds.size();
+        for (int j = 0; j < nj; j++) {
+            const ff_pyr* A = jobs[j].a;
+            const ff_pyr* B = jobs[j].b;
+            SeedProblem sp{};
+            sp.A = A->seed_desc;
+            sp.B = B->seed_desc;
+            sp.normA = A->seed_norm;
+            sp.normB = B->seed_norm;
+            sp.n = A->n_coarse;
+            sp.w = A->ws[L - 1];
+            sp.flow = lb[j][L - 1].flow[0];
+            sp.dist = seed_dist[j];
+            sp.warp_base = tiles;
+            tiles += (sp.n + 15) / 16;
+            seeds.push_back(sp);
+        }
+        l.n_probs = nj;
+        l.total = tiles;
+        pend.push_back({l, o, 0});
+    }
+    // 2. per level: hand-over (cost of the seed at the coarsest level), then the fused propagation launches
+    std::vector<int> cur_buf(nj, 0);
+    for (int s = L - 1; s >= 0; s--) {
+        {
+            Launch l{};
+            l.kind = Kind::Handover;
+            l.phase = s == L - 1 ? FF_PHASE_SEED : FF_PHASE_HANDOVER;
+            size_t o = hos.size();
+            int64_t pix = 0;
+            for (int j = 0; j < nj; j++) {
+                const ff_pyr* A = jobs[j].a;
+                HandoverProblem hp{};
+                hp.fa = A->feat[s];
+                hp.fb = jobs[j].b->feat[s];
+                hp.w = A->ws[s];
+                hp.h = A->hs[s];
+                if (s == L - 1) {
+                    hp.parent = nullptr;
+                    hp.flow_in = lb[j][s].flow[0];
+                } else {
+                    hp.parent = lb[j][s + 1].flow[cur_buf[j]];
+                    hp.pw = A->ws[s + 1];
+                    hp.ph = A->hs[s + 1];
+                }
+                hp.flow_out = lb[j][s].flow[0];
+                hp.cost_out = lb[j][s].cost[0];
+                hp.pix_base = pix;
+                pix += (int64_t)hp.w * hp.h;
+                hos.push_back(hp);
+                cur_buf[j] = 0;
+            }
+            l.n_probs = nj;
+            l.total_pix = pix;
+            pend.push_back({l, o, 0});
+        }
+        int64_t level_pix = 0;
+        for (int j = 0; j < nj; j++) level_pix += (int64_t)jobs[j].a->ws[s] * jobs[j].a->hs[s];
+        TileCfg tc = choose_tiles(level_pix, T);
+        for (int t0 = 0; t0 < T; t0 += tc.k) {
+            int n_iter = std::min(tc.k, T - t0);
+            bool last = t0 + n_iter == T;
+            Launch l{};
+            l.kind = Kind::Propagate;
+            l.phase = FF_PHASE_PROPAGATE;
+            l.prop.tw = tc.tw;
+            l.prop.th = tc.th;
+            l.prop.max_iter = n_iter;
+            size_t o = props.size(), ot = tile_prob.size();
+            int tiles = 0;
+            for (int j = 0; j < nj; j++) {
+                const ff_pyr* A = jobs[j].a;
+                PropProblem pp{};
+                pp.fa = A->feat[s];
+                pp.fb = jobs[j].b->feat[s];
+                pp.w = A->ws[s];
+                pp.h = A->hs[s];
+                int in = cur_buf[j], out = in ^ 1;
+                pp.flow_in = lb[j][s].flow[in];
+                pp.cost_in = lb[j][s].cost[in];
+                if (last && s == 0) {  // the final launch writes the caller's buffers (cost to scratch if NULL)
+                    pp.flow_out = jobs[j].flow_out;
+                    pp.cost_out = jobs[j].cost_out ? jobs[j].cost_out : lb[j][s].cost[out];
+                } else {
+                    pp.flow_out = lb[j][s].flow[out];
+                    pp.cost_out = lb[j][s].cost[out];
+                }
+                cur_buf[j] = out;
+                pp.tiles_x = (pp.w + tc.tw - 1) / tc.tw;
+                int ty = (pp.h + tc.th - 1) / tc.th;
+                pp.tile_base = tiles;
+                pp.t0 = t0;
+                pp.n_iter = n_iter;
+                pp.level = s;
+                pp.dir = jobs[j].dir;
+                pp.seed = c->prm.seed;
+                pp.rs_radius = c->prm.rs_radius;
+                for (int k = 0; k < pp.tiles_x * ty; k++) tile_prob.push_back((int)(props.size()));
+                tiles += pp.tiles_x * ty;
+                props.push_back(pp);
+                P.pixel_iters += (int64_t)pp.w * pp.h * n_iter;
+            }
+            l.n_probs = nj;
+            l.total = tiles;
+            pend.push_back({l, o, ot});
+        }
+    }
+    // 3. consistency of each pair: the forward flow and the inverse flow, both at level 0
+    for (const ConsJob& cj : cons) {
+        Launch l{};
+        l.kind = Kind::Consistency;
+        l.phase = FF_PHASE_CONSISTENCY;
+        l.fwd = jobs[cj.dj_fwd].flow_out;
+        l.bwd = jobs[cj.dj_bwd].flow_out;
+        l.w = jobs[cj.dj_fwd].a->w;
+        l.h = jobs[cj.dj_fwd].a->h;
+        l.eps = c->prm.eps;
+        l.mask = cj.mask;
+        pend.push_back({l, 0, 0});
+    }
+
+    // upload the problem tables in one block
+    size_t o_seed = 0, o_ho = align_up(seeds.size() * sizeof(SeedProblem));
+    size_t o_prop = o_ho + align_up(hos.size() * sizeof(HandoverProblem));
+    size_t o_tile = o_prop + align_up(props.size() * sizeof(PropProblem));
+    size_t tbytes = o_tile + align_up(tile_prob.size() * sizeof(int));
+    std::vector<char> host(tbytes, 0);
+    memcpy(host.data() + o_seed, seeds.data(), seeds.size() * sizeof(SeedProblem));
+    memcpy(host.data() + o_ho, hos.data(), hos.size() * sizeof(HandoverProblem));
+    memcpy(host.data() + o_prop, props.data(), props.size() * sizeof(PropProblem));
+    memcpy(host.data() + o_tile, tile_prob.data(), tile_prob.size() * sizeof(int));
+    P.bufs.emplace_back();
+    st = dev_alloc(c, P.bufs.back(), tbytes);
+    if (st != FF_OK) return st;
+    char* tb = static_cast<char*>(P.bufs.back().p);
+    FF_CUDA(c, cudaMemcpy(tb, host.data(), tbytes, cudaMemcpyHostToDevice));
+    for (Pending& pd : pend) {
+        Launch l = pd.l;
+        switch (l.kind) {
+            case Kind::Seed:
+                l.probs = tb + o_seed + pd.off_probs * sizeof(SeedProblem);
+                break;
+            case Kind::Handover:
+                l.probs = tb + o_ho + pd.off_probs * sizeof(HandoverProblem);
+                break;
+            case Kind::Propagate:
+                l.probs = tb + o_prop;  // tile_prob holds absolute problem indices
+                l.tile_prob = reinterpret_cast<const int*>(tb + o_tile) + pd.off_tiles;
+                break;
+            case Kind::Consistency:
+                break;
+        }
+        P.launches.push_back(l);
+    }
+    // tile_prob entries index the whole problem array; a problem's tile_base is relative to its own launch
+    return FF_OK;
+}
+
+ff_status execute_plan(ff_ctx* c, Plan& P) {
+    // graphs need a capturable (non-legacy) stream; profiling brackets phases with events instead
+    bool use_graph = !c->profiling && c->stream != nullptr;
+    if (!use_graph) return run_launches(c, P.launches);
+    if (!P.exec) {
+        cudaGraph_t g = nullptr;
+        FF_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        ff_status s = FF_OK;
+        for (const Launch& l : P.launches) {
+            s = enqueue_launch(c, l);
+            if (s != FF_OK) break;
+        }
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (s != FF_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return fail(c, FF_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&P.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            P.exec = nullptr;
+            return fail(c, FF_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+        }
+        P.graph_nodes = (int)P.launches.size();
+    }
+    FF_CUDA(c, cudaGraphLaunch(P.exec, c->stream));
+    c->replays += 1;
+    c->launches += P.graph_nodes;
+    return FF_OK;
+}
+
+ff_status run_jobs(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons) {
+    std::vector<uintptr_t> key;
+    key.reserve(jobs.size() * 5 + cons.size() * 3 + 1);
+    for (const DirJob& j : jobs) {
+        key.push_back((uintptr_t)j.a);
+        key.push_back((uintptr_t)j.b);
+        key.push_back((uintptr_t)j.dir);
+        key.push_back((uintptr_t)j.flow_out);
+        key.push_back((uintptr_t)j.cost_out);
+    }
+    key.push_back(~(uintptr_t)0);
+    for (const ConsJob& cj : cons) {
+        key.push_back((uintptr_t)cj.dj_fwd);
+        key.push_back((uintptr_t)cj.dj_bwd);
+        key.push_back((uintptr_t)cj.mask);
+    }
+    auto it = c->plans.find(key);
+    if (it == c->plans.end()) {
+        if (c->plans.size() >= 64) {  // bound the cache: drop everything (plans are cheap to rebuild)
+            FF_CUDA(c, cudaStreamSynchronize(c->stream));
+            for (auto& kv : c->plans) {
+                if (kv.second->exec) cudaGraphExecDestroy(kv.second->exec);
+                for (DevBuf& b : kv.second->bufs) dev_free(c, b);
+            }
+            c->plans.clear();
+        }
+        auto P = std::make_unique<Plan>();
+        P->key = key;
+        ff_status s = build_plan(c, jobs, cons, *P);
+        if (s != FF_OK) {
+            for (DevBuf& b : P->bufs) dev_free(c, b);
+            return s;
+        }
+        c->plans_built += 1;
+        it = c->plans.emplace(key, std::move(P)).first;
+    }
+    return execute_plan(c, *it->second);
+}
+
+bool aligned4(const void* p) { return ((uintptr_t)p & 3) == 0; }
+
+ff_status check_pyr(ff_ctx* c, const ff_pyr* p, const char* what) {
+    if (!p) return fail(c, FF_ERR_ARG, "%s is NULL", what);
+    bool found = false;
+    for (auto& q : c->pyrs)
+        if (q.get() == p) found = true;
+    if (!found) return fail(c, FF_ERR_ARG, "%s does not belong to this context", what);
+    if (!p->in_use) return fail(c, FF_ERR_ARG, "%s has been released", what);
+    return FF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ff_default_params(ff_params* p) {
+    if (!p) return;
+    p->n_scales = 5;
+    p->iters = 6;
+    p->patch = 8;
+    p->n_coef = 16;
+    p->rs_radius = 2;
+    p->eps = 1;
+    p->seed = 0x20180503u;
+}
+
+ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* cuda_stream) {
+    if (!out) return FF_ERR_ARG;
+    *out = nullptr;
+    ff_status s = check_params(p, nullptr);
+    if (s != FF_OK) return s;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return FF_ERR_ARG;
+    }
+    ff_ctx* c = new (std::nothrow) ff_ctx();
+    if (!c) return FF_ERR_OOM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->prm = *p;
+    if (cudaSetDevice(device) != cudaSuccess || init_kernel_attributes() != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return FF_ERR_CUDA;
+    }
+    *out = c;
+    return FF_OK;
+}
+
+ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch_bytes, ff_pyr** out) {
+    if (!c) return FF_ERR_ARG;
+    if (!out) return fail(c, FF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!rgb_dev) return fail(c, FF_ERR_ARG, "rgb_dev is NULL");
+    if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim) return fail(c, FF_ERR_ARG, "size %dx%d outside 1..%d", w, h, kMaxDim);
+    if (pitch_bytes < 3 * w) return fail(c, FF_ERR_ARG, "pitch %d < 3*w", pitch_bytes);
+    FF_CUDA(c, cudaSetDevice(c->device));
+    const int L = c->prm.n_scales;
+    ff_pyr* P = nullptr;
+    for (auto& q : c->pyrs)
+        if (!q->in_use && q->w == w && q->h == h && q->L == L) {
+            P = q.get();
+            break;
+        }
+    if (!P) {
+        auto np = std::make_unique<ff_pyr>();
+        np->w = w;
+        np->h = h;
+        np->L = L;
+        level_dims(w, h, L, np->ws, np->hs);
+        np->n_coarse = np->ws[L - 1] * np->hs[L - 1];
+        np->n_pad = round_up(np->n_coarse, 16);
+        size_t bytes = 0;
+        for (int s = 1; s < L; s++) bytes += align_up((size_t)np->ws[s] * np->hs[s] * 3);
+        for (int s = 0; s < L; s++) bytes += align_up((size_t)np->ws[s] * np->hs[s] * kDescBytes);
+        bytes += align_up((size_t)np->n_pad * kSeedK) + align_up((size_t)np->n_coarse * 4);
+        ff_status s = dev_alloc(c, np->mem, bytes);
+        if (s != FF_OK) return s;
+        char* b = static_cast<char*>(np->mem.p);
+        size_t o = 0;
+        for (int l = 1; l < L; l++) {
+            np->img[l] = reinterpret_cast<uint8_t*>(b + o);
+            o += align_up((size_t)np->ws[l] * np->hs[l] * 3);
+        }
+        for (int l = 0; l < L; l++) {
+            np->feat[l] = reinterpret_cast<int16_t*>(b + o);
+            o += align_up((size_t)np->ws[l] * np->hs[l] * kDescBytes);
+        }
+        np->seed_desc = reinterpret_cast<int8_t*>(b + o);
+        o += align_up((size_t)np->n_pad * kSeedK);
+        np->seed_norm = reinterpret_cast<int32_t*>(b + o);
+        P = np.get();
+        c->pyrs.push_back(std::move(np));
+    }
+    P->in_use = true;
+
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (c->profiling) {
+        ea = get_event(c);
+        eb = get_event(c);
+        FF_CUDA(c, cudaEventRecord(ea, c->stream));
+    }
+    int nl = 0;
+    for (int s = 1; s < L; s++) {
+        const uint8_t* src = s == 1 ? rgb_dev : P->img[s - 1];
+        int spitch = s == 1 ? pitch_bytes : P->ws[s - 1] * 3;
+        launch_downsample(src, P->ws[s - 1], P->hs[s - 1], spitch, P->img[s], P->ws[s], P->hs[s], c->stream);
+        nl++;
+    }
+    WhtArgs wa{};
+    wa.n = L;
+    int tiles = 0;
+    for (int s = 0; s < L; s++) {
+        WhtLevel& lv = wa.lv[s];
+        lv.img = s == 0 ? rgb_dev : P->img[s];
+        lv.pitch = s == 0 ? pitch_bytes : P->ws[s] * 3;
+        lv.w = P->ws[s];
+        lv.h = P->hs[s];
+        lv.feat = P->feat[s];
+        lv.tiles_x = (P->ws[s] + 31) / 32;
+        lv.tile_base = tiles;
+        tiles += wht_tiles(P->ws[s], P->hs[s]);
+    }
+    launch_wht(wa, tiles, c->stream);
+    launch_seed_pack(P->feat[L - 1], P->n_coarse, P->n_pad, P->seed_desc, P->seed_norm, c->stream);
+    nl += 2;
+    c->launches += nl;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        P->in_use = false;
+        return fail(c, FF_ERR_CUDA, "feature launch failed: %s", cudaGetErrorString(e));
+    }
+    if (c->profiling) {
+        FF_CUDA(c, cudaEventRecord(eb, c->stream));
+        c->events.push_back({FF_PHASE_FEATURES, ea, eb, nl});
+    }
+    *out = P;
+    return FF_OK;
+}
+
+ff_status ff_match_pair(ff_ctx* c, const ff_pyr* a, const ff_pyr* b, int dir, int16_t* flow_dev, int32_t* cost_dev) {
+    if (!c) return FF_ERR_ARG;
+    ff_status s;
+    if ((s = check_pyr(c, a, "a")) != FF_OK) return s;
+    if ((s = check_pyr(c, b, "b")) != FF_OK) return s;
+    if (a->w != b->w || a->h != b->h) return fail(c, FF_ERR_ARG, "pyramids differ in size");
+    if (dir != 0 && dir != 1) return fail(c, FF_ERR_ARG, "dir must be 0 or 1");
+    if (!flow_dev || !aligned4(flow_dev)) return fail(c, FF_ERR_ARG, "flow_dev must be a 4-byte aligned device pointer");
+    if (cost_dev && !aligned4(cost_dev)) return fail(c, FF_ERR_ARG, "cost_dev must be 4-byte aligned");
+    FF_CUDA(c, cudaSetDevice(c->device));
+    std::vector<DirJob> jobs{{a, b, dir, reinterpret_cast<uint32_t*>(flow_dev), cost_dev}};
+    return run_jobs(c, jobs, {});
+}
+
+ff_status ff_match_batch(ff_ctx* c, int n, const ff_pair_job* jobs) {
+    if (!c) return FF_ERR_ARG;
+    if (n < 0 || (n > 0 && !jobs)) return fail(c, FF_ERR_ARG, "bad job list");
+    if (n == 0) return FF_OK;
+    std::vector<DirJob> dj;
+    std::vector<ConsJob> cj;
+    for (int i = 0; i < n; i++) {
+        const ff_pair_job& J = jobs[i];
+        ff_status s;
+        if ((s = check_pyr(c, J.a, "job.a")) != FF_OK) return s;
+        if ((s = check_pyr(c, J.b, "job.b")) != FF_OK) return s;
+        if (J.a->w != J.b->w || J.a->h != J.b->h) return fail(c, FF_ERR_ARG, "job %d: pyramids differ in size", i);
+        if (!J.flow_fwd || !J.flow_bwd || !J.mask) return fail(c, FF_ERR_ARG, "job %d: NULL output", i);
+        if (!aligned4(J.flow_fwd) || !aligned4(J.flow_bwd) || (J.cost_fwd && !aligned4(J.cost_fwd)) ||
+            (J.cost_bwd && !aligned4(J.cost_bwd)))
+            return fail(c, FF_ERR_ARG, "job %d: outputs must be 4-byte aligned", i);
+        dj.push_back({J.a, J.b, 0, reinterpret_cast<uint32_t*>(J.flow_fwd), J.cost_fwd});
+        dj.push_back({J.b, J.a, 1, reinterpret_cast<uint32_t*>(J.flow_bwd), J.cost_bwd});
+        cj.push_back({2 * i, 2 * i + 1, J.mask});
+    }
+    FF_CUDA(c, cudaSetDevice(c->device));
+    return run_jobs(c, dj, cj);
+}
+
+ff_status ff_consistency(ff_ctx* c, const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, uint8_t* mask_dev) {
+    if (!c) return FF_ERR_ARG;
+    if (!fwd || !bwd || !mask_dev || !aligned4(fwd) || !aligned4(bwd)) return fail(c, FF_ERR_ARG, "bad pointer");
+    if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim) return fail(c, FF_ERR_ARG, "size %dx%d outside 1..%d", w, h, kMaxDim);
+    if (eps < 0 || eps > 32767) return fail(c, FF_ERR_ARG, "eps must be 0..32767");
+    FF_CUDA(c, cudaSetDevice(c->device));
+    Launch l{};
+    l.kind = Kind::Consistency;
+    l.phase = FF_PHASE_CONSISTENCY;
+    l.fwd = reinterpret_cast<const uint32_t*>(fwd);
+    l.bwd = reinterpret_cast<const uint32_t*>(bwd);
+    l.w = w;
+    l.h = h;
+    l.eps = eps;
+    l.mask = mask_dev;
+    return run_launches(c, {l});
+}
+
+ff_status ff_pyr_release(ff_ctx* c, ff_pyr* p) {
+    if (!c) return FF_ERR_ARG;
+    ff_status s = check_pyr(c, p, "pyr");
+    if (s != FF_OK) return s;
+    p->in_use = false;
+    return FF_OK;
+}
+
+ff_status ff_pyr_level_dims(const ff_pyr* p, int level, int* w, int* h) {
+    if (!p || level < 0 || level >= p->L) return FF_ERR_ARG;
+    if (w) *w = p->ws[level];
+    if (h) *h = p->hs[level];
+    return FF_OK;
+}
+
+const int16_t* ff_pyr_features(const ff_pyr* p, int level) {
+    if (!p || level < 0 || level >= p->L) return nullptr;
+    return p->feat[level];
+}
+
+const char* ff_last_error(ff_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+ff_status ff_sync(ff_ctx* c) {
+    if (!c) return FF_ERR_ARG;
+    FF_CUDA(c, cudaSetDevice(c->device));
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
+    FF_CUDA(c, cudaGetLastError());
+    return FF_OK;
+}
+
+ff_status ff_get_stats(ff_ctx* c, ff_stats* out) {
+    if (!c || !out) return FF_ERR_ARG;
+    out->kernel_launches = c->launches;
+    out->graph_replays = c->replays;
+    out->plans_built = c->plans_built;
+    out->scratch_bytes = c->bytes;
+    return FF_OK;
+}
+
+ff_status ff_profile_enable(ff_ctx* c, int on) {
+    if (!c) return FF_ERR_ARG;
+    c->profiling = on != 0;
+    return FF_OK;
+}
+
+ff_status ff_profile_read(ff_ctx* c, double* ms, int64_t* launches) {
+    if (!c) return FF_ERR_ARG;
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
+    double acc[FF_N_PHASES] = {0};
+    int64_t cnt[FF_N_PHASES] = {0};
+    for (auto& e : c->events) {
+        float t = 0.f;
+        FF_CUDA(c, cudaEventElapsedTime(&t, e.a, e.b));
+        acc[e.phase] += t;
+        cnt[e.phase] += e.n;
+        c->event_pool.push_back(e.a);
+        c->event_pool.push_back(e.b);
+    }
+    c->events.clear();
+    for (int i = 0; i < FF_N_PHASES; i++) {
+        if (ms) ms[i] = acc[i];
+        if (launches) launches[i] = cnt[i];
+    }
+    return FF_OK;
+}
+
+ff_status ff_work_counts(ff_ctx* c, int w, int h, int64_t* pixel_iters, int64_t* pixels) {
+    if (!c || w < 1 || h < 1 || w > kMaxDim || h > kMaxDim) return FF_ERR_ARG;
+    int ws[kMaxLevels], hs[kMaxLevels];
+    level_dims(w, h, c->prm.n_scales, ws, hs);
+    int64_t pi = 0;
+    for (int s = 0; s < c->prm.n_scales; s++) pi += (int64_t)ws[s] * hs[s] * c->prm.iters;
+    if (pixel_iters) *pixel_iters = pi;
+    if (pixels) *pixels = (int64_t)w * h;
+    return FF_OK;
+}
+
+ff_status ff_destroy(ff_ctx* c) {
+    if (!c) return FF_ERR_ARG;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->plans) {
+        if (kv.second->exec) cudaGraphExecDestroy(kv.second->exec);
+        for (DevBuf& b : kv.second->bufs) dev_free(c, b);
+    }
+    for (auto& p : c->pyrs) dev_free(c, p->mem);
+    for (auto& e : c->events) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    delete c;
+    return FF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// ff_internal.h -- internal types and launch wrappers of libff (GB300 / sm_103a).
+//
+// Device data layout (all row-major, pixel (x, y) at y*w + x):
+//   image     uint8 [h][w][3]
+//   features  int16 [h][w][48]  96 B per pixel: three 32-B sectors (R, G, B), coefficient u*4+v in each
+//   seed desc int8  [N16][64]   coarsest level, C >> 7, zero-padded from 48 to 64 and to a multiple of 16 rows
+//   seed norm int32 [N]         squared norm of the 8-bit descriptor
+//   flow      uint32 [h][w]     packed (dx & 0xffff) | (dy << 16): the int16 [h][w][2] layout of the C-ABI
+//   cost      int32 [h][w]
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ff {
+
+constexpr int kNF = 48;           // int16 coefficients per pixel
+constexpr int kDescBytes = 96;    // bytes per pixel descriptor
+constexpr int kSeedK = 64;        // padded 8-bit seed descriptor length
+constexpr int kMaxLevels = 8;
+constexpr int kHaloPerIter = 4;   // halo growth per fused propagation iteration (one per half-sweep quadrant side)
+
+// ---------------------------------------------------------------------------------------------------------
+// features
+
+struct WhtLevel {
+    const uint8_t* img;  // level image
+    int pitch;           // bytes between rows
+    int w, h;
+    int16_t* feat;       // [h][w][48]
+    int tiles_x;
+    int tile_base;       // first CTA of this level in the fused launch
+};
+struct WhtArgs {
+    WhtLevel lv[kMaxLevels];
+    int n;
+};
+
+void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* dst, int dw, int dh,
+                       cudaStream_t st);
+int wht_tiles(int w, int h);
+void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st);
+void launch_seed_pack(const int16_t* feat, int n, int n8, int8_t* desc, int32_t* norm, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------------------------
+// initial matches (exact nearest neighbour at the coarsest level)
+
+struct SeedProblem {
+    const int8_t* A;       // source descriptors [N16][64]
+    const int8_t* B;       // target descriptors [N16][64]
+    const int32_t* normA;  // [N]
+    const int32_t* normB;  // [N]
+    int n, w;              // pixels and level width (both frames have the same level size)
+    uint32_t* flow;        // [N] packed
+    int32_t* dist;         // [N] squared distance of the winner (may be null)
+    int warp_base;         // first 16-row tile of this problem in the launch
+};
+void launch_seed(const SeedProblem* probs_dev, int n_probs, int total_row_tiles, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------------------------
+// hand-over (coarse-to-fine initialisation) and cost initialisation
+
+struct HandoverProblem {
+    const int16_t* fa;
+    const int16_t* fb;
+    int w, h;
+    const uint32_t* parent;  // flow of the level above (pw x ph), or null: take flow_in as is
+    int pw, ph;
+    const uint32_t* flow_in;
+    uint32_t* flow_out;
+    int32_t* cost_out;
+    int64_t pix_base;        // first pixel of this problem in the launch
+};
+void launch_handover(const HandoverProblem* probs_dev, int n_probs, int64_t total_pix, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------------------------
+// propagation + random search, `n_iter` iterations of one level per launch, temporally blocked tiles
+
+struct PropProblem {
+    const int16_t* fa;
+    const int16_t* fb;
+    const uint32_t* flow_in;
+    const int32_t* cost_in;
+    uint32_t* flow_out;
+    int32_t* cost_out;
+    int w, h;
+    int tiles_x;
+    int tile_base;   // first CTA of this problem in the launch
+    int t0;          // first iteration index (for the random-search hash)
+    int n_iter;      // iterations fused into this launch
+    int level;
+    int dir;
+    uint32_t seed;
+    int rs_radius;
+};
+struct PropLaunch {
+    int tw, th;      // tile interior
+    int max_iter;    // largest n_iter of the launch (sizes the shared-memory halo)
+};
+constexpr size_t kMaxPropSmem = 200 * 1024;
+size_t prop_smem_bytes(int tw, int th, int n_iter);
+cudaError_t init_kernel_attributes();  // once per device, before the first launch
+void launch_propagate(const PropProblem* probs_dev, const int* tile_prob_dev, int total_tiles, const PropLaunch& L,
+                      cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------------------------
+// consistency
+
+void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int eps, uint8_t* mask,
+                        cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------------------------
+// shared device helpers (library only)
+
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    // lowbias32 integer finaliser (C. Wellons, hash-prospector)
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+}  // namespace ff

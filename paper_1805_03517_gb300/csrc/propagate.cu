@@ -1,0 +1,241 @@
+// propagate.cu -- per-level refinement of the matches (FlowFields++, arXiv 1805.03517, Sec. 3.1): coarse-to-fine
+// hand-over, propagation towards the four quadrants with random search, and the forward/backward consistency
+// check.
+//
+// Schedule of one iteration t at one level (the same schedule the oracle runs): for each quadrant direction
+// d = 0..3 (neighbours left+top, right+top, left+bottom, right+bottom), two half-sweeps over the pixels with
+// (x + y) even, then odd.  A pixel of the active colour tries neighbour 1 (horizontal), neighbour 2 (vertical)
+// and, for d >= 1, its current flow plus a hashed random offset in [-R, R]^2 (skipped if zero); a candidate
+// is taken iff its SAD is strictly lower; targets outside the level are rejected.  Neighbours always have the
+// other colour, so every half-sweep is a fully parallel map.
+//
+// Temporal blocking: one CTA owns a tile of a level and runs n_iter whole iterations (8 half-sweeps each) in
+// shared memory before writing the tile back, reading the level state from one buffer and writing another.
+// It loads the tile plus a halo of 4 * n_iter pixels and, before half-sweep j, recomputes every pixel whose
+// value the remaining half-sweeps need: the region grows backwards from the tile by one pixel on the two
+// upstream sides of each later half-sweep.  Recomputed halo pixels use exactly the inputs of the CTA that owns
+// them, so every tile's output equals the global schedule bit for bit.
+#include <climits>
+
+#include "ff_internal.h"
+
+namespace ff {
+
+__device__ __forceinline__ int flow_x(uint32_t f) { return (int)(int16_t)(f & 0xffffu); }
+__device__ __forceinline__ int flow_y(uint32_t f) { return ((int)f) >> 16; }
+__device__ __forceinline__ uint32_t pack_flow(int dx, int dy) { return (uint32_t)(dx & 0xffff) | ((uint32_t)dy << 16); }
+__device__ __forceinline__ bool in_level(int x, int y, int w, int h) {
+    return (unsigned)x < (unsigned)w && (unsigned)y < (unsigned)h;
+}
+
+__device__ __forceinline__ void load_desc(const int16_t* __restrict__ f, int idx, uint4 (&d)[6]) {
+    const uint4* p = reinterpret_cast<const uint4*>(f) + (size_t)idx * 6;
+#pragma unroll
+    for (int k = 0; k < 6; k++) d[k] = __ldg(p + k);
+}
+
+// |a - b| summed over the 2 x 16-bit halves of one word, signed coefficients.
+__device__ __forceinline__ int sad_word(uint32_t a, uint32_t b) {
+    int al = (int)(int16_t)(a & 0xffffu), ah = ((int)a) >> 16;
+    int bl = (int)(int16_t)(b & 0xffffu), bh = ((int)b) >> 16;
+    return abs(al - bl) + abs(ah - bh);
+}
+
+__device__ __forceinline__ int sad96(const uint4 (&a)[6], const uint4 (&b)[6]) {
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+        s += sad_word(a[k].x, b[k].x) + sad_word(a[k].y, b[k].y) + sad_word(a[k].z, b[k].z) + sad_word(a[k].w, b[k].w);
+    return s;
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// hand-over: flow = 2 x parent flow (parent = (min(x/2, pw-1), min(y/2, ph-1))) or the given flow; cost = SAD.
+
+__global__ __launch_bounds__(256) void k_handover(const HandoverProblem* __restrict__ probs, int n_probs,
+                                                  int64_t total) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_probs - 1;
+        while (lo < hi) {  // last problem with pix_base <= i
+            int mid = (lo + hi + 1) >> 1;
+            if (probs[mid].pix_base <= i) lo = mid; else hi = mid - 1;
+        }
+        const HandoverProblem& P = probs[lo];
+        int p = (int)(i - P.pix_base);
+        int x = p % P.w, y = p / P.w;
+        uint32_t f;
+        if (P.parent) {
+            int px = min(x >> 1, P.pw - 1), py = min(y >> 1, P.ph - 1);
+            uint32_t pf = P.parent[py * P.pw + px];
+            f = pack_flow(2 * flow_x(pf), 2 * flow_y(pf));
+        } else {
+            f = P.flow_in[p];
+        }
+        int tx = x + flow_x(f), ty = y + flow_y(f);
+        int c = INT_MAX;  // unreachable for valid inputs: a handed-over flow always lands inside the level
+        if (in_level(tx, ty, P.w, P.h)) {
+            uint4 a[6], b[6];
+            load_desc(P.fa, p, a);
+            load_desc(P.fb, ty * P.w + tx, b);
+            c = sad96(a, b);
+        }
+        P.flow_out[p] = f;
+        P.cost_out[p] = c;
+    }
+}
+
+void launch_handover(const HandoverProblem* probs_dev, int n_probs, int64_t total_pix, cudaStream_t st) {
+    int64_t blocks = (total_pix + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_handover<<<(int)blocks, 256, 0, st>>>(probs_dev, n_probs, total_pix);
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// propagation + random search
+
+// Extra pixels (left, up, right, down) recomputed before half-sweep j = 2*d + colour of the last fused
+// iteration; earlier iterations add kHaloPerIter on every side per remaining iteration.
+__constant__ int8_t c_grow[8][4] = {{3, 3, 4, 4}, {2, 2, 4, 4}, {2, 1, 3, 4}, {2, 0, 2, 4},
+                                    {1, 0, 2, 3}, {0, 0, 2, 2}, {0, 0, 1, 1}, {0, 0, 0, 0}};
+
+size_t prop_smem_bytes(int tw, int th, int n_iter) {
+    int H = kHaloPerIter * n_iter;
+    return (size_t)(tw + 2 * H) * (th + 2 * H) * 8;
+}
+
+__global__ __launch_bounds__(256) void k_propagate(const PropProblem* __restrict__ probs,
+                                                   const int* __restrict__ tile_prob, PropLaunch L) {
+    extern __shared__ uint32_t smem[];
+    const PropProblem& P = probs[tile_prob[blockIdx.x]];
+    const int w = P.w, h = P.h;
+    const int tile = blockIdx.x - P.tile_base;
+    const int x0 = (tile % P.tiles_x) * L.tw, y0 = (tile / P.tiles_x) * L.th;
+    const int x1 = min(x0 + L.tw, w), y1 = min(y0 + L.th, h);
+    const int H = kHaloPerIter * P.n_iter;
+    const int lx0 = max(x0 - H, 0), ly0 = max(y0 - H, 0), lx1 = min(x1 + H, w), ly1 = min(y1 + H, h);
+    const int RW = lx1 - lx0, RH = ly1 - ly0;
+    uint32_t* sflow = smem;
+    int32_t* scost = reinterpret_cast<int32_t*>(smem + RW * RH);
+
+    for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
+        int r = i / RW, c = i - r * RW;
+        size_t g = (size_t)(ly0 + r) * w + lx0 + c;
+        sflow[i] = P.flow_in[g];
+        scost[i] = P.cost_in[g];
+    }
+    __syncthreads();
+
+    const int R = P.rs_radius;
+    const uint32_t span = 2u * R + 1u;
+    for (int it = 0; it < P.n_iter; it++) {
+        const int t = P.t0 + it;
+        const int rem = kHaloPerIter * (P.n_iter - 1 - it);
+        const uint32_t k1 = mix32(P.seed ^ mix32((uint32_t)P.dir * 65536u + (uint32_t)P.level * 256u + (uint32_t)t));
+        for (int j = 0; j < 8; j++) {
+            const int d = j >> 1, colour = j & 1;
+            const int rx0 = max(x0 - c_grow[j][0] - rem, 0), ry0 = max(y0 - c_grow[j][1] - rem, 0);
+            const int rx1 = min(x1 + c_grow[j][2] + rem, w), ry1 = min(y1 + c_grow[j][3] + rem, h);
+            const int HW = (rx1 - rx0 + 1) >> 1;
+            const int total = HW * (ry1 - ry0);
+            for (int i = threadIdx.x; i < total; i += blockDim.x) {
+                const int row = i / HW, slot = i - row * HW;
+                const int y = ry0 + row;
+                const int x = rx0 + 2 * slot + ((rx0 + y + colour) & 1);
+                if (x >= rx1) continue;
+                const int sidx = (y - ly0) * RW + (x - lx0);
+                uint32_t cur = sflow[sidx];
+                int c = scost[sidx];
+                const int n1x = x + ((d & 1) ? 1 : -1);
+                const int n2y = y + ((d & 2) ? 1 : -1);
+                const bool v1 = (unsigned)n1x < (unsigned)w;
+                const bool v2 = (unsigned)n2y < (unsigned)h;
+                const uint32_t f1 = v1 ? sflow[sidx + (n1x - x)] : 0u;
+                const uint32_t f2 = v2 ? sflow[sidx + (n2y - y) * RW] : 0u;
+                // a candidate equal to the current flow (or to an already tried one) cannot be strictly cheaper
+                const bool e1 = v1 && f1 != cur && in_level(x + flow_x(f1), y + flow_y(f1), w, h);
+                const bool e2 = v2 && f2 != cur && !(v1 && f2 == f1) && in_level(x + flow_x(f2), y + flow_y(f2), w, h);
+                if (!(e1 || e2 || d >= 1)) continue;
+                uint4 a[6];
+                load_desc(P.fa, y * w + x, a);
+                if (e1) {
+                    uint4 b[6];
+                    load_desc(P.fb, (y + flow_y(f1)) * w + x + flow_x(f1), b);
+                    int s = sad96(a, b);
+                    if (s < c) { cur = f1; c = s; }
+                }
+                if (e2) {
+                    uint4 b[6];
+                    load_desc(P.fb, (y + flow_y(f2)) * w + x + flow_x(f2), b);
+                    int s = sad96(a, b);
+                    if (s < c) { cur = f2; c = s; }
+                }
+                if (d >= 1) {
+                    const uint32_t k2 = mix32(k1 ^ ((uint32_t)y * 65536u + (uint32_t)x));
+                    const int ox = (int)(mix32(k2 ^ (uint32_t)(2 * d)) % span) - R;
+                    const int oy = (int)(mix32(k2 ^ (uint32_t)(2 * d + 1)) % span) - R;
+                    if (ox != 0 || oy != 0) {
+                        const int fx = flow_x(cur) + ox, fy = flow_y(cur) + oy;
+                        if (in_level(x + fx, y + fy, w, h)) {
+                            uint4 b[6];
+                            load_desc(P.fb, (y + fy) * w + x + fx, b);
+                            int s = sad96(a, b);
+                            if (s < c) { cur = pack_flow(fx, fy); c = s; }
+                        }
+                    }
+                }
+                sflow[sidx] = cur;
+                scost[sidx] = c;
+            }
+            __syncthreads();
+        }
+    }
+
+    const int TW = x1 - x0;
+    for (int i = threadIdx.x; i < TW * (y1 - y0); i += blockDim.x) {
+        int r = i / TW, c = i - r * TW;
+        int sidx = (y0 + r - ly0) * RW + (x0 + c - lx0);
+        size_t g = (size_t)(y0 + r) * w + x0 + c;
+        P.flow_out[g] = sflow[sidx];
+        P.cost_out[g] = scost[sidx];
+    }
+}
+
+cudaError_t init_kernel_attributes() {
+    return cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
+}
+
+void launch_propagate(const PropProblem* probs_dev, const int* tile_prob_dev, int total_tiles, const PropLaunch& L,
+                      cudaStream_t st) {
+    size_t smem = prop_smem_bytes(L.tw, L.th, L.max_iter);
+    k_propagate<<<total_tiles, 256, smem, st>>>(probs_dev, tile_prob_dev, L);
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// forward/backward consistency (Sec. 3.1; eps in Table 3): keep p iff q = p + f(p) is inside the image and
+// (f_x(p) + b_x(q))^2 + (f_y(p) + b_y(q))^2 <= eps^2.
+
+__global__ void k_consistency(const uint32_t* __restrict__ fwd, const uint32_t* __restrict__ bwd, int w, int h,
+                              int eps, uint8_t* __restrict__ mask) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w * h) return;
+    int x = i % w, y = i / w;
+    uint32_t f = fwd[i];
+    int fx = flow_x(f), fy = flow_y(f);
+    int qx = x + fx, qy = y + fy;
+    uint8_t m = 0;
+    if (in_level(qx, qy, w, h)) {
+        uint32_t b = bwd[qy * w + qx];
+        long long ex = fx + flow_x(b), ey = fy + flow_y(b);
+        m = (ex * ex + ey * ey <= (long long)eps * eps) ? 1 : 0;
+    }
+    mask[i] = m;
+}
+
+void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int eps, uint8_t* mask,
+                        cudaStream_t st) {
+    int n = w * h;
+    k_consistency<<<(n + 255) / 256, 256, 0, st>>>(fwd, bwd, w, h, eps, mask);
+}
+
+}  // namespace ff

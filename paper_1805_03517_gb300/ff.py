@@ -1,0 +1,298 @@
+"""Python binding of libff (include/ff.h): the Flow Fields dense-matching stage of FlowFields++ on GB300.
+
+The functions named ``ff_*`` are one-to-one wrappers of the C-ABI (argument marshalling only; every step of the
+matching runs in the library's CUDA kernels).  They take raw device pointers (``tensor.data_ptr()``) and raise
+``FFError`` on a non-OK status.  ``Matcher`` is a small convenience layer that allocates outputs as torch
+tensors on the context's device and stream.
+
+There is no CPU fallback: if ``libff.so`` has not been built this module raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libff.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "ff.h")
+
+FF_OK, FF_ERR_ARG, FF_ERR_OOM, FF_ERR_CUDA, FF_ERR_TIMEOUT, FF_ERR_BUSY = range(6)
+STATUS_NAMES = {0: "FF_OK", 1: "FF_ERR_ARG", 2: "FF_ERR_OOM", 3: "FF_ERR_CUDA", 4: "FF_ERR_TIMEOUT", 5: "FF_ERR_BUSY"}
+PHASES = ("features", "seed", "handover", "propagate", "consistency")
+
+
+class FFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_scales", ctypes.c_int), ("iters", ctypes.c_int), ("patch", ctypes.c_int),
+                ("n_coef", ctypes.c_int), ("rs_radius", ctypes.c_int), ("eps", ctypes.c_int),
+                ("seed", ctypes.c_uint32)]
+
+
+class PairJob(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("flow_fwd", ctypes.c_void_p),
+                ("flow_bwd", ctypes.c_void_p), ("cost_fwd", ctypes.c_void_p), ("cost_bwd", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
+                ("plans_built", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/ff.h declares."""
+    with open(path) as f:
+        return re.findall(r"^FF_API [^(]*?\b(ff_\w+)\(", f.read(), flags=re.M)
+
+
+def lib():
+    """Load libff.so (built by ``paper_1805_03517_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libff.so is not built ({LIB_PATH}); run `python -m paper_1805_03517_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, i64p = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)
+    S = ctypes.c_int
+    sig = {
+        "ff_default_params": (None, [ctypes.POINTER(Params)]),
+        "ff_create": (S, [ctypes.POINTER(vp), ctypes.POINTER(Params), i, vp]),
+        "ff_features": (S, [vp, vp, i, i, i, ctypes.POINTER(vp)]),
+        "ff_match_pair": (S, [vp, vp, vp, i, vp, vp]),
+        "ff_match_batch": (S, [vp, i, ctypes.POINTER(PairJob)]),
+        "ff_consistency": (S, [vp, vp, vp, i, i, i, vp]),
+        "ff_pyr_release": (S, [vp, vp]),
+        "ff_pyr_level_dims": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "ff_pyr_features": (vp, [vp, i]),
+        "ff_last_error": (ctypes.c_char_p, [vp]),
+        "ff_sync": (S, [vp]),
+        "ff_get_stats": (S, [vp, ctypes.POINTER(Stats)]),
+        "ff_profile_enable": (S, [vp, i]),
+        "ff_profile_read": (S, [vp, ctypes.POINTER(ctypes.c_double), i64p]),
+        "ff_work_counts": (S, [vp, i, i, i64p, i64p]),
+        "ff_destroy": (S, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(ctx, status):
+    if status != FF_OK:
+        msg = lib().ff_last_error(ctx).decode() if ctx else ""
+        raise FFError(status, msg)
+
+
+# ------------------------------------------------------------------------------------------------------------
+# one-to-one wrappers of the C-ABI
+
+
+def ff_default_params() -> Params:
+    p = Params()
+    lib().ff_default_params(ctypes.byref(p))
+    return p
+
+
+def ff_create(params: Params, device: int = 0, stream: int | None = 0):
+    ctx = ctypes.c_void_p()
+    _check(None, lib().ff_create(ctypes.byref(ctx), ctypes.byref(params), device, stream or None))
+    return ctx
+
+
+def ff_features(ctx, rgb_dev: int, w: int, h: int, pitch_bytes: int):
+    pyr = ctypes.c_void_p()
+    _check(ctx, lib().ff_features(ctx, rgb_dev, w, h, pitch_bytes, ctypes.byref(pyr)))
+    return pyr
+
+
+def ff_match_pair(ctx, a, b, dir: int, flow_dev: int, cost_dev: int | None):
+    _check(ctx, lib().ff_match_pair(ctx, a, b, dir, flow_dev, cost_dev or None))
+
+
+def ff_match_batch(ctx, jobs):
+    arr = (PairJob * len(jobs))(*jobs)
+    _check(ctx, lib().ff_match_batch(ctx, len(jobs), arr))
+
+
+def ff_consistency(ctx, fwd: int, bwd: int, w: int, h: int, eps: int, mask_dev: int):
+    _check(ctx, lib().ff_consistency(ctx, fwd, bwd, w, h, eps, mask_dev))
+
+
+def ff_pyr_release(ctx, pyr):
+    _check(ctx, lib().ff_pyr_release(ctx, pyr))
+
+
+def ff_pyr_level_dims(pyr, level: int):
+    w, h = ctypes.c_int(), ctypes.c_int()
+    _check(None, lib().ff_pyr_level_dims(pyr, level, ctypes.byref(w), ctypes.byref(h)))
+    return w.value, h.value
+
+
+def ff_pyr_features(pyr, level: int) -> int:
+    return lib().ff_pyr_features(pyr, level) or 0
+
+
+def ff_last_error(ctx) -> str:
+    return lib().ff_last_error(ctx).decode()
+
+
+def ff_sync(ctx):
+    _check(ctx, lib().ff_sync(ctx))
+
+
+def ff_get_stats(ctx) -> dict:
+    s = Stats()
+    _check(ctx, lib().ff_get_stats(ctx, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def ff_profile_enable(ctx, on: bool):
+    _check(ctx, lib().ff_profile_enable(ctx, 1 if on else 0))
+
+
+def ff_profile_read(ctx):
+    ms = (ctypes.c_double * len(PHASES))()
+    n = (ctypes.c_int64 * len(PHASES))()
+    _check(ctx, lib().ff_profile_read(ctx, ms, n))
+    return {p: (ms[i], n[i]) for i, p in enumerate(PHASES)}
+
+
+def ff_work_counts(ctx, w: int, h: int):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, lib().ff_work_counts(ctx, w, h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def ff_destroy(ctx):
+    _check(None, lib().ff_destroy(ctx))
+
+
+# ------------------------------------------------------------------------------------------------------------
+# torch-facing convenience layer
+
+
+def to_params(p) -> Params:
+    """Accept a Params, a configs.MatchParams or any object with the same fields."""
+    if isinstance(p, Params):
+        return p
+    return Params(p.n_scales, p.iters, getattr(p, "patch", 8), getattr(p, "n_coef", 16), p.rs_radius, p.eps,
+                  p.seed & 0xFFFFFFFF)
+
+
+@dataclass
+class Pyramid:
+    handle: ctypes.c_void_p
+    w: int
+    h: int
+
+
+class Matcher:
+    """One matching context on one device and stream; outputs are torch tensors on that device."""
+
+    def __init__(self, params, device: int = 0, stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.params = to_params(params)
+        self.ctx = ff_create(self.params, device, self.stream.cuda_stream)
+
+    def close(self):
+        if self.ctx:
+            ff_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # interpreter shutdown: the library or CUDA may already be gone
+            pass
+
+    def _empty(self, shape, dtype):
+        with self.torch.cuda.stream(self.stream):
+            return self.torch.empty(shape, dtype=dtype, device=self.device)
+
+    def features(self, img) -> Pyramid:
+        """img: uint8 [h][w][3] CUDA tensor (rows may be strided)."""
+        assert img.dtype == self.torch.uint8 and img.is_cuda and img.dim() == 3 and img.shape[2] == 3
+        assert img.stride(2) == 1 and img.stride(1) == 3
+        h, w = int(img.shape[0]), int(img.shape[1])
+        return Pyramid(ff_features(self.ctx, img.data_ptr(), w, h, img.stride(0)), w, h)
+
+    def release(self, pyr: Pyramid):
+        ff_pyr_release(self.ctx, pyr.handle)
+
+    def level_features(self, pyr: Pyramid, level: int):
+        """Copy of the int16 [h][w][48] features of one level (for inspection and tests)."""
+        w, h = ff_pyr_level_dims(pyr.handle, level)
+        ptr = ff_pyr_features(pyr.handle, level)
+        out = self._empty((h, w, 48), self.torch.int16)
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        src = _DevView(ptr, h * w * 96)
+        out.view(-1).view(self.torch.uint8).copy_(self.torch.as_tensor(src, device=self.device))
+        return out
+
+    def match_pair(self, a: Pyramid, b: Pyramid, dir: int = 0, with_cost: bool = True):
+        flow = self._empty((a.h, a.w, 2), self.torch.int16)
+        cost = self._empty((a.h, a.w), self.torch.int32) if with_cost else None
+        ff_match_pair(self.ctx, a.handle, b.handle, dir, flow.data_ptr(), cost.data_ptr() if cost is not None else None)
+        return flow, cost
+
+    def alloc_outputs(self, pairs, with_cost=True):
+        outs = []
+        for a, _ in pairs:
+            o = {"flow_fwd": self._empty((a.h, a.w, 2), self.torch.int16),
+                 "flow_bwd": self._empty((a.h, a.w, 2), self.torch.int16),
+                 "mask": self._empty((a.h, a.w), self.torch.uint8)}
+            if with_cost:
+                o["cost_fwd"] = self._empty((a.h, a.w), self.torch.int32)
+                o["cost_bwd"] = self._empty((a.h, a.w), self.torch.int32)
+            outs.append(o)
+        return outs
+
+    def match_batch(self, pairs, outs=None, with_cost=True):
+        """pairs: list of (Pyramid a, Pyramid b).  Returns (or fills) one dict of outputs per pair."""
+        if outs is None:
+            outs = self.alloc_outputs(pairs, with_cost)
+        jobs = []
+        for (a, b), o in zip(pairs, outs):
+            jobs.append(PairJob(a.handle, b.handle, o["flow_fwd"].data_ptr(), o["flow_bwd"].data_ptr(),
+                                o["cost_fwd"].data_ptr() if "cost_fwd" in o else None,
+                                o["cost_bwd"].data_ptr() if "cost_bwd" in o else None, o["mask"].data_ptr()))
+        ff_match_batch(self.ctx, jobs)
+        return outs
+
+    def consistency(self, fwd, bwd, eps: int):
+        h, w = int(fwd.shape[0]), int(fwd.shape[1])
+        mask = self._empty((h, w), self.torch.uint8)
+        ff_consistency(self.ctx, fwd.data_ptr(), bwd.data_ptr(), w, h, eps, mask.data_ptr())
+        return mask
+
+    def sync(self):
+        ff_sync(self.ctx)
+
+    def stats(self):
+        return ff_get_stats(self.ctx)
+
+
+class _DevView:
+    """Minimal __cuda_array_interface__ over a device pointer owned by the library (read-only bytes)."""
+
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3,
+                                         "strides": None}
