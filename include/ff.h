@@ -113,6 +113,22 @@ typedef struct {
  * pyramids and output buffers) are matched again. */
 FF_API ff_status ff_match_batch(ff_ctx* ctx, int n, const ff_pair_job* jobs);
 
+/* Choose, per pyramid level, the propagation tile shape and the number of iterations fused into one launch for
+ * batches shaped like `jobs` (same level sizes and number of pairs): every candidate configuration is run
+ * `reps` (1..100) times on these jobs and the fastest is kept for each level.  Results never depend on the
+ * configuration; the jobs' outputs are overwritten.  Cached plans are dropped so later calls use the choice.
+ * This is a property of the GB300 implementation (the paper has no counterpart). */
+FF_API ff_status ff_autotune(ff_ctx* ctx, int n, const ff_pair_job* jobs, int reps);
+
+/* Impose the propagation configuration of one level (tile width and height in pixels, iterations fused per
+ * launch) on every later plan of this context, overriding the autotuner; all zeros removes the override.
+ * FF_ERR_ARG if the tile with its halo does not fit in shared memory.  Cached plans are dropped. */
+FF_API ff_status ff_set_tuning(ff_ctx* ctx, int level, int tile_w, int tile_h, int iters_per_launch);
+
+/* The configuration in force for `level`: the override if set, else the autotuner's choice (tile width,
+ * height, iterations per launch); FF_ERR_ARG if neither exists. */
+FF_API ff_status ff_get_tuning(ff_ctx* ctx, int level, int* tile_w, int* tile_h, int* iters_per_launch);
+
 /* Forward/backward consistency check (Sec. 3.1, eps as in Table 3): mask[p] = 1 iff q = p + fwd(p) lies in
  * the image and (fwd_x(p) + bwd_x(q))^2 + (fwd_y(p) + bwd_y(q))^2 <= eps^2.  All pointers are device
  * buffers of size w x h. */

@@ -10,6 +10,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "ff.h"
@@ -56,23 +57,29 @@ struct ff_pyr {
 
 namespace {
 
-enum class Kind { Seed, Handover, Propagate, Consistency };
+enum class Kind { ZeroCounters, Seed, Handover, Propagate, Consistency };
 
 struct Launch {
     Kind kind;
     int phase;
+    int level = -1;
     // seed / handover / propagate: problem arrays in the plan's device table
     const void* probs = nullptr;
-    const int* tile_prob = nullptr;
     int n_probs = 0;
-    int total = 0;           // row tiles (seed) / CTAs (propagate)
+    int total = 0;           // row tiles (seed) / queue length (propagate)
     int64_t total_pix = 0;   // handover
+    const int2* queue = nullptr;
+    int* counter = nullptr;
+    int grid = 0;
     PropLaunch prop{};
     // consistency
     const uint32_t* fwd = nullptr;
     const uint32_t* bwd = nullptr;
     int w = 0, h = 0, eps = 0;
     uint8_t* mask = nullptr;
+    // zero counters
+    void* zero_ptr = nullptr;
+    size_t zero_bytes = 0;
 };
 
 // One direction of one pair.
@@ -94,26 +101,36 @@ struct Plan {
     std::vector<DevBuf> bufs;
     cudaGraphExec_t exec = nullptr;
     int graph_nodes = 0;
-    int64_t pixel_iters = 0;
 };
 
 struct TileCfg {
-    int tw, th, k;
+    int tw, th, k;  // tile interior and iterations fused per launch
 };
+
+// Candidate propagation configurations (tile shape, fused iterations) the autotuner times per level.
+const TileCfg kCands[] = {{64, 32, 1}, {32, 32, 1}, {64, 16, 1}, {32, 16, 1}, {16, 16, 1}, {32, 16, 2},
+                          {16, 16, 2}, {16, 8, 2},  {16, 16, 3}, {16, 8, 3},  {8, 8, 3},   {8, 8, 6}};
+constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
+
+// Tuning key: level index, level size of the first job, number of directions in the launch, iterations.
+using TuneKey = std::tuple<int, int, int, int, int>;
 
 }  // namespace
 
 struct ff_ctx {
     int device = 0;
+    int n_sms = 0;
     cudaStream_t stream = nullptr;
     ff_params prm{};
     std::vector<std::unique_ptr<ff_pyr>> pyrs;
     std::map<std::vector<uintptr_t>, std::unique_ptr<Plan>> plans;
+    std::map<TuneKey, TileCfg> tuned;
+    TileCfg forced[kMaxLevels] = {};  // per-level override (tw == 0: none)
     std::string err;
     int64_t launches = 0, replays = 0, plans_built = 0, bytes = 0;
     bool profiling = false;
     struct Ev {
-        int phase;
+        int phase, level;
         cudaEvent_t a, b;
         int n;
     };
@@ -180,19 +197,24 @@ ff_status check_params(const ff_params* p, ff_ctx* c) {
     return FF_OK;
 }
 
-// Tile shape and iterations fused per launch for one level, from the total work of the launch.
-TileCfg choose_tiles(int64_t level_pixels_all_jobs, int T) {
-    // enough CTAs to cover the GPU a few times over, tiles no smaller than 16x16
-    static const TileCfg cands[] = {{64, 32, 1}, {32, 32, 1}, {32, 16, 1}, {16, 16, 1}};
-    for (const TileCfg& c : cands)
-        if (level_pixels_all_jobs / (c.tw * c.th) >= 2 * 152) return c;
-    (void)T;
-    return {16, 16, 1};
+bool cfg_fits(const TileCfg& t) { return prop_smem_bytes(t.tw, t.th, t.k) <= kMaxPropSmem; }
+
+// Default propagation configuration of a level when it has not been tuned: large tiles with one iteration per
+// launch when the level fills the GPU, otherwise small tiles with fused iterations (idle SMs absorb the halo).
+TileCfg default_cfg(const ff_ctx* c, int64_t level_pix_all, int T) {
+    const int64_t slots = (int64_t)c->n_sms * 2;
+    if (level_pix_all / (64 * 32) >= 2 * slots) return {64, 32, 1};
+    if (level_pix_all / (32 * 16) >= 2 * slots) return {32, 16, 1};
+    if (level_pix_all / (16 * 16) >= slots) return {16, 16, std::min(2, T)};
+    return {8, 8, std::min(3, T)};
 }
 
 ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
     cudaStream_t st = c->stream;
     switch (L.kind) {
+        case Kind::ZeroCounters:
+            FF_CUDA(c, cudaMemsetAsync(L.zero_ptr, 0, L.zero_bytes, st));
+            return FF_OK;
         case Kind::Seed:
             launch_seed(static_cast<const SeedProblem*>(L.probs), L.n_probs, L.total, st);
             break;
@@ -200,7 +222,8 @@ ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
             launch_handover(static_cast<const HandoverProblem*>(L.probs), L.n_probs, L.total_pix, st);
             break;
         case Kind::Propagate:
-            launch_propagate(static_cast<const PropProblem*>(L.probs), L.tile_prob, L.total, L.prop, st);
+            launch_propagate(static_cast<const PropProblem*>(L.probs), L.queue, L.total, L.counter, L.grid, L.prop,
+                             st);
             break;
         case Kind::Consistency:
             launch_consistency(L.fwd, L.bwd, L.w, L.h, L.eps, L.mask, st);
@@ -210,6 +233,8 @@ ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
     if (e != cudaSuccess) return fail(c, FF_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     return FF_OK;
 }
+
+bool is_kernel(const Launch& l) { return l.kind != Kind::ZeroCounters; }
 
 cudaEvent_t get_event(ff_ctx* c) {
     if (!c->event_pool.empty()) {
@@ -222,34 +247,39 @@ cudaEvent_t get_event(ff_ctx* c) {
     return e;
 }
 
-// Enqueue a sequence of launches; with profiling on, each phase group is bracketed by events.
-ff_status run_launches(ff_ctx* c, const std::vector<Launch>& ls) {
+// Enqueue a sequence of launches; with `timed`, each run of consecutive launches of the same phase (and, for
+// propagation, the same level) is bracketed by events recorded into c->events.
+ff_status run_launches(ff_ctx* c, const std::vector<Launch>& ls, bool timed) {
     size_t i = 0;
     while (i < ls.size()) {
         size_t j = i;
-        while (j < ls.size() && ls[j].phase == ls[i].phase) j++;
+        while (j < ls.size() && ls[j].phase == ls[i].phase && ls[j].level == ls[i].level) j++;
         cudaEvent_t ea = nullptr, eb = nullptr;
-        if (c->profiling) {
+        if (timed) {
             ea = get_event(c);
             eb = get_event(c);
             FF_CUDA(c, cudaEventRecord(ea, c->stream));
         }
+        int nk = 0;
         for (size_t k = i; k < j; k++) {
             ff_status s = enqueue_launch(c, ls[k]);
             if (s != FF_OK) return s;
-            c->launches += 1;
+            nk += is_kernel(ls[k]);
         }
-        if (c->profiling) {
+        c->launches += nk;
+        if (timed) {
             FF_CUDA(c, cudaEventRecord(eb, c->stream));
-            c->events.push_back({ls[i].phase, ea, eb, (int)(j - i)});
+            c->events.push_back({ls[i].phase, ls[i].level, ea, eb, nk});
         }
         i = j;
     }
     return FF_OK;
 }
 
-// Build the launch sequence of a set of matching directions (+ consistency checks).
-ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons, Plan& P) {
+// Build the launch sequence of a set of matching directions (+ consistency checks).  `force` (optional) imposes
+// one propagation configuration on every level (used by the autotuner).
+ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons, Plan& P,
+                     const TileCfg* force) {
     const int L = c->prm.n_scales, T = c->prm.iters;
     const int nj = (int)jobs.size();
     // per job and level: two flow and two cost buffers (ping-pong) + seed distances
@@ -264,18 +294,6 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         for (int s = 0; s < L; s++) scratch += 4 * align_up((size_t)jobs[j].a->ws[s] * jobs[j].a->hs[s] * 4);
         scratch += align_up((size_t)jobs[j].a->n_coarse * 4);
     }
-    // problem tables
-    std::vector<SeedProblem> seeds;
-    std::vector<HandoverProblem> hos;
-    std::vector<PropProblem> props;
-    std::vector<int> tile_prob;
-    // record table offsets per launch, patched to device pointers after upload
-    struct Pending {
-        Launch l;
-        size_t off_probs, off_tiles;
-    };
-    std::vector<Pending> pend;
-
     P.bufs.emplace_back();
     ff_status st = dev_alloc(c, P.bufs.back(), scratch);
     if (st != FF_OK) return st;
@@ -294,6 +312,29 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         seed_dist[j] = reinterpret_cast<int32_t*>(base + off);
         off += align_up((size_t)jobs[j].a->n_coarse * 4);
     }
+    // queue order: the two directions of a pair interleaved tile by tile (they read the same two frames), pairs
+    // one after another; directions without a partner follow
+    std::vector<std::vector<int>> groups;
+    std::vector<bool> grouped(nj, false);
+    for (const ConsJob& cj : cons) {
+        groups.push_back({cj.dj_fwd, cj.dj_bwd});
+        grouped[cj.dj_fwd] = grouped[cj.dj_bwd] = true;
+    }
+    for (int j = 0; j < nj; j++)
+        if (!grouped[j]) groups.push_back({j});
+
+    std::vector<SeedProblem> seeds;
+    std::vector<HandoverProblem> hos;
+    std::vector<PropProblem> props;
+    std::vector<int2> queue;
+    int n_counters = 0;
+    struct Pending {
+        Launch l;
+        size_t off_probs, off_queue;
+        int counter;
+    };
+    std::vector<Pending> pend;
+    pend.push_back({Launch{Kind::ZeroCounters, FF_PHASE_SEED}, 0, 0, -1});
 
     // 1. exact initial matches at the coarsest level
     {
@@ -320,9 +361,9 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         }
         l.n_probs = nj;
         l.total = tiles;
-        pend.push_back({l, o, 0});
+        pend.push_back({l, o, 0, -1});
     }
-    // 2. per level: hand-over (cost of the seed at the coarsest level), then the fused propagation launches
+    // 2. per level: hand-over (the cost of the seed at the coarsest level), then the propagation launches
     std::vector<int> cur_buf(nj, 0);
     for (int s = L - 1; s >= 0; s--) {
         {
@@ -355,22 +396,35 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             }
             l.n_probs = nj;
             l.total_pix = pix;
-            pend.push_back({l, o, 0});
+            pend.push_back({l, o, 0, -1});
         }
         int64_t level_pix = 0;
         for (int j = 0; j < nj; j++) level_pix += (int64_t)jobs[j].a->ws[s] * jobs[j].a->hs[s];
-        TileCfg tc = choose_tiles(level_pix, T);
+        TileCfg tc;
+        if (force) {
+            tc = *force;
+            tc.k = std::min(tc.k, T);
+        } else if (c->forced[s].tw > 0) {
+            tc = c->forced[s];
+            tc.k = std::min(tc.k, T);
+        } else {
+            auto it = c->tuned.find(TuneKey{s, jobs[0].a->ws[s], jobs[0].a->hs[s], nj, T});
+            tc = it != c->tuned.end() ? it->second : default_cfg(c, level_pix, T);
+        }
+        const size_t smem = prop_smem_bytes(tc.tw, tc.th, tc.k);
+        const int blocks = prop_blocks_per_sm(smem) * c->n_sms;
         for (int t0 = 0; t0 < T; t0 += tc.k) {
             int n_iter = std::min(tc.k, T - t0);
             bool last = t0 + n_iter == T;
             Launch l{};
             l.kind = Kind::Propagate;
             l.phase = FF_PHASE_PROPAGATE;
+            l.level = s;
             l.prop.tw = tc.tw;
             l.prop.th = tc.th;
             l.prop.max_iter = n_iter;
-            size_t o = props.size(), ot = tile_prob.size();
-            int tiles = 0;
+            size_t oq = queue.size();
+            std::vector<int> pidx(nj), ntiles(nj);
             for (int j = 0; j < nj; j++) {
                 const ff_pyr* A = jobs[j].a;
                 PropProblem pp{};
@@ -390,22 +444,27 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
                 }
                 cur_buf[j] = out;
                 pp.tiles_x = (pp.w + tc.tw - 1) / tc.tw;
-                int ty = (pp.h + tc.th - 1) / tc.th;
-                pp.tile_base = tiles;
+                ntiles[j] = pp.tiles_x * ((pp.h + tc.th - 1) / tc.th);
                 pp.t0 = t0;
                 pp.n_iter = n_iter;
                 pp.level = s;
                 pp.dir = jobs[j].dir;
                 pp.seed = c->prm.seed;
                 pp.rs_radius = c->prm.rs_radius;
-                for (int k = 0; k < pp.tiles_x * ty; k++) tile_prob.push_back((int)(props.size()));
-                tiles += pp.tiles_x * ty;
+                pidx[j] = (int)props.size();
                 props.push_back(pp);
-                P.pixel_iters += (int64_t)pp.w * pp.h * n_iter;
+            }
+            for (const std::vector<int>& g : groups) {
+                int most = 0;
+                for (int j : g) most = std::max(most, ntiles[j]);
+                for (int k = 0; k < most; k++)
+                    for (int j : g)
+                        if (k < ntiles[j]) queue.push_back(make_int2(pidx[j], k));
             }
             l.n_probs = nj;
-            l.total = tiles;
-            pend.push_back({l, o, ot});
+            l.total = (int)(queue.size() - oq);
+            l.grid = std::min(l.total, blocks);
+            pend.push_back({l, 0, oq, n_counters++});
         }
     }
     // 3. consistency of each pair: the forward flow and the inverse flow, both at level 0
@@ -419,19 +478,20 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         l.h = jobs[cj.dj_fwd].a->h;
         l.eps = c->prm.eps;
         l.mask = cj.mask;
-        pend.push_back({l, 0, 0});
+        pend.push_back({l, 0, 0, -1});
     }
 
-    // upload the problem tables in one block
+    // upload the problem tables, queues and counters in one block
     size_t o_seed = 0, o_ho = align_up(seeds.size() * sizeof(SeedProblem));
     size_t o_prop = o_ho + align_up(hos.size() * sizeof(HandoverProblem));
-    size_t o_tile = o_prop + align_up(props.size() * sizeof(PropProblem));
-    size_t tbytes = o_tile + align_up(tile_prob.size() * sizeof(int));
+    size_t o_q = o_prop + align_up(props.size() * sizeof(PropProblem));
+    size_t o_cnt = o_q + align_up(queue.size() * sizeof(int2));
+    size_t tbytes = o_cnt + align_up((size_t)std::max(n_counters, 1) * sizeof(int));
     std::vector<char> host(tbytes, 0);
     memcpy(host.data() + o_seed, seeds.data(), seeds.size() * sizeof(SeedProblem));
     memcpy(host.data() + o_ho, hos.data(), hos.size() * sizeof(HandoverProblem));
     memcpy(host.data() + o_prop, props.data(), props.size() * sizeof(PropProblem));
-    memcpy(host.data() + o_tile, tile_prob.data(), tile_prob.size() * sizeof(int));
+    memcpy(host.data() + o_q, queue.data(), queue.size() * sizeof(int2));
     P.bufs.emplace_back();
     st = dev_alloc(c, P.bufs.back(), tbytes);
     if (st != FF_OK) return st;
@@ -440,36 +500,48 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     for (Pending& pd : pend) {
         Launch l = pd.l;
         switch (l.kind) {
+            case Kind::ZeroCounters:
+                l.zero_ptr = tb + o_cnt;
+                l.zero_bytes = (size_t)std::max(n_counters, 1) * sizeof(int);
+                break;
             case Kind::Seed:
                 l.probs = tb + o_seed + pd.off_probs * sizeof(SeedProblem);
                 break;
             case Kind::Handover:
                 l.probs = tb + o_ho + pd.off_probs * sizeof(HandoverProblem);
                 break;
-            case Kind::Propagate:
-                l.probs = tb + o_prop;  // tile_prob holds absolute problem indices
-                l.tile_prob = reinterpret_cast<const int*>(tb + o_tile) + pd.off_tiles;
+            case Kind::Propagate:  // queue entries hold absolute indices into the problem table
+                l.probs = tb + o_prop;
+                l.queue = reinterpret_cast<const int2*>(tb + o_q) + pd.off_queue;
+                l.counter = reinterpret_cast<int*>(tb + o_cnt) + pd.counter;
                 break;
             case Kind::Consistency:
                 break;
         }
         P.launches.push_back(l);
     }
-    // tile_prob entries index the whole problem array; a problem's tile_base is relative to its own launch
     return FF_OK;
+}
+
+void free_plan(ff_ctx* c, Plan& P) {
+    if (P.exec) cudaGraphExecDestroy(P.exec);
+    P.exec = nullptr;
+    for (DevBuf& b : P.bufs) dev_free(c, b);
 }
 
 ff_status execute_plan(ff_ctx* c, Plan& P) {
     // graphs need a capturable (non-legacy) stream; profiling brackets phases with events instead
     bool use_graph = !c->profiling && c->stream != nullptr;
-    if (!use_graph) return run_launches(c, P.launches);
+    if (!use_graph) return run_launches(c, P.launches, c->profiling);
     if (!P.exec) {
         cudaGraph_t g = nullptr;
         FF_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         ff_status s = FF_OK;
+        int nk = 0;
         for (const Launch& l : P.launches) {
             s = enqueue_launch(c, l);
             if (s != FF_OK) break;
+            nk += is_kernel(l);
         }
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (s != FF_OK) {
@@ -483,7 +555,7 @@ ff_status execute_plan(ff_ctx* c, Plan& P) {
             P.exec = nullptr;
             return fail(c, FF_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
         }
-        P.graph_nodes = (int)P.launches.size();
+        P.graph_nodes = nk;
     }
     FF_CUDA(c, cudaGraphLaunch(P.exec, c->stream));
     c->replays += 1;
@@ -491,7 +563,7 @@ ff_status execute_plan(ff_ctx* c, Plan& P) {
     return FF_OK;
 }
 
-ff_status run_jobs(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons) {
+std::vector<uintptr_t> plan_key(const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons) {
     std::vector<uintptr_t> key;
     key.reserve(jobs.size() * 5 + cons.size() * 3 + 1);
     for (const DirJob& j : jobs) {
@@ -507,27 +579,92 @@ ff_status run_jobs(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
         key.push_back((uintptr_t)cj.dj_bwd);
         key.push_back((uintptr_t)cj.mask);
     }
+    return key;
+}
+
+ff_status drop_plans(ff_ctx* c) {
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto& kv : c->plans) free_plan(c, *kv.second);
+    c->plans.clear();
+    return FF_OK;
+}
+
+ff_status run_jobs(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons) {
+    std::vector<uintptr_t> key = plan_key(jobs, cons);
     auto it = c->plans.find(key);
     if (it == c->plans.end()) {
         if (c->plans.size() >= 64) {  // bound the cache: drop everything (plans are cheap to rebuild)
-            FF_CUDA(c, cudaStreamSynchronize(c->stream));
-            for (auto& kv : c->plans) {
-                if (kv.second->exec) cudaGraphExecDestroy(kv.second->exec);
-                for (DevBuf& b : kv.second->bufs) dev_free(c, b);
-            }
-            c->plans.clear();
+            ff_status s = drop_plans(c);
+            if (s != FF_OK) return s;
         }
         auto P = std::make_unique<Plan>();
         P->key = key;
-        ff_status s = build_plan(c, jobs, cons, *P);
+        ff_status s = build_plan(c, jobs, cons, *P, nullptr);
         if (s != FF_OK) {
-            for (DevBuf& b : P->bufs) dev_free(c, b);
+            free_plan(c, *P);
             return s;
         }
         c->plans_built += 1;
         it = c->plans.emplace(key, std::move(P)).first;
     }
     return execute_plan(c, *it->second);
+}
+
+// Time every candidate configuration on the given jobs and keep, per level, the fastest.  Runs the real
+// matching (outputs are overwritten by every trial; all configurations give identical results).
+ff_status autotune(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons, int reps) {
+    const int L = c->prm.n_scales, T = c->prm.iters, nj = (int)jobs.size();
+    std::vector<std::vector<double>> best_ms(L, std::vector<double>(kNCands, 1e30));
+    ff_status s = drop_plans(c);
+    if (s != FF_OK) return s;
+    bool was_profiling = c->profiling;
+    for (int ci = 0; ci < kNCands; ci++) {
+        TileCfg cfg = kCands[ci];
+        cfg.k = std::min(cfg.k, T);
+        if (!cfg_fits(cfg)) continue;
+        Plan P;
+        s = build_plan(c, jobs, cons, P, &cfg);
+        if (s != FF_OK) {
+            free_plan(c, P);
+            return s;
+        }
+        for (int r = 0; r < reps + 1; r++) {
+            c->events.clear();
+            s = run_launches(c, P.launches, true);
+            if (s == FF_OK) s = [&]() -> ff_status {
+                FF_CUDA(c, cudaStreamSynchronize(c->stream));
+                return FF_OK;
+            }();
+            if (s != FF_OK) {
+                free_plan(c, P);
+                return s;
+            }
+            std::vector<double> lv(L, 0.0);
+            for (auto& e : c->events) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e.a, e.b);
+                if (e.phase == FF_PHASE_PROPAGATE && e.level >= 0) lv[e.level] += t;
+                c->event_pool.push_back(e.a);
+                c->event_pool.push_back(e.b);
+            }
+            c->events.clear();
+            if (r > 0)  // the first run warms caches and clocks
+                for (int l = 0; l < L; l++) best_ms[l][ci] = std::min(best_ms[l][ci], lv[l]);
+        }
+        free_plan(c, P);
+    }
+    c->profiling = was_profiling;
+    for (int l = 0; l < L; l++) {
+        int bi = -1;
+        for (int ci = 0; ci < kNCands; ci++)
+            if (best_ms[l][ci] < 1e29 && (bi < 0 || best_ms[l][ci] < best_ms[l][bi])) bi = ci;
+        if (bi >= 0) {
+            TileCfg cfg = kCands[bi];
+            cfg.k = std::min(cfg.k, T);
+            c->tuned[TuneKey{l, jobs[0].a->ws[l], jobs[0].a->hs[l], nj, T}] = cfg;
+        }
+    }
+    return FF_OK;
 }
 
 bool aligned4(const void* p) { return ((uintptr_t)p & 3) == 0; }
@@ -572,7 +709,8 @@ ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* cuda_str
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->prm = *p;
-    if (cudaSetDevice(device) != cudaSuccess || init_kernel_attributes() != cudaSuccess) {
+    if (cudaSetDevice(device) != cudaSuccess || init_kernel_attributes() != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return FF_ERR_CUDA;
@@ -666,7 +804,7 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
     }
     if (c->profiling) {
         FF_CUDA(c, cudaEventRecord(eb, c->stream));
-        c->events.push_back({FF_PHASE_FEATURES, ea, eb, nl});
+        c->events.push_back({FF_PHASE_FEATURES, -1, ea, eb, nl});
     }
     *out = P;
     return FF_OK;
@@ -686,12 +824,8 @@ ff_status ff_match_pair(ff_ctx* c, const ff_pyr* a, const ff_pyr* b, int dir, in
     return run_jobs(c, jobs, {});
 }
 
-ff_status ff_match_batch(ff_ctx* c, int n, const ff_pair_job* jobs) {
-    if (!c) return FF_ERR_ARG;
-    if (n < 0 || (n > 0 && !jobs)) return fail(c, FF_ERR_ARG, "bad job list");
-    if (n == 0) return FF_OK;
-    std::vector<DirJob> dj;
-    std::vector<ConsJob> cj;
+static ff_status collect_batch(ff_ctx* c, int n, const ff_pair_job* jobs, std::vector<DirJob>& dj,
+                               std::vector<ConsJob>& cj) {
     for (int i = 0; i < n; i++) {
         const ff_pair_job& J = jobs[i];
         ff_status s;
@@ -706,8 +840,65 @@ ff_status ff_match_batch(ff_ctx* c, int n, const ff_pair_job* jobs) {
         dj.push_back({J.b, J.a, 1, reinterpret_cast<uint32_t*>(J.flow_bwd), J.cost_bwd});
         cj.push_back({2 * i, 2 * i + 1, J.mask});
     }
+    return FF_OK;
+}
+
+ff_status ff_match_batch(ff_ctx* c, int n, const ff_pair_job* jobs) {
+    if (!c) return FF_ERR_ARG;
+    if (n < 0 || (n > 0 && !jobs)) return fail(c, FF_ERR_ARG, "bad job list");
+    if (n == 0) return FF_OK;
+    std::vector<DirJob> dj;
+    std::vector<ConsJob> cj;
+    ff_status s = collect_batch(c, n, jobs, dj, cj);
+    if (s != FF_OK) return s;
     FF_CUDA(c, cudaSetDevice(c->device));
     return run_jobs(c, dj, cj);
+}
+
+ff_status ff_autotune(ff_ctx* c, int n, const ff_pair_job* jobs, int reps) {
+    if (!c) return FF_ERR_ARG;
+    if (n < 1 || !jobs || reps < 1 || reps > 100) return fail(c, FF_ERR_ARG, "bad autotune arguments");
+    std::vector<DirJob> dj;
+    std::vector<ConsJob> cj;
+    ff_status s = collect_batch(c, n, jobs, dj, cj);
+    if (s != FF_OK) return s;
+    FF_CUDA(c, cudaSetDevice(c->device));
+    return autotune(c, dj, cj, reps);
+}
+
+ff_status ff_set_tuning(ff_ctx* c, int level, int tile_w, int tile_h, int iters_per_launch) {
+    if (!c) return FF_ERR_ARG;
+    if (level < 0 || level >= kMaxLevels) return fail(c, FF_ERR_ARG, "level %d outside 0..%d", level, kMaxLevels - 1);
+    TileCfg cfg{tile_w, tile_h, iters_per_launch};
+    if (tile_w != 0 || tile_h != 0 || iters_per_launch != 0) {
+        if (tile_w < 1 || tile_h < 1 || tile_w > 1024 || tile_h > 1024 || iters_per_launch < 1 ||
+            iters_per_launch > 255 || !cfg_fits(cfg))
+            return fail(c, FF_ERR_ARG, "configuration %dx%d, %d iterations does not fit", tile_w, tile_h,
+                        iters_per_launch);
+    }
+    FF_CUDA(c, cudaSetDevice(c->device));
+    ff_status s = drop_plans(c);
+    if (s != FF_OK) return s;
+    c->forced[level] = cfg;
+    return FF_OK;
+}
+
+ff_status ff_get_tuning(ff_ctx* c, int level, int* tile_w, int* tile_h, int* iters_per_launch) {
+    if (!c || level < 0 || level >= kMaxLevels) return FF_ERR_ARG;
+    if (c->forced[level].tw > 0) {
+        if (tile_w) *tile_w = c->forced[level].tw;
+        if (tile_h) *tile_h = c->forced[level].th;
+        if (iters_per_launch) *iters_per_launch = c->forced[level].k;
+        return FF_OK;
+    }
+    for (auto& kv : c->tuned)
+        if (std::get<0>(kv.first) == level) {
+            if (tile_w) *tile_w = kv.second.tw;
+            if (tile_h) *tile_h = kv.second.th;
+            if (iters_per_launch) *iters_per_launch = kv.second.k;
+            return FF_OK;
+        }
+    return fail(c, FF_ERR_ARG, "level %d has not been tuned", level);
 }
 
 ff_status ff_consistency(ff_ctx* c, const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, uint8_t* mask_dev) {
@@ -725,7 +916,7 @@ ff_status ff_consistency(ff_ctx* c, const int16_t* fwd, const int16_t* bwd, int 
     l.h = h;
     l.eps = eps;
     l.mask = mask_dev;
-    return run_launches(c, {l});
+    return run_launches(c, {l}, c->profiling);
 }
 
 ff_status ff_pyr_release(ff_ctx* c, ff_pyr* p) {
@@ -809,10 +1000,7 @@ ff_status ff_destroy(ff_ctx* c) {
     if (!c) return FF_ERR_ARG;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    for (auto& kv : c->plans) {
-        if (kv.second->exec) cudaGraphExecDestroy(kv.second->exec);
-        for (DevBuf& b : kv.second->bufs) dev_free(c, b);
-    }
+    for (auto& kv : c->plans) free_plan(c, *kv.second);
     for (auto& p : c->pyrs) dev_free(c, p->mem);
     for (auto& e : c->events) {
         cudaEventDestroy(e.a);

@@ -75,7 +75,7 @@ void launch_handover(const HandoverProblem* probs_dev, int n_probs, int64_t tota
 // ---------------------------------------------------------------------------------------------------------
 // propagation + random search, `n_iter` iterations of one level per launch, temporally blocked tiles
 
-struct PropProblem {
+struct PropProblem {  // one (pair, direction, level) of a propagation launch
     const int16_t* fa;
     const int16_t* fb;
     const uint32_t* flow_in;
@@ -84,7 +84,6 @@ struct PropProblem {
     int32_t* cost_out;
     int w, h;
     int tiles_x;
-    int tile_base;   // first CTA of this problem in the launch
     int t0;          // first iteration index (for the random-search hash)
     int n_iter;      // iterations fused into this launch
     int level;
@@ -99,8 +98,10 @@ struct PropLaunch {
 constexpr size_t kMaxPropSmem = 200 * 1024;
 size_t prop_smem_bytes(int tw, int th, int n_iter);
 cudaError_t init_kernel_attributes();  // once per device, before the first launch
-void launch_propagate(const PropProblem* probs_dev, const int* tile_prob_dev, int total_tiles, const PropLaunch& L,
-                      cudaStream_t st);
+int prop_blocks_per_sm(size_t smem);   // resident CTAs per SM of the propagation kernel
+// queue_dev[i] = (problem index, tile index); counter_dev must be zero when the launch starts
+void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
+                      const PropLaunch& L, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------------------
 // consistency

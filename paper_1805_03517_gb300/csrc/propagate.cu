@@ -28,25 +28,48 @@ __device__ __forceinline__ bool in_level(int x, int y, int w, int h) {
     return (unsigned)x < (unsigned)w && (unsigned)y < (unsigned)h;
 }
 
-__device__ __forceinline__ void load_desc(const int16_t* __restrict__ f, int idx, uint4 (&d)[6]) {
-    const uint4* p = reinterpret_cast<const uint4*>(f) + (size_t)idx * 6;
+// One pixel descriptor (96 B = three 32-B sectors) with three 256-bit read-only loads, one sector per load.
+__device__ __forceinline__ void load_desc(const int16_t* __restrict__ f, int idx, uint32_t (&d)[24]) {
+    const char* p = reinterpret_cast<const char*>(f) + (size_t)idx * kDescBytes;
 #pragma unroll
-    for (int k = 0; k < 6; k++) d[k] = __ldg(p + k);
+    for (int k = 0; k < 3; k++)
+        asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=r"(d[8 * k]), "=r"(d[8 * k + 1]), "=r"(d[8 * k + 2]), "=r"(d[8 * k + 3]), "=r"(d[8 * k + 4]),
+              "=r"(d[8 * k + 5]), "=r"(d[8 * k + 6]), "=r"(d[8 * k + 7])
+            : "l"(p + 32 * k));
 }
 
-// |a - b| summed over the 2 x 16-bit halves of one word, signed coefficients.
-__device__ __forceinline__ int sad_word(uint32_t a, uint32_t b) {
-    int al = (int)(int16_t)(a & 0xffffu), ah = ((int)a) >> 16;
-    int bl = (int)(int16_t)(b & 0xffffu), bh = ((int)b) >> 16;
-    return abs(al - bl) + abs(ah - bh);
+// Exact SAD of the 48 int16 coefficients, two per 32-bit word.  Both operands are mapped to offset binary
+// (x ^ 0x8000 per half, which preserves order), so per half max - min is |a - b| in [0, 32640] and a plain
+// 32-bit subtraction of the packed max/min never borrows across halves.  Two packed differences add without
+// carrying (2 * 32640 < 65536); __dp2a_lo then adds both 16-bit halves into the int32 sum.
+constexpr uint32_t kBias = 0x80008000u;
+
+__device__ __forceinline__ void bias_desc(uint32_t (&d)[24]) {
+#pragma unroll
+    for (int k = 0; k < 24; k++) d[k] ^= kBias;
 }
 
-__device__ __forceinline__ int sad96(const uint4 (&a)[6], const uint4 (&b)[6]) {
-    int s = 0;
+__device__ __forceinline__ int sad_biased(const uint32_t (&a)[24], const uint32_t (&b)[24]) {
+    unsigned s = 0;
 #pragma unroll
-    for (int k = 0; k < 6; k++)
-        s += sad_word(a[k].x, b[k].x) + sad_word(a[k].y, b[k].y) + sad_word(a[k].z, b[k].z) + sad_word(a[k].w, b[k].w);
-    return s;
+    for (int k = 0; k < 24; k += 2) {
+        uint32_t b0 = b[k] ^ kBias, b1 = b[k + 1] ^ kBias;
+        uint32_t d0 = __vmaxu2(a[k], b0) - __vminu2(a[k], b0);
+        uint32_t d1 = __vmaxu2(a[k + 1], b1) - __vminu2(a[k + 1], b1);
+        s = __dp2a_lo(d0 + d1, 0x0101u, s);
+    }
+    return (int)s;
+}
+
+// SAD of the descriptor at (x, y) of fa against (tx, ty) of fb (both inside the level).
+__device__ __forceinline__ int sad_at(const int16_t* __restrict__ fa, const int16_t* __restrict__ fb, int w, int x,
+                                      int y, int tx, int ty) {
+    uint32_t a[24], b[24];
+    load_desc(fa, y * w + x, a);
+    load_desc(fb, ty * w + tx, b);
+    bias_desc(a);
+    return sad_biased(a, b);
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -73,12 +96,7 @@ __global__ __launch_bounds__(256) void k_handover(const HandoverProblem* __restr
         }
         int tx = x + flow_x(f), ty = y + flow_y(f);
         int c = INT_MAX;  // unreachable for valid inputs: a handed-over flow always lands inside the level
-        if (in_level(tx, ty, P.w, P.h)) {
-            uint4 a[6], b[6];
-            load_desc(P.fa, p, a);
-            load_desc(P.fb, ty * P.w + tx, b);
-            c = sad96(a, b);
-        }
+        if (in_level(tx, ty, P.w, P.h)) c = sad_at(P.fa, P.fb, P.w, x, y, tx, ty);
         P.flow_out[p] = f;
         P.cost_out[p] = c;
     }
@@ -104,12 +122,14 @@ size_t prop_smem_bytes(int tw, int th, int n_iter) {
     return (size_t)(tw + 2 * H) * (th + 2 * H) * 8;
 }
 
-__global__ __launch_bounds__(256) void k_propagate(const PropProblem* __restrict__ probs,
-                                                   const int* __restrict__ tile_prob, PropLaunch L) {
-    extern __shared__ uint32_t smem[];
-    const PropProblem& P = probs[tile_prob[blockIdx.x]];
+#ifndef FF_PROP_MINB
+#define FF_PROP_MINB 2
+#endif
+constexpr int kPropThreads = 256;
+
+// One tile of one problem: load the tile and its halo, run n_iter iterations in shared memory, write the tile.
+__device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, const PropLaunch& L, uint32_t* smem) {
     const int w = P.w, h = P.h;
-    const int tile = blockIdx.x - P.tile_base;
     const int x0 = (tile % P.tiles_x) * L.tw, y0 = (tile / P.tiles_x) * L.th;
     const int x1 = min(x0 + L.tw, w), y1 = min(y0 + L.th, h);
     const int H = kHaloPerIter * P.n_iter;
@@ -156,19 +176,19 @@ __global__ __launch_bounds__(256) void k_propagate(const PropProblem* __restrict
                 const bool e1 = v1 && f1 != cur && in_level(x + flow_x(f1), y + flow_y(f1), w, h);
                 const bool e2 = v2 && f2 != cur && !(v1 && f2 == f1) && in_level(x + flow_x(f2), y + flow_y(f2), w, h);
                 if (!(e1 || e2 || d >= 1)) continue;
-                uint4 a[6];
+                // issue every independent load (own descriptor, both neighbour candidates) before any compute
+                uint32_t a[24], b1[24], b2[24];
                 load_desc(P.fa, y * w + x, a);
+                if (e1) load_desc(P.fb, (y + flow_y(f1)) * w + x + flow_x(f1), b1);
+                if (e2) load_desc(P.fb, (y + flow_y(f2)) * w + x + flow_x(f2), b2);
+                bias_desc(a);
                 if (e1) {
-                    uint4 b[6];
-                    load_desc(P.fb, (y + flow_y(f1)) * w + x + flow_x(f1), b);
-                    int s = sad96(a, b);
-                    if (s < c) { cur = f1; c = s; }
+                    int s1 = sad_biased(a, b1);
+                    if (s1 < c) { cur = f1; c = s1; }
                 }
                 if (e2) {
-                    uint4 b[6];
-                    load_desc(P.fb, (y + flow_y(f2)) * w + x + flow_x(f2), b);
-                    int s = sad96(a, b);
-                    if (s < c) { cur = f2; c = s; }
+                    int s2 = sad_biased(a, b2);
+                    if (s2 < c) { cur = f2; c = s2; }
                 }
                 if (d >= 1) {
                     const uint32_t k2 = mix32(k1 ^ ((uint32_t)y * 65536u + (uint32_t)x));
@@ -177,10 +197,9 @@ __global__ __launch_bounds__(256) void k_propagate(const PropProblem* __restrict
                     if (ox != 0 || oy != 0) {
                         const int fx = flow_x(cur) + ox, fy = flow_y(cur) + oy;
                         if (in_level(x + fx, y + fy, w, h)) {
-                            uint4 b[6];
-                            load_desc(P.fb, (y + fy) * w + x + fx, b);
-                            int s = sad96(a, b);
-                            if (s < c) { cur = pack_flow(fx, fy); c = s; }
+                            load_desc(P.fb, (y + fy) * w + x + fx, b1);
+                            int s3 = sad_biased(a, b1);
+                            if (s3 < c) { cur = pack_flow(fx, fy); c = s3; }
                         }
                     }
                 }
@@ -201,14 +220,42 @@ __global__ __launch_bounds__(256) void k_propagate(const PropProblem* __restrict
     }
 }
 
+// Persistent launch: each CTA takes tiles from the launch's queue (an atomic counter, zeroed before the launch)
+// until it is empty, so the last wave has no idle tail.  queue[i] = (problem index, tile index in problem).
+__global__ __launch_bounds__(kPropThreads, FF_PROP_MINB) void k_propagate(const PropProblem* __restrict__ probs,
+                                                                         const int2* __restrict__ queue,
+                                                                         int n_tiles, int* __restrict__ counter,
+                                                                         PropLaunch L) {
+    extern __shared__ uint32_t smem[];
+    __shared__ int s_next;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int q = s_next;
+        if (q >= n_tiles) return;
+        const int2 e = queue[q];
+        propagate_tile(probs[e.x], e.y, L, smem);
+        __syncthreads();
+    }
+}
+
 cudaError_t init_kernel_attributes() {
     return cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
 }
 
-void launch_propagate(const PropProblem* probs_dev, const int* tile_prob_dev, int total_tiles, const PropLaunch& L,
-                      cudaStream_t st) {
+int prop_blocks_per_sm(size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate, kPropThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
+void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
+                      const PropLaunch& L, cudaStream_t st) {
     size_t smem = prop_smem_bytes(L.tw, L.th, L.max_iter);
-    k_propagate<<<total_tiles, 256, smem, st>>>(probs_dev, tile_prob_dev, L);
+    k_propagate<<<grid, kPropThreads, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
 }
 
 // ---------------------------------------------------------------------------------------------------------

@@ -71,6 +71,9 @@ def lib():
         "ff_features": (S, [vp, vp, i, i, i, ctypes.POINTER(vp)]),
         "ff_match_pair": (S, [vp, vp, vp, i, vp, vp]),
         "ff_match_batch": (S, [vp, i, ctypes.POINTER(PairJob)]),
+        "ff_autotune": (S, [vp, i, ctypes.POINTER(PairJob), i]),
+        "ff_set_tuning": (S, [vp, i, i, i, i]),
+        "ff_get_tuning": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "ff_consistency": (S, [vp, vp, vp, i, i, i, vp]),
         "ff_pyr_release": (S, [vp, vp]),
         "ff_pyr_level_dims": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
@@ -126,6 +129,21 @@ def ff_match_pair(ctx, a, b, dir: int, flow_dev: int, cost_dev: int | None):
 def ff_match_batch(ctx, jobs):
     arr = (PairJob * len(jobs))(*jobs)
     _check(ctx, lib().ff_match_batch(ctx, len(jobs), arr))
+
+
+def ff_autotune(ctx, jobs, reps: int = 3):
+    arr = (PairJob * len(jobs))(*jobs)
+    _check(ctx, lib().ff_autotune(ctx, len(jobs), arr, reps))
+
+
+def ff_set_tuning(ctx, level: int, tile_w: int, tile_h: int, iters_per_launch: int):
+    _check(ctx, lib().ff_set_tuning(ctx, level, tile_w, tile_h, iters_per_launch))
+
+
+def ff_get_tuning(ctx, level: int):
+    tw, th, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().ff_get_tuning(ctx, level, ctypes.byref(tw), ctypes.byref(th), ctypes.byref(k)))
+    return tw.value, th.value, k.value
 
 
 def ff_consistency(ctx, fwd: int, bwd: int, w: int, h: int, eps: int, mask_dev: int):
@@ -265,17 +283,28 @@ class Matcher:
             outs.append(o)
         return outs
 
-    def match_batch(self, pairs, outs=None, with_cost=True):
-        """pairs: list of (Pyramid a, Pyramid b).  Returns (or fills) one dict of outputs per pair."""
-        if outs is None:
-            outs = self.alloc_outputs(pairs, with_cost)
+    @staticmethod
+    def _jobs(pairs, outs):
         jobs = []
         for (a, b), o in zip(pairs, outs):
             jobs.append(PairJob(a.handle, b.handle, o["flow_fwd"].data_ptr(), o["flow_bwd"].data_ptr(),
                                 o["cost_fwd"].data_ptr() if "cost_fwd" in o else None,
                                 o["cost_bwd"].data_ptr() if "cost_bwd" in o else None, o["mask"].data_ptr()))
-        ff_match_batch(self.ctx, jobs)
+        return jobs
+
+    def match_batch(self, pairs, outs=None, with_cost=True):
+        """pairs: list of (Pyramid a, Pyramid b).  Returns (or fills) one dict of outputs per pair."""
+        if outs is None:
+            outs = self.alloc_outputs(pairs, with_cost)
+        ff_match_batch(self.ctx, self._jobs(pairs, outs))
         return outs
+
+    def autotune(self, pairs, outs=None, reps=3):
+        """Tune the per-level propagation configuration for batches shaped like `pairs` (outputs overwritten)."""
+        if outs is None:
+            outs = self.alloc_outputs(pairs, with_cost=False)
+        ff_autotune(self.ctx, self._jobs(pairs, outs), reps)
+        return [ff_get_tuning(self.ctx, s) for s in range(self.params.n_scales)]
 
     def consistency(self, fwd, bwd, eps: int):
         h, w = int(fwd.shape[0]), int(fwd.shape[1])
