@@ -195,7 +195,8 @@ def test_profiled_run_is_identical(lib_built):
     got = G.gpu_bidir(M, a, b, torch)
     prof = ff.ff_profile_read(M.ctx)
     G.assert_same(got, base)
-    assert prof["propagate"][0] > 0 and prof["propagate"][1] == 3 * 2
+    # one launch per level covers between 1 and all iterations (the configuration decides)
+    assert prof["propagate"][0] > 0 and 3 <= prof["propagate"][1] <= 3 * 2
     assert prof["features"][1] > 0 and prof["seed"][1] >= 1 and prof["consistency"][1] == 1
     M.close()
 

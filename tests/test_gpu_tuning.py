@@ -73,7 +73,9 @@ def test_autotune_then_bit_exact(ffm):
 
 def test_set_tuning_rejects_bad_configurations(ffm):
     M = ffm.Matcher(mp(2, 1), 0)
-    for args in ((0, 8, 8, 1), (-1, 8, 8, 1), (8, 8, 8, 1), (0, 0, 8, 1), (0, 8, 8, 0), (0, 1024, 1024, 1),
+    ffm.ff_set_tuning(M.ctx, 0, 8, 8, 1)  # valid
+    assert ffm.ff_get_tuning(M.ctx, 0) == (8, 8, 1)
+    for args in ((-1, 8, 8, 1), (8, 8, 8, 1), (0, 0, 8, 1), (0, 8, 8, 0), (0, 1024, 1024, 1),
                  (0, 64, 64, 40)):
         with pytest.raises(ffm.FFError) as e:
             ffm.ff_set_tuning(M.ctx, *args)
