@@ -171,6 +171,24 @@ FF_API ff_status ff_profile_read(ff_ctx* ctx, double* ms /* [FF_N_PHASES] */, in
  * number of (pixel, iteration) updates summed over all levels, and the number of level-0 pixels. */
 FF_API ff_status ff_work_counts(ff_ctx* ctx, int w, int h, int64_t* pixel_iters, int64_t* pixels);
 
+/* Size of the fixed device scratch array used by ff_match_pair_noalloc (32 MiB): enough for frames of up to
+ * about 1.5 million pixels at level 0. */
+#define FF_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* ff_match_pair without any memory allocation.  The paper has no counterpart: this serves callers that must
+ * not allocate device memory while they run -- a real-time frame loop (cudaMalloc/cudaFree may synchronise the
+ * device and stall other streams), code whose device memory belongs to another framework's fixed pool, or a
+ * hot path that must not hit out-of-memory half way.  Same arguments, semantics and results as
+ * ff_match_pair (the caller still passes the pyramids, built beforehand by ff_features, and the outputs); all
+ * scratch lives in one file-scope device array of FF_NOALLOC_SCRATCH_BYTES that every device loading the
+ * library keeps until the process exits.  Pyramids needing more scratch than that return FF_ERR_ARG.
+ * The first call on a device looks up the array's device address (a one-time set-up per device), so make it
+ * before any stream capture.  Every call reuses the same array, which keeps the last call's contents (the call
+ * clears what must start at zero); calls whose work overlaps on the GPU -- on different streams or contexts of
+ * the same device -- race on the array and must be serialised by the caller. */
+FF_API ff_status ff_match_pair_noalloc(ff_ctx* ctx, const ff_pyr* a, const ff_pyr* b, int dir, int16_t* flow_dev,
+                                       int32_t* cost_dev);
+
 /* Release every resource of the context (pyramids, plans, graphs); ctx must not be used afterwards. */
 FF_API ff_status ff_destroy(ff_ctx* ctx);
 

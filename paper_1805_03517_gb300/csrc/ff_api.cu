@@ -667,6 +667,66 @@ ff_status autotune(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
     return FF_OK;
 }
 
+}  // namespace
+
+namespace ff {
+
+bool ctx_view(const ff_ctx* c, CtxView* out) {
+    if (!c || !out) return false;
+    out->device = c->device;
+    out->n_sms = c->n_sms;
+    out->stream = c->stream;
+    out->n_scales = c->prm.n_scales;
+    out->iters = c->prm.iters;
+    out->rs_radius = c->prm.rs_radius;
+    out->seed = c->prm.seed;
+    return true;
+}
+
+bool ctx_owns_live_pyr(const ff_ctx* c, const ff_pyr* p) {
+    if (!c || !p) return false;
+    for (auto& q : c->pyrs)
+        if (q.get() == p) return p->in_use;
+    return false;
+}
+
+bool pyr_view(const ff_pyr* p, PyrView* out) {
+    if (!p || !out) return false;
+    out->w = p->w;
+    out->h = p->h;
+    out->L = p->L;
+    for (int s = 0; s < kMaxLevels; s++) {
+        out->ws[s] = p->ws[s];
+        out->hs[s] = p->hs[s];
+        out->feat[s] = p->feat[s];
+    }
+    out->seed_desc = p->seed_desc;
+    out->seed_norm = p->seed_norm;
+    out->n_coarse = p->n_coarse;
+    return true;
+}
+
+// The configuration build_plan would use for this level (override, tuned, or default).
+TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all) {
+    const int T = c->prm.iters;
+    TileCfg tc;
+    if (c->forced[level].tw > 0) {
+        tc = c->forced[level];
+    } else {
+        auto it = c->tuned.find(TuneKey{level, w, h, n_dirs, T});
+        tc = it != c->tuned.end() ? it->second : default_cfg(c, level_pix_all, T);
+    }
+    return {tc.tw, tc.th, std::min(tc.k, T)};
+}
+
+int ctx_set_error(ff_ctx* c, int status, const char* msg) {
+    return (int)fail(c, (ff_status)status, "%s", msg);
+}
+
+}  // namespace ff
+
+namespace {
+
 bool aligned4(const void* p) { return ((uintptr_t)p & 3) == 0; }
 
 ff_status check_pyr(ff_ctx* c, const ff_pyr* p, const char* what) {

@@ -110,6 +110,27 @@ void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, int w, int h, 
                         cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------------------
+// read-only views of context and pyramid internals for other translation units of the library
+
+struct PyrView {
+    int w, h, L;
+    int ws[kMaxLevels], hs[kMaxLevels];
+    const int16_t* feat[kMaxLevels];
+    const int8_t* seed_desc;
+    const int32_t* seed_norm;
+    int n_coarse;
+};
+struct CtxView {
+    int device, n_sms;
+    cudaStream_t stream;
+    int n_scales, iters, rs_radius;
+    uint32_t seed;
+};
+struct TileChoice {
+    int tw, th, k;
+};
+
+// ---------------------------------------------------------------------------------------------------------
 // shared device helpers (library only)
 
 __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
@@ -122,4 +143,15 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     return x;
 }
 
+}  // namespace ff
+
+// Accessors implemented in ff_api.cu (ff_ctx and ff_pyr are opaque outside it).
+struct ff_ctx;
+struct ff_pyr;
+namespace ff {
+bool ctx_view(const ff_ctx* c, CtxView* out);
+bool ctx_owns_live_pyr(const ff_ctx* c, const ff_pyr* p);
+bool pyr_view(const ff_pyr* p, PyrView* out);
+TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all);
+int ctx_set_error(ff_ctx* c, int status, const char* msg);
 }  // namespace ff

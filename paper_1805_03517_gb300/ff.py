@@ -84,6 +84,7 @@ def lib():
         "ff_profile_enable": (S, [vp, i]),
         "ff_profile_read": (S, [vp, ctypes.POINTER(ctypes.c_double), i64p]),
         "ff_work_counts": (S, [vp, i, i, i64p, i64p]),
+        "ff_match_pair_noalloc": (S, [vp, vp, vp, i, vp, vp]),
         "ff_destroy": (S, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -193,6 +194,11 @@ def ff_work_counts(ctx, w: int, h: int):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(ctx, lib().ff_work_counts(ctx, w, h, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def ff_match_pair_noalloc(ctx, a, b, dir: int, flow_dev: int, cost_dev: int | None):
+    """ff_match_pair for callers that must not allocate device memory (fixed file-scope scratch)."""
+    _check(ctx, lib().ff_match_pair_noalloc(ctx, a, b, dir, flow_dev, cost_dev or None))
 
 
 def ff_destroy(ctx):
