@@ -60,11 +60,12 @@ SERVE_SIZES = ((320, 240, "rects"), (640, 480, "rects"), (1024, 436, "sintel"), 
 
 
 def _batch48():
+    # one parameter set for the whole batch (the KITTI settings, eps = 1, as for the served stream)
     pairs = []
     for i in range(16):
         pairs.append(PairSpec("kitti", 1242, 375, 4000 + i, KITTI))
     for i in range(16):
-        pairs.append(PairSpec("sintel", 1024, 436, 4016 + i, SINTEL))
+        pairs.append(PairSpec("sintel", 1024, 436, 4016 + i, KITTI))
     for i in range(16):
         pairs.append(PairSpec("rects", 640, 480, 4032 + i, KITTI))
     return tuple(pairs)
@@ -78,7 +79,7 @@ WORKLOADS = {
     "sintel_1024x436": Workload("sintel_1024x436", (PairSpec("sintel", 1024, 436, 3000, SINTEL),),
                                 "Sintel-shaped 1024x436 pair, L=5, T=6, eps=7"),
     "batch48_mixed": Workload("batch48_mixed", _batch48(),
-                              "48 pairs: 16x 1242x375, 16x 1024x436, 16x 640x480"),
+                              "48 pairs: 16x 1242x375, 16x 1024x436, 16x 640x480, L=5, T=6, eps=1"),
 }
 
 
@@ -93,5 +94,4 @@ def serve_pair(i: int) -> PairSpec:
     rng = np.random.Generator(np.random.PCG64(5000))
     choices = rng.integers(0, len(SERVE_SIZES), size=i + 1)
     w, h, kind = SERVE_SIZES[int(choices[i])]
-    prm = SINTEL if kind == "sintel" else KITTI
-    return PairSpec(kind, w, h, 5000 + i, prm)
+    return PairSpec(kind, w, h, 5000 + i, KITTI)  # one parameter set for the whole stream (eps = 1)

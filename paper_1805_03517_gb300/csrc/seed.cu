@@ -4,6 +4,7 @@
 // For every source pixel p: q* = argmin_q |a_p - b_q|^2 over all target pixels q, ties to the smallest q.
 // Since |a_p|^2 does not depend on q, q* = argmin_q (|b_q|^2 - 2 a_p.b_q): a dense 8-bit contraction A.B^T
 // followed by an argmin epilogue, computed exactly in int32 on the tensor cores (m16n8k32 s8 x s8 -> s32).
+// (tcgen05.mma has no 8-bit integer kind on sm_103a: ptxas rejects .kind::i8 for that target.)
 #include <climits>
 
 #include "ff_internal.h"
@@ -25,17 +26,22 @@ __device__ __forceinline__ void argmin_take(int& s, int& i, int s2, int i2) {
     }
 }
 
-// One warp per 16 source rows; it sweeps all target columns 8 at a time.  Fragment layout of m16n8k32 (8-bit):
-// lane = 4*g + t; A regs {row g, row g+8} x {k 4t..4t+3, k 16+4t..}; B regs col g, k 4t.. and 16+4t..;
-// C regs (row g, cols 2t, 2t+1), (row g+8, cols 2t, 2t+1).
-__global__ __launch_bounds__(128) void k_seed(const SeedProblem* __restrict__ probs, int n_probs, int total_tiles) {
-    int wg = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (wg >= total_tiles) return;
+// One CTA of 8 warps per 16 source rows; warp k sweeps the target column tiles k, k+8, k+16, ... (8 columns
+// each), so every thread still meets its columns in increasing order, then the 8 partial minima are reduced
+// through shared memory (smaller index on equal score: the column slices are disjoint, so this keeps the
+// first-index tie rule).  Fragment layout of m16n8k32 (8-bit): lane = 4*g + t; A regs {row g, row g+8} x
+// {k 4t..4t+3, k 16+4t..}; B regs col g, k 4t.. and 16+4t..; C regs (row g, cols 2t, 2t+1), (row g+8, ...).
+constexpr int kSeedWarps = 8;
+
+__global__ __launch_bounds__(32 * kSeedWarps) void k_seed(const SeedProblem* __restrict__ probs, int n_probs,
+                                                          int total_tiles) {
+    __shared__ int s_best[kSeedWarps][16], s_idx[kSeedWarps][16];
+    const int tile = blockIdx.x;
     int pi = 0;
-    while (pi + 1 < n_probs && wg >= probs[pi + 1].warp_base) pi++;
+    while (pi + 1 < n_probs && tile >= probs[pi + 1].warp_base) pi++;
     const SeedProblem P = probs[pi];
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int r0 = (wg - P.warp_base) * 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int r0 = (tile - P.warp_base) * 16;
     const uint32_t* A0 = reinterpret_cast<const uint32_t*>(P.A + (size_t)(r0 + g) * kSeedK);
     const uint32_t* A1 = reinterpret_cast<const uint32_t*>(P.A + (size_t)(r0 + g + 8) * kSeedK);
     uint32_t a[2][4];
@@ -47,7 +53,7 @@ __global__ __launch_bounds__(128) void k_seed(const SeedProblem* __restrict__ pr
         a[kk][3] = A1[kk * 8 + 4 + t];
     }
     int best0 = INT_MAX, best1 = INT_MAX, idx0 = 0, idx1 = 0;
-    for (int n0 = 0; n0 < P.n; n0 += 8) {
+    for (int n0 = warp * 8; n0 < P.n; n0 += 8 * kSeedWarps) {
         const uint32_t* Bq = reinterpret_cast<const uint32_t*>(P.B + (size_t)(n0 + g) * kSeedK);
         uint32_t b[2][2];
 #pragma unroll
@@ -78,12 +84,17 @@ __global__ __launch_bounds__(128) void k_seed(const SeedProblem* __restrict__ pr
         argmin_take(best1, idx1, s, i);
     }
     if (t == 0) {
-#pragma unroll
-        for (int hh = 0; hh < 2; hh++) {
-            int p = r0 + g + 8 * hh;
-            if (p >= P.n) continue;
-            int q = hh ? idx1 : idx0;
-            int best = hh ? best1 : best0;
+        s_best[warp][g] = best0;
+        s_idx[warp][g] = idx0;
+        s_best[warp][g + 8] = best1;
+        s_idx[warp][g + 8] = idx1;
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        const int r = threadIdx.x, p = r0 + r;
+        int best = s_best[0][r], q = s_idx[0][r];
+        for (int k = 1; k < kSeedWarps; k++) argmin_take(best, q, s_best[k][r], s_idx[k][r]);
+        if (p < P.n) {
             int dx = q % P.w - p % P.w, dy = q / P.w - p / P.w;
             P.flow[p] = (uint32_t)(dx & 0xffff) | ((uint32_t)dy << 16);
             if (P.dist) P.dist[p] = P.normA[p] + best;
@@ -92,7 +103,7 @@ __global__ __launch_bounds__(128) void k_seed(const SeedProblem* __restrict__ pr
 }
 
 void launch_seed(const SeedProblem* probs_dev, int n_probs, int total_row_tiles, cudaStream_t st) {
-    k_seed<<<(total_row_tiles + 3) / 4, 128, 0, st>>>(probs_dev, n_probs, total_row_tiles);
+    k_seed<<<total_row_tiles, 32 * kSeedWarps, 0, st>>>(probs_dev, n_probs, total_row_tiles);
 }
 
 }  // namespace ff
