@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--workload", default="kitti_1242x375")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 48-pair batched measurement")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-stream measurement")
+    ap.add_argument("--serve-requests", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -109,6 +112,83 @@ def make_inputs(workload):
     from paper_1805_03517_gb300 import synth
 
     return [synth.make_pair(p.kind, p.seed, p.w, p.h)[:2] for p in workload.pairs]
+
+
+def measure_batched(torch, ff, configs, stream, local_rank, steps):
+    """48 pairs of three sizes per step in merged launches (graph replay), inputs larger than L2."""
+    wl = configs.workload("batch48_mixed")
+    imgs = make_inputs(wl)
+    dev = torch.device("cuda", local_rank)
+    M = ff.Matcher(wl.pairs[0].params, local_rank, stream)
+    with torch.cuda.stream(stream):
+        d = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in imgs]
+    stream.synchronize()
+    pyrs = [(M.features(a), M.features(b)) for a, b in d]
+    tuning = M.autotune(pyrs, reps=2)
+    for pa, pb in pyrs:
+        M.release(pa)
+        M.release(pb)
+    outs = None
+
+    def step():
+        nonlocal outs
+        pyrs = [(M.features(a), M.features(b)) for a, b in d]
+        outs = M.match_batch(pyrs, outs=outs, with_cost=False)
+        for pa, pb in pyrs:
+            M.release(pa)
+            M.release(pb)
+
+    for _ in range(3):
+        step()
+    s0 = M.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = M.stats()["kernel_launches"] - s0["kernel_launches"]
+    M.close()
+    return {"workload": wl.name, "pairs_per_step": len(wl.pairs), "px_per_step": wl.pixels,
+            "value": wl.pixels / (ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "gpu_launches_per_step": launches / steps, "tiles_per_level": [list(c) for c in tuning],
+            "l2": "not flushed: 5 GB of features per step exceed L2"}
+
+
+def measure_served(torch, ff, configs, stream, local_rank, n_req):
+    """Served stream: Poisson arrivals (200 pairs/s) of frame pairs of four sizes, continuous batching under a
+    60 GB device budget; latency from arrival to completion.  Also the same requests all arriving at once."""
+    from paper_1805_03517_gb300 import serve, synth
+
+    dev = torch.device("cuda", local_rank)
+    prm = configs.KITTI
+    M = ff.Matcher(prm, local_rank, stream)
+    pool = {}
+    with torch.cuda.stream(stream):
+        for (w, h, kind) in configs.SERVE_SIZES:
+            pool[(w, h)] = []
+            for k in range(8):
+                a, b, _ = synth.make_pair(kind, 5000 + 100 * len(pool) + k, w, h)
+                pool[(w, h)].append((torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)))
+    stream.synchronize()
+    for (w, h), prs in pool.items():  # per-size launch configuration, as a deployment would tune once
+        pa, pb = M.features(prs[0][0]), M.features(prs[0][1])
+        M.autotune([(pa, pb)], reps=2)
+        M.release(pa)
+        M.release(pb)
+    frames = []
+    for i, (w, h, _) in enumerate(configs.serve_sizes(n_req)):
+        frames.append(pool[(w, h)][i % 8])
+    arrivals = serve.poisson_arrivals(n_req, 200.0, seed=5)
+    serve.serve(M, frames[:32], [0.0] * 32)  # warm-up: pools, plans and caches
+    offered = serve.serve(M, frames, arrivals, mem_budget_bytes=60 << 30)
+    saturated = serve.serve(M, frames, [0.0] * n_req, mem_budget_bytes=60 << 30)
+    M.close()
+    out = {"requests": n_req, "arrival_rate_per_s": 200.0, "sizes": [f"{w}x{h}" for w, h, _ in configs.SERVE_SIZES],
+           "mem_budget_gb": 60, "inputs": "32 distinct synthetic pairs (8 per size) cycled over the stream",
+           "offered_load": offered.as_dict(), "saturated": saturated.as_dict()}
+    return out
 
 
 def cpu_baseline(workload, imgs):
@@ -348,6 +428,15 @@ def main():
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(workload, imgs)
+    if not args.no_batched:
+        batched = measure_batched(torch, ff, configs, stream, local_rank, steps=max(5, min(30, args.steps // 10)))
+        if rank == 0:
+            line["batched"] = batched
+    if not args.no_served:
+        served = measure_served(torch, ff, configs, stream, local_rank, args.serve_requests)
+        if rank == 0:
+            line["served"] = served
+    if rank == 0:
         print(json.dumps(line), flush=True)
     M.close()
     if dist:

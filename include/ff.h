@@ -113,7 +113,7 @@ typedef struct {
  * pyramids and output buffers) are matched again. */
 FF_API ff_status ff_match_batch(ff_ctx* ctx, int n, const ff_pair_job* jobs);
 
-/* Choose, per pyramid level, the propagation tile shape and the number of iterations fused into one launch for
+/* Choose, per pyramid level, the propagation tile shape, CTA size and the number of iterations fused into one launch for
  * batches shaped like `jobs` (same level sizes and number of pairs): every candidate configuration is run
  * `reps` (1..100) times on these jobs and the fastest is kept for each level.  Results never depend on the
  * configuration; the jobs' outputs are overwritten.  Cached plans are dropped so later calls use the choice.
@@ -121,13 +121,14 @@ FF_API ff_status ff_match_batch(ff_ctx* ctx, int n, const ff_pair_job* jobs);
 FF_API ff_status ff_autotune(ff_ctx* ctx, int n, const ff_pair_job* jobs, int reps);
 
 /* Impose the propagation configuration of one level (tile width and height in pixels, iterations fused per
- * launch) on every later plan of this context, overriding the autotuner; all zeros removes the override.
- * FF_ERR_ARG if the tile with its halo does not fit in shared memory.  Cached plans are dropped. */
-FF_API ff_status ff_set_tuning(ff_ctx* ctx, int level, int tile_w, int tile_h, int iters_per_launch);
+ * launch, threads per CTA: 128, 256 or 512) on every later plan of this context, overriding the autotuner; all
+ * zeros removes the override.  FF_ERR_ARG if the tile with its halo does not fit in shared memory.  Cached
+ * plans are dropped. */
+FF_API ff_status ff_set_tuning(ff_ctx* ctx, int level, int tile_w, int tile_h, int iters_per_launch, int threads);
 
 /* The configuration in force for `level`: the override if set, else the autotuner's choice (tile width,
- * height, iterations per launch); FF_ERR_ARG if neither exists. */
-FF_API ff_status ff_get_tuning(ff_ctx* ctx, int level, int* tile_w, int* tile_h, int* iters_per_launch);
+ * height, iterations per launch, threads per CTA); FF_ERR_ARG if neither exists. */
+FF_API ff_status ff_get_tuning(ff_ctx* ctx, int level, int* tile_w, int* tile_h, int* iters_per_launch, int* threads);
 
 /* Forward/backward consistency check (Sec. 3.1, eps as in Table 3): mask[p] = 1 iff q = p + fwd(p) lies in
  * the image and (fwd_x(p) + bwd_x(q))^2 + (fwd_y(p) + bwd_y(q))^2 <= eps^2.  All pointers are device
@@ -170,6 +171,42 @@ FF_API ff_status ff_profile_read(ff_ctx* ctx, double* ms /* [FF_N_PHASES] */, in
 /* Algorithmic work of a plan for pyramids of size w x h with the context's parameters: per direction, the
  * number of (pixel, iteration) updates summed over all levels, and the number of level-0 pixels. */
 FF_API ff_status ff_work_counts(ff_ctx* ctx, int w, int h, int64_t* pixel_iters, int64_t* pixels);
+
+/* ---- continuous-batching server ------------------------------------------------------------------------
+ * One request = one frame pair (Sec. 3.1): forward field, inverse field, consistency mask.  Requests are
+ * admitted first come first served while at most `max_active` are in flight and the device bytes of the
+ * admitted requests (two feature pyramids + flow/cost scratch each) stay within `mem_budget_bytes`.  Each
+ * ff_server_step enqueues one tick on the context's stream: every active request advances by one propagation
+ * launch of its current level, with the work of all active requests merged into one launch per kernel kind;
+ * requests that arrive while others are on the GPU join at the next tick.  A request's results are identical
+ * to matching it alone (ff_match_batch), whatever else is in flight.  Not thread-safe per server. */
+typedef struct ff_server ff_server;
+
+/* Inputs and outputs of one request; all device buffers owned by the caller and valid until the request has
+ * been reported by ff_server_poll.  Frames uint8 [h][w][3] (rows pitch_bytes apart); flows int16 [h][w][2];
+ * mask uint8 [h][w]; cost_fwd/cost_bwd int32 [h][w] or NULL. */
+typedef struct {
+    const uint8_t* rgb_a;
+    const uint8_t* rgb_b;
+    int w, h, pitch_bytes;
+    int16_t* flow_fwd;
+    int16_t* flow_bwd;
+    int32_t* cost_fwd;
+    int32_t* cost_bwd;
+    uint8_t* mask;
+} ff_request;
+
+FF_API ff_status ff_server_create(ff_ctx* ctx, int64_t mem_budget_bytes, int max_active, ff_server** out);
+/* Queue a request under the caller's id; FF_ERR_ARG if it could never fit the memory budget. */
+FF_API ff_status ff_server_submit(ff_server* srv, uint64_t id, const ff_request* req);
+/* Admit what fits and enqueue one tick; reports the requests in flight and still queued. */
+FF_API ff_status ff_server_step(ff_server* srv, int* n_active, int* n_queued);
+/* Ids (up to max_ids) of requests whose outputs are complete; with wait != 0 blocks until at least one is. */
+FF_API ff_status ff_server_poll(ff_server* srv, int wait, uint64_t* ids, int max_ids, int* n_done);
+/* Ticks enqueued, kernel launches enqueued, and device bytes of the admitted requests. */
+FF_API ff_status ff_server_stats(ff_server* srv, int64_t* ticks, int64_t* launches, int64_t* bytes_in_use);
+/* Wait for the stream, release every resource of the server (not the context). */
+FF_API ff_status ff_server_destroy(ff_server* srv);
 
 /* Size of the fixed device scratch array used by ff_match_pair_noalloc (32 MiB): enough for frames of up to
  * about 1.5 million pixels at level 0. */

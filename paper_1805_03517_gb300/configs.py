@@ -87,11 +87,15 @@ def workload(name: str) -> Workload:
     return WORKLOADS[name]
 
 
-def serve_pair(i: int) -> PairSpec:
-    """The i-th pair of the served stream: size drawn uniformly from SERVE_SIZES (seeded by i)."""
+def serve_sizes(n: int):
+    """Sizes (w, h, kind) of the first n pairs of the served stream, uniform over SERVE_SIZES (seeded)."""
     import numpy as np
 
     rng = np.random.Generator(np.random.PCG64(5000))
-    choices = rng.integers(0, len(SERVE_SIZES), size=i + 1)
-    w, h, kind = SERVE_SIZES[int(choices[i])]
-    return PairSpec(kind, w, h, 5000 + i, KITTI)  # one parameter set for the whole stream (eps = 1)
+    return [SERVE_SIZES[int(c)] for c in rng.integers(0, len(SERVE_SIZES), size=n)]
+
+
+def serve_pair(i: int) -> PairSpec:
+    """The i-th pair of the served stream (one parameter set for the whole stream, eps = 1)."""
+    w, h, kind = serve_sizes(i + 1)[i]
+    return PairSpec(kind, w, h, 5000 + i, KITTI)

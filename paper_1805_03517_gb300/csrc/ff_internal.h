@@ -94,11 +94,13 @@ struct PropProblem {  // one (pair, direction, level) of a propagation launch
 struct PropLaunch {
     int tw, th;      // tile interior
     int max_iter;    // largest n_iter of the launch (sizes the shared-memory halo)
+    int threads;     // CTA size: 128, 256 or 512
 };
 constexpr size_t kMaxPropSmem = 200 * 1024;
 size_t prop_smem_bytes(int tw, int th, int n_iter);
 cudaError_t init_kernel_attributes();  // once per device, before the first launch
-int prop_blocks_per_sm(size_t smem);   // resident CTAs per SM of the propagation kernel
+bool prop_threads_ok(int threads);
+int prop_blocks_per_sm(size_t smem, int threads);  // resident CTAs per SM of the propagation kernel
 // queue_dev[i] = (problem index, tile index); counter_dev must be zero when the launch starts
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st);
@@ -123,11 +125,11 @@ struct PyrView {
 struct CtxView {
     int device, n_sms;
     cudaStream_t stream;
-    int n_scales, iters, rs_radius;
+    int n_scales, iters, rs_radius, eps;
     uint32_t seed;
 };
 struct TileChoice {
-    int tw, th, k;
+    int tw, th, k, threads;
 };
 
 // ---------------------------------------------------------------------------------------------------------

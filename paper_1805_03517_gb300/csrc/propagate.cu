@@ -122,99 +122,126 @@ size_t prop_smem_bytes(int tw, int th, int n_iter) {
     return (size_t)(tw + 2 * H) * (th + 2 * H) * 8;
 }
 
-#ifndef FF_PROP_MINB
-#define FF_PROP_MINB 2
-#endif
-constexpr int kPropThreads = 256;
+
+// Geometry of the tile a CTA is working on (all coordinates are level coordinates).
+struct TileGeom {
+    int x0, y0, x1, y1;      // tile interior
+    int lx0, ly0, RW, RH;    // loaded region (tile + halo, clipped to the level)
+};
+
+// Region of half-sweep j (colour j&1 of direction j>>1) with `rem` halo pixels still to be consumed.
+__device__ __forceinline__ void halfsweep_region(const TileGeom& G, int w, int h, int j, int rem, int& rx0, int& ry0,
+                                                 int& rx1, int& ry1) {
+    rx0 = max(G.x0 - c_grow[j][0] - rem, 0);
+    ry0 = max(G.y0 - c_grow[j][1] - rem, 0);
+    rx1 = min(G.x1 + c_grow[j][2] + rem, w);
+    ry1 = min(G.y1 + c_grow[j][3] + rem, h);
+}
+
+// Pixel i of the active colour of a region, row-major over (row, slot); false past the row's end.
+__device__ __forceinline__ bool region_pixel(int i, int HW, int rx0, int ry0, int rx1, int colour, int& x, int& y) {
+    const int row = i / HW, slot = i - row * HW;
+    y = ry0 + row;
+    x = rx0 + 2 * slot + ((rx0 + y + colour) & 1);
+    return x < rx1;
+}
+
+// One half-sweep with one thread per pixel (the whole 96-B descriptor per thread).
+__device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& G, uint32_t* sflow, int32_t* scost,
+                                          int j, int rem, uint32_t k1) {
+    const int w = P.w, h = P.h;
+    const int d = j >> 1, colour = j & 1;
+    int rx0, ry0, rx1, ry1;
+    halfsweep_region(G, w, h, j, rem, rx0, ry0, rx1, ry1);
+    const int HW = (rx1 - rx0 + 1) >> 1;
+    const int total = HW * (ry1 - ry0);
+    const int R = P.rs_radius;
+    const uint32_t span = 2u * R + 1u;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        int x, y;
+        if (!region_pixel(i, HW, rx0, ry0, rx1, colour, x, y)) continue;
+        const int sidx = (y - G.ly0) * G.RW + (x - G.lx0);
+        uint32_t cur = sflow[sidx];
+        int c = scost[sidx];
+        const int n1x = x + ((d & 1) ? 1 : -1);
+        const int n2y = y + ((d & 2) ? 1 : -1);
+        const bool v1 = (unsigned)n1x < (unsigned)w;
+        const bool v2 = (unsigned)n2y < (unsigned)h;
+        const uint32_t f1 = v1 ? sflow[sidx + (n1x - x)] : 0u;
+        const uint32_t f2 = v2 ? sflow[sidx + (n2y - y) * G.RW] : 0u;
+        // a candidate equal to the current flow (or to an already tried one) cannot be strictly cheaper
+        const bool e1 = v1 && f1 != cur && in_level(x + flow_x(f1), y + flow_y(f1), w, h);
+        const bool e2 = v2 && f2 != cur && !(v1 && f2 == f1) && in_level(x + flow_x(f2), y + flow_y(f2), w, h);
+        if (!(e1 || e2 || d >= 1)) continue;
+        // issue every independent load (own descriptor, both neighbour candidates) before any compute
+        uint32_t a[24], b1[24], b2[24];
+        load_desc(P.fa, y * w + x, a);
+        if (e1) load_desc(P.fb, (y + flow_y(f1)) * w + x + flow_x(f1), b1);
+        if (e2) load_desc(P.fb, (y + flow_y(f2)) * w + x + flow_x(f2), b2);
+        bias_desc(a);
+        if (e1) {
+            int s1 = sad_biased(a, b1);
+            if (s1 < c) { cur = f1; c = s1; }
+        }
+        if (e2) {
+            int s2 = sad_biased(a, b2);
+            if (s2 < c) { cur = f2; c = s2; }
+        }
+        if (d >= 1) {
+            const uint32_t k2 = mix32(k1 ^ ((uint32_t)y * 65536u + (uint32_t)x));
+            const int ox = (int)(mix32(k2 ^ (uint32_t)(2 * d)) % span) - R;
+            const int oy = (int)(mix32(k2 ^ (uint32_t)(2 * d + 1)) % span) - R;
+            if (ox != 0 || oy != 0) {
+                const int fx = flow_x(cur) + ox, fy = flow_y(cur) + oy;
+                if (in_level(x + fx, y + fy, w, h)) {
+                    load_desc(P.fb, (y + fy) * w + x + fx, b1);
+                    int s3 = sad_biased(a, b1);
+                    if (s3 < c) { cur = pack_flow(fx, fy); c = s3; }
+                }
+            }
+        }
+        sflow[sidx] = cur;
+        scost[sidx] = c;
+    }
+}
 
 // One tile of one problem: load the tile and its halo, run n_iter iterations in shared memory, write the tile.
 __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, const PropLaunch& L, uint32_t* smem) {
     const int w = P.w, h = P.h;
-    const int x0 = (tile % P.tiles_x) * L.tw, y0 = (tile / P.tiles_x) * L.th;
-    const int x1 = min(x0 + L.tw, w), y1 = min(y0 + L.th, h);
+    TileGeom G;
+    G.x0 = (tile % P.tiles_x) * L.tw;
+    G.y0 = (tile / P.tiles_x) * L.th;
+    G.x1 = min(G.x0 + L.tw, w);
+    G.y1 = min(G.y0 + L.th, h);
     const int H = kHaloPerIter * P.n_iter;
-    const int lx0 = max(x0 - H, 0), ly0 = max(y0 - H, 0), lx1 = min(x1 + H, w), ly1 = min(y1 + H, h);
-    const int RW = lx1 - lx0, RH = ly1 - ly0;
+    G.lx0 = max(G.x0 - H, 0);
+    G.ly0 = max(G.y0 - H, 0);
+    G.RW = min(G.x1 + H, w) - G.lx0;
+    G.RH = min(G.y1 + H, h) - G.ly0;
     uint32_t* sflow = smem;
-    int32_t* scost = reinterpret_cast<int32_t*>(smem + RW * RH);
+    int32_t* scost = reinterpret_cast<int32_t*>(smem + G.RW * G.RH);
 
-    for (int i = threadIdx.x; i < RW * RH; i += blockDim.x) {
-        int r = i / RW, c = i - r * RW;
-        size_t g = (size_t)(ly0 + r) * w + lx0 + c;
+    for (int i = threadIdx.x; i < G.RW * G.RH; i += blockDim.x) {
+        int r = i / G.RW, c = i - r * G.RW;
+        size_t g = (size_t)(G.ly0 + r) * w + G.lx0 + c;
         sflow[i] = P.flow_in[g];
         scost[i] = P.cost_in[g];
     }
     __syncthreads();
-
-    const int R = P.rs_radius;
-    const uint32_t span = 2u * R + 1u;
     for (int it = 0; it < P.n_iter; it++) {
         const int t = P.t0 + it;
         const int rem = kHaloPerIter * (P.n_iter - 1 - it);
         const uint32_t k1 = mix32(P.seed ^ mix32((uint32_t)P.dir * 65536u + (uint32_t)P.level * 256u + (uint32_t)t));
         for (int j = 0; j < 8; j++) {
-            const int d = j >> 1, colour = j & 1;
-            const int rx0 = max(x0 - c_grow[j][0] - rem, 0), ry0 = max(y0 - c_grow[j][1] - rem, 0);
-            const int rx1 = min(x1 + c_grow[j][2] + rem, w), ry1 = min(y1 + c_grow[j][3] + rem, h);
-            const int HW = (rx1 - rx0 + 1) >> 1;
-            const int total = HW * (ry1 - ry0);
-            for (int i = threadIdx.x; i < total; i += blockDim.x) {
-                const int row = i / HW, slot = i - row * HW;
-                const int y = ry0 + row;
-                const int x = rx0 + 2 * slot + ((rx0 + y + colour) & 1);
-                if (x >= rx1) continue;
-                const int sidx = (y - ly0) * RW + (x - lx0);
-                uint32_t cur = sflow[sidx];
-                int c = scost[sidx];
-                const int n1x = x + ((d & 1) ? 1 : -1);
-                const int n2y = y + ((d & 2) ? 1 : -1);
-                const bool v1 = (unsigned)n1x < (unsigned)w;
-                const bool v2 = (unsigned)n2y < (unsigned)h;
-                const uint32_t f1 = v1 ? sflow[sidx + (n1x - x)] : 0u;
-                const uint32_t f2 = v2 ? sflow[sidx + (n2y - y) * RW] : 0u;
-                // a candidate equal to the current flow (or to an already tried one) cannot be strictly cheaper
-                const bool e1 = v1 && f1 != cur && in_level(x + flow_x(f1), y + flow_y(f1), w, h);
-                const bool e2 = v2 && f2 != cur && !(v1 && f2 == f1) && in_level(x + flow_x(f2), y + flow_y(f2), w, h);
-                if (!(e1 || e2 || d >= 1)) continue;
-                // issue every independent load (own descriptor, both neighbour candidates) before any compute
-                uint32_t a[24], b1[24], b2[24];
-                load_desc(P.fa, y * w + x, a);
-                if (e1) load_desc(P.fb, (y + flow_y(f1)) * w + x + flow_x(f1), b1);
-                if (e2) load_desc(P.fb, (y + flow_y(f2)) * w + x + flow_x(f2), b2);
-                bias_desc(a);
-                if (e1) {
-                    int s1 = sad_biased(a, b1);
-                    if (s1 < c) { cur = f1; c = s1; }
-                }
-                if (e2) {
-                    int s2 = sad_biased(a, b2);
-                    if (s2 < c) { cur = f2; c = s2; }
-                }
-                if (d >= 1) {
-                    const uint32_t k2 = mix32(k1 ^ ((uint32_t)y * 65536u + (uint32_t)x));
-                    const int ox = (int)(mix32(k2 ^ (uint32_t)(2 * d)) % span) - R;
-                    const int oy = (int)(mix32(k2 ^ (uint32_t)(2 * d + 1)) % span) - R;
-                    if (ox != 0 || oy != 0) {
-                        const int fx = flow_x(cur) + ox, fy = flow_y(cur) + oy;
-                        if (in_level(x + fx, y + fy, w, h)) {
-                            load_desc(P.fb, (y + fy) * w + x + fx, b1);
-                            int s3 = sad_biased(a, b1);
-                            if (s3 < c) { cur = pack_flow(fx, fy); c = s3; }
-                        }
-                    }
-                }
-                sflow[sidx] = cur;
-                scost[sidx] = c;
-            }
+            halfsweep(P, G, sflow, scost, j, rem, k1);
             __syncthreads();
         }
     }
-
-    const int TW = x1 - x0;
-    for (int i = threadIdx.x; i < TW * (y1 - y0); i += blockDim.x) {
+    const int TW = G.x1 - G.x0;
+    for (int i = threadIdx.x; i < TW * (G.y1 - G.y0); i += blockDim.x) {
         int r = i / TW, c = i - r * TW;
-        int sidx = (y0 + r - ly0) * RW + (x0 + c - lx0);
-        size_t g = (size_t)(y0 + r) * w + x0 + c;
+        int sidx = (G.y0 + r - G.ly0) * G.RW + (G.x0 + c - G.lx0);
+        size_t g = (size_t)(G.y0 + r) * w + G.x0 + c;
         P.flow_out[g] = sflow[sidx];
         P.cost_out[g] = scost[sidx];
     }
@@ -222,10 +249,11 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
 
 // Persistent launch: each CTA takes tiles from the launch's queue (an atomic counter, zeroed before the launch)
 // until it is empty, so the last wave has no idle tail.  queue[i] = (problem index, tile index in problem).
-__global__ __launch_bounds__(kPropThreads, FF_PROP_MINB) void k_propagate(const PropProblem* __restrict__ probs,
-                                                                         const int2* __restrict__ queue,
-                                                                         int n_tiles, int* __restrict__ counter,
-                                                                         PropLaunch L) {
+// Instantiated for 128, 256 and 512 threads (at most 128 registers per thread in every case).
+template <int THREADS>
+__global__ __launch_bounds__(THREADS, 512 / THREADS) void k_propagate(
+    const PropProblem* __restrict__ probs, const int2* __restrict__ queue, int n_tiles, int* __restrict__ counter,
+    PropLaunch L) {
     extern __shared__ uint32_t smem[];
     __shared__ int s_next;
     for (;;) {
@@ -240,12 +268,22 @@ __global__ __launch_bounds__(kPropThreads, FF_PROP_MINB) void k_propagate(const 
 }
 
 cudaError_t init_kernel_attributes() {
-    return cudaFuncSetAttribute(k_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_propagate<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_propagate<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_propagate<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
+    return e;
 }
 
-int prop_blocks_per_sm(size_t smem) {
+bool prop_threads_ok(int threads) { return threads == 128 || threads == 256 || threads == 512; }
+
+int prop_blocks_per_sm(size_t smem, int threads) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate, kPropThreads, smem) != cudaSuccess) {
+    cudaError_t e = threads == 128   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<128>, 128, smem)
+                    : threads == 512 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<512>, 512, smem)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<256>, 256, smem);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -255,7 +293,12 @@ int prop_blocks_per_sm(size_t smem) {
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st) {
     size_t smem = prop_smem_bytes(L.tw, L.th, L.max_iter);
-    k_propagate<<<grid, kPropThreads, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
+    if (L.threads == 128)
+        k_propagate<128><<<grid, 128, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
+    else if (L.threads == 512)
+        k_propagate<512><<<grid, 512, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
+    else
+        k_propagate<256><<<grid, 256, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
 }
 
 // ---------------------------------------------------------------------------------------------------------

@@ -1,0 +1,515 @@
+// server.cu -- continuous-batching server for the Flow Fields matching stage (FlowFields++, arXiv 1805.03517,
+// Sec. 3.1, one request = one frame pair: forward field, inverse field, consistency mask).
+//
+// Requests are queued by ff_server_submit and admitted, first come first served, while the number of active
+// requests stays below max_active and the device bytes of admitted requests (their two feature pyramids and
+// their flow/cost scratch) stay within the memory budget.  Every ff_server_step enqueues one tick: each active
+// request advances by one propagation launch-chunk of its current level; a request's first tick also builds its
+// pyramids, finds its initial matches and does the first hand-over, the first chunk of every level carries that
+// level's hand-over, and the last chunk of level 0 is followed by the consistency check.  Work of all active
+// requests of a tick is merged into one launch per kernel kind (propagation: one per launch configuration), so
+// requests that arrive while others are on the GPU join the next tick.  Results depend only on the request
+// (the random-search hash is keyed by pixel, level, iteration and direction), never on the mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "ff.h"
+#include "ff_internal.h"
+
+using namespace ff;
+
+namespace {
+
+constexpr int kRing = 4;  // ticks in flight before the host waits
+
+size_t a256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct Req {
+    uint64_t id = 0;
+    ff_request io{};
+    ff_pyr* pa = nullptr;
+    ff_pyr* pb = nullptr;
+    PyrView A{}, B{};
+    int L = 0, T = 0;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int64_t footprint = 0;
+    uint32_t* flow[2][kMaxLevels][2] = {};
+    int32_t* cost[2][kMaxLevels][2] = {};
+    int32_t* dist[2] = {};
+    TileChoice cfg[kMaxLevels] = {};
+    int n_chunks[kMaxLevels] = {};
+    int level = 0, chunk = 0, cur[2] = {0, 0};
+    bool started = false;
+    int64_t done_tick = -1;
+    bool counted = false;  // footprint added to the server's bytes in use
+};
+
+struct RingSlot {
+    char* host = nullptr;   // pinned
+    char* dev = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    int64_t tick = -1;
+};
+
+int64_t pyr_bytes(int w, int h, int L) {
+    int64_t b = 0;
+    int ws = w, hs = h;
+    for (int s = 0; s < L; s++) {
+        if (s > 0) b += (int64_t)ws * hs * 3;
+        b += (int64_t)ws * hs * kDescBytes;
+        if (s + 1 < L) {
+            ws = std::max(1, ws / 2);
+            hs = std::max(1, hs / 2);
+        }
+    }
+    return b + (int64_t)ws * hs * (kSeedK + 4) + 4096;
+}
+
+size_t scratch_need(int w, int h, int L) {
+    size_t b = 0;
+    int ws = w, hs = h;
+    for (int s = 0; s < L; s++) {
+        b += 2 * 4 * a256((size_t)ws * hs * 4);
+        if (s + 1 < L) {
+            ws = std::max(1, ws / 2);
+            hs = std::max(1, hs / 2);
+        }
+    }
+    return b + 2 * a256((size_t)ws * hs * 4);
+}
+
+}  // namespace
+
+struct ff_server {
+    ff_ctx* ctx = nullptr;
+    CtxView cv{};
+    int64_t budget = 0, in_use = 0;
+    int max_active = 0;
+    std::deque<std::unique_ptr<Req>> queued;
+    std::vector<std::unique_ptr<Req>> active;
+    std::vector<std::unique_ptr<Req>> finishing;  // all launches enqueued, waiting for their tick
+    std::multimap<size_t, void*> free_scratch;    // recycled scratch blocks by size
+    RingSlot ring[kRing];
+    int64_t tick = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+ff_status srv_fail(ff_server* s, ff_status st, const char* msg) { return (ff_status)ctx_set_error(s->ctx, st, msg); }
+
+ff_status ring_reserve(ff_server* s, RingSlot& r, size_t bytes) {
+    if (r.done) {
+        if (cudaEventSynchronize(r.done) != cudaSuccess) return srv_fail(s, FF_ERR_CUDA, "tick event failed");
+    }
+    if (bytes <= r.cap) return FF_OK;
+    if (r.host) cudaFreeHost(r.host);
+    if (r.dev) cudaFree(r.dev);
+    r.host = nullptr;
+    r.dev = nullptr;
+    size_t cap = std::max(bytes, (size_t)1 << 20) * 2;
+    if (cudaMallocHost(&r.host, cap) != cudaSuccess || cudaMalloc(&r.dev, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return srv_fail(s, FF_ERR_OOM, "tick table allocation failed");
+    }
+    r.cap = cap;
+    return FF_OK;
+}
+
+// Scratch of a request: per direction and level two flow and two cost buffers, plus seed distances.
+ff_status take_scratch(ff_server* s, Req& q) {
+    size_t need = scratch_need(q.A.w, q.A.h, q.L);
+    auto it = s->free_scratch.find(need);
+    void* p = nullptr;
+    if (it != s->free_scratch.end()) {
+        p = it->second;
+        s->free_scratch.erase(it);
+    } else if (cudaMalloc(&p, need) != cudaSuccess) {
+        cudaGetLastError();
+        return srv_fail(s, FF_ERR_OOM, "scratch allocation failed");
+    }
+    q.scratch = p;
+    q.scratch_bytes = need;
+    char* b = static_cast<char*>(p);
+    size_t off = 0;
+    for (int d = 0; d < 2; d++)
+        for (int l = 0; l < q.L; l++) {
+            size_t n = (size_t)q.A.ws[l] * q.A.hs[l];
+            for (int k = 0; k < 2; k++) {
+                q.flow[d][l][k] = reinterpret_cast<uint32_t*>(b + off);
+                off += a256(n * 4);
+                q.cost[d][l][k] = reinterpret_cast<int32_t*>(b + off);
+                off += a256(n * 4);
+            }
+        }
+    for (int d = 0; d < 2; d++) {
+        q.dist[d] = reinterpret_cast<int32_t*>(b + off);
+        off += a256((size_t)q.A.n_coarse * 4);
+    }
+    return FF_OK;
+}
+
+void release_req(ff_server* s, Req& q) {
+    if (q.pa) ff_pyr_release(s->ctx, q.pa);
+    if (q.pb) ff_pyr_release(s->ctx, q.pb);
+    q.pa = q.pb = nullptr;
+    if (q.scratch) s->free_scratch.emplace(q.scratch_bytes, q.scratch);
+    q.scratch = nullptr;
+    if (q.counted) s->in_use -= q.footprint;
+    q.counted = false;
+}
+
+ff_status admit(ff_server* s) {
+    while (!s->queued.empty() && (int)s->active.size() < s->max_active) {
+        Req& q = *s->queued.front();
+        const bool idle = s->active.empty() && s->finishing.empty();
+        if (s->in_use + q.footprint > s->budget && !idle) break;  // wait for memory
+        ff_status st = ff_features(s->ctx, q.io.rgb_a, q.io.w, q.io.h, q.io.pitch_bytes, &q.pa);
+        if (st == FF_OK) st = ff_features(s->ctx, q.io.rgb_b, q.io.w, q.io.h, q.io.pitch_bytes, &q.pb);
+        if (st != FF_OK) {
+            release_req(s, q);
+            return st;
+        }
+        pyr_view(q.pa, &q.A);
+        pyr_view(q.pb, &q.B);
+        q.L = q.A.L;
+        q.T = s->cv.iters;
+        st = take_scratch(s, q);
+        if (st != FF_OK) {
+            release_req(s, q);
+            return st;
+        }
+        s->in_use += q.footprint;
+        q.counted = true;
+        for (int l = 0; l < q.L; l++) {
+            q.cfg[l] = ctx_level_choice(s->ctx, l, q.A.ws[l], q.A.hs[l], 2, 2 * (int64_t)q.A.ws[l] * q.A.hs[l]);
+            q.n_chunks[l] = (q.T + q.cfg[l].k - 1) / q.cfg[l].k;
+        }
+        q.level = q.L - 1;
+        q.chunk = 0;
+        s->active.push_back(std::move(s->queued.front()));
+        s->queued.pop_front();
+        s->launches += 2 * (q.L + 1);  // feature launches enqueued by ff_features
+    }
+    return FF_OK;
+}
+
+struct PropGroupKey {
+    int tw, th, n_iter, threads;
+    bool operator<(const PropGroupKey& o) const {
+        return std::tie(tw, th, n_iter, threads) < std::tie(o.tw, o.th, o.n_iter, o.threads);
+    }
+};
+
+// Build and enqueue one tick for every active request.
+ff_status tick(ff_server* s) {
+    if (s->active.empty()) return FF_OK;
+    const int T = s->cv.iters;
+    std::vector<SeedProblem> seeds;
+    std::vector<HandoverProblem> hos;
+    std::map<PropGroupKey, std::vector<std::pair<PropProblem, int>>> groups;  // (problem, tiles)
+    struct Cons {
+        const uint32_t* f;
+        const uint32_t* b;
+        int w, h;
+        uint8_t* mask;
+    };
+    std::vector<Cons> cons;
+    int seed_tiles = 0;
+    int64_t ho_pix = 0;
+    std::vector<size_t> finished;
+    for (size_t ri = 0; ri < s->active.size(); ri++) {
+        Req& q = *s->active[ri];
+        const int sl = q.level, L = q.L;
+        if (!q.started) {  // exact initial matches of both directions at the coarsest level
+            for (int d = 0; d < 2; d++) {
+                const PyrView& X = d == 0 ? q.A : q.B;
+                const PyrView& Y = d == 0 ? q.B : q.A;
+                SeedProblem sp{};
+                sp.A = X.seed_desc;
+                sp.B = Y.seed_desc;
+                sp.normA = X.seed_norm;
+                sp.normB = Y.seed_norm;
+                sp.n = X.n_coarse;
+                sp.w = X.ws[L - 1];
+                sp.flow = q.flow[d][L - 1][0];
+                sp.dist = q.dist[d];
+                sp.warp_base = seed_tiles;
+                seed_tiles += (sp.n + 15) / 16;
+                seeds.push_back(sp);
+            }
+            q.started = true;
+        }
+        if (q.chunk == 0) {  // hand-over into this level (the seed's cost at the coarsest level)
+            for (int d = 0; d < 2; d++) {
+                const PyrView& X = d == 0 ? q.A : q.B;
+                const PyrView& Y = d == 0 ? q.B : q.A;
+                HandoverProblem hp{};
+                hp.fa = X.feat[sl];
+                hp.fb = Y.feat[sl];
+                hp.w = X.ws[sl];
+                hp.h = X.hs[sl];
+                if (sl == L - 1) {
+                    hp.parent = nullptr;
+                    hp.flow_in = q.flow[d][sl][0];
+                } else {
+                    hp.parent = q.flow[d][sl + 1][q.cur[d]];
+                    hp.pw = X.ws[sl + 1];
+                    hp.ph = X.hs[sl + 1];
+                }
+                hp.flow_out = q.flow[d][sl][0];
+                hp.cost_out = q.cost[d][sl][0];
+                hp.pix_base = ho_pix;
+                ho_pix += (int64_t)hp.w * hp.h;
+                hos.push_back(hp);
+                q.cur[d] = 0;
+            }
+        }
+        const TileChoice c = q.cfg[sl];
+        const int t0 = q.chunk * c.k, n_iter = std::min(c.k, T - t0);
+        const bool last = sl == 0 && q.chunk == q.n_chunks[sl] - 1;
+        auto& grp = groups[PropGroupKey{c.tw, c.th, n_iter, c.threads}];
+        for (int d = 0; d < 2; d++) {
+            const PyrView& X = d == 0 ? q.A : q.B;
+            const PyrView& Y = d == 0 ? q.B : q.A;
+            PropProblem pp{};
+            pp.fa = X.feat[sl];
+            pp.fb = Y.feat[sl];
+            pp.w = X.ws[sl];
+            pp.h = X.hs[sl];
+            const int in = q.cur[d], out = in ^ 1;
+            pp.flow_in = q.flow[d][sl][in];
+            pp.cost_in = q.cost[d][sl][in];
+            int32_t* user_cost = d == 0 ? q.io.cost_fwd : q.io.cost_bwd;
+            if (last) {
+                pp.flow_out = reinterpret_cast<uint32_t*>(d == 0 ? q.io.flow_fwd : q.io.flow_bwd);
+                pp.cost_out = user_cost ? user_cost : q.cost[d][sl][out];
+            } else {
+                pp.flow_out = q.flow[d][sl][out];
+                pp.cost_out = q.cost[d][sl][out];
+            }
+            q.cur[d] = out;
+            pp.tiles_x = (pp.w + c.tw - 1) / c.tw;
+            pp.t0 = t0;
+            pp.n_iter = n_iter;
+            pp.level = sl;
+            pp.dir = d;
+            pp.seed = s->cv.seed;
+            pp.rs_radius = s->cv.rs_radius;
+            grp.push_back({pp, pp.tiles_x * ((pp.h + c.th - 1) / c.th)});
+        }
+        if (++q.chunk == q.n_chunks[sl]) {
+            if (sl == 0) {
+                cons.push_back({reinterpret_cast<const uint32_t*>(q.io.flow_fwd),
+                                reinterpret_cast<const uint32_t*>(q.io.flow_bwd), q.A.w, q.A.h, q.io.mask});
+                finished.push_back(ri);
+            } else {
+                q.level--;
+                q.chunk = 0;
+            }
+        }
+    }
+
+    // tables of this tick: seeds | handovers | propagation problems | queues | counters
+    size_t n_props = 0, n_queue = 0;
+    for (auto& kv : groups) {
+        n_props += kv.second.size();
+        for (auto& pr : kv.second) n_queue += pr.second;
+    }
+    const size_t o_seed = 0, o_ho = a256(seeds.size() * sizeof(SeedProblem));
+    const size_t o_prop = o_ho + a256(hos.size() * sizeof(HandoverProblem));
+    const size_t o_q = o_prop + a256(n_props * sizeof(PropProblem));
+    const size_t o_cnt = o_q + a256(n_queue * sizeof(int2));
+    const size_t bytes = o_cnt + a256(groups.size() * sizeof(int) + 4);
+    RingSlot& r = s->ring[s->tick % kRing];
+    ff_status st = ring_reserve(s, r, bytes);
+    if (st != FF_OK) return st;
+    std::memset(r.host, 0, bytes);
+    memcpy(r.host + o_seed, seeds.data(), seeds.size() * sizeof(SeedProblem));
+    memcpy(r.host + o_ho, hos.data(), hos.size() * sizeof(HandoverProblem));
+    PropProblem* hp = reinterpret_cast<PropProblem*>(r.host + o_prop);
+    int2* hq = reinterpret_cast<int2*>(r.host + o_q);
+    struct PL {
+        PropLaunch pl;
+        size_t q0;
+        int nq, grid;
+    };
+    std::vector<PL> pls;
+    size_t pi = 0, qi = 0;
+    for (auto& kv : groups) {
+        const PropGroupKey& k = kv.first;
+        const size_t q0 = qi;
+        // the two directions of each request were pushed next to each other: interleave their tiles
+        for (size_t g = 0; g < kv.second.size(); g += 2) {
+            const int p0 = (int)(pi + g), n0 = kv.second[g].second;
+            const int n1 = g + 1 < kv.second.size() ? kv.second[g + 1].second : 0;
+            for (int t = 0; t < std::max(n0, n1); t++) {
+                if (t < n0) hq[qi++] = make_int2(p0, t);
+                if (t < n1) hq[qi++] = make_int2(p0 + 1, t);
+            }
+        }
+        for (auto& pr : kv.second) hp[pi++] = pr.first;
+        const size_t smem = prop_smem_bytes(k.tw, k.th, k.n_iter);
+        const int nq = (int)(qi - q0);
+        pls.push_back({PropLaunch{k.tw, k.th, k.n_iter, k.threads}, q0, nq,
+                       std::min(nq, prop_blocks_per_sm(smem, k.threads) * s->cv.n_sms)});
+    }
+    cudaStream_t stm = s->cv.stream;
+    if (cudaMemcpyAsync(r.dev, r.host, bytes, cudaMemcpyHostToDevice, stm) != cudaSuccess)
+        return srv_fail(s, FF_ERR_CUDA, "tick table upload failed");
+    int nl = 0;
+    if (!seeds.empty()) {
+        launch_seed(reinterpret_cast<const SeedProblem*>(r.dev + o_seed), (int)seeds.size(), seed_tiles, stm);
+        nl++;
+    }
+    if (!hos.empty()) {
+        launch_handover(reinterpret_cast<const HandoverProblem*>(r.dev + o_ho), (int)hos.size(), ho_pix, stm);
+        nl++;
+    }
+    for (size_t g = 0; g < pls.size(); g++) {
+        launch_propagate(reinterpret_cast<const PropProblem*>(r.dev + o_prop),
+                         reinterpret_cast<const int2*>(r.dev + o_q) + pls[g].q0, pls[g].nq,
+                         reinterpret_cast<int*>(r.dev + o_cnt) + g, pls[g].grid, pls[g].pl, stm);
+        nl++;
+    }
+    for (const Cons& cs : cons) {
+        launch_consistency(cs.f, cs.b, cs.w, cs.h, s->cv.eps, cs.mask, stm);
+        nl++;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return srv_fail(s, FF_ERR_CUDA, cudaGetErrorString(e));
+    if (!r.done && cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess)
+        return srv_fail(s, FF_ERR_CUDA, "event creation failed");
+    if (cudaEventRecord(r.done, stm) != cudaSuccess) return srv_fail(s, FF_ERR_CUDA, "event record failed");
+    r.tick = s->tick;
+    s->launches += nl;
+    // requests whose last launches are in this tick wait for it
+    for (size_t k = finished.size(); k-- > 0;) {
+        size_t ri = finished[k];
+        s->active[ri]->done_tick = s->tick;
+        s->finishing.push_back(std::move(s->active[ri]));
+        s->active.erase(s->active.begin() + ri);
+    }
+    s->tick++;
+    return FF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ff_status ff_server_create(ff_ctx* ctx, int64_t mem_budget_bytes, int max_active, ff_server** out) {
+    if (!out) return FF_ERR_ARG;
+    *out = nullptr;
+    CtxView cv;
+    if (!ctx_view(ctx, &cv)) return FF_ERR_ARG;
+    if (mem_budget_bytes <= 0 || max_active < 1 || max_active > 4096)
+        return (ff_status)ctx_set_error(ctx, FF_ERR_ARG, "bad memory budget or max_active");
+    ff_server* s = new (std::nothrow) ff_server();
+    if (!s) return FF_ERR_OOM;
+    s->ctx = ctx;
+    s->cv = cv;
+    s->budget = mem_budget_bytes;
+    s->max_active = max_active;
+    *out = s;
+    return FF_OK;
+}
+
+ff_status ff_server_submit(ff_server* s, uint64_t id, const ff_request* req) {
+    if (!s) return FF_ERR_ARG;
+    if (!req || !req->rgb_a || !req->rgb_b || !req->flow_fwd || !req->flow_bwd || !req->mask)
+        return srv_fail(s, FF_ERR_ARG, "request has a NULL buffer");
+    if (req->w < 1 || req->h < 1 || req->w > 8192 || req->h > 8192 || req->pitch_bytes < 3 * req->w)
+        return srv_fail(s, FF_ERR_ARG, "request size or pitch out of range");
+    if (((uintptr_t)req->flow_fwd & 3) || ((uintptr_t)req->flow_bwd & 3) || ((uintptr_t)req->cost_fwd & 3) ||
+        ((uintptr_t)req->cost_bwd & 3))
+        return srv_fail(s, FF_ERR_ARG, "request outputs must be 4-byte aligned");
+    auto q = std::make_unique<Req>();
+    q->id = id;
+    q->io = *req;
+    q->footprint = 2 * pyr_bytes(req->w, req->h, s->cv.n_scales) +
+                   (int64_t)scratch_need(req->w, req->h, s->cv.n_scales);
+    if (q->footprint > s->budget) return srv_fail(s, FF_ERR_ARG, "request larger than the memory budget");
+    s->queued.push_back(std::move(q));
+    return FF_OK;
+}
+
+ff_status ff_server_step(ff_server* s, int* n_active, int* n_queued) {
+    if (!s) return FF_ERR_ARG;
+    if (cudaSetDevice(s->cv.device) != cudaSuccess) return srv_fail(s, FF_ERR_CUDA, "cudaSetDevice failed");
+    ff_status st = admit(s);
+    if (st == FF_OK) st = tick(s);
+    if (n_active) *n_active = (int)(s->active.size() + s->finishing.size());
+    if (n_queued) *n_queued = (int)s->queued.size();
+    return st;
+}
+
+ff_status ff_server_poll(ff_server* s, int wait, uint64_t* ids, int max_ids, int* n_done) {
+    if (!s || (max_ids > 0 && !ids)) return FF_ERR_ARG;
+    int n = 0;
+    auto tick_done = [&](int64_t t) {
+        const RingSlot& r = s->ring[t % kRing];
+        if (r.tick != t) return true;  // the slot was reused, so that tick has completed
+        cudaError_t e = cudaEventQuery(r.done);
+        if (e == cudaErrorNotReady) return false;
+        return true;
+    };
+    for (int pass = 0; pass < 2; pass++) {
+        for (size_t i = 0; i < s->finishing.size() && n < max_ids;) {
+            Req& q = *s->finishing[i];
+            if (tick_done(q.done_tick)) {
+                ids[n++] = q.id;
+                release_req(s, q);
+                s->finishing.erase(s->finishing.begin() + i);
+            } else {
+                i++;
+            }
+        }
+        if (n > 0 || !wait || s->finishing.empty()) break;
+        int64_t first = s->finishing.front()->done_tick;
+        for (auto& q : s->finishing) first = std::min(first, q->done_tick);
+        const RingSlot& r = s->ring[first % kRing];
+        if (r.tick == first && cudaEventSynchronize(r.done) != cudaSuccess)
+            return srv_fail(s, FF_ERR_CUDA, "tick event failed");
+    }
+    cudaError_t e = cudaGetLastError();
+    if (n_done) *n_done = n;
+    if (e != cudaSuccess && e != cudaErrorNotReady) return srv_fail(s, FF_ERR_CUDA, cudaGetErrorString(e));
+    return FF_OK;
+}
+
+ff_status ff_server_stats(ff_server* s, int64_t* ticks, int64_t* launches, int64_t* bytes_in_use) {
+    if (!s) return FF_ERR_ARG;
+    if (ticks) *ticks = s->tick;
+    if (launches) *launches = s->launches;
+    if (bytes_in_use) *bytes_in_use = s->in_use;
+    return FF_OK;
+}
+
+ff_status ff_server_destroy(ff_server* s) {
+    if (!s) return FF_ERR_ARG;
+    cudaSetDevice(s->cv.device);
+    cudaStreamSynchronize(s->cv.stream);
+    for (auto& q : s->active) release_req(s, *q);
+    for (auto& q : s->finishing) release_req(s, *q);
+    for (auto& kv : s->free_scratch) cudaFree(kv.second);
+    for (RingSlot& r : s->ring) {
+        if (r.host) cudaFreeHost(r.host);
+        if (r.dev) cudaFree(r.dev);
+        if (r.done) cudaEventDestroy(r.done);
+    }
+    delete s;
+    return FF_OK;
+}
+
+}  // extern "C"

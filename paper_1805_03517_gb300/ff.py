@@ -41,6 +41,12 @@ class PairJob(ctypes.Structure):
                 ("mask", ctypes.c_void_p)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("rgb_a", ctypes.c_void_p), ("rgb_b", ctypes.c_void_p), ("w", ctypes.c_int), ("h", ctypes.c_int),
+                ("pitch_bytes", ctypes.c_int), ("flow_fwd", ctypes.c_void_p), ("flow_bwd", ctypes.c_void_p),
+                ("cost_fwd", ctypes.c_void_p), ("cost_bwd", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
                 ("plans_built", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64)]
@@ -72,8 +78,8 @@ def lib():
         "ff_match_pair": (S, [vp, vp, vp, i, vp, vp]),
         "ff_match_batch": (S, [vp, i, ctypes.POINTER(PairJob)]),
         "ff_autotune": (S, [vp, i, ctypes.POINTER(PairJob), i]),
-        "ff_set_tuning": (S, [vp, i, i, i, i]),
-        "ff_get_tuning": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "ff_set_tuning": (S, [vp, i, i, i, i, i]),
+        "ff_get_tuning": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "ff_consistency": (S, [vp, vp, vp, i, i, i, vp]),
         "ff_pyr_release": (S, [vp, vp]),
         "ff_pyr_level_dims": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
@@ -85,6 +91,12 @@ def lib():
         "ff_profile_read": (S, [vp, ctypes.POINTER(ctypes.c_double), i64p]),
         "ff_work_counts": (S, [vp, i, i, i64p, i64p]),
         "ff_match_pair_noalloc": (S, [vp, vp, vp, i, vp, vp]),
+        "ff_server_create": (S, [vp, ctypes.c_int64, i, ctypes.POINTER(vp)]),
+        "ff_server_submit": (S, [vp, ctypes.c_uint64, ctypes.POINTER(Request)]),
+        "ff_server_step": (S, [vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "ff_server_poll": (S, [vp, i, ctypes.POINTER(ctypes.c_uint64), i, ctypes.POINTER(i)]),
+        "ff_server_stats": (S, [vp, i64p, i64p, i64p]),
+        "ff_server_destroy": (S, [vp]),
         "ff_destroy": (S, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -137,14 +149,18 @@ def ff_autotune(ctx, jobs, reps: int = 3):
     _check(ctx, lib().ff_autotune(ctx, len(jobs), arr, reps))
 
 
-def ff_set_tuning(ctx, level: int, tile_w: int, tile_h: int, iters_per_launch: int):
-    _check(ctx, lib().ff_set_tuning(ctx, level, tile_w, tile_h, iters_per_launch))
+def ff_set_tuning(ctx, level: int, tile_w: int, tile_h: int, iters_per_launch: int, threads: int = 256):
+    if (tile_w, tile_h, iters_per_launch) == (0, 0, 0):
+        threads = 0
+    _check(ctx, lib().ff_set_tuning(ctx, level, tile_w, tile_h, iters_per_launch, threads))
 
 
 def ff_get_tuning(ctx, level: int):
-    tw, th, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(ctx, lib().ff_get_tuning(ctx, level, ctypes.byref(tw), ctypes.byref(th), ctypes.byref(k)))
-    return tw.value, th.value, k.value
+    """(tile width, tile height, iterations per launch, threads per CTA) in force for `level`."""
+    tw, th, k, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().ff_get_tuning(ctx, level, ctypes.byref(tw), ctypes.byref(th), ctypes.byref(k),
+                                    ctypes.byref(n)))
+    return tw.value, th.value, k.value, n.value
 
 
 def ff_consistency(ctx, fwd: int, bwd: int, w: int, h: int, eps: int, mask_dev: int):
@@ -199,6 +215,39 @@ def ff_work_counts(ctx, w: int, h: int):
 def ff_match_pair_noalloc(ctx, a, b, dir: int, flow_dev: int, cost_dev: int | None):
     """ff_match_pair for callers that must not allocate device memory (fixed file-scope scratch)."""
     _check(ctx, lib().ff_match_pair_noalloc(ctx, a, b, dir, flow_dev, cost_dev or None))
+
+
+def ff_server_create(ctx, mem_budget_bytes: int, max_active: int):
+    srv = ctypes.c_void_p()
+    _check(ctx, lib().ff_server_create(ctx, mem_budget_bytes, max_active, ctypes.byref(srv)))
+    return srv
+
+
+def ff_server_submit(ctx, srv, rid: int, req: Request):
+    _check(ctx, lib().ff_server_submit(srv, rid, ctypes.byref(req)))
+
+
+def ff_server_step(ctx, srv):
+    a, q = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().ff_server_step(srv, ctypes.byref(a), ctypes.byref(q)))
+    return a.value, q.value
+
+
+def ff_server_poll(ctx, srv, wait: bool = False, max_ids: int = 256):
+    ids = (ctypes.c_uint64 * max_ids)()
+    n = ctypes.c_int()
+    _check(ctx, lib().ff_server_poll(srv, 1 if wait else 0, ids, max_ids, ctypes.byref(n)))
+    return list(ids[: n.value])
+
+
+def ff_server_stats(ctx, srv):
+    t, l, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, lib().ff_server_stats(srv, ctypes.byref(t), ctypes.byref(l), ctypes.byref(b)))
+    return {"ticks": t.value, "launches": l.value, "bytes_in_use": b.value}
+
+
+def ff_server_destroy(srv):
+    _check(None, lib().ff_server_destroy(srv))
 
 
 def ff_destroy(ctx):
@@ -331,3 +380,39 @@ class _DevView:
     def __init__(self, ptr: int, nbytes: int):
         self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3,
                                          "strides": None}
+
+
+class Server:
+    """Continuous-batching server on a Matcher's context (requests reference caller-owned device tensors)."""
+
+    def __init__(self, matcher: Matcher, mem_budget_bytes: int = 60 << 30, max_active: int = 256):
+        self.m = matcher
+        self.srv = ff_server_create(matcher.ctx, mem_budget_bytes, max_active)
+        self.keep = {}
+
+    def submit(self, rid: int, img_a, img_b, out: dict):
+        """img_a/img_b: uint8 [h][w][3] CUDA tensors; out: dict with flow_fwd, flow_bwd, mask (and optionally
+        cost_fwd, cost_bwd) CUDA tensors.  All must stay alive until `rid` is reported by poll()."""
+        h, w = int(img_a.shape[0]), int(img_a.shape[1])
+        req = Request(img_a.data_ptr(), img_b.data_ptr(), w, h, img_a.stride(0), out["flow_fwd"].data_ptr(),
+                      out["flow_bwd"].data_ptr(), out["cost_fwd"].data_ptr() if "cost_fwd" in out else None,
+                      out["cost_bwd"].data_ptr() if "cost_bwd" in out else None, out["mask"].data_ptr())
+        ff_server_submit(self.m.ctx, self.srv, rid, req)
+        self.keep[rid] = (img_a, img_b, out)
+
+    def step(self):
+        return ff_server_step(self.m.ctx, self.srv)
+
+    def poll(self, wait=False):
+        ids = ff_server_poll(self.m.ctx, self.srv, wait)
+        for i in ids:
+            self.keep.pop(i, None)
+        return ids
+
+    def stats(self):
+        return ff_server_stats(self.m.ctx, self.srv)
+
+    def close(self):
+        if self.srv:
+            ff_server_destroy(self.srv)
+            self.srv = None

@@ -1,0 +1,114 @@
+"""Continuous batching: requests of different sizes are admitted while others are on the GPU, share merged
+launches with them, and each result is bit-identical to matching that pair alone (tolerance zero: the whole
+stage is integer).  One request of each size is also checked against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1805_03517_gb300 import configs
+from tests import gpu_helpers as G
+from tests import oracle_pins as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+NAMES = ("flow_fwd", "flow_bwd", "cost_fwd", "cost_bwd", "mask")
+
+
+@pytest.fixture(scope="module")
+def ffm():
+    from paper_1805_03517_gb300 import build, ff
+
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ff
+
+
+def _pair(i, h, w):
+    a = P.smooth_texture(1000 + i, h, w)
+    b = P.shifted(a, (i % 7) - 3, (i % 5) - 2, 2000 + i)
+    b[h // 3:h // 2, w // 4:w // 2] = P.smooth_texture(3000 + i, h // 2 - h // 3, w // 2 - w // 4)
+    return a, b
+
+
+def _outputs(M, h, w):
+    with torch.cuda.stream(M.stream):
+        return {"flow_fwd": torch.full((h, w, 2), -9, dtype=torch.int16, device="cuda"),
+                "flow_bwd": torch.full((h, w, 2), -9, dtype=torch.int16, device="cuda"),
+                "cost_fwd": torch.full((h, w), -9, dtype=torch.int32, device="cuda"),
+                "cost_bwd": torch.full((h, w), -9, dtype=torch.int32, device="cuda"),
+                "mask": torch.full((h, w), 9, dtype=torch.uint8, device="cuda")}
+
+
+def test_served_mix_equals_alone(ffm):
+    prm = configs.MatchParams(n_scales=4, iters=3, eps=1)
+    M = ffm.Matcher(prm, 0)
+    sizes = [(96, 128), (60, 90), (120, 200), (96, 128), (33, 47), (120, 200), (60, 90), (80, 80)]
+    pairs = [_pair(i, h, w) for i, (h, w) in enumerate(sizes)]
+    dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in pairs]
+    torch.cuda.synchronize()
+    # alone: each pair through ff_match_batch by itself
+    alone = []
+    for da, db in dev:
+        pa, pb = M.features(da), M.features(db)
+        o = M.match_batch([(pa, pb)])[0]
+        M.sync()
+        alone.append(tuple(o[k].cpu().numpy() for k in NAMES))
+        M.release(pa)
+        M.release(pb)
+    # served: staggered arrivals, later requests join while earlier ones are mid-flight
+    S = ffm.Server(M, mem_budget_bytes=1 << 30, max_active=5)
+    outs, done, order = {}, [], []
+    nxt = 0
+    for step in range(400):
+        if nxt < len(dev) and step % 3 == 0:
+            h, w = sizes[nxt]
+            outs[nxt] = _outputs(M, h, w)
+            S.submit(nxt, dev[nxt][0], dev[nxt][1], outs[nxt])
+            nxt += 1
+        n_active, n_queued = S.step()
+        done += S.poll()
+        if nxt == len(dev) and len(done) == len(dev):
+            break
+    while len(done) < len(dev):
+        S.step()
+        done += S.poll(wait=True)
+    assert sorted(done) == list(range(len(dev)))
+    st = S.stats()
+    assert st["ticks"] > 0 and st["bytes_in_use"] == 0
+    M.sync()
+    for i in range(len(dev)):
+        G.assert_same(tuple(outs[i][k].cpu().numpy() for k in NAMES), alone[i])
+    o = oracle.default()
+    for i in (0, 1, 2, 4):
+        a, b = pairs[i]
+        G.assert_same(alone[i], o.match_bidir(a, b, G.oracle_params(prm)))
+    S.close()
+    M.close()
+
+
+def test_server_rejects_and_bounds(ffm):
+    prm = configs.MatchParams(n_scales=3, iters=2, eps=1)
+    M = ffm.Matcher(prm, 0)
+    S = ffm.Server(M, mem_budget_bytes=4 << 20, max_active=2)
+    big = torch.zeros((600, 800, 3), dtype=torch.uint8, device="cuda")
+    out = _outputs(M, 600, 800)
+    with pytest.raises(ffm.FFError) as e:  # can never fit the 4 MiB budget
+        S.submit(1, big, big, out)
+    assert e.value.status == ffm.FF_ERR_ARG
+    small = [_pair(50 + i, 40, 48) for i in range(4)]
+    dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in small]
+    outs = [_outputs(M, 40, 48) for _ in dev]
+    for i, (da, db) in enumerate(dev):
+        S.submit(10 + i, da, db, outs[i])
+    n_active, n_queued = S.step()
+    assert n_active <= 2 and n_active + n_queued == 4
+    done = []
+    while len(done) < 4:
+        S.step()
+        done += S.poll(wait=True)
+    assert sorted(done) == [10, 11, 12, 13]
+    S.close()
+    M.close()
