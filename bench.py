@@ -376,7 +376,7 @@ def main():
     # per-phase device time (profiling context: same kernels and launch shapes, phases bracketed by events)
     P = ff.Matcher(prm, local_rank, stream)
     for lvl, cfg in enumerate(tuning):
-        ff.ff_set_tuning(P.ctx, lvl, *cfg)
+        ff.ff_set_tuning(P.ctx, lvl, cfg)
     ff.ff_profile_enable(P.ctx, True)
     prof_outs = None
 

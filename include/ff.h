@@ -120,15 +120,21 @@ FF_API ff_status ff_match_batch(ff_ctx* ctx, int n, const ff_pair_job* jobs);
  * This is a property of the GB300 implementation (the paper has no counterpart). */
 FF_API ff_status ff_autotune(ff_ctx* ctx, int n, const ff_pair_job* jobs, int reps);
 
-/* Impose the propagation configuration of one level (tile width and height in pixels, iterations fused per
- * launch, threads per CTA: 128, 256 or 512) on every later plan of this context, overriding the autotuner; all
- * zeros removes the override.  FF_ERR_ARG if the tile with its halo does not fit in shared memory.  Cached
- * plans are dropped. */
-FF_API ff_status ff_set_tuning(ff_ctx* ctx, int level, int tile_w, int tile_h, int iters_per_launch, int threads);
+/* Propagation launch configuration of one level: tile interior (pixels), iterations fused per launch, threads
+ * per CTA (128, 256 or 512), and whether the random candidate is fetched together with the neighbour candidates
+ * (speculate = 1; refetched when a neighbour was taken).  None of these changes any result. */
+typedef struct {
+    int tile_w, tile_h, iters_per_launch, threads, speculate;
+} ff_tuning;
 
-/* The configuration in force for `level`: the override if set, else the autotuner's choice (tile width,
- * height, iterations per launch, threads per CTA); FF_ERR_ARG if neither exists. */
-FF_API ff_status ff_get_tuning(ff_ctx* ctx, int level, int* tile_w, int* tile_h, int* iters_per_launch, int* threads);
+/* Impose the configuration of one level on every later plan of this context, overriding the autotuner;
+ * NULL removes the override.  FF_ERR_ARG if the tile with its halo does not fit in shared memory or a field is
+ * out of range.  Cached plans are dropped. */
+FF_API ff_status ff_set_tuning(ff_ctx* ctx, int level, const ff_tuning* cfg);
+
+/* The configuration in force for `level`: the override if set, else the autotuner's choice; FF_ERR_ARG if
+ * neither exists. */
+FF_API ff_status ff_get_tuning(ff_ctx* ctx, int level, ff_tuning* out);
 
 /* Forward/backward consistency check (Sec. 3.1, eps as in Table 3): mask[p] = 1 iff q = p + fwd(p) lies in
  * the image and (fwd_x(p) + bwd_x(q))^2 + (fwd_y(p) + bwd_y(q))^2 <= eps^2.  All pointers are device

@@ -104,15 +104,17 @@ struct Plan {
 };
 
 struct TileCfg {
-    int tw, th, k, threads;  // tile interior, iterations fused per launch, CTA size
+    int tw, th, k, threads, spec;  // tile interior, iterations fused per launch, CTA size, speculative random
 };
 
 // Candidate propagation configurations (tile shape, fused iterations, CTA size) the autotuner times per level.
-const TileCfg kCands[] = {{64, 32, 1, 256}, {32, 32, 1, 256}, {32, 16, 1, 256}, {16, 16, 1, 256},
-                          {32, 16, 2, 256}, {16, 16, 2, 256}, {16, 8, 2, 256},  {16, 8, 3, 256},
-                          {8, 8, 3, 256},   {8, 8, 6, 256},   {32, 16, 1, 128}, {16, 16, 1, 128},
-                          {16, 8, 2, 128},  {8, 8, 3, 128},   {64, 32, 1, 512}, {32, 32, 1, 512},
-                          {32, 16, 2, 512}, {16, 16, 2, 512}, {16, 16, 3, 512}, {24, 24, 1, 512}};
+const TileCfg kCands[] = {
+    {64, 32, 1, 256, 0}, {32, 32, 1, 256, 0}, {32, 16, 1, 256, 0}, {16, 16, 1, 256, 0}, {32, 16, 2, 256, 0},
+    {16, 16, 2, 256, 0}, {16, 8, 2, 256, 0},  {16, 8, 3, 256, 0},  {8, 8, 3, 256, 0},   {8, 8, 6, 256, 0},
+    {32, 16, 1, 128, 0}, {16, 16, 1, 128, 0}, {16, 8, 2, 128, 0},  {8, 8, 3, 128, 0},   {32, 32, 1, 512, 0},
+    {32, 16, 2, 512, 0}, {16, 16, 2, 512, 0}, {24, 24, 1, 512, 0}, {32, 16, 1, 128, 1}, {16, 16, 1, 128, 1},
+    {16, 8, 2, 128, 1},  {8, 8, 3, 128, 1},   {32, 16, 1, 256, 1}, {16, 16, 1, 256, 1}, {16, 8, 2, 256, 1},
+    {8, 8, 3, 256, 1},   {32, 32, 1, 512, 1}, {16, 16, 2, 512, 1}, {24, 24, 1, 512, 1}};
 constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
 
 // Tuning key: level index, level size of the first job, number of directions in the launch, iterations.
@@ -206,10 +208,10 @@ bool cfg_fits(const TileCfg& t) { return prop_smem_bytes(t.tw, t.th, t.k) <= kMa
 // launch when the level fills the GPU, otherwise small tiles with fused iterations (idle SMs absorb the halo).
 TileCfg default_cfg(const ff_ctx* c, int64_t level_pix_all, int T) {
     const int64_t slots = (int64_t)c->n_sms * 2;
-    if (level_pix_all / (32 * 32) >= 2 * slots) return {32, 32, 1, 256};
-    if (level_pix_all / (32 * 16) >= 2 * slots) return {32, 16, 1, 256};
-    if (level_pix_all / (16 * 16) >= slots) return {16, 16, std::min(2, T), 256};
-    return {8, 8, std::min(3, T), 256};
+    if (level_pix_all / (32 * 32) >= 2 * slots) return {32, 32, 1, 256, 0};
+    if (level_pix_all / (32 * 16) >= 2 * slots) return {32, 16, 1, 256, 0};
+    if (level_pix_all / (16 * 16) >= slots) return {16, 16, std::min(2, T), 256, 1};
+    return {8, 8, std::min(3, T), 256, 1};
 }
 
 ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
@@ -415,7 +417,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             tc = it != c->tuned.end() ? it->second : default_cfg(c, level_pix, T);
         }
         const size_t smem = prop_smem_bytes(tc.tw, tc.th, tc.k);
-        const int blocks = prop_blocks_per_sm(smem, tc.threads) * c->n_sms;
+        const int blocks = prop_blocks_per_sm(smem, tc.threads, tc.spec != 0) * c->n_sms;
         for (int t0 = 0; t0 < T; t0 += tc.k) {
             int n_iter = std::min(tc.k, T - t0);
             bool last = t0 + n_iter == T;
@@ -427,6 +429,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             l.prop.th = tc.th;
             l.prop.max_iter = n_iter;
             l.prop.threads = tc.threads;
+            l.prop.spec = tc.spec;
             size_t oq = queue.size();
             std::vector<int> pidx(nj), ntiles(nj);
             for (int j = 0; j < nj; j++) {
@@ -721,7 +724,7 @@ TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs
         auto it = c->tuned.find(TuneKey{level, w, h, n_dirs, T});
         tc = it != c->tuned.end() ? it->second : default_cfg(c, level_pix_all, T);
     }
-    return {tc.tw, tc.th, std::min(tc.k, T), tc.threads};
+    return {tc.tw, tc.th, std::min(tc.k, T), tc.threads, tc.spec};
 }
 
 int ctx_set_error(ff_ctx* c, int status, const char* msg) {
@@ -931,15 +934,17 @@ ff_status ff_autotune(ff_ctx* c, int n, const ff_pair_job* jobs, int reps) {
     return autotune(c, dj, cj, reps);
 }
 
-ff_status ff_set_tuning(ff_ctx* c, int level, int tile_w, int tile_h, int iters_per_launch, int threads) {
+ff_status ff_set_tuning(ff_ctx* c, int level, const ff_tuning* t) {
     if (!c) return FF_ERR_ARG;
     if (level < 0 || level >= kMaxLevels) return fail(c, FF_ERR_ARG, "level %d outside 0..%d", level, kMaxLevels - 1);
-    TileCfg cfg{tile_w, tile_h, iters_per_launch, threads};
-    if (tile_w != 0 || tile_h != 0 || iters_per_launch != 0 || threads != 0) {
-        if (tile_w < 1 || tile_h < 1 || tile_w > 1024 || tile_h > 1024 || iters_per_launch < 1 ||
-            iters_per_launch > 255 || !prop_threads_ok(threads) || !cfg_fits(cfg))
-            return fail(c, FF_ERR_ARG, "configuration %dx%d, %d iterations, %d threads is not valid", tile_w,
-                        tile_h, iters_per_launch, threads);
+    TileCfg cfg{0, 0, 0, 0, 0};
+    if (t) {
+        cfg = TileCfg{t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate};
+        if (t->tile_w < 1 || t->tile_h < 1 || t->tile_w > 1024 || t->tile_h > 1024 || t->iters_per_launch < 1 ||
+            t->iters_per_launch > 255 || !prop_threads_ok(t->threads) || (t->speculate != 0 && t->speculate != 1) ||
+            !cfg_fits(cfg))
+            return fail(c, FF_ERR_ARG, "configuration %dx%d, %d iterations, %d threads, speculate %d is not valid",
+                        t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate);
     }
     FF_CUDA(c, cudaSetDevice(c->device));
     ff_status s = drop_plans(c);
@@ -948,24 +953,21 @@ ff_status ff_set_tuning(ff_ctx* c, int level, int tile_w, int tile_h, int iters_
     return FF_OK;
 }
 
-ff_status ff_get_tuning(ff_ctx* c, int level, int* tile_w, int* tile_h, int* iters_per_launch, int* threads) {
-    if (!c || level < 0 || level >= kMaxLevels) return FF_ERR_ARG;
+ff_status ff_get_tuning(ff_ctx* c, int level, ff_tuning* out) {
+    if (!c || !out || level < 0 || level >= kMaxLevels) return FF_ERR_ARG;
+    const TileCfg* f = nullptr;
     if (c->forced[level].tw > 0) {
-        if (tile_w) *tile_w = c->forced[level].tw;
-        if (tile_h) *tile_h = c->forced[level].th;
-        if (iters_per_launch) *iters_per_launch = c->forced[level].k;
-        if (threads) *threads = c->forced[level].threads;
-        return FF_OK;
+        f = &c->forced[level];
+    } else {
+        for (auto& kv : c->tuned)
+            if (std::get<0>(kv.first) == level) {
+                f = &kv.second;
+                break;
+            }
     }
-    for (auto& kv : c->tuned)
-        if (std::get<0>(kv.first) == level) {
-            if (tile_w) *tile_w = kv.second.tw;
-            if (tile_h) *tile_h = kv.second.th;
-            if (iters_per_launch) *iters_per_launch = kv.second.k;
-            if (threads) *threads = kv.second.threads;
-            return FF_OK;
-        }
-    return fail(c, FF_ERR_ARG, "level %d has not been tuned", level);
+    if (!f) return fail(c, FF_ERR_ARG, "level %d has not been tuned", level);
+    *out = ff_tuning{f->tw, f->th, f->k, f->threads, f->spec};
+    return FF_OK;
 }
 
 ff_status ff_consistency(ff_ctx* c, const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, uint8_t* mask_dev) {

@@ -95,12 +95,13 @@ struct PropLaunch {
     int tw, th;      // tile interior
     int max_iter;    // largest n_iter of the launch (sizes the shared-memory halo)
     int threads;     // CTA size: 128, 256 or 512
+    int spec;        // 1: load the random candidate together with the neighbour candidates
 };
 constexpr size_t kMaxPropSmem = 200 * 1024;
 size_t prop_smem_bytes(int tw, int th, int n_iter);
 cudaError_t init_kernel_attributes();  // once per device, before the first launch
 bool prop_threads_ok(int threads);
-int prop_blocks_per_sm(size_t smem, int threads);  // resident CTAs per SM of the propagation kernel
+int prop_blocks_per_sm(size_t smem, int threads, bool spec);  // resident CTAs per SM of the propagation kernel
 // queue_dev[i] = (problem index, tile index); counter_dev must be zero when the launch starts
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st);
@@ -129,7 +130,7 @@ struct CtxView {
     uint32_t seed;
 };
 struct TileChoice {
-    int tw, th, k, threads;
+    int tw, th, k, threads, spec;
 };
 
 // ---------------------------------------------------------------------------------------------------------

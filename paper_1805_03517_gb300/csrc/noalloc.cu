@@ -129,7 +129,7 @@ extern "C" ff_status ff_match_pair_noalloc(ff_ctx* c, const ff_pyr* a, const ff_
         int tiles_x = (A.ws[s] + tc[s].tw - 1) / tc[s].tw;
         sa.ntiles[s] = tiles_x * ((A.hs[s] + tc[s].th - 1) / tc[s].th);
         size_t smem = prop_smem_bytes(tc[s].tw, tc[s].th, tc[s].k);
-        grid[s] = std::min(sa.ntiles[s], prop_blocks_per_sm(smem, tc[s].threads) * cv.n_sms);
+        grid[s] = std::min(sa.ntiles[s], prop_blocks_per_sm(smem, tc[s].threads, tc[s].spec != 0) * cv.n_sms);
         PropProblem& p = sa.base[s];
         p.fa = A.feat[s];
         p.fb = B.feat[s];
@@ -207,7 +207,7 @@ extern "C" ff_status ff_match_pair_noalloc(ff_ctx* c, const ff_pyr* a, const ff_
         launch_handover(sa.ho_dst + s, 1, (int64_t)A.ws[s] * A.hs[s], st);
         for (int j = 0; j < sa.n_launch[s]; j++) {
             const int li = sa.first_launch[s] + j;
-            PropLaunch pl{tc[s].tw, tc[s].th, std::min(tc[s].k, T - j * tc[s].k), tc[s].threads};
+            PropLaunch pl{tc[s].tw, tc[s].th, std::min(tc[s].k, T - j * tc[s].k), tc[s].threads, tc[s].spec};
             launch_propagate(sa.props + li, sa.queue[s], sa.ntiles[s], counters + li, grid[s], pl, st);
         }
     }

@@ -146,7 +146,11 @@ __device__ __forceinline__ bool region_pixel(int i, int HW, int rx0, int ry0, in
     return x < rx1;
 }
 
-// One half-sweep with one thread per pixel (the whole 96-B descriptor per thread).
+// One half-sweep with one thread per pixel (the whole 96-B descriptor per thread).  With SPEC the random
+// candidate of directions 1..3 is fetched together with the neighbour candidates, assuming the neighbours will
+// not change the pixel's flow; if one of them is taken, the random candidate is fetched again from the new
+// flow.  Either way the candidate evaluated is the one the schedule defines, so results are identical.
+template <bool SPEC>
 __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& G, uint32_t* sflow, int32_t* scost,
                                           int j, int rem, uint32_t k1) {
     const int w = P.w, h = P.h;
@@ -173,11 +177,26 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
         const bool e1 = v1 && f1 != cur && in_level(x + flow_x(f1), y + flow_y(f1), w, h);
         const bool e2 = v2 && f2 != cur && !(v1 && f2 == f1) && in_level(x + flow_x(f2), y + flow_y(f2), w, h);
         if (!(e1 || e2 || d >= 1)) continue;
-        // issue every independent load (own descriptor, both neighbour candidates) before any compute
+        int ox = 0, oy = 0;
+        if (d >= 1) {
+            const uint32_t k2 = mix32(k1 ^ ((uint32_t)y * 65536u + (uint32_t)x));
+            ox = (int)(mix32(k2 ^ (uint32_t)(2 * d)) % span) - R;
+            oy = (int)(mix32(k2 ^ (uint32_t)(2 * d + 1)) % span) - R;
+        }
+        const bool rnd = ox != 0 || oy != 0;
+        const uint32_t cur0 = cur;
+        // issue every independent load (own descriptor, neighbour candidates, speculative random) before compute
         uint32_t a[24], b1[24], b2[24];
+        uint32_t b3[SPEC ? 24 : 1];
+        bool e3s = false;
         load_desc(P.fa, y * w + x, a);
         if (e1) load_desc(P.fb, (y + flow_y(f1)) * w + x + flow_x(f1), b1);
         if (e2) load_desc(P.fb, (y + flow_y(f2)) * w + x + flow_x(f2), b2);
+        if constexpr (SPEC) {
+            const int sx = flow_x(cur) + ox, sy = flow_y(cur) + oy;
+            e3s = rnd && in_level(x + sx, y + sy, w, h);
+            if (e3s) load_desc(P.fb, (y + sy) * w + x + sx, b3);
+        }
         bias_desc(a);
         if (e1) {
             int s1 = sad_biased(a, b1);
@@ -187,25 +206,32 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
             int s2 = sad_biased(a, b2);
             if (s2 < c) { cur = f2; c = s2; }
         }
-        if (d >= 1) {
-            const uint32_t k2 = mix32(k1 ^ ((uint32_t)y * 65536u + (uint32_t)x));
-            const int ox = (int)(mix32(k2 ^ (uint32_t)(2 * d)) % span) - R;
-            const int oy = (int)(mix32(k2 ^ (uint32_t)(2 * d + 1)) % span) - R;
-            if (ox != 0 || oy != 0) {
-                const int fx = flow_x(cur) + ox, fy = flow_y(cur) + oy;
-                if (in_level(x + fx, y + fy, w, h)) {
+        if (rnd) {
+            const int fx = flow_x(cur) + ox, fy = flow_y(cur) + oy;
+            if (in_level(x + fx, y + fy, w, h)) {
+                int s3;
+                if constexpr (SPEC) {
+                    if (cur == cur0) {
+                        s3 = sad_biased(a, b3);  // e3s holds: same target as speculated
+                    } else {
+                        load_desc(P.fb, (y + fy) * w + x + fx, b1);
+                        s3 = sad_biased(a, b1);
+                    }
+                } else {
                     load_desc(P.fb, (y + fy) * w + x + fx, b1);
-                    int s3 = sad_biased(a, b1);
-                    if (s3 < c) { cur = pack_flow(fx, fy); c = s3; }
+                    s3 = sad_biased(a, b1);
                 }
+                if (s3 < c) { cur = pack_flow(fx, fy); c = s3; }
             }
         }
+        (void)e3s;
         sflow[sidx] = cur;
         scost[sidx] = c;
     }
 }
 
 // One tile of one problem: load the tile and its halo, run n_iter iterations in shared memory, write the tile.
+template <bool SPEC>
 __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, const PropLaunch& L, uint32_t* smem) {
     const int w = P.w, h = P.h;
     TileGeom G;
@@ -233,7 +259,7 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
         const int rem = kHaloPerIter * (P.n_iter - 1 - it);
         const uint32_t k1 = mix32(P.seed ^ mix32((uint32_t)P.dir * 65536u + (uint32_t)P.level * 256u + (uint32_t)t));
         for (int j = 0; j < 8; j++) {
-            halfsweep(P, G, sflow, scost, j, rem, k1);
+            halfsweep<SPEC>(P, G, sflow, scost, j, rem, k1);
             __syncthreads();
         }
     }
@@ -249,9 +275,9 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
 
 // Persistent launch: each CTA takes tiles from the launch's queue (an atomic counter, zeroed before the launch)
 // until it is empty, so the last wave has no idle tail.  queue[i] = (problem index, tile index in problem).
-// Instantiated for 128, 256 and 512 threads (at most 128 registers per thread in every case).
-template <int THREADS>
-__global__ __launch_bounds__(THREADS, 512 / THREADS) void k_propagate(
+// Instantiated for 128, 256 and 512 threads, with and without speculative random-candidate loads.
+template <int THREADS, bool SPEC>
+__global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate(
     const PropProblem* __restrict__ probs, const int2* __restrict__ queue, int n_tiles, int* __restrict__ counter,
     PropLaunch L) {
     extern __shared__ uint32_t smem[];
@@ -262,28 +288,33 @@ __global__ __launch_bounds__(THREADS, 512 / THREADS) void k_propagate(
         const int q = s_next;
         if (q >= n_tiles) return;
         const int2 e = queue[q];
-        propagate_tile(probs[e.x], e.y, L, smem);
+        propagate_tile<SPEC>(probs[e.x], e.y, L, smem);
         __syncthreads();
     }
 }
 
+using PropKernel = void (*)(const PropProblem*, const int2*, int, int*, PropLaunch);
+
+PropKernel prop_kernel(int threads, bool spec) {
+    if (spec) return threads == 128 ? k_propagate<128, true> : threads == 512 ? k_propagate<512, true> : k_propagate<256, true>;
+    return threads == 128 ? k_propagate<128, false> : threads == 512 ? k_propagate<512, false> : k_propagate<256, false>;
+}
+
 cudaError_t init_kernel_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(k_propagate<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_propagate<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_propagate<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
-    return e;
+    for (int t : {128, 256, 512})
+        for (bool sp : {false, true}) {
+            cudaError_t e = cudaFuncSetAttribute(prop_kernel(t, sp), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kMaxPropSmem);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
 }
 
 bool prop_threads_ok(int threads) { return threads == 128 || threads == 256 || threads == 512; }
 
-int prop_blocks_per_sm(size_t smem, int threads) {
+int prop_blocks_per_sm(size_t smem, int threads, bool spec) {
     int n = 0;
-    cudaError_t e = threads == 128   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<128>, 128, smem)
-                    : threads == 512 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<512>, 512, smem)
-                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_propagate<256>, 256, smem);
-    if (e != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prop_kernel(threads, spec), threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -293,12 +324,7 @@ int prop_blocks_per_sm(size_t smem, int threads) {
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st) {
     size_t smem = prop_smem_bytes(L.tw, L.th, L.max_iter);
-    if (L.threads == 128)
-        k_propagate<128><<<grid, 128, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
-    else if (L.threads == 512)
-        k_propagate<512><<<grid, 512, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
-    else
-        k_propagate<256><<<grid, 256, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
+    prop_kernel(L.threads, L.spec != 0)<<<grid, L.threads, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
 }
 
 // ---------------------------------------------------------------------------------------------------------

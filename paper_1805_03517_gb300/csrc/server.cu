@@ -205,9 +205,9 @@ ff_status admit(ff_server* s) {
 }
 
 struct PropGroupKey {
-    int tw, th, n_iter, threads;
+    int tw, th, n_iter, threads, spec;
     bool operator<(const PropGroupKey& o) const {
-        return std::tie(tw, th, n_iter, threads) < std::tie(o.tw, o.th, o.n_iter, o.threads);
+        return std::tie(tw, th, n_iter, threads, spec) < std::tie(o.tw, o.th, o.n_iter, o.threads, o.spec);
     }
 };
 
@@ -278,7 +278,7 @@ ff_status tick(ff_server* s) {
         const TileChoice c = q.cfg[sl];
         const int t0 = q.chunk * c.k, n_iter = std::min(c.k, T - t0);
         const bool last = sl == 0 && q.chunk == q.n_chunks[sl] - 1;
-        auto& grp = groups[PropGroupKey{c.tw, c.th, n_iter, c.threads}];
+        auto& grp = groups[PropGroupKey{c.tw, c.th, n_iter, c.threads, c.spec}];
         for (int d = 0; d < 2; d++) {
             const PyrView& X = d == 0 ? q.A : q.B;
             const PyrView& Y = d == 0 ? q.B : q.A;
@@ -361,8 +361,8 @@ ff_status tick(ff_server* s) {
         for (auto& pr : kv.second) hp[pi++] = pr.first;
         const size_t smem = prop_smem_bytes(k.tw, k.th, k.n_iter);
         const int nq = (int)(qi - q0);
-        pls.push_back({PropLaunch{k.tw, k.th, k.n_iter, k.threads}, q0, nq,
-                       std::min(nq, prop_blocks_per_sm(smem, k.threads) * s->cv.n_sms)});
+        pls.push_back({PropLaunch{k.tw, k.th, k.n_iter, k.threads, k.spec}, q0, nq,
+                       std::min(nq, prop_blocks_per_sm(smem, k.threads, k.spec != 0) * s->cv.n_sms)});
     }
     cudaStream_t stm = s->cv.stream;
     if (cudaMemcpyAsync(r.dev, r.host, bytes, cudaMemcpyHostToDevice, stm) != cudaSuccess)

@@ -47,6 +47,11 @@ class Request(ctypes.Structure):
                 ("cost_fwd", ctypes.c_void_p), ("cost_bwd", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("iters_per_launch", ctypes.c_int),
+                ("threads", ctypes.c_int), ("speculate", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
                 ("plans_built", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64)]
@@ -78,8 +83,8 @@ def lib():
         "ff_match_pair": (S, [vp, vp, vp, i, vp, vp]),
         "ff_match_batch": (S, [vp, i, ctypes.POINTER(PairJob)]),
         "ff_autotune": (S, [vp, i, ctypes.POINTER(PairJob), i]),
-        "ff_set_tuning": (S, [vp, i, i, i, i, i]),
-        "ff_get_tuning": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "ff_set_tuning": (S, [vp, i, ctypes.POINTER(Tuning)]),
+        "ff_get_tuning": (S, [vp, i, ctypes.POINTER(Tuning)]),
         "ff_consistency": (S, [vp, vp, vp, i, i, i, vp]),
         "ff_pyr_release": (S, [vp, vp]),
         "ff_pyr_level_dims": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
@@ -149,18 +154,20 @@ def ff_autotune(ctx, jobs, reps: int = 3):
     _check(ctx, lib().ff_autotune(ctx, len(jobs), arr, reps))
 
 
-def ff_set_tuning(ctx, level: int, tile_w: int, tile_h: int, iters_per_launch: int, threads: int = 256):
-    if (tile_w, tile_h, iters_per_launch) == (0, 0, 0):
-        threads = 0
-    _check(ctx, lib().ff_set_tuning(ctx, level, tile_w, tile_h, iters_per_launch, threads))
+def ff_set_tuning(ctx, level: int, cfg):
+    """cfg: (tile_w, tile_h, iters_per_launch, threads, speculate) or None to remove the override."""
+    if cfg is None:
+        _check(ctx, lib().ff_set_tuning(ctx, level, None))
+        return
+    t = Tuning(*cfg) if len(cfg) == 5 else Tuning(*cfg, *((256, 0)[len(cfg) - 3:]))
+    _check(ctx, lib().ff_set_tuning(ctx, level, ctypes.byref(t)))
 
 
 def ff_get_tuning(ctx, level: int):
-    """(tile width, tile height, iterations per launch, threads per CTA) in force for `level`."""
-    tw, th, k, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(ctx, lib().ff_get_tuning(ctx, level, ctypes.byref(tw), ctypes.byref(th), ctypes.byref(k),
-                                    ctypes.byref(n)))
-    return tw.value, th.value, k.value, n.value
+    """(tile_w, tile_h, iters_per_launch, threads, speculate) in force for `level`."""
+    t = Tuning()
+    _check(ctx, lib().ff_get_tuning(ctx, level, ctypes.byref(t)))
+    return t.tile_w, t.tile_h, t.iters_per_launch, t.threads, t.speculate
 
 
 def ff_consistency(ctx, fwd: int, bwd: int, w: int, h: int, eps: int, mask_dev: int):
