@@ -142,6 +142,14 @@ FF_API ff_status ff_get_tuning(ff_ctx* ctx, int level, ff_tuning* out);
 FF_API ff_status ff_consistency(ff_ctx* ctx, const int16_t* fwd, const int16_t* bwd, int w, int h, int eps,
                          uint8_t* mask_dev);
 
+/* Sparsification of the consistent matches (Sec. 3.1; s in Table 3: 7 for KITTI, 4 for Sintel): the image is
+ * tiled by 3x3 blocks from (0, 0) (blocks at the right and bottom edges may be smaller); in every block with at
+ * least `min_matches` (1..9) matches that pass the consistency check with `eps`, only the match with the
+ * lowest squared consistency error is kept (the first in row-major order on ties).  sparse_dev[p] = 1 for kept
+ * matches, 0 elsewhere.  fwd/bwd: device int16 [h][w][2] flows; sparse_dev: device uint8 [h][w]. */
+FF_API ff_status ff_sparsify(ff_ctx* ctx, const int16_t* fwd, const int16_t* bwd, int w, int h, int eps,
+                             int min_matches, uint8_t* sparse_dev);
+
 /* Return a pyramid to the context's pool (its memory is reused by a later ff_features of the same size). */
 FF_API ff_status ff_pyr_release(ff_ctx* ctx, ff_pyr* pyr);
 
@@ -231,6 +239,19 @@ FF_API ff_status ff_server_destroy(ff_server* srv);
  * the same device -- race on the array and must be serialised by the caller. */
 FF_API ff_status ff_match_pair_noalloc(ff_ctx* ctx, const ff_pyr* a, const ff_pyr* b, int dir, int16_t* flow_dev,
                                        int32_t* cost_dev);
+
+/* Context options (ff_set_option).  Changing one drops the cached plans.
+ *   FF_OPT_SEED_KERNEL           which kernel computes the initial matches: FF_SEED_TCGEN05 (default; tcgen05
+ *                                tensor cores, TMA-fed) or FF_SEED_MMA_SYNC (warp-level mma.sync); identical
+ *                                results.
+ *   FF_OPT_WAIT_LIMIT            polls (1..2^30, default 2^22, about a second) before a device-side wait gives
+ *                                up; the kernel then records the failure, cleans up and returns, and the next
+ *                                ff_sync reports FF_ERR_TIMEOUT with the context still usable.
+ *   FF_OPT_TEST_WITHHOLD_COPIES  1: the tensor-core seed issues no copies, so its waits can only expire (a test of
+ *                                the bounded waits); 0 (default) normal operation. */
+enum { FF_OPT_SEED_KERNEL = 1, FF_OPT_WAIT_LIMIT = 2, FF_OPT_TEST_WITHHOLD_COPIES = 3 };
+enum { FF_SEED_MMA_SYNC = 0, FF_SEED_TCGEN05 = 1 };
+FF_API ff_status ff_set_option(ff_ctx* ctx, int option, int64_t value);
 
 /* Release every resource of the context (pyramids, plans, graphs); ctx must not be used afterwards. */
 FF_API ff_status ff_destroy(ff_ctx* ctx);

@@ -91,6 +91,8 @@ def _declare(lib):
     lib.ffo_match_dir.restype = c_int
     lib.ffo_consistency.argtypes = [i16p, i16p, c_int, c_int, c_int, u8p]
     lib.ffo_consistency.restype = None
+    lib.ffo_sparsify.argtypes = [i16p, i16p, c_int, c_int, c_int, c_int, u8p]
+    lib.ffo_sparsify.restype = None
     lib.ffo_match_bidir.argtypes = [u8p, u8p, c_int, c_int, ctypes.POINTER(Params), i16p, i16p, i32p, i32p, u8p]
     lib.ffo_match_bidir.restype = c_int
     return lib
@@ -206,6 +208,12 @@ class Oracle:
         mask = np.empty((h, w), np.uint8)
         self.L.ffo_consistency(_i16(fwd), _i16(bwd), w, h, eps, mask)
         return mask
+
+    def sparsify(self, fwd, bwd, eps, s):
+        h, w, _ = fwd.shape
+        out = np.empty((h, w), np.uint8)
+        self.L.ffo_sparsify(_i16(fwd), _i16(bwd), w, h, eps, s, out)
+        return out
 
     def match_bidir(self, img_a, img_b, params: Params):
         """The whole stage for one pair: (flow_fwd, flow_bwd, cost_fwd, cost_bwd, mask)."""

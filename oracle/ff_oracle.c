@@ -326,6 +326,37 @@ void ffo_consistency(const int16_t* fwd, const int16_t* bwd, int w, int h, int e
         }
 }
 
+/* Sparsification (Sec. 3.1; s in Table 3): in each 3x3 block that contains at least s matches that pass the
+ * consistency check, keep only the match with the lowest consistency error; drop every other match.
+ * Reading: blocks tile the image from (0, 0) (blocks at the right and bottom edges may be smaller); the error is
+ * the squared Euclidean consistency error |f(p) + b(p + f(p))|^2; ties go to the first pixel in row-major order
+ * within the block.  out[p] = 1 for kept matches, 0 elsewhere. */
+void ffo_sparsify(const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, int s, uint8_t* out) {
+    for (long p = 0; p < (long)w * h; p++) out[p] = 0;
+    for (int by = 0; by < h; by += 3)
+        for (int bx = 0; bx < w; bx += 3) {
+            int count = 0;
+            long best_p = -1, best_e = 0;
+            for (int y = by; y < by + 3 && y < h; y++)
+                for (int x = bx; x < bx + 3 && x < w; x++) {
+                    long p = (long)y * w + x;
+                    int fx = fwd[2 * p], fy = fwd[2 * p + 1];
+                    int qx = x + fx, qy = y + fy;
+                    if (qx < 0 || qx >= w || qy < 0 || qy >= h) continue;
+                    long q = (long)qy * w + qx;
+                    long ex = (long)fx + bwd[2 * q], ey = (long)fy + bwd[2 * q + 1];
+                    long e = ex * ex + ey * ey;
+                    if (e > (long)eps * eps) continue;
+                    count++;
+                    if (best_p < 0 || e < best_e) {
+                        best_p = p;
+                        best_e = e;
+                    }
+                }
+            if (count >= s && best_p >= 0) out[best_p] = 1;
+        }
+}
+
 /* The whole stage for one frame pair: pyramids and features of both frames, matching frame 1 -> 2
  * (dir 0) and the inverse field 2 -> 1 (dir 1), then the consistency mask of the forward field. */
 int ffo_match_bidir(const uint8_t* rgb_a, const uint8_t* rgb_b, int w, int h, const ffo_params* prm,

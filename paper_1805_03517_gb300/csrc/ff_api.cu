@@ -51,13 +51,16 @@ struct ff_pyr {
     int8_t* seed_desc = nullptr;     // [n_pad][64]
     int32_t* seed_norm = nullptr;    // [n_coarse]
     int n_coarse = 0, n_pad = 0;
+    void* desc16 = nullptr;          // f16 [n_pad128][64] for the tensor-core seed
+    void* tmap = nullptr;            // device copy of its TMA tensor map (128 B)
+    int n_pad128 = 0;
     DevBuf mem;
     bool in_use = false;
 };
 
 namespace {
 
-enum class Kind { ZeroCounters, Seed, Handover, Propagate, Consistency };
+enum class Kind { Memset, Seed, SeedTc, Handover, Propagate, Consistency };
 
 struct Launch {
     Kind kind;
@@ -77,9 +80,14 @@ struct Launch {
     const uint32_t* bwd = nullptr;
     int w = 0, h = 0, eps = 0;
     uint8_t* mask = nullptr;
-    // zero counters
-    void* zero_ptr = nullptr;
-    size_t zero_bytes = 0;
+    // memset
+    void* set_ptr = nullptr;
+    size_t set_bytes = 0;
+    int set_value = 0;
+    // tensor-core seed
+    uint32_t wait_limit = 0;
+    int withhold = 0;
+    int* err = nullptr;
 };
 
 // One direction of one pair.
@@ -131,6 +139,10 @@ struct ff_ctx {
     std::map<std::vector<uintptr_t>, std::unique_ptr<Plan>> plans;
     std::map<TuneKey, TileCfg> tuned;
     TileCfg forced[kMaxLevels] = {};  // per-level override (tw == 0: none)
+    int seed_kernel = FF_SEED_TCGEN05;
+    uint32_t wait_limit = 1u << 22;    // polls before a device-side wait gives up (~1 s)
+    int withhold = 0;                  // test of the bounded waits: the tensor-core seed issues no copies
+    int* d_err = nullptr;              // device error word of bounded waits
     std::string err;
     int64_t launches = 0, replays = 0, plans_built = 0, bytes = 0;
     bool profiling = false;
@@ -217,9 +229,13 @@ TileCfg default_cfg(const ff_ctx* c, int64_t level_pix_all, int T) {
 ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
     cudaStream_t st = c->stream;
     switch (L.kind) {
-        case Kind::ZeroCounters:
-            FF_CUDA(c, cudaMemsetAsync(L.zero_ptr, 0, L.zero_bytes, st));
+        case Kind::Memset:
+            FF_CUDA(c, cudaMemsetAsync(L.set_ptr, L.set_value, L.set_bytes, st));
             return FF_OK;
+        case Kind::SeedTc:
+            launch_seed_tc(static_cast<const SeedTcProblem*>(L.probs), L.n_probs, L.total, L.total_pix, L.wait_limit,
+                           L.withhold, L.err, st);
+            break;
         case Kind::Seed:
             launch_seed(static_cast<const SeedProblem*>(L.probs), L.n_probs, L.total, st);
             break;
@@ -239,7 +255,18 @@ ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
     return FF_OK;
 }
 
-bool is_kernel(const Launch& l) { return l.kind != Kind::ZeroCounters; }
+int kernels_of(const Launch& l) { return l.kind == Kind::Memset ? 0 : l.kind == Kind::SeedTc ? 2 : 1; }
+
+ff_status ensure_err_word(ff_ctx* c) {
+    if (c->d_err) return FF_OK;
+    if (cudaMalloc(&c->d_err, 256) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_err = nullptr;
+        return fail(c, FF_ERR_OOM, "error word allocation failed");
+    }
+    FF_CUDA(c, cudaMemset(c->d_err, 0, 256));
+    return FF_OK;
+}
 
 cudaEvent_t get_event(ff_ctx* c) {
     if (!c->event_pool.empty()) {
@@ -269,7 +296,7 @@ ff_status run_launches(ff_ctx* c, const std::vector<Launch>& ls, bool timed) {
         for (size_t k = i; k < j; k++) {
             ff_status s = enqueue_launch(c, ls[k]);
             if (s != FF_OK) return s;
-            nk += is_kernel(ls[k]);
+            nk += kernels_of(ls[k]);
         }
         c->launches += nk;
         if (timed) {
@@ -294,11 +321,19 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     };
     std::vector<std::vector<LevelBufs>> lb(nj, std::vector<LevelBufs>(L));
     std::vector<int32_t*> seed_dist(nj);
-    size_t scratch = 0;
+    std::vector<unsigned long long*> seed_keys(nj);
+    const bool tc = c->seed_kernel == FF_SEED_TCGEN05;
+    if (tc) {
+        ff_status se = ensure_err_word(c);
+        if (se != FF_OK) return se;
+    }
+    size_t scratch = 0, keys_bytes = 0;
     for (int j = 0; j < nj; j++) {
         for (int s = 0; s < L; s++) scratch += 4 * align_up((size_t)jobs[j].a->ws[s] * jobs[j].a->hs[s] * 4);
         scratch += align_up((size_t)jobs[j].a->n_coarse * 4);
+        if (tc) keys_bytes += (size_t)jobs[j].a->n_coarse * 8;
     }
+    scratch += align_up(keys_bytes);
     P.bufs.emplace_back();
     ff_status st = dev_alloc(c, P.bufs.back(), scratch);
     if (st != FF_OK) return st;
@@ -317,6 +352,11 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         seed_dist[j] = reinterpret_cast<int32_t*>(base + off);
         off += align_up((size_t)jobs[j].a->n_coarse * 4);
     }
+    char* keys_base = base + off;
+    for (int j = 0, ko = 0; j < nj && tc; j++) {
+        seed_keys[j] = reinterpret_cast<unsigned long long*>(keys_base) + ko;
+        ko += jobs[j].a->n_coarse;
+    }
     // queue order: the two directions of a pair interleaved tile by tile (they read the same two frames), pairs
     // one after another; directions without a partner follow
     std::vector<std::vector<int>> groups;
@@ -329,6 +369,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         if (!grouped[j]) groups.push_back({j});
 
     std::vector<SeedProblem> seeds;
+    std::vector<SeedTcProblem> tcseeds;
     std::vector<HandoverProblem> hos;
     std::vector<PropProblem> props;
     std::vector<int2> queue;
@@ -339,10 +380,53 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         int counter;
     };
     std::vector<Pending> pend;
-    pend.push_back({Launch{Kind::ZeroCounters, FF_PHASE_SEED}, 0, 0, -1});
+    pend.push_back({Launch{Kind::Memset, FF_PHASE_SEED}, 0, 0, -1});  // queue counters <- 0
+    if (tc) {  // seed keys <- all ones (the neutral element of the atomicMin merge)
+        Launch l{};
+        l.kind = Kind::Memset;
+        l.phase = FF_PHASE_SEED;
+        l.set_ptr = keys_base;
+        l.set_bytes = keys_bytes;
+        l.set_value = 0xFF;
+        pend.push_back({l, 0, 0, -1});
+    }
 
     // 1. exact initial matches at the coarsest level
-    {
+    if (tc) {
+        Launch l{};
+        l.kind = Kind::SeedTc;
+        l.phase = FF_PHASE_SEED;
+        int ctas = 0;
+        int64_t pix = 0;
+        for (int j = 0; j < nj; j++) {
+            const ff_pyr* A = jobs[j].a;
+            const ff_pyr* B = jobs[j].b;
+            SeedTcProblem sp{};
+            sp.map_a = A->tmap;
+            sp.map_b = B->tmap;
+            sp.normA = A->seed_norm;
+            sp.normB = B->seed_norm;
+            sp.n = A->n_coarse;
+            sp.w = A->ws[L - 1];
+            sp.row_tiles = (sp.n + kSeedTcRows - 1) / kSeedTcRows;
+            sp.col_tiles = (sp.n + kSeedTcCols - 1) / kSeedTcCols;
+            sp.cta_base = ctas;
+            ctas += sp.row_tiles * sp.col_tiles;
+            sp.keys = seed_keys[j];
+            sp.flow = lb[j][L - 1].flow[0];
+            sp.dist = seed_dist[j];
+            sp.pix_base = pix;
+            pix += sp.n;
+            tcseeds.push_back(sp);
+        }
+        l.n_probs = nj;
+        l.total = ctas;
+        l.total_pix = pix;
+        l.wait_limit = c->wait_limit;
+        l.withhold = c->withhold;
+        l.err = c->d_err;
+        pend.push_back({l, 0, 0, -1});
+    } else {
         Launch l{};
         l.kind = Kind::Seed;
         l.phase = FF_PHASE_SEED;
@@ -489,13 +573,15 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     }
 
     // upload the problem tables, queues and counters in one block
-    size_t o_seed = 0, o_ho = align_up(seeds.size() * sizeof(SeedProblem));
+    size_t o_seed = 0, o_tc = align_up(seeds.size() * sizeof(SeedProblem));
+    size_t o_ho = o_tc + align_up(tcseeds.size() * sizeof(SeedTcProblem));
     size_t o_prop = o_ho + align_up(hos.size() * sizeof(HandoverProblem));
     size_t o_q = o_prop + align_up(props.size() * sizeof(PropProblem));
     size_t o_cnt = o_q + align_up(queue.size() * sizeof(int2));
     size_t tbytes = o_cnt + align_up((size_t)std::max(n_counters, 1) * sizeof(int));
     std::vector<char> host(tbytes, 0);
     memcpy(host.data() + o_seed, seeds.data(), seeds.size() * sizeof(SeedProblem));
+    memcpy(host.data() + o_tc, tcseeds.data(), tcseeds.size() * sizeof(SeedTcProblem));
     memcpy(host.data() + o_ho, hos.data(), hos.size() * sizeof(HandoverProblem));
     memcpy(host.data() + o_prop, props.data(), props.size() * sizeof(PropProblem));
     memcpy(host.data() + o_q, queue.data(), queue.size() * sizeof(int2));
@@ -507,9 +593,14 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     for (Pending& pd : pend) {
         Launch l = pd.l;
         switch (l.kind) {
-            case Kind::ZeroCounters:
-                l.zero_ptr = tb + o_cnt;
-                l.zero_bytes = (size_t)std::max(n_counters, 1) * sizeof(int);
+            case Kind::Memset:
+                if (!l.set_ptr) {  // the queue counters of this plan
+                    l.set_ptr = tb + o_cnt;
+                    l.set_bytes = (size_t)std::max(n_counters, 1) * sizeof(int);
+                }
+                break;
+            case Kind::SeedTc:
+                l.probs = tb + o_tc;
                 break;
             case Kind::Seed:
                 l.probs = tb + o_seed + pd.off_probs * sizeof(SeedProblem);
@@ -548,7 +639,7 @@ ff_status execute_plan(ff_ctx* c, Plan& P) {
         for (const Launch& l : P.launches) {
             s = enqueue_launch(c, l);
             if (s != FF_OK) break;
-            nk += is_kernel(l);
+            nk += kernels_of(l);
         }
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (s != FF_OK) {
@@ -778,6 +869,7 @@ ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* cuda_str
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->prm = *p;
     if (cudaSetDevice(device) != cudaSuccess || init_kernel_attributes() != cudaSuccess ||
+        seed_tc_init_attributes() != cudaSuccess ||
         cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -810,10 +902,12 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
         level_dims(w, h, L, np->ws, np->hs);
         np->n_coarse = np->ws[L - 1] * np->hs[L - 1];
         np->n_pad = round_up(np->n_coarse, 16);
+        np->n_pad128 = round_up(np->n_coarse, kSeedTcRows);
         size_t bytes = 0;
         for (int s = 1; s < L; s++) bytes += align_up((size_t)np->ws[s] * np->hs[s] * 3);
         for (int s = 0; s < L; s++) bytes += align_up((size_t)np->ws[s] * np->hs[s] * kDescBytes);
         bytes += align_up((size_t)np->n_pad * kSeedK) + align_up((size_t)np->n_coarse * 4);
+        bytes += align_up((size_t)np->n_pad128 * 128) + align_up(128);
         ff_status s = dev_alloc(c, np->mem, bytes);
         if (s != FF_OK) return s;
         char* b = static_cast<char*>(np->mem.p);
@@ -829,6 +923,16 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
         np->seed_desc = reinterpret_cast<int8_t*>(b + o);
         o += align_up((size_t)np->n_pad * kSeedK);
         np->seed_norm = reinterpret_cast<int32_t*>(b + o);
+        o += align_up((size_t)np->n_coarse * 4);
+        np->desc16 = b + o;
+        o += align_up((size_t)np->n_pad128 * 128);
+        np->tmap = b + o;
+        alignas(64) unsigned char map[128];
+        if (!seed_tc_encode_map(map, np->desc16, np->n_pad128)) {
+            dev_free(c, np->mem);
+            return fail(c, FF_ERR_CUDA, "TMA tensor map encoding failed");
+        }
+        FF_CUDA(c, cudaMemcpy(np->tmap, map, sizeof map, cudaMemcpyHostToDevice));
         P = np.get();
         c->pyrs.push_back(std::move(np));
     }
@@ -863,7 +967,8 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
     }
     launch_wht(wa, tiles, c->stream);
     launch_seed_pack(P->feat[L - 1], P->n_coarse, P->n_pad, P->seed_desc, P->seed_norm, c->stream);
-    nl += 2;
+    launch_seed_pack16(P->feat[L - 1], P->n_coarse, P->n_pad128, P->desc16, c->stream);
+    nl += 3;
     c->launches += nl;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -988,6 +1093,21 @@ ff_status ff_consistency(ff_ctx* c, const int16_t* fwd, const int16_t* bwd, int 
     return run_launches(c, {l}, c->profiling);
 }
 
+ff_status ff_sparsify(ff_ctx* c, const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, int min_matches,
+                      uint8_t* sparse_dev) {
+    if (!c) return FF_ERR_ARG;
+    if (!fwd || !bwd || !sparse_dev || !aligned4(fwd) || !aligned4(bwd)) return fail(c, FF_ERR_ARG, "bad pointer");
+    if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim) return fail(c, FF_ERR_ARG, "size %dx%d outside 1..%d", w, h, kMaxDim);
+    if (eps < 0 || eps > 32767) return fail(c, FF_ERR_ARG, "eps must be 0..32767");
+    if (min_matches < 1 || min_matches > 9) return fail(c, FF_ERR_ARG, "min_matches must be 1..9");
+    FF_CUDA(c, cudaSetDevice(c->device));
+    launch_sparsify(reinterpret_cast<const uint32_t*>(fwd), reinterpret_cast<const uint32_t*>(bwd), w, h, eps,
+                    min_matches, sparse_dev, c->stream);
+    FF_CUDA(c, cudaGetLastError());
+    c->launches += 1;
+    return FF_OK;
+}
+
 ff_status ff_pyr_release(ff_ctx* c, ff_pyr* p) {
     if (!c) return FF_ERR_ARG;
     ff_status s = check_pyr(c, p, "pyr");
@@ -1015,6 +1135,38 @@ ff_status ff_sync(ff_ctx* c) {
     FF_CUDA(c, cudaSetDevice(c->device));
     FF_CUDA(c, cudaStreamSynchronize(c->stream));
     FF_CUDA(c, cudaGetLastError());
+    if (c->d_err) {  // a bounded device-side wait gave up since the last check
+        int e = 0;
+        FF_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
+        if (e != 0) {
+            FF_CUDA(c, cudaMemset(c->d_err, 0, sizeof e));
+            return fail(c, FF_ERR_TIMEOUT, "a device-side wait of the tensor-core seed expired (code %d)", e);
+        }
+    }
+    return FF_OK;
+}
+
+ff_status ff_set_option(ff_ctx* c, int option, int64_t value) {
+    if (!c) return FF_ERR_ARG;
+    switch (option) {
+        case FF_OPT_SEED_KERNEL:
+            if (value != FF_SEED_MMA_SYNC && value != FF_SEED_TCGEN05) return fail(c, FF_ERR_ARG, "bad seed kernel");
+            break;
+        case FF_OPT_WAIT_LIMIT:
+            if (value < 1 || value > (1ll << 30)) return fail(c, FF_ERR_ARG, "wait limit must be 1..2^30 polls");
+            break;
+        case FF_OPT_TEST_WITHHOLD_COPIES:
+            if (value != 0 && value != 1) return fail(c, FF_ERR_ARG, "withhold must be 0 or 1");
+            break;
+        default:
+            return fail(c, FF_ERR_ARG, "unknown option %d", option);
+    }
+    FF_CUDA(c, cudaSetDevice(c->device));
+    ff_status s = drop_plans(c);  // plans bake the options in
+    if (s != FF_OK) return s;
+    if (option == FF_OPT_SEED_KERNEL) c->seed_kernel = (int)value;
+    if (option == FF_OPT_WAIT_LIMIT) c->wait_limit = (uint32_t)value;
+    if (option == FF_OPT_TEST_WITHHOLD_COPIES) c->withhold = (int)value;
     return FF_OK;
 }
 
@@ -1071,6 +1223,7 @@ ff_status ff_destroy(ff_ctx* c) {
     cudaStreamSynchronize(c->stream);
     for (auto& kv : c->plans) free_plan(c, *kv.second);
     for (auto& p : c->pyrs) dev_free(c, p->mem);
+    if (c->d_err) cudaFree(c->d_err);
     for (auto& e : c->events) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);

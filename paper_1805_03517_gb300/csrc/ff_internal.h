@@ -56,6 +56,28 @@ struct SeedProblem {
 };
 void launch_seed(const SeedProblem* probs_dev, int n_probs, int total_row_tiles, cudaStream_t st);
 
+// Tensor-core (tcgen05) version: descriptors as f16 [n_pad][64] behind a TMA tensor map (128 x 64 boxes).
+constexpr int kSeedTcRows = 128, kSeedTcCols = 256;
+struct SeedTcProblem {
+    const void* map_a;             // device address of the source frame's CUtensorMap
+    const void* map_b;             // target frame's
+    const int32_t* normA;
+    const int32_t* normB;
+    int n, w;
+    int row_tiles, col_tiles;      // ceil(n / 128), ceil(n / 256)
+    int cta_base;                  // first CTA of this problem in the launch
+    unsigned long long* keys;      // [n] (score + 2^31) << 32 | q, must start at all ones
+    uint32_t* flow;                // [n] packed q - p
+    int32_t* dist;                 // [n] or null
+    int64_t pix_base;              // first pixel of this problem in the launch
+};
+cudaError_t seed_tc_init_attributes();
+bool seed_tc_encode_map(void* map_host_128b, const void* desc16_dev, int n_pad);
+void launch_seed_pack16(const int16_t* feat, int n, int n_pad, void* desc16, cudaStream_t st);
+// wait_limit: polls before a wait gives up (then *err_dev is set); withhold: issue no copies (test of the waits)
+void launch_seed_tc(const SeedTcProblem* probs_dev, int n_probs, int total_ctas, int64_t total_pix,
+                    uint32_t wait_limit, int withhold, int* err_dev, cudaStream_t st);
+
 // ---------------------------------------------------------------------------------------------------------
 // hand-over (coarse-to-fine initialisation) and cost initialisation
 
@@ -111,6 +133,8 @@ void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n
 
 void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int eps, uint8_t* mask,
                         cudaStream_t st);
+void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int eps, int s, uint8_t* out,
+                     cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------------------
 // read-only views of context and pyramid internals for other translation units of the library

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libff.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "ff.h")
 
 FF_OK, FF_ERR_ARG, FF_ERR_OOM, FF_ERR_CUDA, FF_ERR_TIMEOUT, FF_ERR_BUSY = range(6)
+FF_OPT_SEED_KERNEL, FF_OPT_WAIT_LIMIT, FF_OPT_TEST_WITHHOLD_COPIES = 1, 2, 3
+FF_SEED_MMA_SYNC, FF_SEED_TCGEN05 = 0, 1
 STATUS_NAMES = {0: "FF_OK", 1: "FF_ERR_ARG", 2: "FF_ERR_OOM", 3: "FF_ERR_CUDA", 4: "FF_ERR_TIMEOUT", 5: "FF_ERR_BUSY"}
 PHASES = ("features", "seed", "handover", "propagate", "consistency")
 
@@ -86,6 +88,7 @@ def lib():
         "ff_set_tuning": (S, [vp, i, ctypes.POINTER(Tuning)]),
         "ff_get_tuning": (S, [vp, i, ctypes.POINTER(Tuning)]),
         "ff_consistency": (S, [vp, vp, vp, i, i, i, vp]),
+        "ff_sparsify": (S, [vp, vp, vp, i, i, i, i, vp]),
         "ff_pyr_release": (S, [vp, vp]),
         "ff_pyr_level_dims": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "ff_pyr_features": (vp, [vp, i]),
@@ -102,6 +105,7 @@ def lib():
         "ff_server_poll": (S, [vp, i, ctypes.POINTER(ctypes.c_uint64), i, ctypes.POINTER(i)]),
         "ff_server_stats": (S, [vp, i64p, i64p, i64p]),
         "ff_server_destroy": (S, [vp]),
+        "ff_set_option": (S, [vp, i, ctypes.c_int64]),
         "ff_destroy": (S, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -172,6 +176,10 @@ def ff_get_tuning(ctx, level: int):
 
 def ff_consistency(ctx, fwd: int, bwd: int, w: int, h: int, eps: int, mask_dev: int):
     _check(ctx, lib().ff_consistency(ctx, fwd, bwd, w, h, eps, mask_dev))
+
+
+def ff_sparsify(ctx, fwd: int, bwd: int, w: int, h: int, eps: int, min_matches: int, sparse_dev: int):
+    _check(ctx, lib().ff_sparsify(ctx, fwd, bwd, w, h, eps, min_matches, sparse_dev))
 
 
 def ff_pyr_release(ctx, pyr):
@@ -255,6 +263,10 @@ def ff_server_stats(ctx, srv):
 
 def ff_server_destroy(srv):
     _check(None, lib().ff_server_destroy(srv))
+
+
+def ff_set_option(ctx, option: int, value: int):
+    _check(ctx, lib().ff_set_option(ctx, option, value))
 
 
 def ff_destroy(ctx):
@@ -373,6 +385,12 @@ class Matcher:
         mask = self._empty((h, w), self.torch.uint8)
         ff_consistency(self.ctx, fwd.data_ptr(), bwd.data_ptr(), w, h, eps, mask.data_ptr())
         return mask
+
+    def sparsify(self, fwd, bwd, eps: int, min_matches: int):
+        h, w = int(fwd.shape[0]), int(fwd.shape[1])
+        out = self._empty((h, w), self.torch.uint8)
+        ff_sparsify(self.ctx, fwd.data_ptr(), bwd.data_ptr(), w, h, eps, min_matches, out.data_ptr())
+        return out
 
     def sync(self):
         ff_sync(self.ctx)

@@ -432,6 +432,52 @@ def check_consistency(o):
     assert o.consistency(fwd, bwd, 1).tolist() == [[1, 0]]
 
 
+def sparsify_numpy(fwd, bwd, eps, s):
+    """Brute-force restatement: per 3x3 block, the lowest-error inlier if the block has >= s inliers."""
+    h, w, _ = fwd.shape
+    ys, xs = np.mgrid[0:h, 0:w]
+    qx = xs + fwd[..., 0].astype(np.int64)
+    qy = ys + fwd[..., 1].astype(np.int64)
+    inside = (qx >= 0) & (qx < w) & (qy >= 0) & (qy < h)
+    qxc, qyc = np.clip(qx, 0, w - 1), np.clip(qy, 0, h - 1)
+    e = (fwd[..., 0] + bwd[qyc, qxc, 0].astype(np.int64)) ** 2 + (fwd[..., 1] + bwd[qyc, qxc, 1].astype(np.int64)) ** 2
+    ok = inside & (e <= eps * eps)
+    out = np.zeros((h, w), np.uint8)
+    for by in range(0, h, 3):
+        for bx in range(0, w, 3):
+            cand = [(int(e[y, x]), y, x) for y in range(by, min(by + 3, h)) for x in range(bx, min(bx + 3, w))
+                    if ok[y, x]]
+            if len(cand) >= s:
+                _, y, x = min(cand)  # smallest error, then row-major first
+                out[y, x] = 1
+    return out
+
+
+def check_sparsify(o):
+    # hand example: one 3x3 block, errors 0 at (1,1) and 0 at (2,2) -> the first in row-major order wins
+    fwd = np.zeros((3, 3, 2), np.int16)
+    bwd = np.zeros((3, 3, 2), np.int16)
+    bwd[..., 0] = 1  # every pixel has error 1 ...
+    bwd[1, 1] = (0, 0)
+    bwd[2, 2] = (0, 0)  # ... except (1,1) and (2,2), error 0
+    assert o.sparsify(fwd, bwd, 1, 9).tolist() == [[0, 0, 0], [0, 1, 0], [0, 0, 0]]
+    assert o.sparsify(fwd, bwd, 0, 2).tolist() == [[0, 0, 0], [0, 1, 0], [0, 0, 0]]  # 2 inliers at eps 0
+    assert o.sparsify(fwd, bwd, 0, 3).sum() == 0  # only 2 inliers < s
+    # partial edge blocks, random flows, several s and eps: brute force
+    rng = np.random.default_rng(17)
+    for (h, w) in ((7, 8), (10, 11), (1, 5), (3, 3)):
+        fwd = rng.integers(-2, 3, size=(h, w, 2)).astype(np.int16)
+        bwd = rng.integers(-2, 3, size=(h, w, 2)).astype(np.int16)
+        for eps, s in ((1, 1), (2, 4), (3, 7), (0, 1)):
+            got = o.sparsify(fwd, bwd, eps, s)
+            assert np.array_equal(got, sparsify_numpy(fwd, bwd, eps, s)), (h, w, eps, s)
+            # at most one match per block, and only consistent matches survive
+            for by in range(0, h, 3):
+                for bx in range(0, w, 3):
+                    assert got[by:by + 3, bx:bx + 3].sum() <= 1
+            assert np.all(got <= o.consistency(fwd, bwd, eps))
+
+
 def check_pipeline_composition(o):
     """The whole stage equals its steps composed in the order of Sec. 3.1 (pyramid, WHT, seed at the coarsest
     level, per level hand-over + propagation keyed by (direction, level), inverse field with the frames
@@ -477,5 +523,6 @@ ALL_CHECKS = [
     check_propagation_schedule,
     check_translation,
     check_consistency,
+    check_sparsify,
     check_pipeline_composition,
 ]

@@ -235,3 +235,24 @@ def test_errors_are_reported(lib_built):
         ff.ff_match_pair(M.ctx, pa.handle, pb.handle, 0, flow.data_ptr(), None)
     M.release(pa)
     M.sync()
+
+
+def test_sparsify_parity(lib_built):
+    """Sparsification (Sec. 3.1) of random flows (ragged edge blocks) and of real matches, against the oracle."""
+    o = oracle.default()
+    M = matcher(mp(1, 1))
+    rng = np.random.default_rng(4)
+    for (h, w) in ((1, 1), (7, 8), (31, 47), (96, 128)):
+        fwd = rng.integers(-2, 3, size=(h, w, 2)).astype(np.int16)
+        bwd = rng.integers(-2, 3, size=(h, w, 2)).astype(np.int16)
+        for eps, s in ((1, 1), (2, 4), (3, 7), (0, 9)):
+            got = M.sparsify(torch.from_numpy(fwd).cuda(), torch.from_numpy(bwd).cuda(), eps, s)
+            M.sync()
+            assert np.array_equal(got.cpu().numpy(), o.sparsify(fwd, bwd, eps, s)), (h, w, eps, s)
+    spec = configs.workload("small_128x96").pairs[0]
+    a, b, _ = synth.make_pair(spec.kind, spec.seed, spec.w, spec.h)
+    ff_, fb_, _, _, _ = check_pair(a, b, spec.params)
+    for s in (4, 7):
+        got = M.sparsify(torch.from_numpy(ff_).cuda(), torch.from_numpy(fb_).cuda(), 1, s)
+        M.sync()
+        assert np.array_equal(got.cpu().numpy(), o.sparsify(ff_, fb_, 1, s))

@@ -41,6 +41,10 @@ MUTANTS = {
     "inverse_same_direction_key": ("ws, hs, prm, 1,", "ws, hs, prm, 0,"),
     "consistency_strict": ("<= (long)eps * eps", "< (long)eps * eps"),
     "consistency_sign": ("long ex = fx + bwd[2 * q]", "long ex = fx - bwd[2 * q]"),
+    "sparsify_error_sign": ("long ex = (long)fx + bwd[2 * q]", "long ex = (long)fx - bwd[2 * q]"),
+    "sparsify_last_tie_wins": ("if (best_p < 0 || e < best_e) {", "if (best_p < 0 || e <= best_e) {"),
+    "sparsify_count_off": ("if (count >= s && best_p >= 0)", "if (count > s && best_p >= 0)"),
+    "sparsify_block_4": ("for (int bx = 0; bx < w; bx += 3) {", "for (int bx = 0; bx < w; bx += 4) {"),
 }
 
 
