@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libff.so")
 
-SOURCES = ["features.cu", "seed.cu", "seed_tc.cu", "propagate.cu", "ff_api.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["features.cu", "seed.cu", "seed_tc.cu", "propagate.cu", "filter.cu", "ff_api.cu", "server.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
