@@ -69,9 +69,12 @@ typedef struct {
     int rs_radius;
     int eps;
     uint32_t seed;
+    int rs_radius2;  /* random-search radius (0..16) of the second inverse field of the two-check mode (Sec. 3.1
+                        computes each inverse field "with different matching parameters"); it also runs on its own
+                        random stream */
 } ff_params;
 
-/* Default parameters: L=5, iters=6, patch=8, n_coef=16, rs_radius=2, eps=1, seed=0x20180503. */
+/* Default parameters: L=5, iters=6, patch=8, n_coef=16, rs_radius=2, eps=1, seed=0x20180503, rs_radius2=4. */
 FF_API void ff_default_params(ff_params* p);
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a cudaStream_t; NULL
@@ -96,7 +99,10 @@ FF_API ff_status ff_match_pair(ff_ctx* ctx, const ff_pyr* a, const ff_pyr* b, in
                         int32_t* cost_dev);
 
 /* One frame pair of a batch: forward field a -> b, inverse field b -> a and the consistency mask of the
- * forward field.  All outputs are device buffers of the pair's level-0 size; cost_fwd/cost_bwd may be NULL. */
+ * forward field.  All outputs are device buffers of the pair's level-0 size; cost_fwd/cost_bwd may be NULL.
+ * If flow_bwd2 is not NULL, a second inverse field is computed with the second parameter set (rs_radius2 and its
+ * own random stream) into flow_bwd2, and mask keeps a match only if it passes both consistency checks (the two
+ * checks of Sec. 3.1). */
 typedef struct {
     const ff_pyr* a;
     const ff_pyr* b;
@@ -105,6 +111,7 @@ typedef struct {
     int32_t* cost_fwd;
     int32_t* cost_bwd;
     uint8_t* mask;
+    int16_t* flow_bwd2;
 } ff_pair_job;
 
 /* Match n pairs of possibly different sizes in merged launches: for every job, the forward field, the
@@ -156,7 +163,9 @@ FF_API ff_status ff_pyr_release(ff_ctx* ctx, ff_pyr* pyr);
 /* Sizes of level `level` of a pyramid; FF_ERR_ARG if the level does not exist. */
 FF_API ff_status ff_pyr_level_dims(const ff_pyr* pyr, int level, int* w, int* h);
 
-/* Device pointer to the int16 [h][w][48] features of `level` (read-only view owned by the pyramid). */
+/* Device pointer to the 48 int16 features per pixel of `level` (read-only view owned by the pyramid).  Rows are
+ * stored colour-split: row y holds the descriptors of x = 0, 2, 4, ... followed by those of x = 1, 3, 5, ...,
+ * i.e. pixel (x, y) is descriptor y*w + (x even ? x/2 : (w+1)/2 + x/2). */
 FF_API const int16_t* ff_pyr_features(const ff_pyr* pyr, int level);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next call on the context. */

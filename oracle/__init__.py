@@ -91,6 +91,8 @@ def _declare(lib):
     lib.ffo_match_dir.restype = c_int
     lib.ffo_consistency.argtypes = [i16p, i16p, c_int, c_int, c_int, u8p]
     lib.ffo_consistency.restype = None
+    lib.ffo_match_bidir2.argtypes = [u8p, u8p, c_int, c_int, ctypes.POINTER(Params), c_int, i16p, i16p, i16p, u8p]
+    lib.ffo_match_bidir2.restype = c_int
     lib.ffo_sparsify.argtypes = [i16p, i16p, c_int, c_int, c_int, c_int, u8p]
     lib.ffo_sparsify.restype = None
     lib.ffo_match_bidir.argtypes = [u8p, u8p, c_int, c_int, ctypes.POINTER(Params), i16p, i16p, i32p, i32p, u8p]
@@ -208,6 +210,20 @@ class Oracle:
         mask = np.empty((h, w), np.uint8)
         self.L.ffo_consistency(_i16(fwd), _i16(bwd), w, h, eps, mask)
         return mask
+
+    def match_bidir2(self, img_a, img_b, params: Params, rs_radius2):
+        """Forward field, both inverse fields and the mask of the two consistency checks."""
+        a = np.ascontiguousarray(img_a, dtype=np.uint8)
+        b = np.ascontiguousarray(img_b, dtype=np.uint8)
+        h, w, _ = a.shape
+        ff = np.empty((h, w, 2), np.int16)
+        fb = np.empty((h, w, 2), np.int16)
+        fb2 = np.empty((h, w, 2), np.int16)
+        mask = np.empty((h, w), np.uint8)
+        rc = self.L.ffo_match_bidir2(a, b, w, h, ctypes.byref(params), rs_radius2, ff, fb, fb2, mask)
+        if rc != 0:
+            raise RuntimeError(f"ffo_match_bidir2 failed: {rc}")
+        return ff, fb, fb2, mask
 
     def sparsify(self, fwd, bwd, eps, s):
         h, w, _ = fwd.shape

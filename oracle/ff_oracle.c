@@ -326,6 +326,64 @@ void ffo_consistency(const int16_t* fwd, const int16_t* bwd, int w, int h, int e
         }
 }
 
+/* Two consistency checks (Sec. 3.1): the forward field is compared with two inverse fields computed with
+ * different matching parameters, and kept only if it passes both.  Reading: the second inverse field uses the
+ * random-search radius rs_radius2 and its own random stream (direction id 2); everything else is shared. */
+int ffo_match_bidir2(const uint8_t* rgb_a, const uint8_t* rgb_b, int w, int h, const ffo_params* prm, int rs_radius2,
+                     int16_t* flow_fwd, int16_t* flow_bwd, int16_t* flow_bwd2, uint8_t* mask) {
+    long n = (long)w * h;
+    int32_t* cf = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* cb = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    uint8_t* m2 = (uint8_t*)malloc((size_t)n);
+    int L = prm->n_scales, rc = 0;
+    int ws[16], hs[16];
+    if (!cf || !cb || !m2 || L < 1 || L > 16 || ffo_level_dims(w, h, L, ws, hs) != 0) rc = -1;
+    uint8_t* img[2][16];
+    int16_t* feat[2][16];
+    memset(img, 0, sizeof img);
+    memset(feat, 0, sizeof feat);
+    for (int f = 0; f < 2 && rc == 0; f++) {
+        const uint8_t* src = f == 0 ? rgb_a : rgb_b;
+        for (int s = 0; s < L; s++) {
+            long ns = (long)ws[s] * hs[s];
+            img[f][s] = (uint8_t*)malloc((size_t)ns * 3);
+            feat[f][s] = (int16_t*)malloc((size_t)ns * FFO_NF * sizeof(int16_t));
+            if (!img[f][s] || !feat[f][s]) {
+                rc = -1;
+                break;
+            }
+            if (s == 0)
+                memcpy(img[f][s], src, (size_t)ns * 3);
+            else
+                ffo_downsample(img[f][s - 1], ws[s - 1], hs[s - 1], img[f][s]);
+            ffo_wht(img[f][s], ws[s], hs[s], feat[f][s]);
+        }
+    }
+    const ffo_params* p1 = prm;
+    ffo_params p2 = *prm;
+    p2.rs_radius = rs_radius2;
+    if (rc == 0) rc = ffo_match_dir((const int16_t* const*)feat[0], (const int16_t* const*)feat[1], ws, hs, p1, 0,
+                                    flow_fwd, cf);
+    if (rc == 0) rc = ffo_match_dir((const int16_t* const*)feat[1], (const int16_t* const*)feat[0], ws, hs, p1, 1,
+                                    flow_bwd, cb);
+    if (rc == 0) rc = ffo_match_dir((const int16_t* const*)feat[1], (const int16_t* const*)feat[0], ws, hs, &p2, 2,
+                                    flow_bwd2, cb);
+    if (rc == 0) {
+        ffo_consistency(flow_fwd, flow_bwd, w, h, prm->eps, mask);
+        ffo_consistency(flow_fwd, flow_bwd2, w, h, prm->eps, m2);
+        for (long p = 0; p < n; p++) mask[p] = (uint8_t)(mask[p] & m2[p]);
+    }
+    for (int f = 0; f < 2; f++)
+        for (int s = 0; s < 16; s++) {
+            free(img[f][s]);
+            free(feat[f][s]);
+        }
+    free(cf);
+    free(cb);
+    free(m2);
+    return rc;
+}
+
 /* Sparsification (Sec. 3.1; s in Table 3): in each 3x3 block that contains at least s matches that pass the
  * consistency check, keep only the match with the lowest consistency error; drop every other match.
  * Reading: blocks tile the image from (0, 0) (blocks at the right and bottom edges may be smaller); the error is

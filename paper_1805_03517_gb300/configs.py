@@ -26,6 +26,7 @@ class MatchParams:
     rs_radius: int = 2
     eps: int = 1
     seed: int = HASH_SEED
+    rs_radius2: int = 4  # random-search radius of the second inverse field (two-check mode)
 
 
 @dataclass(frozen=True)

@@ -89,7 +89,7 @@ __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
             for (int v = 0; v < 4; v += 2)
                 out[ch * 8 + u * 2 + v / 2] = (uint32_t)(C[u][v] & 0xffff) | ((uint32_t)C[u][v + 1] << 16);
     }
-    uint4* dst = reinterpret_cast<uint4*>(L.feat + ((size_t)y * L.w + x) * kNF);
+    uint4* dst = reinterpret_cast<uint4*>(L.feat + (size_t)feat_index(x, y, L.w) * kNF);
 #pragma unroll
     for (int k = 0; k < 6; k++) dst[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
 }
@@ -102,14 +102,14 @@ void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st) {
 
 // 8-bit descriptor of the coarsest level: C >> 7 (arithmetic, i.e. floor(C / 128), in [-128, 127]) for the 48
 // coefficients, zero for the 16 padding lanes and for padding rows n..n8-1; norm = sum of squares.
-__global__ void k_seed_pack(const int16_t* __restrict__ feat, int n, int n8, int8_t* __restrict__ desc,
+__global__ void k_seed_pack(const int16_t* __restrict__ feat, int n, int w, int n8, int8_t* __restrict__ desc,
                             int32_t* __restrict__ norm) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n8) return;
     uint32_t words[16];
     int s = 0;
     if (p < n) {
-        const int16_t* f = feat + (size_t)p * kNF;
+        const int16_t* f = feat + (size_t)feat_index(p % w, p / w, w) * kNF;
 #pragma unroll
         for (int k = 0; k < 12; k++) {
             uint32_t wv = 0;
@@ -133,8 +133,8 @@ __global__ void k_seed_pack(const int16_t* __restrict__ feat, int n, int n8, int
     for (int k = 0; k < 4; k++) dst[k] = make_uint4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
 }
 
-void launch_seed_pack(const int16_t* feat, int n, int n8, int8_t* desc, int32_t* norm, cudaStream_t st) {
-    k_seed_pack<<<(n8 + 127) / 128, 128, 0, st>>>(feat, n, n8, desc, norm);
+void launch_seed_pack(const int16_t* feat, int n, int w, int n8, int8_t* desc, int32_t* norm, cudaStream_t st) {
+    k_seed_pack<<<(n8 + 127) / 128, 128, 0, st>>>(feat, n, w, n8, desc, norm);
 }
 
 }  // namespace ff

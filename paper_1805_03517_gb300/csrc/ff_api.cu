@@ -78,6 +78,7 @@ struct Launch {
     // consistency
     const uint32_t* fwd = nullptr;
     const uint32_t* bwd = nullptr;
+    const uint32_t* bwd2 = nullptr;
     int w = 0, h = 0, eps = 0;
     uint8_t* mask = nullptr;
     // memset
@@ -94,13 +95,15 @@ struct Launch {
 struct DirJob {
     const ff_pyr* a;
     const ff_pyr* b;
-    int dir;
+    int dir;            // 0 forward, 1 inverse, 2 second inverse (its own random stream)
     uint32_t* flow_out;
     int32_t* cost_out;  // may be null
+    int rs_radius;
 };
 struct ConsJob {
     int dj_fwd, dj_bwd;  // indices into the plan's DirJobs
     uint8_t* mask;
+    int dj_bwd2;         // second inverse field, or -1
 };
 
 struct Plan {
@@ -211,6 +214,7 @@ ff_status check_params(const ff_params* p, ff_ctx* c) {
     if (p->n_coef != 16) return fail(c, FF_ERR_ARG, "n_coef must be 16");
     if (p->rs_radius < 0 || p->rs_radius > 16) return fail(c, FF_ERR_ARG, "rs_radius must be 0..16");
     if (p->eps < 0 || p->eps > 32767) return fail(c, FF_ERR_ARG, "eps must be 0..32767");
+    if (p->rs_radius2 < 0 || p->rs_radius2 > 16) return fail(c, FF_ERR_ARG, "rs_radius2 must be 0..16");
     return FF_OK;
 }
 
@@ -247,7 +251,7 @@ ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
                              st);
             break;
         case Kind::Consistency:
-            launch_consistency(L.fwd, L.bwd, L.w, L.h, L.eps, L.mask, st);
+            launch_consistency(L.fwd, L.bwd, L.bwd2, L.w, L.h, L.eps, L.mask, st);
             break;
     }
     cudaError_t e = cudaGetLastError();
@@ -362,7 +366,12 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     std::vector<std::vector<int>> groups;
     std::vector<bool> grouped(nj, false);
     for (const ConsJob& cj : cons) {
-        groups.push_back({cj.dj_fwd, cj.dj_bwd});
+        if (cj.dj_bwd2 >= 0) {
+            groups.push_back({cj.dj_fwd, cj.dj_bwd, cj.dj_bwd2});
+            grouped[cj.dj_bwd2] = true;
+        } else {
+            groups.push_back({cj.dj_fwd, cj.dj_bwd});
+        }
         grouped[cj.dj_fwd] = grouped[cj.dj_bwd] = true;
     }
     for (int j = 0; j < nj; j++)
@@ -541,7 +550,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
                 pp.level = s;
                 pp.dir = jobs[j].dir;
                 pp.seed = c->prm.seed;
-                pp.rs_radius = c->prm.rs_radius;
+                pp.rs_radius = jobs[j].rs_radius;
                 pidx[j] = (int)props.size();
                 props.push_back(pp);
             }
@@ -565,6 +574,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         l.phase = FF_PHASE_CONSISTENCY;
         l.fwd = jobs[cj.dj_fwd].flow_out;
         l.bwd = jobs[cj.dj_bwd].flow_out;
+        l.bwd2 = cj.dj_bwd2 >= 0 ? jobs[cj.dj_bwd2].flow_out : nullptr;
         l.w = jobs[cj.dj_fwd].a->w;
         l.h = jobs[cj.dj_fwd].a->h;
         l.eps = c->prm.eps;
@@ -670,12 +680,14 @@ std::vector<uintptr_t> plan_key(const std::vector<DirJob>& jobs, const std::vect
         key.push_back((uintptr_t)j.dir);
         key.push_back((uintptr_t)j.flow_out);
         key.push_back((uintptr_t)j.cost_out);
+        key.push_back((uintptr_t)j.rs_radius);
     }
     key.push_back(~(uintptr_t)0);
     for (const ConsJob& cj : cons) {
         key.push_back((uintptr_t)cj.dj_fwd);
         key.push_back((uintptr_t)cj.dj_bwd);
         key.push_back((uintptr_t)cj.mask);
+        key.push_back((uintptr_t)(intptr_t)cj.dj_bwd2);
     }
     return key;
 }
@@ -851,6 +863,7 @@ void ff_default_params(ff_params* p) {
     p->rs_radius = 2;
     p->eps = 1;
     p->seed = 0x20180503u;
+    p->rs_radius2 = 4;
 }
 
 ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* cuda_stream) {
@@ -966,8 +979,8 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
         tiles += wht_tiles(P->ws[s], P->hs[s]);
     }
     launch_wht(wa, tiles, c->stream);
-    launch_seed_pack(P->feat[L - 1], P->n_coarse, P->n_pad, P->seed_desc, P->seed_norm, c->stream);
-    launch_seed_pack16(P->feat[L - 1], P->n_coarse, P->n_pad128, P->desc16, c->stream);
+    launch_seed_pack(P->feat[L - 1], P->n_coarse, P->ws[L - 1], P->n_pad, P->seed_desc, P->seed_norm, c->stream);
+    launch_seed_pack16(P->feat[L - 1], P->n_coarse, P->ws[L - 1], P->n_pad128, P->desc16, c->stream);
     nl += 3;
     c->launches += nl;
     cudaError_t e = cudaGetLastError();
@@ -993,7 +1006,7 @@ ff_status ff_match_pair(ff_ctx* c, const ff_pyr* a, const ff_pyr* b, int dir, in
     if (!flow_dev || !aligned4(flow_dev)) return fail(c, FF_ERR_ARG, "flow_dev must be a 4-byte aligned device pointer");
     if (cost_dev && !aligned4(cost_dev)) return fail(c, FF_ERR_ARG, "cost_dev must be 4-byte aligned");
     FF_CUDA(c, cudaSetDevice(c->device));
-    std::vector<DirJob> jobs{{a, b, dir, reinterpret_cast<uint32_t*>(flow_dev), cost_dev}};
+    std::vector<DirJob> jobs{{a, b, dir, reinterpret_cast<uint32_t*>(flow_dev), cost_dev, c->prm.rs_radius}};
     return run_jobs(c, jobs, {});
 }
 
@@ -1009,9 +1022,16 @@ static ff_status collect_batch(ff_ctx* c, int n, const ff_pair_job* jobs, std::v
         if (!aligned4(J.flow_fwd) || !aligned4(J.flow_bwd) || (J.cost_fwd && !aligned4(J.cost_fwd)) ||
             (J.cost_bwd && !aligned4(J.cost_bwd)))
             return fail(c, FF_ERR_ARG, "job %d: outputs must be 4-byte aligned", i);
-        dj.push_back({J.a, J.b, 0, reinterpret_cast<uint32_t*>(J.flow_fwd), J.cost_fwd});
-        dj.push_back({J.b, J.a, 1, reinterpret_cast<uint32_t*>(J.flow_bwd), J.cost_bwd});
-        cj.push_back({2 * i, 2 * i + 1, J.mask});
+        if (J.flow_bwd2 && !aligned4(J.flow_bwd2)) return fail(c, FF_ERR_ARG, "job %d: flow_bwd2 misaligned", i);
+        const int f0 = (int)dj.size();
+        dj.push_back({J.a, J.b, 0, reinterpret_cast<uint32_t*>(J.flow_fwd), J.cost_fwd, c->prm.rs_radius});
+        dj.push_back({J.b, J.a, 1, reinterpret_cast<uint32_t*>(J.flow_bwd), J.cost_bwd, c->prm.rs_radius});
+        int b2 = -1;
+        if (J.flow_bwd2) {
+            b2 = (int)dj.size();
+            dj.push_back({J.b, J.a, 2, reinterpret_cast<uint32_t*>(J.flow_bwd2), nullptr, c->prm.rs_radius2});
+        }
+        cj.push_back({f0, f0 + 1, J.mask, b2});
     }
     return FF_OK;
 }

@@ -2,7 +2,9 @@
 //
 // Device data layout (all row-major, pixel (x, y) at y*w + x):
 //   image     uint8 [h][w][3]
-//   features  int16 [h][w][48]  96 B per pixel: three 32-B sectors (R, G, B), coefficient u*4+v in each
+//   features  int16 [h][w][48]  96 B per pixel: three 32-B sectors (R, G, B), coefficient u*4+v in each;
+//                               colour-split rows: within row y the descriptors of even x come first, then odd x
+//                               (feat_index), so the pixels of one red-black half-sweep are contiguous
 //   seed desc int8  [N16][64]   coarsest level, C >> 7, zero-padded from 48 to 64 and to a multiple of 16 rows
 //   seed norm int32 [N]         squared norm of the 8-bit descriptor
 //   flow      uint32 [h][w]     packed (dx & 0xffff) | (dy << 16): the int16 [h][w][2] layout of the C-ABI
@@ -39,7 +41,7 @@ void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* 
                        cudaStream_t st);
 int wht_tiles(int w, int h);
 void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st);
-void launch_seed_pack(const int16_t* feat, int n, int n8, int8_t* desc, int32_t* norm, cudaStream_t st);
+void launch_seed_pack(const int16_t* feat, int n, int w, int n8, int8_t* desc, int32_t* norm, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------------------
 // initial matches (exact nearest neighbour at the coarsest level)
@@ -73,7 +75,7 @@ struct SeedTcProblem {
 };
 cudaError_t seed_tc_init_attributes();
 bool seed_tc_encode_map(void* map_host_128b, const void* desc16_dev, int n_pad);
-void launch_seed_pack16(const int16_t* feat, int n, int n_pad, void* desc16, cudaStream_t st);
+void launch_seed_pack16(const int16_t* feat, int n, int w, int n_pad, void* desc16, cudaStream_t st);
 // wait_limit: polls before a wait gives up (then *err_dev is set); withhold: issue no copies (test of the waits)
 void launch_seed_tc(const SeedTcProblem* probs_dev, int n_probs, int total_ctas, int64_t total_pix,
                     uint32_t wait_limit, int withhold, int* err_dev, cudaStream_t st);
@@ -131,8 +133,8 @@ void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n
 // ---------------------------------------------------------------------------------------------------------
 // consistency
 
-void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int eps, uint8_t* mask,
-                        cudaStream_t st);
+void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, const uint32_t* bwd2, int w, int h, int eps,
+                        uint8_t* mask, cudaStream_t st);  // bwd2 may be null
 void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int eps, int s, uint8_t* out,
                      cudaStream_t st);
 
@@ -159,6 +161,11 @@ struct TileChoice {
 
 // ---------------------------------------------------------------------------------------------------------
 // shared device helpers (library only)
+
+// Position of pixel (x, y) in a colour-split feature map of width w.
+__host__ __device__ __forceinline__ int feat_index(int x, int y, int w) {
+    return y * w + ((x & 1) ? ((w + 1) >> 1) + (x >> 1) : (x >> 1));
+}
 
 __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     // lowbias32 integer finaliser (C. Wellons, hash-prospector)

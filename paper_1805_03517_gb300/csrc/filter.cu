@@ -1,4 +1,5 @@
-// filter.cu -- sparsification of the consistent matches (FlowFields++, arXiv 1805.03517, Sec. 3.1; s in Table 3).
+// filter.cu -- outlier filtering of the matches (FlowFields++, arXiv 1805.03517, Sec. 3.1; eps and s in Table 3):
+// the forward/backward consistency check (with one or two inverse fields) and the 3x3 sparsification.
 #include "ff_internal.h"
 
 namespace ff {
@@ -42,6 +43,36 @@ void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int
     const int nbx = (w + 2) / 3, nby = (h + 2) / 3;
     dim3 grid((nbx + 127) / 128, nby);
     k_sparsify<<<grid, 128, 0, st>>>(fwd, bwd, w, h, eps, s, out);
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// forward/backward consistency (Sec. 3.1; eps in Table 3): keep p iff q = p + f(p) is inside the image and
+// (f_x(p) + b_x(q))^2 + (f_y(p) + b_y(q))^2 <= eps^2; with a second inverse field b2, the same must hold for it.
+
+__device__ __forceinline__ bool consistent(uint32_t f, const uint32_t* __restrict__ bwd, int x, int y, int w, int h,
+                                           int eps) {
+    const int fx = flow_x(f), fy = flow_y(f), qx = x + fx, qy = y + fy;
+    if (!in_level(qx, qy, w, h)) return false;
+    const uint32_t b = bwd[qy * w + qx];
+    const long long ex = fx + flow_x(b), ey = fy + flow_y(b);
+    return ex * ex + ey * ey <= (long long)eps * eps;
+}
+
+__global__ void k_consistency(const uint32_t* __restrict__ fwd, const uint32_t* __restrict__ bwd,
+                              const uint32_t* __restrict__ bwd2, int w, int h, int eps, uint8_t* __restrict__ mask) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w * h) return;
+    const int x = i % w, y = i / w;
+    const uint32_t f = fwd[i];
+    bool ok = consistent(f, bwd, x, y, w, h, eps);
+    if (bwd2) ok = ok && consistent(f, bwd2, x, y, w, h, eps);
+    mask[i] = ok ? 1 : 0;
+}
+
+void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, const uint32_t* bwd2, int w, int h, int eps,
+                        uint8_t* mask, cudaStream_t st) {
+    int n = w * h;
+    k_consistency<<<(n + 255) / 256, 256, 0, st>>>(fwd, bwd, bwd2, w, h, eps, mask);
 }
 
 }  // namespace ff

@@ -1,6 +1,5 @@
 // propagate.cu -- per-level refinement of the matches (FlowFields++, arXiv 1805.03517, Sec. 3.1): coarse-to-fine
-// hand-over, propagation towards the four quadrants with random search, and the forward/backward consistency
-// check.
+// hand-over and propagation towards the four quadrants with random search.
 //
 // Schedule of one iteration t at one level (the same schedule the oracle runs): for each quadrant direction
 // d = 0..3 (neighbours left+top, right+top, left+bottom, right+bottom), two half-sweeps over the pixels with
@@ -66,8 +65,8 @@ __device__ __forceinline__ int sad_biased(const uint32_t (&a)[24], const uint32_
 __device__ __forceinline__ int sad_at(const int16_t* __restrict__ fa, const int16_t* __restrict__ fb, int w, int x,
                                       int y, int tx, int ty) {
     uint32_t a[24], b[24];
-    load_desc(fa, y * w + x, a);
-    load_desc(fb, ty * w + tx, b);
+    load_desc(fa, feat_index(x, y, w), a);
+    load_desc(fb, feat_index(tx, ty, w), b);
     bias_desc(a);
     return sad_biased(a, b);
 }
@@ -189,13 +188,13 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
         uint32_t a[24], b1[24], b2[24];
         uint32_t b3[SPEC ? 24 : 1];
         bool e3s = false;
-        load_desc(P.fa, y * w + x, a);
-        if (e1) load_desc(P.fb, (y + flow_y(f1)) * w + x + flow_x(f1), b1);
-        if (e2) load_desc(P.fb, (y + flow_y(f2)) * w + x + flow_x(f2), b2);
+        load_desc(P.fa, feat_index(x, y, w), a);
+        if (e1) load_desc(P.fb, feat_index(x + flow_x(f1), y + flow_y(f1), w), b1);
+        if (e2) load_desc(P.fb, feat_index(x + flow_x(f2), y + flow_y(f2), w), b2);
         if constexpr (SPEC) {
             const int sx = flow_x(cur) + ox, sy = flow_y(cur) + oy;
             e3s = rnd && in_level(x + sx, y + sy, w, h);
-            if (e3s) load_desc(P.fb, (y + sy) * w + x + sx, b3);
+            if (e3s) load_desc(P.fb, feat_index(x + sx, y + sy, w), b3);
         }
         bias_desc(a);
         if (e1) {
@@ -214,11 +213,11 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
                     if (cur == cur0) {
                         s3 = sad_biased(a, b3);  // e3s holds: same target as speculated
                     } else {
-                        load_desc(P.fb, (y + fy) * w + x + fx, b1);
+                        load_desc(P.fb, feat_index(x + fx, y + fy, w), b1);
                         s3 = sad_biased(a, b1);
                     }
                 } else {
-                    load_desc(P.fb, (y + fy) * w + x + fx, b1);
+                    load_desc(P.fb, feat_index(x + fx, y + fy, w), b1);
                     s3 = sad_biased(a, b1);
                 }
                 if (s3 < c) { cur = pack_flow(fx, fy); c = s3; }
@@ -325,33 +324,6 @@ void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n
                       const PropLaunch& L, cudaStream_t st) {
     size_t smem = prop_smem_bytes(L.tw, L.th, L.max_iter);
     prop_kernel(L.threads, L.spec != 0)<<<grid, L.threads, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
-}
-
-// ---------------------------------------------------------------------------------------------------------
-// forward/backward consistency (Sec. 3.1; eps in Table 3): keep p iff q = p + f(p) is inside the image and
-// (f_x(p) + b_x(q))^2 + (f_y(p) + b_y(q))^2 <= eps^2.
-
-__global__ void k_consistency(const uint32_t* __restrict__ fwd, const uint32_t* __restrict__ bwd, int w, int h,
-                              int eps, uint8_t* __restrict__ mask) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w * h) return;
-    int x = i % w, y = i / w;
-    uint32_t f = fwd[i];
-    int fx = flow_x(f), fy = flow_y(f);
-    int qx = x + fx, qy = y + fy;
-    uint8_t m = 0;
-    if (in_level(qx, qy, w, h)) {
-        uint32_t b = bwd[qy * w + qx];
-        long long ex = fx + flow_x(b), ey = fy + flow_y(b);
-        m = (ex * ex + ey * ey <= (long long)eps * eps) ? 1 : 0;
-    }
-    mask[i] = m;
-}
-
-void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int eps, uint8_t* mask,
-                        cudaStream_t st) {
-    int n = w * h;
-    k_consistency<<<(n + 255) / 256, 256, 0, st>>>(fwd, bwd, w, h, eps, mask);
 }
 
 }  // namespace ff

@@ -383,7 +383,7 @@ ff_status tick(ff_server* s) {
         nl++;
     }
     for (const Cons& cs : cons) {
-        launch_consistency(cs.f, cs.b, cs.w, cs.h, s->cv.eps, cs.mask, stm);
+        launch_consistency(cs.f, cs.b, nullptr, cs.w, cs.h, s->cv.eps, cs.mask, stm);
         nl++;
     }
     cudaError_t e = cudaGetLastError();

@@ -34,13 +34,13 @@ class FFError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("n_scales", ctypes.c_int), ("iters", ctypes.c_int), ("patch", ctypes.c_int),
                 ("n_coef", ctypes.c_int), ("rs_radius", ctypes.c_int), ("eps", ctypes.c_int),
-                ("seed", ctypes.c_uint32)]
+                ("seed", ctypes.c_uint32), ("rs_radius2", ctypes.c_int)]
 
 
 class PairJob(ctypes.Structure):
     _fields_ = [("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("flow_fwd", ctypes.c_void_p),
                 ("flow_bwd", ctypes.c_void_p), ("cost_fwd", ctypes.c_void_p), ("cost_bwd", ctypes.c_void_p),
-                ("mask", ctypes.c_void_p)]
+                ("mask", ctypes.c_void_p), ("flow_bwd2", ctypes.c_void_p)]
 
 
 class Request(ctypes.Structure):
@@ -282,7 +282,7 @@ def to_params(p) -> Params:
     if isinstance(p, Params):
         return p
     return Params(p.n_scales, p.iters, getattr(p, "patch", 8), getattr(p, "n_coef", 16), p.rs_radius, p.eps,
-                  p.seed & 0xFFFFFFFF)
+                  p.seed & 0xFFFFFFFF, getattr(p, "rs_radius2", 4))
 
 
 @dataclass
@@ -330,13 +330,18 @@ class Matcher:
         ff_pyr_release(self.ctx, pyr.handle)
 
     def level_features(self, pyr: Pyramid, level: int):
-        """Copy of the int16 [h][w][48] features of one level (for inspection and tests)."""
+        """Copy of the features of one level as int16 [h][w][48] in plain row order (the library stores rows
+        colour-split: even x first, then odd x)."""
         w, h = ff_pyr_level_dims(pyr.handle, level)
         ptr = ff_pyr_features(pyr.handle, level)
-        out = self._empty((h, w, 48), self.torch.int16)
+        split = self._empty((h, w, 48), self.torch.int16)
         self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
         src = _DevView(ptr, h * w * 96)
-        out.view(-1).view(self.torch.uint8).copy_(self.torch.as_tensor(src, device=self.device))
+        split.view(-1).view(self.torch.uint8).copy_(self.torch.as_tensor(src, device=self.device))
+        out = self.torch.empty_like(split)
+        ne = (w + 1) // 2
+        out[:, 0::2] = split[:, :ne]
+        out[:, 1::2] = split[:, ne:]
         return out
 
     def match_pair(self, a: Pyramid, b: Pyramid, dir: int = 0, with_cost: bool = True):
@@ -345,12 +350,14 @@ class Matcher:
         ff_match_pair(self.ctx, a.handle, b.handle, dir, flow.data_ptr(), cost.data_ptr() if cost is not None else None)
         return flow, cost
 
-    def alloc_outputs(self, pairs, with_cost=True):
+    def alloc_outputs(self, pairs, with_cost=True, second_check=False):
         outs = []
         for a, _ in pairs:
             o = {"flow_fwd": self._empty((a.h, a.w, 2), self.torch.int16),
                  "flow_bwd": self._empty((a.h, a.w, 2), self.torch.int16),
                  "mask": self._empty((a.h, a.w), self.torch.uint8)}
+            if second_check:
+                o["flow_bwd2"] = self._empty((a.h, a.w, 2), self.torch.int16)
             if with_cost:
                 o["cost_fwd"] = self._empty((a.h, a.w), self.torch.int32)
                 o["cost_bwd"] = self._empty((a.h, a.w), self.torch.int32)
@@ -363,13 +370,15 @@ class Matcher:
         for (a, b), o in zip(pairs, outs):
             jobs.append(PairJob(a.handle, b.handle, o["flow_fwd"].data_ptr(), o["flow_bwd"].data_ptr(),
                                 o["cost_fwd"].data_ptr() if "cost_fwd" in o else None,
-                                o["cost_bwd"].data_ptr() if "cost_bwd" in o else None, o["mask"].data_ptr()))
+                                o["cost_bwd"].data_ptr() if "cost_bwd" in o else None, o["mask"].data_ptr(),
+                                o["flow_bwd2"].data_ptr() if "flow_bwd2" in o else None))
         return jobs
 
-    def match_batch(self, pairs, outs=None, with_cost=True):
-        """pairs: list of (Pyramid a, Pyramid b).  Returns (or fills) one dict of outputs per pair."""
+    def match_batch(self, pairs, outs=None, with_cost=True, second_check=False):
+        """pairs: list of (Pyramid a, Pyramid b).  Returns (or fills) one dict of outputs per pair; with
+        second_check, also the second inverse field 'flow_bwd2', and the mask applies both checks."""
         if outs is None:
-            outs = self.alloc_outputs(pairs, with_cost)
+            outs = self.alloc_outputs(pairs, with_cost, second_check)
         ff_match_batch(self.ctx, self._jobs(pairs, outs))
         return outs
 

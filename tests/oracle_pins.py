@@ -478,6 +478,27 @@ def check_sparsify(o):
             assert np.all(got <= o.consistency(fwd, bwd, eps))
 
 
+def check_second_consistency(o):
+    """Two checks (Sec. 3.1): the first inverse field and forward field equal the single-check stage, the second
+    inverse field is the inverse matching with radius rs_radius2 and direction id 2, the mask is the AND."""
+    import oracle as _o
+
+    h, w, L, T = 30, 40, 2, 2
+    ia = smooth_texture(600, h, w)
+    ib = shifted(ia, 2, -1, 601)
+    ib[5:15, 10:25] = smooth_texture(602, 10, 15)
+    prm = _o.params(n_scales=L, iters=T, rs_radius=2, eps=1, seed=5)
+    ff, fb, fb2, mask = o.match_bidir2(ia, ib, prm, 4)
+    one = o.match_bidir(ia, ib, prm)
+    assert np.array_equal(ff, one[0]) and np.array_equal(fb, one[1])
+    fa = [o.wht(x) for x in o.pyramid(ia, L)]
+    fbb = [o.wht(x) for x in o.pyramid(ib, L)]
+    want2, _ = o.match_dir(fbb, fa, _o.params(n_scales=L, iters=T, rs_radius=4, eps=1, seed=5), 2)
+    assert np.array_equal(fb2, want2)
+    assert not np.array_equal(fb2, fb)  # different parameters give a different inverse field here
+    assert np.array_equal(mask, one[4] & o.consistency(ff, fb2, 1))
+
+
 def check_pipeline_composition(o):
     """The whole stage equals its steps composed in the order of Sec. 3.1 (pyramid, WHT, seed at the coarsest
     level, per level hand-over + propagation keyed by (direction, level), inverse field with the frames
@@ -524,5 +545,6 @@ ALL_CHECKS = [
     check_translation,
     check_consistency,
     check_sparsify,
+    check_second_consistency,
     check_pipeline_composition,
 ]

@@ -256,3 +256,21 @@ def test_sparsify_parity(lib_built):
         got = M.sparsify(torch.from_numpy(ff_).cuda(), torch.from_numpy(fb_).cuda(), 1, s)
         M.sync()
         assert np.array_equal(got.cpu().numpy(), o.sparsify(ff_, fb_, 1, s))
+
+
+@pytest.mark.parametrize("h,w,L,T", [(48, 64, 3, 2), (96, 128, 3, 4), (70, 133, 2, 3)])
+def test_two_consistency_checks(lib_built, h, w, L, T):
+    """Two checks of Sec. 3.1: a second inverse field with its own radius and random stream; mask = both pass."""
+    prm = mp(L, T)
+    a = P.smooth_texture(900 + h, h, w)
+    b = P.shifted(a, 3, -2, 901 + h)
+    b[h // 4:h // 2, w // 3:w // 2] = P.smooth_texture(902, h // 2 - h // 4, w // 2 - w // 3)
+    M = matcher(prm)
+    pa, pb = M.features(torch.from_numpy(a).cuda()), M.features(torch.from_numpy(b).cuda())
+    out = M.match_batch([(pa, pb)], second_check=True)[0]
+    M.sync()
+    want = oracle.default().match_bidir2(a, b, G.oracle_params(prm), prm.rs_radius2)
+    for k, wv in zip(("flow_fwd", "flow_bwd", "flow_bwd2", "mask"), want):
+        assert np.array_equal(out[k].cpu().numpy(), wv), k
+    M.release(pa)
+    M.release(pb)

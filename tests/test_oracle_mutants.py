@@ -41,6 +41,10 @@ MUTANTS = {
     "inverse_same_direction_key": ("ws, hs, prm, 1,", "ws, hs, prm, 0,"),
     "consistency_strict": ("<= (long)eps * eps", "< (long)eps * eps"),
     "consistency_sign": ("long ex = fx + bwd[2 * q]", "long ex = fx - bwd[2 * q]"),
+    "second_check_same_stream": ("ws, hs, &p2, 2,", "ws, hs, &p2, 1,"),
+    "second_check_first_inverse_key": ("ws, hs, p1, 1,", "ws, hs, p1, 0,"),
+    "second_check_radius_ignored": ("p2.rs_radius = rs_radius2;", "p2.rs_radius = prm->rs_radius;"),
+    "second_check_ignored": ("mask[p] = (uint8_t)(mask[p] & m2[p]);", "mask[p] = (uint8_t)(mask[p] | m2[p]);"),
     "sparsify_error_sign": ("long ex = (long)fx + bwd[2 * q]", "long ex = (long)fx - bwd[2 * q]"),
     "sparsify_last_tie_wins": ("if (best_p < 0 || e < best_e) {", "if (best_p < 0 || e <= best_e) {"),
     "sparsify_count_off": ("if (count >= s && best_p >= 0)", "if (count > s && best_p >= 0)"),
