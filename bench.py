@@ -48,6 +48,16 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_ranks(torch, dist, dev, ms_local, px_per_step, world):
+    """Weak scaling over replicas: the slowest rank's step time, and the pixels all ranks matched per second.
+    Returns (ms_per_step over ranks, Mpx/s of the whole job)."""
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, px_per_step * world / (ms / 1000.0) / 1e6
+
+
 def propagate_traffic():
     """DRAM bytes per k_propagate launch from the committed ncu capture, if the kernel source is unchanged."""
     import hashlib
@@ -362,12 +372,7 @@ def main():
     s1 = M.stats()
     if dist:
         dist.barrier()
-    ms = sum(times) / len(times)
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms = float(t_max.item())
-    value = px_per_step * world / (ms / 1000.0) / 1e6
+    ms, value = aggregate_ranks(torch, dist, dev, sum(times) / len(times), px_per_step, world)
     launches = int(s1["kernel_launches"] - s0["kernel_launches"])
 
     # end to end through the public API: pinned host frames in, flows and mask out, copies inside the timing

@@ -34,8 +34,10 @@ void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* 
 // sequency-ordered Walsh functions are sums of the pair sums s01, s23, s45, s67 with signs
 //   W0 = + + + +,  W1 = + + - -,  W2 = + - - +,  W3 = + - + -
 // so the transform is separable: a row pass (4 outputs per patch row) then a column pass.
-// CTA = 32x8 output pixels; its 39x15 input window (with the clamped halo) is staged in shared memory.
-constexpr int kWtx = 32, kWty = 8;
+// CTA = 32x16 output pixels: its 39x23 input window (clamped halo) is staged in shared memory, the row pass is
+// computed once per (window row, output column, channel) into shared memory (|value| <= 8*255 fits int16), and
+// each thread then runs the column pass for two output pixels.
+constexpr int kWtx = 32, kWty = 16;
 constexpr int kWinX = kWtx + 7, kWinY = kWty + 7;
 
 __device__ __forceinline__ void walsh4(int a0, int a1, int a2, int a3, int a4, int a5, int a6, int a7, int& c0,
@@ -50,6 +52,7 @@ __device__ __forceinline__ void walsh4(int a0, int a1, int a2, int a3, int a4, i
 
 __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
     __shared__ uint8_t win[3][kWinY][kWinX];
+    __shared__ short4 rowt[3][kWinY][kWtx];  // row pass: 4 horizontal Walsh sums per window row and output column
     int b = blockIdx.x, li = 0;
     while (li + 1 < args.n && b >= args.lv[li + 1].tile_base) li++;
     const WhtLevel L = args.lv[li];
@@ -65,39 +68,46 @@ __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
         win[2][r][c] = px[2];
     }
     __syncthreads();
-    int lx = threadIdx.x % kWtx, ly = threadIdx.x / kWtx;
-    int x = tx0 + lx, y = ty0 + ly;
-    if (x >= L.w || y >= L.h) return;
-    uint32_t out[24];
-#pragma unroll
-    for (int ch = 0; ch < 3; ch++) {
-        int R[8][4];
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const uint8_t* row = &win[ch][ly + i][lx];
-            walsh4(row[0], row[1], row[2], row[3], row[4], row[5], row[6], row[7], R[i][0], R[i][1], R[i][2],
-                   R[i][3]);
-        }
-        int C[4][4];
-#pragma unroll
-        for (int v = 0; v < 4; v++)
-            walsh4(R[0][v], R[1][v], R[2][v], R[3][v], R[4][v], R[5][v], R[6][v], R[7][v], C[0][v], C[1][v],
-                   C[2][v], C[3][v]);
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-#pragma unroll
-            for (int v = 0; v < 4; v += 2)
-                out[ch * 8 + u * 2 + v / 2] = (uint32_t)(C[u][v] & 0xffff) | ((uint32_t)C[u][v + 1] << 16);
+    for (int i = threadIdx.x; i < 3 * kWinY * kWtx; i += blockDim.x) {
+        const int ch = i / (kWinY * kWtx), rem = i - ch * kWinY * kWtx, r = rem / kWtx, c = rem - r * kWtx;
+        const uint8_t* row = &win[ch][r][c];
+        int v0, v1, v2, v3;
+        walsh4(row[0], row[1], row[2], row[3], row[4], row[5], row[6], row[7], v0, v1, v2, v3);
+        rowt[ch][r][c] = make_short4((short)v0, (short)v1, (short)v2, (short)v3);
     }
-    uint4* dst = reinterpret_cast<uint4*>(L.feat + (size_t)feat_index(x, y, L.w) * kNF);
+    __syncthreads();
+    const int lx = threadIdx.x % kWtx;
+    for (int ly = threadIdx.x / kWtx; ly < kWty; ly += blockDim.x / kWtx) {
+        const int x = tx0 + lx, y = ty0 + ly;
+        if (x >= L.w || y >= L.h) continue;
+        uint32_t out[24];
 #pragma unroll
-    for (int k = 0; k < 6; k++) dst[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+        for (int ch = 0; ch < 3; ch++) {
+            short4 R[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) R[i] = rowt[ch][ly + i][lx];
+            int C[4][4];
+            walsh4(R[0].x, R[1].x, R[2].x, R[3].x, R[4].x, R[5].x, R[6].x, R[7].x, C[0][0], C[1][0], C[2][0], C[3][0]);
+            walsh4(R[0].y, R[1].y, R[2].y, R[3].y, R[4].y, R[5].y, R[6].y, R[7].y, C[0][1], C[1][1], C[2][1], C[3][1]);
+            walsh4(R[0].z, R[1].z, R[2].z, R[3].z, R[4].z, R[5].z, R[6].z, R[7].z, C[0][2], C[1][2], C[2][2], C[3][2]);
+            walsh4(R[0].w, R[1].w, R[2].w, R[3].w, R[4].w, R[5].w, R[6].w, R[7].w, C[0][3], C[1][3], C[2][3], C[3][3]);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int v = 0; v < 4; v += 2)
+                    out[ch * 8 + u * 2 + v / 2] = (uint32_t)(C[u][v] & 0xffff) | ((uint32_t)C[u][v + 1] << 16);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(L.feat + (size_t)feat_index(x, y, L.w) * kNF);
+#pragma unroll
+        for (int k = 0; k < 6; k++) dst[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+    }
 }
 
-int wht_tiles(int w, int h) { return ((w + kWtx - 1) / kWtx) * ((h + kWty - 1) / kWty); }
+int wht_tiles_x(int w) { return (w + kWtx - 1) / kWtx; }
+int wht_tiles(int w, int h) { return wht_tiles_x(w) * ((h + kWty - 1) / kWty); }
 
 void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st) {
-    k_wht<<<total_tiles, kWtx * kWty, 0, st>>>(a);
+    k_wht<<<total_tiles, 256, 0, st>>>(a);
 }
 
 // 8-bit descriptor of the coarsest level: C >> 7 (arithmetic, i.e. floor(C / 128), in [-128, 127]) for the 48

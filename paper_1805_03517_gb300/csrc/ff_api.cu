@@ -974,7 +974,7 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
         lv.w = P->ws[s];
         lv.h = P->hs[s];
         lv.feat = P->feat[s];
-        lv.tiles_x = (P->ws[s] + 31) / 32;
+        lv.tiles_x = wht_tiles_x(P->ws[s]);
         lv.tile_base = tiles;
         tiles += wht_tiles(P->ws[s], P->hs[s]);
     }

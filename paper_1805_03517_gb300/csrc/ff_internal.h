@@ -39,6 +39,7 @@ struct WhtArgs {
 
 void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* dst, int dw, int dh,
                        cudaStream_t st);
+int wht_tiles_x(int w);
 int wht_tiles(int w, int h);
 void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st);
 void launch_seed_pack(const int16_t* feat, int n, int w, int n8, int8_t* desc, int32_t* norm, cudaStream_t st);
