@@ -36,6 +36,7 @@ class Params(ctypes.Structure):
         ("rs_radius", ctypes.c_int),
         ("eps", ctypes.c_int),
         ("seed", ctypes.c_uint32),
+        ("cost", ctypes.c_int),
     ]
 
 
@@ -93,6 +94,14 @@ def _declare(lib):
     lib.ffo_consistency.restype = None
     lib.ffo_match_bidir2.argtypes = [u8p, u8p, c_int, c_int, ctypes.POINTER(Params), c_int, i16p, i16p, i16p, u8p]
     lib.ffo_match_bidir2.restype = c_int
+    u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+    lib.ffo_census.argtypes = [u8p, c_int, c_int, u64p]
+    lib.ffo_census.restype = None
+    lib.ffo_hamming.argtypes = [u64p, u64p, c_int, c_int, c_int, c_int, c_int, c_int]
+    lib.ffo_hamming.restype = ctypes.c_int32
+    lib.ffo_propagate_census.argtypes = [u64p, u64p, c_int, c_int, i16p, i32p, c_int, c_int, c_u32, c_int, c_int,
+                                         c_long]
+    lib.ffo_propagate_census.restype = c_long
     lib.ffo_sparsify.argtypes = [i16p, i16p, c_int, c_int, c_int, c_int, u8p]
     lib.ffo_sparsify.restype = None
     lib.ffo_match_bidir.argtypes = [u8p, u8p, c_int, c_int, ctypes.POINTER(Params), i16p, i16p, i32p, i32p, u8p]
@@ -225,6 +234,28 @@ class Oracle:
             raise RuntimeError(f"ffo_match_bidir2 failed: {rc}")
         return ff, fb, fb2, mask
 
+    def census(self, img):
+        """uint64 [h][w][3]: the 48-bit Census pattern of every pixel and channel."""
+        img = np.ascontiguousarray(img, dtype=np.uint8)
+        h, w, _ = img.shape
+        out = np.empty((h, w, 3), np.uint64)
+        self.L.ffo_census(img, w, h, out)
+        return out
+
+    def hamming(self, ca, cb, x, y, fx, fy):
+        h, w, _ = ca.shape
+        return int(self.L.ffo_hamming(_u64(ca), _u64(cb), w, h, x, y, fx, fy))
+
+    def propagate_census(self, ca, cb, flow, cost, iters, rs_radius, seed, dir, level, max_halfsweeps=-1):
+        h, w, _ = ca.shape
+        flow = np.array(flow, dtype=np.int16, order="C", copy=True)
+        cost = np.array(cost, dtype=np.int32, order="C", copy=True)
+        n = self.L.ffo_propagate_census(_u64(ca), _u64(cb), w, h, flow, cost, iters, rs_radius, seed & 0xFFFFFFFF,
+                                        dir, level, max_halfsweeps)
+        if n < 0:
+            raise MemoryError("ffo_propagate_census")
+        return flow, cost
+
     def sparsify(self, fwd, bwd, eps, s):
         h, w, _ = fwd.shape
         out = np.empty((h, w), np.uint8)
@@ -251,8 +282,15 @@ def _i16(a):
     return np.ascontiguousarray(a, dtype=np.int16)
 
 
-def params(n_scales, iters, rs_radius=2, eps=1, seed=0) -> Params:
-    return Params(n_scales, iters, rs_radius, eps, seed & 0xFFFFFFFF)
+def _u64(a):
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+COST_WHT_SAD, COST_CENSUS = 0, 1
+
+
+def params(n_scales, iters, rs_radius=2, eps=1, seed=0, cost=COST_WHT_SAD) -> Params:
+    return Params(n_scales, iters, rs_radius, eps, seed & 0xFFFFFFFF, cost)
 
 
 _default = None

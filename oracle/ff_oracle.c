@@ -132,6 +132,62 @@ int32_t ffo_sad(const int16_t* fa, const int16_t* fb, int w, int h, int x, int y
     return s;
 }
 
+/* Census transform (Sec. 3.1: binary patterns of the Census transform in a 7x7 patch for all colour channels).
+ * Reading: the RGB channels stand in for CIELab (integer, exact); bit k of channel c is 1 iff the k-th neighbour
+ * -- row-major over rows y-3..y+3 and columns x-3..x+3, centre skipped, edge pixels repeated -- is strictly darker
+ * than the centre pixel.  desc[(y*w + x)*3 + c] holds the 48 bits of channel c. */
+void ffo_census(const uint8_t* img, int w, int h, uint64_t* desc) {
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++)
+            for (int c = 0; c < 3; c++) {
+                int centre = img[((long)y * w + x) * 3 + c];
+                uint64_t bits = 0;
+                int k = 0;
+                for (int dy = -3; dy <= 3; dy++)
+                    for (int dx = -3; dx <= 3; dx++) {
+                        if (dy == 0 && dx == 0) continue;
+                        int v = img[((long)clampi(y + dy, 0, h - 1) * w + clampi(x + dx, 0, w - 1)) * 3 + c];
+                        if (v < centre) bits |= (uint64_t)1 << k;
+                        k++;
+                    }
+                desc[((long)y * w + x) * 3 + c] = bits;
+            }
+}
+
+static int popcount64(uint64_t v) {
+    int n = 0;
+    while (v) {
+        v &= v - 1;
+        n++;
+    }
+    return n;
+}
+
+/* Census matching cost (Sec. 3.1): Hamming distance of the three 48-bit patterns of pixel (x, y) in frame A
+ * and (x+fx, y+fy) in frame B; -1 when the target lies outside the level. */
+int32_t ffo_hamming(const uint64_t* ca, const uint64_t* cb, int w, int h, int x, int y, int fx, int fy) {
+    int qx = x + fx, qy = y + fy;
+    if (qx < 0 || qx >= w || qy < 0 || qy >= h) return -1;
+    int32_t s = 0;
+    for (int c = 0; c < 3; c++) s += popcount64(ca[((long)y * w + x) * 3 + c] ^ cb[((long)qy * w + qx) * 3 + c]);
+    return s;
+}
+
+/* The descriptors a level is matched with: WHT coefficients (cost = SAD) or, if ca is set, Census patterns
+ * (cost = Hamming distance). */
+typedef struct {
+    const int16_t* fa;
+    const int16_t* fb;
+    const uint64_t* ca;
+    const uint64_t* cb;
+    int w, h;
+} costsrc;
+
+static int32_t cost_of(const costsrc* cs, int x, int y, int fx, int fy) {
+    return cs->ca ? ffo_hamming(cs->ca, cs->cb, cs->w, cs->h, x, y, fx, fy)
+                  : ffo_sad(cs->fa, cs->fb, cs->w, cs->h, x, y, fx, fy);
+}
+
 /* floor(c / 128), the arithmetic shift C >> 7 written without relying on signed shifts. */
 static int quant7(int c) { return c >= 0 ? c / 128 : -((-c + 127) / 128); }
 
@@ -161,20 +217,25 @@ void ffo_seed(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* flow,
     }
 }
 
-/* cost(p) = SAD of p's current flow; every flow handed in must point inside the level. */
-void ffo_init_cost(const int16_t* fa, const int16_t* fb, int w, int h, const int16_t* flow, int32_t* cost) {
-    for (int y = 0; y < h; y++)
-        for (int x = 0; x < w; x++) {
-            long p = (long)y * w + x;
-            cost[p] = ffo_sad(fa, fb, w, h, x, y, flow[2 * p], flow[2 * p + 1]);
+/* cost(p) = matching cost of p's current flow; every flow handed in must point inside the level. */
+static void init_cost_c(const costsrc* cs, const int16_t* flow, int32_t* cost) {
+    for (int y = 0; y < cs->h; y++)
+        for (int x = 0; x < cs->w; x++) {
+            long p = (long)y * cs->w + x;
+            cost[p] = cost_of(cs, x, y, flow[2 * p], flow[2 * p + 1]);
         }
+}
+
+void ffo_init_cost(const int16_t* fa, const int16_t* fb, int w, int h, const int16_t* flow, int32_t* cost) {
+    costsrc cs = {fa, fb, NULL, NULL, w, h};
+    init_cost_c(&cs, flow, cost);
 }
 
 /* Coarse-to-fine hand-over (Sec. 3): a pixel starts from twice the flow of its parent pixel one level up,
  * parent = (min(x/2, wc-1), min(y/2, hc-1)), and its cost is recomputed at the finer level.  Such a flow
  * always lands inside the finer level; returns -2 if one does not (a broken assertion). */
-int ffo_upsample(const int16_t* fa, const int16_t* fb, int w, int h, const int16_t* flow_coarse, int wc, int hc,
-                 int16_t* flow, int32_t* cost) {
+static int upsample_c(const costsrc* cs, const int16_t* flow_coarse, int wc, int hc, int16_t* flow, int32_t* cost) {
+    const int w = cs->w, h = cs->h;
     for (int y = 0; y < h; y++)
         for (int x = 0; x < w; x++) {
             int px = mini(x / 2, wc - 1), py = mini(y / 2, hc - 1);
@@ -182,10 +243,16 @@ int ffo_upsample(const int16_t* fa, const int16_t* fb, int w, int h, const int16
             int fx = 2 * flow_coarse[2 * pc], fy = 2 * flow_coarse[2 * pc + 1];
             flow[2 * p] = (int16_t)fx;
             flow[2 * p + 1] = (int16_t)fy;
-            cost[p] = ffo_sad(fa, fb, w, h, x, y, fx, fy);
+            cost[p] = cost_of(cs, x, y, fx, fy);
             if (cost[p] < 0) return -2;
         }
     return 0;
+}
+
+int ffo_upsample(const int16_t* fa, const int16_t* fb, int w, int h, const int16_t* flow_coarse, int wc, int hc,
+                 int16_t* flow, int32_t* cost) {
+    costsrc cs = {fa, fb, NULL, NULL, w, h};
+    return upsample_c(&cs, flow_coarse, wc, hc, flow, cost);
 }
 
 /* The two neighbours a pixel looks at in propagation direction d (one direction per quadrant, Sec. 3.1).
@@ -206,8 +273,9 @@ static void neighbours(int d, int x, int y, int* n1x, int* n1y, int* n2x, int* n
  * random offset (ox, oy), each component uniform in [-R, R] from the hash, skipped if (0, 0).  A candidate
  * replaces the current flow iff its cost is strictly lower; candidates outside the level are rejected.
  * Stops after max_halfsweeps half-sweeps if max_halfsweeps >= 0; returns the number run. */
-long ffo_propagate(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* flow, int32_t* cost, int iters,
-                   int rs_radius, uint32_t seed, int dir, int level, long max_halfsweeps) {
+static long propagate_c(const costsrc* cs, int16_t* flow, int32_t* cost, int iters, int rs_radius, uint32_t seed,
+                        int dir, int level, long max_halfsweeps) {
+    const int w = cs->w, h = cs->h;
     long n = (long)w * h, done = 0;
     int16_t* prev = (int16_t*)malloc(sizeof(int16_t) * 2 * (size_t)n);
     if (!prev) return -1;
@@ -232,7 +300,7 @@ long ffo_propagate(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* 
                             if (nx[k] < 0 || nx[k] >= w || ny[k] < 0 || ny[k] >= h) continue;
                             long q = (long)ny[k] * w + nx[k];
                             int cx = prev[2 * q], cy = prev[2 * q + 1];
-                            int32_t cc = ffo_sad(fa, fb, w, h, x, y, cx, cy);
+                            int32_t cc = cost_of(cs, x, y, cx, cy);
                             if (cc >= 0 && cc < c) {
                                 fx = cx;
                                 fy = cy;
@@ -243,7 +311,7 @@ long ffo_propagate(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* 
                             int ox = (int)(ffo_hash(seed, dir, level, t, d, x, y, 0) % (uint32_t)span) - rs_radius;
                             int oy = (int)(ffo_hash(seed, dir, level, t, d, x, y, 1) % (uint32_t)span) - rs_radius;
                             if (ox != 0 || oy != 0) {
-                                int32_t cc = ffo_sad(fa, fb, w, h, x, y, fx + ox, fy + oy);
+                                int32_t cc = cost_of(cs, x, y, fx + ox, fy + oy);
                                 if (cc >= 0 && cc < c) {
                                     fx += ox;
                                     fy += oy;
@@ -264,12 +332,25 @@ long ffo_propagate(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* 
     return done;
 }
 
+long ffo_propagate(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* flow, int32_t* cost, int iters,
+                   int rs_radius, uint32_t seed, int dir, int level, long max_halfsweeps) {
+    costsrc cs = {fa, fb, NULL, NULL, w, h};
+    return propagate_c(&cs, flow, cost, iters, rs_radius, seed, dir, level, max_halfsweeps);
+}
+
+long ffo_propagate_census(const uint64_t* ca, const uint64_t* cb, int w, int h, int16_t* flow, int32_t* cost,
+                          int iters, int rs_radius, uint32_t seed, int dir, int level, long max_halfsweeps) {
+    costsrc cs = {NULL, NULL, ca, cb, w, h};
+    return propagate_c(&cs, flow, cost, iters, rs_radius, seed, dir, level, max_halfsweeps);
+}
+
 /* One matching direction over a prepared pyramid of features (Sec. 3.1): exact seed at the coarsest level,
  * then for every level from coarse to fine: hand-over from the level above (except the coarsest), cost,
  * propagation with random search.  Writes the level-0 flow and cost.  feat_a/feat_b[s] are the level-s
  * feature maps of the source and target frames; both frames have the sizes ws[s] x hs[s]. */
-int ffo_match_dir(const int16_t* const* feat_a, const int16_t* const* feat_b, const int* ws, const int* hs,
-                  const ffo_params* prm, int dir, int16_t* flow, int32_t* cost) {
+static int match_dir_c(const int16_t* const* feat_a, const int16_t* const* feat_b, const uint64_t* const* cen_a,
+                       const uint64_t* const* cen_b, const int* ws, const int* hs, const ffo_params* prm, int dir,
+                       int16_t* flow, int32_t* cost) {
     int L = prm->n_scales;
     int16_t* f_prev = NULL;
     int w_prev = 0, h_prev = 0;
@@ -284,16 +365,17 @@ int ffo_match_dir(const int16_t* const* feat_a, const int16_t* const* feat_b, co
             free(f_prev);
             return -1;
         }
+        costsrc cs = {feat_a[s], feat_b[s], cen_a ? cen_a[s] : NULL, cen_b ? cen_b[s] : NULL, w, h};
         if (s == L - 1) {
-            ffo_seed(feat_a[s], feat_b[s], w, h, f, c);
-            ffo_init_cost(feat_a[s], feat_b[s], w, h, f, c);
-        } else if (ffo_upsample(feat_a[s], feat_b[s], w, h, f_prev, w_prev, h_prev, f, c) != 0) {
+            ffo_seed(feat_a[s], feat_b[s], w, h, f, c);  /* initial matches on the WHT descriptors in both modes */
+            init_cost_c(&cs, f, c);
+        } else if (upsample_c(&cs, f_prev, w_prev, h_prev, f, c) != 0) {
             free(f);
             free(c);
             free(f_prev);
             return -2;
         }
-        ffo_propagate(feat_a[s], feat_b[s], w, h, f, c, prm->iters, prm->rs_radius, prm->seed, dir, s, -1);
+        propagate_c(&cs, f, c, prm->iters, prm->rs_radius, prm->seed, dir, s, -1);
         free(f_prev);
         f_prev = f;
         w_prev = w;
@@ -306,6 +388,17 @@ int ffo_match_dir(const int16_t* const* feat_a, const int16_t* const* feat_b, co
     }
     free(f_prev);
     return 0;
+}
+
+int ffo_match_dir(const int16_t* const* feat_a, const int16_t* const* feat_b, const int* ws, const int* hs,
+                  const ffo_params* prm, int dir, int16_t* flow, int32_t* cost) {
+    return match_dir_c(feat_a, feat_b, NULL, NULL, ws, hs, prm, dir, flow, cost);
+}
+
+int ffo_match_dir_census(const int16_t* const* feat_a, const int16_t* const* feat_b, const uint64_t* const* cen_a,
+                         const uint64_t* const* cen_b, const int* ws, const int* hs, const ffo_params* prm, int dir,
+                         int16_t* flow, int32_t* cost) {
+    return match_dir_c(feat_a, feat_b, cen_a, cen_b, ws, hs, prm, dir, flow, cost);
 }
 
 /* Forward/backward consistency check (Sec. 3.1; eps in Table 3).  p is kept iff q = p + f(p) lies in the
@@ -326,58 +419,68 @@ void ffo_consistency(const int16_t* fwd, const int16_t* bwd, int w, int h, int e
         }
 }
 
+/* Pyramid, WHT features and (for the Census cost) Census patterns of one frame, all levels. */
+static int frame_features(const uint8_t* rgb, int L, const int* ws, const int* hs, int census, uint8_t** img,
+                          int16_t** feat, uint64_t** cen) {
+    for (int s = 0; s < L; s++) {
+        long ns = (long)ws[s] * hs[s];
+        img[s] = (uint8_t*)malloc((size_t)ns * 3);
+        feat[s] = (int16_t*)malloc((size_t)ns * FFO_NF * sizeof(int16_t));
+        cen[s] = census ? (uint64_t*)malloc((size_t)ns * 3 * sizeof(uint64_t)) : NULL;
+        if (!img[s] || !feat[s] || (census && !cen[s])) return -1;
+        if (s == 0)
+            memcpy(img[s], rgb, (size_t)ns * 3);
+        else
+            ffo_downsample(img[s - 1], ws[s - 1], hs[s - 1], img[s]);
+        ffo_wht(img[s], ws[s], hs[s], feat[s]);
+        if (census) ffo_census(img[s], ws[s], hs[s], cen[s]);
+    }
+    return 0;
+}
+
+static void free_features(int L, uint8_t** img, int16_t** feat, uint64_t** cen) {
+    for (int s = 0; s < L; s++) {
+        free(img[s]);
+        free(feat[s]);
+        free(cen[s]);
+    }
+}
+
 /* Two consistency checks (Sec. 3.1): the forward field is compared with two inverse fields computed with
  * different matching parameters, and kept only if it passes both.  Reading: the second inverse field uses the
  * random-search radius rs_radius2 and its own random stream (direction id 2); everything else is shared. */
 int ffo_match_bidir2(const uint8_t* rgb_a, const uint8_t* rgb_b, int w, int h, const ffo_params* prm, int rs_radius2,
                      int16_t* flow_fwd, int16_t* flow_bwd, int16_t* flow_bwd2, uint8_t* mask) {
     long n = (long)w * h;
+    int L = prm->n_scales, rc = 0;
+    int ws[16], hs[16];
+    if (L < 1 || L > 16 || ffo_level_dims(w, h, L, ws, hs) != 0) return -1;
     int32_t* cf = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     int32_t* cb = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
     uint8_t* m2 = (uint8_t*)malloc((size_t)n);
-    int L = prm->n_scales, rc = 0;
-    int ws[16], hs[16];
-    if (!cf || !cb || !m2 || L < 1 || L > 16 || ffo_level_dims(w, h, L, ws, hs) != 0) rc = -1;
-    uint8_t* img[2][16];
-    int16_t* feat[2][16];
-    memset(img, 0, sizeof img);
-    memset(feat, 0, sizeof feat);
-    for (int f = 0; f < 2 && rc == 0; f++) {
-        const uint8_t* src = f == 0 ? rgb_a : rgb_b;
-        for (int s = 0; s < L; s++) {
-            long ns = (long)ws[s] * hs[s];
-            img[f][s] = (uint8_t*)malloc((size_t)ns * 3);
-            feat[f][s] = (int16_t*)malloc((size_t)ns * FFO_NF * sizeof(int16_t));
-            if (!img[f][s] || !feat[f][s]) {
-                rc = -1;
-                break;
-            }
-            if (s == 0)
-                memcpy(img[f][s], src, (size_t)ns * 3);
-            else
-                ffo_downsample(img[f][s - 1], ws[s - 1], hs[s - 1], img[f][s]);
-            ffo_wht(img[f][s], ws[s], hs[s], feat[f][s]);
-        }
-    }
+    uint8_t* img[2][16] = {{0}};
+    int16_t* feat[2][16] = {{0}};
+    uint64_t* cen[2][16] = {{0}};
+    if (!cf || !cb || !m2) rc = -1;
+    for (int f = 0; f < 2 && rc == 0; f++)
+        rc = frame_features(f == 0 ? rgb_a : rgb_b, L, ws, hs, prm->cost, img[f], feat[f], cen[f]);
+    const uint64_t* const* ca = prm->cost ? (const uint64_t* const*)cen[0] : NULL;
+    const uint64_t* const* cb2 = prm->cost ? (const uint64_t* const*)cen[1] : NULL;
     const ffo_params* p1 = prm;
     ffo_params p2 = *prm;
     p2.rs_radius = rs_radius2;
-    if (rc == 0) rc = ffo_match_dir((const int16_t* const*)feat[0], (const int16_t* const*)feat[1], ws, hs, p1, 0,
-                                    flow_fwd, cf);
-    if (rc == 0) rc = ffo_match_dir((const int16_t* const*)feat[1], (const int16_t* const*)feat[0], ws, hs, p1, 1,
-                                    flow_bwd, cb);
-    if (rc == 0) rc = ffo_match_dir((const int16_t* const*)feat[1], (const int16_t* const*)feat[0], ws, hs, &p2, 2,
-                                    flow_bwd2, cb);
+    if (rc == 0) rc = match_dir_c((const int16_t* const*)feat[0], (const int16_t* const*)feat[1], ca, cb2, ws, hs, p1, 0,
+                                  flow_fwd, cf);
+    if (rc == 0) rc = match_dir_c((const int16_t* const*)feat[1], (const int16_t* const*)feat[0], cb2, ca, ws, hs, p1, 1,
+                                  flow_bwd, cb);
+    if (rc == 0) rc = match_dir_c((const int16_t* const*)feat[1], (const int16_t* const*)feat[0], cb2, ca, ws, hs, &p2, 2,
+                                  flow_bwd2, cb);
     if (rc == 0) {
         ffo_consistency(flow_fwd, flow_bwd, w, h, prm->eps, mask);
         ffo_consistency(flow_fwd, flow_bwd2, w, h, prm->eps, m2);
         for (long p = 0; p < n; p++) mask[p] = (uint8_t)(mask[p] & m2[p]);
     }
-    for (int f = 0; f < 2; f++)
-        for (int s = 0; s < 16; s++) {
-            free(img[f][s]);
-            free(feat[f][s]);
-        }
+    for (int f = 0; f < 2; f++) free_features(L, img[f], feat[f], cen[f]);
     free(cf);
     free(cb);
     free(m2);
@@ -416,44 +519,27 @@ void ffo_sparsify(const int16_t* fwd, const int16_t* bwd, int w, int h, int eps,
 }
 
 /* The whole stage for one frame pair: pyramids and features of both frames, matching frame 1 -> 2
- * (dir 0) and the inverse field 2 -> 1 (dir 1), then the consistency mask of the forward field. */
+ * (dir 0) and the inverse field 2 -> 1 (dir 1), then the consistency mask of the forward field.  prm->cost
+ * selects the matching cost: 0 = SAD of the WHT descriptors, 1 = Hamming distance of the Census patterns. */
 int ffo_match_bidir(const uint8_t* rgb_a, const uint8_t* rgb_b, int w, int h, const ffo_params* prm,
                     int16_t* flow_fwd, int16_t* flow_bwd, int32_t* cost_fwd, int32_t* cost_bwd, uint8_t* mask) {
     int L = prm->n_scales;
     if (L < 1 || L > 16) return -1;
     int ws[16], hs[16];
     if (ffo_level_dims(w, h, L, ws, hs) != 0) return -1;
-    uint8_t* img[2][16];
-    int16_t* feat[2][16];
-    memset(img, 0, sizeof img);
-    memset(feat, 0, sizeof feat);
+    uint8_t* img[2][16] = {{0}};
+    int16_t* feat[2][16] = {{0}};
+    uint64_t* cen[2][16] = {{0}};
     int rc = 0;
-    for (int f = 0; f < 2 && rc == 0; f++) {
-        const uint8_t* src = f == 0 ? rgb_a : rgb_b;
-        for (int s = 0; s < L; s++) {
-            long n = (long)ws[s] * hs[s];
-            img[f][s] = (uint8_t*)malloc((size_t)n * 3);
-            feat[f][s] = (int16_t*)malloc((size_t)n * FFO_NF * sizeof(int16_t));
-            if (!img[f][s] || !feat[f][s]) {
-                rc = -1;
-                break;
-            }
-            if (s == 0)
-                memcpy(img[f][s], src, (size_t)n * 3);
-            else
-                ffo_downsample(img[f][s - 1], ws[s - 1], hs[s - 1], img[f][s]);
-            ffo_wht(img[f][s], ws[s], hs[s], feat[f][s]);
-        }
-    }
-    if (rc == 0) rc = ffo_match_dir((const int16_t* const*)feat[0], (const int16_t* const*)feat[1], ws, hs, prm, 0,
-                                    flow_fwd, cost_fwd);
-    if (rc == 0) rc = ffo_match_dir((const int16_t* const*)feat[1], (const int16_t* const*)feat[0], ws, hs, prm, 1,
-                                    flow_bwd, cost_bwd);
+    for (int f = 0; f < 2 && rc == 0; f++)
+        rc = frame_features(f == 0 ? rgb_a : rgb_b, L, ws, hs, prm->cost, img[f], feat[f], cen[f]);
+    const uint64_t* const* ca = prm->cost ? (const uint64_t* const*)cen[0] : NULL;
+    const uint64_t* const* cb = prm->cost ? (const uint64_t* const*)cen[1] : NULL;
+    if (rc == 0) rc = match_dir_c((const int16_t* const*)feat[0], (const int16_t* const*)feat[1], ca, cb, ws, hs, prm, 0,
+                                  flow_fwd, cost_fwd);
+    if (rc == 0) rc = match_dir_c((const int16_t* const*)feat[1], (const int16_t* const*)feat[0], cb, ca, ws, hs, prm, 1,
+                                  flow_bwd, cost_bwd);
     if (rc == 0) ffo_consistency(flow_fwd, flow_bwd, w, h, prm->eps, mask);
-    for (int f = 0; f < 2; f++)
-        for (int s = 0; s < L; s++) {
-            free(img[f][s]);
-            free(feat[f][s]);
-        }
+    for (int f = 0; f < 2; f++) free_features(L, img[f], feat[f], cen[f]);
     return rc;
 }

@@ -16,6 +16,7 @@
  *   flow     int16 [h][w][2]    (dx, dy), integer pixel displacement at the flow's own scale
  *   cost     int32 [h][w]       patch SAD of the pixel's current flow
  *   mask     uint8 [h][w]       1 = consistent (inlier)
+ *   census   uint64 [h][w][3]   48-bit Census pattern per colour channel
  */
 #ifndef FF_ORACLE_H
 #define FF_ORACLE_H
@@ -33,12 +34,20 @@ typedef struct {
     int rs_radius; /* random-search radius R: offsets drawn uniformly from [-R, R] per component */
     int eps;       /* consistency threshold in pixels */
     uint32_t seed; /* random-search hash seed */
+    int cost;      /* 0: SAD of the WHT descriptors, 1: Hamming distance of the Census patterns */
 } ffo_params;
 
 /* 0 on success; negative on an argument error or a broken internal assertion. */
 int ffo_level_dims(int w, int h, int n_scales, int* ws, int* hs);
 void ffo_downsample(const uint8_t* src, int w, int h, uint8_t* dst);
 void ffo_wht(const uint8_t* img, int w, int h, int16_t* feat);
+void ffo_census(const uint8_t* img, int w, int h, uint64_t* desc);
+int32_t ffo_hamming(const uint64_t* ca, const uint64_t* cb, int w, int h, int x, int y, int fx, int fy);
+long ffo_propagate_census(const uint64_t* ca, const uint64_t* cb, int w, int h, int16_t* flow, int32_t* cost,
+                          int iters, int rs_radius, uint32_t seed, int dir, int level, long max_halfsweeps);
+int ffo_match_dir_census(const int16_t* const* feat_a, const int16_t* const* feat_b, const uint64_t* const* cen_a,
+                         const uint64_t* const* cen_b, const int* ws, const int* hs, const ffo_params* prm, int dir,
+                         int16_t* flow, int32_t* cost);
 uint32_t ffo_mix32(uint32_t x);
 uint32_t ffo_hash(uint32_t seed, int dir, int level, int t, int d, int x, int y, int comp);
 int32_t ffo_sad(const int16_t* fa, const int16_t* fb, int w, int h, int x, int y, int fx, int fy);

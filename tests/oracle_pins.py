@@ -499,6 +499,84 @@ def check_second_consistency(o):
     assert np.array_equal(mask, one[4] & o.consistency(ff, fb2, 1))
 
 
+def census_numpy(img):
+    """Brute-force restatement of the 7x7 Census transform: bit k = k-th neighbour (row-major, centre skipped,
+    edge pixels repeated) strictly darker than the centre."""
+    h, w, _ = img.shape
+    pad = np.pad(img.astype(np.int64), ((3, 3), (3, 3), (0, 0)), mode="edge")
+    out = np.zeros((h, w, 3), np.uint64)
+    k = 0
+    for dy in range(-3, 4):
+        for dx in range(-3, 4):
+            if dy == 0 and dx == 0:
+                continue
+            nb = pad[3 + dy:3 + dy + h, 3 + dx:3 + dx + w]
+            out |= (nb < img).astype(np.uint64) << np.uint64(k)
+            k += 1
+    return out
+
+
+def check_census(o):
+    flat = np.full((9, 9, 3), 77, np.uint8)
+    assert not o.census(flat).any()  # no neighbour is darker
+    spot = np.zeros((9, 9, 3), np.uint8)
+    spot[4, 4] = (200, 0, 30)
+    c = o.census(spot)
+    assert int(c[4, 4, 0]) == (1 << 48) - 1 and int(c[4, 4, 1]) == 0 and int(c[4, 4, 2]) == (1 << 48) - 1
+    # bit order: only the top-left neighbour (dy=-3, dx=-3) darker -> bit 0; bottom-right -> bit 47
+    one = np.full((7, 7, 3), 100, np.uint8)
+    one[0, 0] = 10
+    assert int(o.census(one)[3, 3, 0]) == 1
+    one = np.full((7, 7, 3), 100, np.uint8)
+    one[6, 6] = 10
+    assert int(o.census(one)[3, 3, 0]) == 1 << 47
+    # equal neighbours do not count (strictly darker)
+    eq = np.full((7, 7, 3), 100, np.uint8)
+    eq[3, 3] = 100
+    assert int(o.census(eq)[3, 3, 0]) == 0
+    for seed, (h, w) in enumerate(((9, 13), (1, 5), (6, 1), (17, 11))):
+        im = rand_img(40 + seed, h, w)
+        assert np.array_equal(o.census(im), census_numpy(im)), (h, w)
+    ca = o.census(rand_img(50, 8, 9))
+    cb = o.census(rand_img(51, 8, 9))
+    for (x, y, fx, fy) in ((0, 0, 0, 0), (3, 4, 2, -1), (8, 7, -8, -7)):
+        want = sum(bin(int(ca[y, x, ch]) ^ int(cb[y + fy, x + fx, ch])).count("1") for ch in range(3))
+        assert o.hamming(ca, cb, x, y, fx, fy) == want
+    assert o.hamming(ca, ca, 2, 2, 0, 0) == 0 and o.hamming(ca, cb, 0, 0, -1, 0) == -1
+    assert o.hamming(o.census(spot), o.census(flat), 4, 4, 0, 0) == 96  # 2 x 48 bits differ
+
+
+def check_census_matching(o):
+    """Under the Census cost: propagation never raises a cost, cost = Hamming of the flow, and an integer
+    translation is recovered exactly (cost 0) by the whole stage."""
+    import oracle as _o
+
+    h, w = 11, 13
+    ia, ib = _tiny_level(71, h, w)
+    ca, cb = o.census(ia), o.census(ib)
+    rng = np.random.default_rng(72)
+    flow0 = np.zeros((h, w, 2), np.int16)
+    for y in range(h):
+        for x in range(w):
+            flow0[y, x] = (rng.integers(-x, w - x), rng.integers(-y, h - y))
+    cost0 = np.array([[o.hamming(ca, cb, x, y, *flow0[y, x].tolist()) for x in range(w)] for y in range(h)], np.int32)
+    prev = cost0
+    for k in range(1, 17):
+        f, c = o.propagate_census(ca, cb, flow0, cost0, 2, 2, 5, 0, 1, max_halfsweeps=k)
+        assert np.all(c <= prev)
+        assert all(c[y, x] == o.hamming(ca, cb, x, y, *f[y, x].tolist()) for y in range(h) for x in range(w))
+        prev = c
+    for (hh, ww, L, dx, dy) in ((40, 48, 1, 3, -2), (48, 56, 2, -4, 2)):
+        ia = smooth_texture(800 + L, hh, ww)
+        ib = shifted(ia, dx, dy, 801 + L)
+        prm = _o.params(n_scales=L, iters=3, rs_radius=2, eps=0, seed=9, cost=_o.COST_CENSUS)
+        ff, fb, cf, cb_, mask = o.match_bidir(ia, ib, prm)
+        m = 4 + 2 ** (L - 1)
+        ys, xs = np.mgrid[0:hh, 0:ww]
+        inner = (xs >= m + max(0, -dx)) & (xs < ww - m - max(0, dx)) & (ys >= m + max(0, -dy)) & (ys < hh - m - max(0, dy))
+        assert np.all(ff[inner] == (dx, dy)) and np.all(cf[inner] == 0) and np.all(mask[inner] == 1)
+
+
 def check_pipeline_composition(o):
     """The whole stage equals its steps composed in the order of Sec. 3.1 (pyramid, WHT, seed at the coarsest
     level, per level hand-over + propagation keyed by (direction, level), inverse field with the frames
@@ -546,5 +624,7 @@ ALL_CHECKS = [
     check_consistency,
     check_sparsify,
     check_second_consistency,
+    check_census,
+    check_census_matching,
     check_pipeline_composition,
 ]

@@ -45,6 +45,11 @@ MUTANTS = {
     "second_check_first_inverse_key": ("ws, hs, p1, 1,", "ws, hs, p1, 0,"),
     "second_check_radius_ignored": ("p2.rs_radius = rs_radius2;", "p2.rs_radius = prm->rs_radius;"),
     "second_check_ignored": ("mask[p] = (uint8_t)(mask[p] & m2[p]);", "mask[p] = (uint8_t)(mask[p] | m2[p]);"),
+    "census_not_strict": ("if (v < centre) bits |= (uint64_t)1 << k;", "if (v <= centre) bits |= (uint64_t)1 << k;"),
+    "census_reversed": ("if (v < centre) bits |= (uint64_t)1 << k;", "if (v > centre) bits |= (uint64_t)1 << k;"),
+    "census_centre_counted": ("if (dy == 0 && dx == 0) continue;", "if (dy == 9) continue;"),
+    "census_wrong_window": ("for (int dx = -3; dx <= 3; dx++) {", "for (int dx = -2; dx <= 4; dx++) {"),
+    "hamming_drops_channel": ("for (int c = 0; c < 3; c++) s += popcount64(", "for (int c = 0; c < 2; c++) s += popcount64("),
     "sparsify_error_sign": ("long ex = (long)fx + bwd[2 * q]", "long ex = (long)fx - bwd[2 * q]"),
     "sparsify_last_tie_wins": ("if (best_p < 0 || e < best_e) {", "if (best_p < 0 || e <= best_e) {"),
     "sparsify_count_off": ("if (count >= s && best_p >= 0)", "if (count > s && best_p >= 0)"),
