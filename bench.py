@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-pair batched measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream measurement")
+    ap.add_argument("--no-census", action="store_true", help="skip the Census-cost measurement")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--tuning", default=None,
                     help="JSON list of per-level [tile_w, tile_h, iters_per_launch, threads, speculate] instead of "
@@ -182,6 +183,55 @@ def measure_batched(torch, ff, configs, stream, local_rank, steps):
             "value": wl.pixels / (ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "gpu_launches_per_step": launches / steps, "tiles_per_level": [list(c) for c in tuning],
             "l2": "not flushed: 5 GB of features per step exceed L2"}
+
+
+def measure_census(torch, ff, configs, stream, local_rank, steps, flush):
+    """The Sintel-shaped 1024x436 pair matched with the Census cost (7x7 patterns, Hamming distance: the cost
+    the paper takes for Sintel) and, for comparison, with the WHT-SAD cost; autotuned, L2 flushed per step."""
+    import dataclasses
+
+    wl = configs.workload("sintel_1024x436")
+    spec = wl.pairs[0]
+    imgs = make_inputs(wl)
+    dev = torch.device("cuda", local_rank)
+    with torch.cuda.stream(stream):
+        d = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in imgs]
+    stream.synchronize()
+    out = {"workload": wl.name, "px_per_step": wl.pixels, "eps": spec.params.eps, "steps": steps,
+           "l2": "flushed before every timed step"}
+    for name, cost in (("census", 1), ("wht_sad", 0)):
+        M = ff.Matcher(dataclasses.replace(spec.params, cost=cost), local_rank, stream)
+        pyrs = [(M.features(a), M.features(b)) for a, b in d]
+        tuning = M.autotune(pyrs, reps=2)
+        for pa, pb in pyrs:
+            M.release(pa)
+            M.release(pb)
+        outs = None
+
+        def step():
+            nonlocal outs
+            pyrs = [(M.features(a), M.features(b)) for a, b in d]
+            outs = M.match_batch(pyrs, outs=outs, with_cost=False)
+            for pa, pb in pyrs:
+                M.release(pa)
+                M.release(pb)
+
+        for _ in range(3):
+            step()
+        ev = []
+        for _ in range(steps):
+            flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            ev.append((e0, e1))
+        stream.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        M.close()
+        out[name] = {"value": wl.pixels / (ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                     "tiles_per_level": [list(c) for c in tuning]}
+    return out
 
 
 def measure_served(torch, ff, configs, stream, local_rank, n_req):
@@ -456,6 +506,10 @@ def main():
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(workload, imgs)
+    if not args.no_census:
+        census = measure_census(torch, ff, configs, stream, local_rank, max(10, min(100, args.steps // 3)), flush_l2)
+        if rank == 0:
+            line["census_cost"] = census
     if not args.no_batched:
         batched = measure_batched(torch, ff, configs, stream, local_rank, steps=max(5, min(30, args.steps // 10)))
         if rank == 0:

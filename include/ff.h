@@ -14,7 +14,8 @@
  *   - Image     uint8 [h][w][3] (RGB), rows `pitch_bytes` apart (pitch_bytes >= 3*w).
  *   - Flow      int16 [h][w][2] row-major, (dx, dy) in whole pixels; pixel (x, y) of the source frame
  *               matches pixel (x+dx, y+dy) of the target frame.  4-byte aligned.
- *   - Cost      int32 [h][w]: sum of absolute differences of the 48 int16 descriptor coefficients.
+ *   - Cost      int32 [h][w]: the matching cost of the match (ff_params.cost): by default the sum of absolute
+ *               differences of the 48 int16 descriptor coefficients.
  *   - Mask      uint8 [h][w]: 1 = the match passed the consistency check, 0 = rejected.
  *   - Pointers marked "device" must point to memory of the context's device; the caller owns them.
  *     Calls only enqueue work on the context's stream and return; a device buffer handed in must stay
@@ -70,11 +71,23 @@ typedef struct {
     int eps;
     uint32_t seed;
     int rs_radius2;  /* random-search radius (0..16) of the second inverse field of the two-check mode (Sec. 3.1
-                        computes each inverse field "with different matching parameters"); it also runs on its own
+                        computes the two inverse fields with differing matching settings); it also runs on its own
                         random stream */
+    int cost;        /* matching cost of propagation and random search: FF_COST_WHT_SAD (default) or
+                        FF_COST_CENSUS (see below); the coarsest-level initial matches use the WHT descriptors
+                        either way */
 } ff_params;
 
-/* Default parameters: L=5, iters=6, patch=8, n_coef=16, rs_radius=2, eps=1, seed=0x20180503, rs_radius2=4. */
+/* Matching costs (Sec. 3.1 matches with a Census cost or SIFT descriptors; Sec. 4.1 takes Census for Sintel).
+ *   FF_COST_WHT_SAD  sum of absolute differences of the 48 int16 WHT coefficients (cost range 0..3*16*2*2040).
+ *   FF_COST_CENSUS   Hamming distance of the 7x7 Census patterns of the three colour channels (0..144): bit k
+ *                    of channel c is 1 iff the k-th neighbour of the 7x7 window -- row-major over rows y-3..y+3
+ *                    and columns x-3..x+3, centre skipped, edge pixels repeated -- is strictly darker than the
+ *                    centre.  RGB stands in for CIELab (integer and exact). */
+enum { FF_COST_WHT_SAD = 0, FF_COST_CENSUS = 1 };
+
+/* Default parameters: L=5, iters=6, patch=8, n_coef=16, rs_radius=2, eps=1, seed=0x20180503, rs_radius2=4,
+ * cost=FF_COST_WHT_SAD. */
 FF_API void ff_default_params(ff_params* p);
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a cudaStream_t; NULL
@@ -84,7 +97,8 @@ FF_API ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* c
 /* Build the feature pyramid of one frame (Sec. 3 and 3.1): L pyramid levels (2x2 box average, rounded half
  * up, sizes halved rounding down, at least 1), the 48 int16 Walsh-Hadamard coefficients of the 8x8 patch
  * around every pixel of every level (edge pixels repeated), and the packed 8-bit descriptors of the coarsest
- * level used by the initial matching.  `rgb_dev` is a device image [h][w][3] with rows pitch_bytes apart.
+ * level used by the initial matching; with FF_COST_CENSUS also the Census patterns of every level.  `rgb_dev`
+ * is a device image [h][w][3] with rows pitch_bytes apart.
  * *out receives a pyramid owned by the context; it stays valid until ff_pyr_release or ff_destroy.
  * Released pyramids of the same size are recycled, so steady-state calls allocate nothing. */
 FF_API ff_status ff_features(ff_ctx* ctx, const uint8_t* rgb_dev, int w, int h, int pitch_bytes, ff_pyr** out);
@@ -167,6 +181,12 @@ FF_API ff_status ff_pyr_level_dims(const ff_pyr* pyr, int level, int* w, int* h)
  * stored colour-split: row y holds the descriptors of x = 0, 2, 4, ... followed by those of x = 1, 3, 5, ...,
  * i.e. pixel (x, y) is descriptor y*w + (x even ? x/2 : (w+1)/2 + x/2). */
 FF_API const int16_t* ff_pyr_features(const ff_pyr* pyr, int level);
+
+/* Device pointer to the Census patterns of `level` (read-only view owned by the pyramid), or NULL when the
+ * pyramid's context does not match with FF_COST_CENSUS.  32 bytes per pixel, as 8 uint32 words: words 2c and
+ * 2c+1 are the low and high halves of channel c's 48-bit pattern (bit k as for FF_COST_CENSUS), words 6 and 7
+ * are zero.  Same colour-split pixel order as ff_pyr_features. */
+FF_API const uint32_t* ff_pyr_census(const ff_pyr* pyr, int level);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next call on the context. */
 FF_API const char* ff_last_error(ff_ctx* ctx);

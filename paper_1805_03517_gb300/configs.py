@@ -27,6 +27,7 @@ class MatchParams:
     eps: int = 1
     seed: int = HASH_SEED
     rs_radius2: int = 4  # random-search radius of the second inverse field (two-check mode)
+    cost: int = 0        # 0: SAD of the WHT descriptors, 1: Hamming distance of 7x7 Census patterns
 
 
 @dataclass(frozen=True)

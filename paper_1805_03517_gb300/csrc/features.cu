@@ -50,6 +50,35 @@ __device__ __forceinline__ void walsh4(int a0, int a1, int a2, int a3, int a4, i
     c3 = r + t;  // + + - - + + - -
 }
 
+// Census pattern (Sec. 3.1, Census cost) of the output pixel at (lx, ly) of the tile from the same clamped input
+// window: the 7x7 neighbourhood is window rows ly..ly+6, columns lx..lx+6 (the WHT window reaches one row and
+// column further).  Bit k of channel c: the k-th neighbour in row-major order, centre skipped, is strictly
+// darker than the centre.  Written as 8 words: (low, high) 32 bits of channels 0, 1, 2, then two zero words.
+__device__ __forceinline__ void census_pixel(const uint8_t (&win)[3][kWinY][kWinX], int lx, int ly,
+                                             uint32_t* __restrict__ dst) {
+    uint32_t w[6];
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        const int centre = win[ch][ly + 3][lx + 3];
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int r = 0; r < 7; r++)
+#pragma unroll
+            for (int c = 0; c < 7; c++) {
+                if (r == 3 && c == 3) continue;
+                const int k = r * 7 + c - (r * 7 + c > 24 ? 1 : 0);
+                const uint32_t bit = win[ch][ly + r][lx + c] < centre ? 1u : 0u;
+                if (k < 32) lo |= bit << k;
+                else hi |= bit << (k - 32);
+            }
+        w[2 * ch] = lo;
+        w[2 * ch + 1] = hi;
+    }
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d[1] = make_uint4(w[4], w[5], 0u, 0u);
+}
+
 __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
     __shared__ uint8_t win[3][kWinY][kWinX];
     __shared__ short4 rowt[3][kWinY][kWtx];  // row pass: 4 horizontal Walsh sums per window row and output column
@@ -100,6 +129,7 @@ __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
         uint4* dst = reinterpret_cast<uint4*>(L.feat + (size_t)feat_index(x, y, L.w) * kNF);
 #pragma unroll
         for (int k = 0; k < 6; k++) dst[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+        if (L.census) census_pixel(win, lx, ly, L.census + (size_t)feat_index(x, y, L.w) * (kCensusBytes / 4));
     }
 }
 

@@ -48,6 +48,7 @@ struct ff_pyr {
     int ws[kMaxLevels] = {}, hs[kMaxLevels] = {};
     uint8_t* img[kMaxLevels] = {};   // levels 1..L-1 (level 0 is the caller's image, read only by ff_features)
     int16_t* feat[kMaxLevels] = {};
+    uint32_t* cen[kMaxLevels] = {};  // Census patterns [h][w][8] (contexts with the Census cost only)
     int8_t* seed_desc = nullptr;     // [n_pad][64]
     int32_t* seed_norm = nullptr;    // [n_coarse]
     int n_coarse = 0, n_pad = 0;
@@ -85,6 +86,8 @@ struct Launch {
     void* set_ptr = nullptr;
     size_t set_bytes = 0;
     int set_value = 0;
+    // hand-over
+    int cost = 0;
     // tensor-core seed
     uint32_t wait_limit = 0;
     int withhold = 0;
@@ -215,6 +218,8 @@ ff_status check_params(const ff_params* p, ff_ctx* c) {
     if (p->rs_radius < 0 || p->rs_radius > 16) return fail(c, FF_ERR_ARG, "rs_radius must be 0..16");
     if (p->eps < 0 || p->eps > 32767) return fail(c, FF_ERR_ARG, "eps must be 0..32767");
     if (p->rs_radius2 < 0 || p->rs_radius2 > 16) return fail(c, FF_ERR_ARG, "rs_radius2 must be 0..16");
+    if (p->cost != FF_COST_WHT_SAD && p->cost != FF_COST_CENSUS)
+        return fail(c, FF_ERR_ARG, "cost must be FF_COST_WHT_SAD or FF_COST_CENSUS");
     return FF_OK;
 }
 
@@ -244,7 +249,7 @@ ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
             launch_seed(static_cast<const SeedProblem*>(L.probs), L.n_probs, L.total, st);
             break;
         case Kind::Handover:
-            launch_handover(static_cast<const HandoverProblem*>(L.probs), L.n_probs, L.total_pix, st);
+            launch_handover(static_cast<const HandoverProblem*>(L.probs), L.n_probs, L.total_pix, L.cost, st);
             break;
         case Kind::Propagate:
             launch_propagate(static_cast<const PropProblem*>(L.probs), L.queue, L.total, L.counter, L.grid, L.prop,
@@ -312,11 +317,16 @@ ff_status run_launches(ff_ctx* c, const std::vector<Launch>& ls, bool timed) {
     return FF_OK;
 }
 
+// The descriptors a level is matched with: the WHT features, or the Census patterns under the Census cost.
+const void* cost_desc(const ff_pyr* p, int level, int cost) {
+    return cost == FF_COST_CENSUS ? static_cast<const void*>(p->cen[level]) : static_cast<const void*>(p->feat[level]);
+}
+
 // Build the launch sequence of a set of matching directions (+ consistency checks).  `force` (optional) imposes
 // one propagation configuration on every level (used by the autotuner).
 ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons, Plan& P,
                      const TileCfg* force) {
-    const int L = c->prm.n_scales, T = c->prm.iters;
+    const int L = c->prm.n_scales, T = c->prm.iters, cost = c->prm.cost;
     const int nj = (int)jobs.size();
     // per job and level: two flow and two cost buffers (ping-pong) + seed distances
     struct LevelBufs {
@@ -473,8 +483,8 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             for (int j = 0; j < nj; j++) {
                 const ff_pyr* A = jobs[j].a;
                 HandoverProblem hp{};
-                hp.fa = A->feat[s];
-                hp.fb = jobs[j].b->feat[s];
+                hp.fa = cost_desc(A, s, cost);
+                hp.fb = cost_desc(jobs[j].b, s, cost);
                 hp.w = A->ws[s];
                 hp.h = A->hs[s];
                 if (s == L - 1) {
@@ -494,6 +504,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             }
             l.n_probs = nj;
             l.total_pix = pix;
+            l.cost = cost;
             pend.push_back({l, o, 0, -1});
         }
         int64_t level_pix = 0;
@@ -510,7 +521,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             tc = it != c->tuned.end() ? it->second : default_cfg(c, level_pix, T);
         }
         const size_t smem = prop_smem_bytes(tc.tw, tc.th, tc.k);
-        const int blocks = prop_blocks_per_sm(smem, tc.threads, tc.spec != 0) * c->n_sms;
+        const int blocks = prop_blocks_per_sm(smem, tc.threads, tc.spec != 0, cost) * c->n_sms;
         for (int t0 = 0; t0 < T; t0 += tc.k) {
             int n_iter = std::min(tc.k, T - t0);
             bool last = t0 + n_iter == T;
@@ -523,13 +534,14 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             l.prop.max_iter = n_iter;
             l.prop.threads = tc.threads;
             l.prop.spec = tc.spec;
+            l.prop.cost = cost;
             size_t oq = queue.size();
             std::vector<int> pidx(nj), ntiles(nj);
             for (int j = 0; j < nj; j++) {
                 const ff_pyr* A = jobs[j].a;
                 PropProblem pp{};
-                pp.fa = A->feat[s];
-                pp.fb = jobs[j].b->feat[s];
+                pp.fa = cost_desc(A, s, cost);
+                pp.fb = cost_desc(jobs[j].b, s, cost);
                 pp.w = A->ws[s];
                 pp.h = A->hs[s];
                 int in = cur_buf[j], out = in ^ 1;
@@ -791,6 +803,7 @@ bool ctx_view(const ff_ctx* c, CtxView* out) {
     out->rs_radius = c->prm.rs_radius;
     out->eps = c->prm.eps;
     out->seed = c->prm.seed;
+    out->cost = c->prm.cost;
     return true;
 }
 
@@ -810,6 +823,7 @@ bool pyr_view(const ff_pyr* p, PyrView* out) {
         out->ws[s] = p->ws[s];
         out->hs[s] = p->hs[s];
         out->feat[s] = p->feat[s];
+        out->cen[s] = p->cen[s];
     }
     out->seed_desc = p->seed_desc;
     out->seed_norm = p->seed_norm;
@@ -864,6 +878,7 @@ void ff_default_params(ff_params* p) {
     p->eps = 1;
     p->seed = 0x20180503u;
     p->rs_radius2 = 4;
+    p->cost = FF_COST_WHT_SAD;
 }
 
 ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* cuda_stream) {
@@ -901,6 +916,7 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
     if (pitch_bytes < 3 * w) return fail(c, FF_ERR_ARG, "pitch %d < 3*w", pitch_bytes);
     FF_CUDA(c, cudaSetDevice(c->device));
     const int L = c->prm.n_scales;
+    const bool census = c->prm.cost == FF_COST_CENSUS;
     ff_pyr* P = nullptr;
     for (auto& q : c->pyrs)
         if (!q->in_use && q->w == w && q->h == h && q->L == L) {
@@ -919,6 +935,8 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
         size_t bytes = 0;
         for (int s = 1; s < L; s++) bytes += align_up((size_t)np->ws[s] * np->hs[s] * 3);
         for (int s = 0; s < L; s++) bytes += align_up((size_t)np->ws[s] * np->hs[s] * kDescBytes);
+        if (census)
+            for (int s = 0; s < L; s++) bytes += align_up((size_t)np->ws[s] * np->hs[s] * kCensusBytes);
         bytes += align_up((size_t)np->n_pad * kSeedK) + align_up((size_t)np->n_coarse * 4);
         bytes += align_up((size_t)np->n_pad128 * 128) + align_up(128);
         ff_status s = dev_alloc(c, np->mem, bytes);
@@ -933,6 +951,11 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
             np->feat[l] = reinterpret_cast<int16_t*>(b + o);
             o += align_up((size_t)np->ws[l] * np->hs[l] * kDescBytes);
         }
+        if (census)
+            for (int l = 0; l < L; l++) {
+                np->cen[l] = reinterpret_cast<uint32_t*>(b + o);
+                o += align_up((size_t)np->ws[l] * np->hs[l] * kCensusBytes);
+            }
         np->seed_desc = reinterpret_cast<int8_t*>(b + o);
         o += align_up((size_t)np->n_pad * kSeedK);
         np->seed_norm = reinterpret_cast<int32_t*>(b + o);
@@ -974,6 +997,7 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
         lv.w = P->ws[s];
         lv.h = P->hs[s];
         lv.feat = P->feat[s];
+        lv.census = P->cen[s];
         lv.tiles_x = wht_tiles_x(P->ws[s]);
         lv.tile_base = tiles;
         tiles += wht_tiles(P->ws[s], P->hs[s]);
@@ -1146,6 +1170,11 @@ ff_status ff_pyr_level_dims(const ff_pyr* p, int level, int* w, int* h) {
 const int16_t* ff_pyr_features(const ff_pyr* p, int level) {
     if (!p || level < 0 || level >= p->L) return nullptr;
     return p->feat[level];
+}
+
+const uint32_t* ff_pyr_census(const ff_pyr* p, int level) {
+    if (!p || level < 0 || level >= p->L) return nullptr;
+    return p->cen[level];
 }
 
 const char* ff_last_error(ff_ctx* c) { return c ? c->err.c_str() : "null context"; }

@@ -5,6 +5,8 @@
 //   features  int16 [h][w][48]  96 B per pixel: three 32-B sectors (R, G, B), coefficient u*4+v in each;
 //                               colour-split rows: within row y the descriptors of even x come first, then odd x
 //                               (feat_index), so the pixels of one red-black half-sweep are contiguous
+//   census    uint32 [h][w][8]  32 B per pixel (FF_COST_CENSUS only): words 2c, 2c+1 = channel c's 48-bit 7x7
+//                               Census pattern, words 6, 7 zero; same colour-split order as the features
 //   seed desc int8  [N16][64]   coarsest level, C >> 7, zero-padded from 48 to 64 and to a multiple of 16 rows
 //   seed norm int32 [N]         squared norm of the 8-bit descriptor
 //   flow      uint32 [h][w]     packed (dx & 0xffff) | (dy << 16): the int16 [h][w][2] layout of the C-ABI
@@ -13,10 +15,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ff.h"
+
 namespace ff {
 
 constexpr int kNF = 48;           // int16 coefficients per pixel
 constexpr int kDescBytes = 96;    // bytes per pixel descriptor
+constexpr int kCensusBytes = 32;  // bytes per pixel Census pattern
 constexpr int kSeedK = 64;        // padded 8-bit seed descriptor length
 constexpr int kMaxLevels = 8;
 constexpr int kHaloPerIter = 4;   // halo growth per fused propagation iteration (one per half-sweep quadrant side)
@@ -29,6 +34,7 @@ struct WhtLevel {
     int pitch;           // bytes between rows
     int w, h;
     int16_t* feat;       // [h][w][48]
+    uint32_t* census;    // [h][w][8], or null: no Census patterns
     int tiles_x;
     int tile_base;       // first CTA of this level in the fused launch
 };
@@ -85,8 +91,8 @@ void launch_seed_tc(const SeedTcProblem* probs_dev, int n_probs, int total_ctas,
 // hand-over (coarse-to-fine initialisation) and cost initialisation
 
 struct HandoverProblem {
-    const int16_t* fa;
-    const int16_t* fb;
+    const void* fa;          // cost descriptors of the source frame (WHT features or Census patterns)
+    const void* fb;          // and of the target frame
     int w, h;
     const uint32_t* parent;  // flow of the level above (pw x ph), or null: take flow_in as is
     int pw, ph;
@@ -95,14 +101,15 @@ struct HandoverProblem {
     int32_t* cost_out;
     int64_t pix_base;        // first pixel of this problem in the launch
 };
-void launch_handover(const HandoverProblem* probs_dev, int n_probs, int64_t total_pix, cudaStream_t st);
+// cost: FF_COST_WHT_SAD or FF_COST_CENSUS (selects the descriptor type of fa/fb)
+void launch_handover(const HandoverProblem* probs_dev, int n_probs, int64_t total_pix, int cost, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------------------
 // propagation + random search, `n_iter` iterations of one level per launch, temporally blocked tiles
 
 struct PropProblem {  // one (pair, direction, level) of a propagation launch
-    const int16_t* fa;
-    const int16_t* fb;
+    const void* fa;  // cost descriptors of the source frame (WHT features or Census patterns)
+    const void* fb;  // and of the target frame
     const uint32_t* flow_in;
     const int32_t* cost_in;
     uint32_t* flow_out;
@@ -121,12 +128,13 @@ struct PropLaunch {
     int max_iter;    // largest n_iter of the launch (sizes the shared-memory halo)
     int threads;     // CTA size: 128, 256 or 512
     int spec;        // 1: load the random candidate together with the neighbour candidates
+    int cost;        // FF_COST_WHT_SAD or FF_COST_CENSUS
 };
 constexpr size_t kMaxPropSmem = 200 * 1024;
 size_t prop_smem_bytes(int tw, int th, int n_iter);
 cudaError_t init_kernel_attributes();  // once per device, before the first launch
 bool prop_threads_ok(int threads);
-int prop_blocks_per_sm(size_t smem, int threads, bool spec);  // resident CTAs per SM of the propagation kernel
+int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost);  // resident CTAs per SM of the kernel
 // queue_dev[i] = (problem index, tile index); counter_dev must be zero when the launch starts
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st);
@@ -146,6 +154,7 @@ struct PyrView {
     int w, h, L;
     int ws[kMaxLevels], hs[kMaxLevels];
     const int16_t* feat[kMaxLevels];
+    const uint32_t* cen[kMaxLevels];  // null unless the context matches with the Census cost
     const int8_t* seed_desc;
     const int32_t* seed_norm;
     int n_coarse;
@@ -155,6 +164,7 @@ struct CtxView {
     cudaStream_t stream;
     int n_scales, iters, rs_radius, eps;
     uint32_t seed;
+    int cost;
 };
 struct TileChoice {
     int tw, th, k, threads, spec;

@@ -27,6 +27,11 @@ void* g_scratch_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, 
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
+// The descriptors a level is matched with (WHT features, or Census patterns under the Census cost).
+const void* cost_desc(const PyrView& v, int level, int cost) {
+    return cost == FF_COST_CENSUS ? static_cast<const void*>(v.cen[level]) : static_cast<const void*>(v.feat[level]);
+}
+
 // Set-up, once per device, with that device current: the device address of the scratch array.  (In host code
 // the array's name is only a host-side stand-in; kernels must be given this address.)
 ff_status scratch_address(int device, void** out) {
@@ -129,10 +134,10 @@ extern "C" ff_status ff_match_pair_noalloc(ff_ctx* c, const ff_pyr* a, const ff_
         int tiles_x = (A.ws[s] + tc[s].tw - 1) / tc[s].tw;
         sa.ntiles[s] = tiles_x * ((A.hs[s] + tc[s].th - 1) / tc[s].th);
         size_t smem = prop_smem_bytes(tc[s].tw, tc[s].th, tc[s].k);
-        grid[s] = std::min(sa.ntiles[s], prop_blocks_per_sm(smem, tc[s].threads, tc[s].spec != 0) * cv.n_sms);
+        grid[s] = std::min(sa.ntiles[s], prop_blocks_per_sm(smem, tc[s].threads, tc[s].spec != 0, cv.cost) * cv.n_sms);
         PropProblem& p = sa.base[s];
-        p.fa = A.feat[s];
-        p.fb = B.feat[s];
+        p.fa = cost_desc(A, s, cv.cost);
+        p.fb = cost_desc(B, s, cv.cost);
         p.w = A.ws[s];
         p.h = A.hs[s];
         p.tiles_x = tiles_x;
@@ -178,8 +183,8 @@ extern "C" ff_status ff_match_pair_noalloc(ff_ctx* c, const ff_pyr* a, const ff_
     sp.warp_base = 0;
     for (int s = L - 1; s >= 0; s--) {
         HandoverProblem& hp = sa.ho[s];
-        hp.fa = A.feat[s];
-        hp.fb = B.feat[s];
+        hp.fa = cost_desc(A, s, cv.cost);
+        hp.fb = cost_desc(B, s, cv.cost);
         hp.w = A.ws[s];
         hp.h = A.hs[s];
         if (s == L - 1) {
@@ -204,10 +209,10 @@ extern "C" ff_status ff_match_pair_noalloc(ff_ctx* c, const ff_pyr* a, const ff_
     k_noalloc_setup<<<64, 256, 0, st>>>(sa);
     launch_seed(sa.seed_dst, 1, (A.n_coarse + 15) / 16, st);
     for (int s = L - 1; s >= 0; s--) {
-        launch_handover(sa.ho_dst + s, 1, (int64_t)A.ws[s] * A.hs[s], st);
+        launch_handover(sa.ho_dst + s, 1, (int64_t)A.ws[s] * A.hs[s], cv.cost, st);
         for (int j = 0; j < sa.n_launch[s]; j++) {
             const int li = sa.first_launch[s] + j;
-            PropLaunch pl{tc[s].tw, tc[s].th, std::min(tc[s].k, T - j * tc[s].k), tc[s].threads, tc[s].spec};
+            PropLaunch pl{tc[s].tw, tc[s].th, std::min(tc[s].k, T - j * tc[s].k), tc[s].threads, tc[s].spec, cv.cost};
             launch_propagate(sa.props + li, sa.queue[s], sa.ntiles[s], counters + li, grid[s], pl, st);
         }
     }

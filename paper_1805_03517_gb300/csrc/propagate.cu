@@ -5,8 +5,8 @@
 // d = 0..3 (neighbours left+top, right+top, left+bottom, right+bottom), two half-sweeps over the pixels with
 // (x + y) even, then odd.  A pixel of the active colour tries neighbour 1 (horizontal), neighbour 2 (vertical)
 // and, for d >= 1, its current flow plus a hashed random offset in [-R, R]^2 (skipped if zero); a candidate
-// is taken iff its SAD is strictly lower; targets outside the level are rejected.  Neighbours always have the
-// other colour, so every half-sweep is a fully parallel map.
+// is taken iff its cost (WHT SAD or Census Hamming distance) is strictly lower; targets outside the level are
+// rejected.  Neighbours always have the other colour, so every half-sweep is a fully parallel map.
 //
 // Temporal blocking: one CTA owns a tile of a level and runs n_iter whole iterations (8 half-sweeps each) in
 // shared memory before writing the tile back, reading the level state from one buffer and writing another.
@@ -28,7 +28,7 @@ __device__ __forceinline__ bool in_level(int x, int y, int w, int h) {
 }
 
 // One pixel descriptor (96 B = three 32-B sectors) with three 256-bit read-only loads, one sector per load.
-__device__ __forceinline__ void load_desc(const int16_t* __restrict__ f, int idx, uint32_t (&d)[24]) {
+__device__ __forceinline__ void load_desc(const void* __restrict__ f, int idx, uint32_t (&d)[24]) {
     const char* p = reinterpret_cast<const char*>(f) + (size_t)idx * kDescBytes;
 #pragma unroll
     for (int k = 0; k < 3; k++)
@@ -61,19 +61,51 @@ __device__ __forceinline__ int sad_biased(const uint32_t (&a)[24], const uint32_
     return (int)s;
 }
 
-// SAD of the descriptor at (x, y) of fa against (tx, ty) of fb (both inside the level).
-__device__ __forceinline__ int sad_at(const int16_t* __restrict__ fa, const int16_t* __restrict__ fb, int w, int x,
-                                      int y, int tx, int ty) {
-    uint32_t a[24], b[24];
-    load_desc(fa, feat_index(x, y, w), a);
-    load_desc(fb, feat_index(tx, ty, w), b);
-    bias_desc(a);
-    return sad_biased(a, b);
+// The two matching costs (Sec. 3.1), as policies of the hand-over and propagation kernels: descriptor size in
+// 32-bit words, load of one pixel's descriptor, one-time preparation of the source pixel's descriptor, distance.
+struct CostSad {  // SAD of the 48 int16 WHT coefficients
+    static constexpr int kWords = 24;
+    __device__ __forceinline__ static void load(const void* __restrict__ f, int idx, uint32_t (&d)[kWords]) {
+        load_desc(f, idx, d);
+    }
+    __device__ __forceinline__ static void prep(uint32_t (&a)[kWords]) { bias_desc(a); }
+    __device__ __forceinline__ static int dist(const uint32_t (&a)[kWords], const uint32_t (&b)[kWords]) {
+        return sad_biased(a, b);
+    }
+};
+
+struct CostCensus {  // Hamming distance of the three 48-bit Census patterns (one 32-B sector per pixel)
+    static constexpr int kWords = 8;
+    __device__ __forceinline__ static void load(const void* __restrict__ f, int idx, uint32_t (&d)[kWords]) {
+        const char* p = reinterpret_cast<const char*>(f) + (size_t)idx * kCensusBytes;
+        asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7])
+            : "l"(p));
+    }
+    __device__ __forceinline__ static void prep(uint32_t (&)[kWords]) {}
+    __device__ __forceinline__ static int dist(const uint32_t (&a)[kWords], const uint32_t (&b)[kWords]) {
+        int s = 0;
+#pragma unroll
+        for (int k = 0; k < 6; k++) s += __popc(a[k] ^ b[k]);  // words 6 and 7 are zero
+        return s;
+    }
+};
+
+// Cost of the descriptor at (x, y) of fa against (tx, ty) of fb (both inside the level).
+template <class C>
+__device__ __forceinline__ int cost_at(const void* __restrict__ fa, const void* __restrict__ fb, int w, int x, int y,
+                                       int tx, int ty) {
+    uint32_t a[C::kWords], b[C::kWords];
+    C::load(fa, feat_index(x, y, w), a);
+    C::load(fb, feat_index(tx, ty, w), b);
+    C::prep(a);
+    return C::dist(a, b);
 }
 
 // ---------------------------------------------------------------------------------------------------------
-// hand-over: flow = 2 x parent flow (parent = (min(x/2, pw-1), min(y/2, ph-1))) or the given flow; cost = SAD.
+// hand-over: flow = 2 x parent flow (parent = (min(x/2, pw-1), min(y/2, ph-1))) or the given flow; cost of it.
 
+template <class C>
 __global__ __launch_bounds__(256) void k_handover(const HandoverProblem* __restrict__ probs, int n_probs,
                                                   int64_t total) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -95,17 +127,20 @@ __global__ __launch_bounds__(256) void k_handover(const HandoverProblem* __restr
         }
         int tx = x + flow_x(f), ty = y + flow_y(f);
         int c = INT_MAX;  // unreachable for valid inputs: a handed-over flow always lands inside the level
-        if (in_level(tx, ty, P.w, P.h)) c = sad_at(P.fa, P.fb, P.w, x, y, tx, ty);
+        if (in_level(tx, ty, P.w, P.h)) c = cost_at<C>(P.fa, P.fb, P.w, x, y, tx, ty);
         P.flow_out[p] = f;
         P.cost_out[p] = c;
     }
 }
 
-void launch_handover(const HandoverProblem* probs_dev, int n_probs, int64_t total_pix, cudaStream_t st) {
+void launch_handover(const HandoverProblem* probs_dev, int n_probs, int64_t total_pix, int cost, cudaStream_t st) {
     int64_t blocks = (total_pix + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_handover<<<(int)blocks, 256, 0, st>>>(probs_dev, n_probs, total_pix);
+    if (cost == FF_COST_CENSUS)
+        k_handover<CostCensus><<<(int)blocks, 256, 0, st>>>(probs_dev, n_probs, total_pix);
+    else
+        k_handover<CostSad><<<(int)blocks, 256, 0, st>>>(probs_dev, n_probs, total_pix);
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -145,11 +180,13 @@ __device__ __forceinline__ bool region_pixel(int i, int HW, int rx0, int ry0, in
     return x < rx1;
 }
 
-// One half-sweep with one thread per pixel (the whole 96-B descriptor per thread).  With SPEC the random
-// candidate of directions 1..3 is fetched together with the neighbour candidates, assuming the neighbours will
-// not change the pixel's flow; if one of them is taken, the random candidate is fetched again from the new
-// flow.  Either way the candidate evaluated is the one the schedule defines, so results are identical.
-template <bool SPEC>
+// One half-sweep with one thread per pixel (the whole descriptor per thread: 96 B WHT, 32 B Census).  With SPEC
+// the random candidate of directions 1..3 is fetched together with the neighbour candidates, assuming the
+// neighbours will not change the pixel's flow; if one of them is taken, the random candidate is fetched again
+// from the new flow.  Either way the candidate evaluated is the one the schedule defines, so results are
+// identical.  (Fetching it early only into a buffer no neighbour needs, without SPEC, measured 16 % slower on
+// the 1242x375 pair.)
+template <class C, bool SPEC>
 __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& G, uint32_t* sflow, int32_t* scost,
                                           int j, int rem, uint32_t k1) {
     const int w = P.w, h = P.h;
@@ -185,24 +222,22 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
         const bool rnd = ox != 0 || oy != 0;
         const uint32_t cur0 = cur;
         // issue every independent load (own descriptor, neighbour candidates, speculative random) before compute
-        uint32_t a[24], b1[24], b2[24];
-        uint32_t b3[SPEC ? 24 : 1];
-        bool e3s = false;
-        load_desc(P.fa, feat_index(x, y, w), a);
-        if (e1) load_desc(P.fb, feat_index(x + flow_x(f1), y + flow_y(f1), w), b1);
-        if (e2) load_desc(P.fb, feat_index(x + flow_x(f2), y + flow_y(f2), w), b2);
+        uint32_t a[C::kWords], b1[C::kWords], b2[C::kWords];
+        uint32_t b3[SPEC ? C::kWords : 1];
+        C::load(P.fa, feat_index(x, y, w), a);
+        if (e1) C::load(P.fb, feat_index(x + flow_x(f1), y + flow_y(f1), w), b1);
+        if (e2) C::load(P.fb, feat_index(x + flow_x(f2), y + flow_y(f2), w), b2);
         if constexpr (SPEC) {
             const int sx = flow_x(cur) + ox, sy = flow_y(cur) + oy;
-            e3s = rnd && in_level(x + sx, y + sy, w, h);
-            if (e3s) load_desc(P.fb, feat_index(x + sx, y + sy, w), b3);
+            if (rnd && in_level(x + sx, y + sy, w, h)) C::load(P.fb, feat_index(x + sx, y + sy, w), b3);
         }
-        bias_desc(a);
+        C::prep(a);
         if (e1) {
-            int s1 = sad_biased(a, b1);
+            int s1 = C::dist(a, b1);
             if (s1 < c) { cur = f1; c = s1; }
         }
         if (e2) {
-            int s2 = sad_biased(a, b2);
+            int s2 = C::dist(a, b2);
             if (s2 < c) { cur = f2; c = s2; }
         }
         if (rnd) {
@@ -211,26 +246,25 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
                 int s3;
                 if constexpr (SPEC) {
                     if (cur == cur0) {
-                        s3 = sad_biased(a, b3);  // e3s holds: same target as speculated
+                        s3 = C::dist(a, b3);  // same target as speculated (which was then in the level)
                     } else {
-                        load_desc(P.fb, feat_index(x + fx, y + fy, w), b1);
-                        s3 = sad_biased(a, b1);
+                        C::load(P.fb, feat_index(x + fx, y + fy, w), b1);
+                        s3 = C::dist(a, b1);
                     }
                 } else {
-                    load_desc(P.fb, feat_index(x + fx, y + fy, w), b1);
-                    s3 = sad_biased(a, b1);
+                    C::load(P.fb, feat_index(x + fx, y + fy, w), b1);
+                    s3 = C::dist(a, b1);
                 }
                 if (s3 < c) { cur = pack_flow(fx, fy); c = s3; }
             }
         }
-        (void)e3s;
         sflow[sidx] = cur;
         scost[sidx] = c;
     }
 }
 
 // One tile of one problem: load the tile and its halo, run n_iter iterations in shared memory, write the tile.
-template <bool SPEC>
+template <class C, bool SPEC>
 __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, const PropLaunch& L, uint32_t* smem) {
     const int w = P.w, h = P.h;
     TileGeom G;
@@ -258,7 +292,7 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
         const int rem = kHaloPerIter * (P.n_iter - 1 - it);
         const uint32_t k1 = mix32(P.seed ^ mix32((uint32_t)P.dir * 65536u + (uint32_t)P.level * 256u + (uint32_t)t));
         for (int j = 0; j < 8; j++) {
-            halfsweep<SPEC>(P, G, sflow, scost, j, rem, k1);
+            halfsweep<C, SPEC>(P, G, sflow, scost, j, rem, k1);
             __syncthreads();
         }
     }
@@ -274,8 +308,8 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
 
 // Persistent launch: each CTA takes tiles from the launch's queue (an atomic counter, zeroed before the launch)
 // until it is empty, so the last wave has no idle tail.  queue[i] = (problem index, tile index in problem).
-// Instantiated for 128, 256 and 512 threads, with and without speculative random-candidate loads.
-template <int THREADS, bool SPEC>
+// Instantiated for 128, 256 and 512 threads, with and without speculative random-candidate loads, per cost.
+template <int THREADS, bool SPEC, class C>
 __global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate(
     const PropProblem* __restrict__ probs, const int2* __restrict__ queue, int n_tiles, int* __restrict__ counter,
     PropLaunch L) {
@@ -287,33 +321,41 @@ __global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate
         const int q = s_next;
         if (q >= n_tiles) return;
         const int2 e = queue[q];
-        propagate_tile<SPEC>(probs[e.x], e.y, L, smem);
+        propagate_tile<C, SPEC>(probs[e.x], e.y, L, smem);
         __syncthreads();
     }
 }
 
 using PropKernel = void (*)(const PropProblem*, const int2*, int, int*, PropLaunch);
 
-PropKernel prop_kernel(int threads, bool spec) {
-    if (spec) return threads == 128 ? k_propagate<128, true> : threads == 512 ? k_propagate<512, true> : k_propagate<256, true>;
-    return threads == 128 ? k_propagate<128, false> : threads == 512 ? k_propagate<512, false> : k_propagate<256, false>;
+template <class C>
+PropKernel prop_kernel_c(int threads, bool spec) {
+    if (spec) return threads == 128 ? k_propagate<128, true, C> : threads == 512 ? k_propagate<512, true, C> : k_propagate<256, true, C>;
+    return threads == 128 ? k_propagate<128, false, C> : threads == 512 ? k_propagate<512, false, C> : k_propagate<256, false, C>;
+}
+
+PropKernel prop_kernel(int threads, bool spec, int cost) {
+    return cost == FF_COST_CENSUS ? prop_kernel_c<CostCensus>(threads, spec) : prop_kernel_c<CostSad>(threads, spec);
 }
 
 cudaError_t init_kernel_attributes() {
-    for (int t : {128, 256, 512})
-        for (bool sp : {false, true}) {
-            cudaError_t e = cudaFuncSetAttribute(prop_kernel(t, sp), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)kMaxPropSmem);
-            if (e != cudaSuccess) return e;
-        }
+    for (int cost : {FF_COST_WHT_SAD, FF_COST_CENSUS})
+        for (int t : {128, 256, 512})
+            for (bool sp : {false, true}) {
+                cudaError_t e = cudaFuncSetAttribute(prop_kernel(t, sp, cost),
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
+                if (e != cudaSuccess) return e;
+
+            }
     return cudaSuccess;
 }
 
 bool prop_threads_ok(int threads) { return threads == 128 || threads == 256 || threads == 512; }
 
-int prop_blocks_per_sm(size_t smem, int threads, bool spec) {
+int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prop_kernel(threads, spec), threads, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prop_kernel(threads, spec, cost), threads, smem) !=
+        cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -323,7 +365,8 @@ int prop_blocks_per_sm(size_t smem, int threads, bool spec) {
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st) {
     size_t smem = prop_smem_bytes(L.tw, L.th, L.max_iter);
-    prop_kernel(L.threads, L.spec != 0)<<<grid, L.threads, smem, st>>>(probs_dev, queue_dev, n_tiles, counter_dev, L);
+    prop_kernel(L.threads, L.spec != 0, L.cost)<<<grid, L.threads, smem, st>>>(probs_dev, queue_dev, n_tiles,
+                                                                                counter_dev, L);
 }
 
 }  // namespace ff

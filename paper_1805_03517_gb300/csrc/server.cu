@@ -61,18 +61,23 @@ struct RingSlot {
     int64_t tick = -1;
 };
 
-int64_t pyr_bytes(int w, int h, int L) {
+int64_t pyr_bytes(int w, int h, int L, bool census) {
     int64_t b = 0;
     int ws = w, hs = h;
     for (int s = 0; s < L; s++) {
         if (s > 0) b += (int64_t)ws * hs * 3;
-        b += (int64_t)ws * hs * kDescBytes;
+        b += (int64_t)ws * hs * (kDescBytes + (census ? kCensusBytes : 0));
         if (s + 1 < L) {
             ws = std::max(1, ws / 2);
             hs = std::max(1, hs / 2);
         }
     }
     return b + (int64_t)ws * hs * (kSeedK + 4) + 4096;
+}
+
+// The descriptors a level is matched with (WHT features, or Census patterns under the Census cost).
+const void* cost_desc(const PyrView& v, int level, int cost) {
+    return cost == FF_COST_CENSUS ? static_cast<const void*>(v.cen[level]) : static_cast<const void*>(v.feat[level]);
 }
 
 size_t scratch_need(int w, int h, int L) {
@@ -255,8 +260,8 @@ ff_status tick(ff_server* s) {
                 const PyrView& X = d == 0 ? q.A : q.B;
                 const PyrView& Y = d == 0 ? q.B : q.A;
                 HandoverProblem hp{};
-                hp.fa = X.feat[sl];
-                hp.fb = Y.feat[sl];
+                hp.fa = cost_desc(X, sl, s->cv.cost);
+                hp.fb = cost_desc(Y, sl, s->cv.cost);
                 hp.w = X.ws[sl];
                 hp.h = X.hs[sl];
                 if (sl == L - 1) {
@@ -283,8 +288,8 @@ ff_status tick(ff_server* s) {
             const PyrView& X = d == 0 ? q.A : q.B;
             const PyrView& Y = d == 0 ? q.B : q.A;
             PropProblem pp{};
-            pp.fa = X.feat[sl];
-            pp.fb = Y.feat[sl];
+            pp.fa = cost_desc(X, sl, s->cv.cost);
+            pp.fb = cost_desc(Y, sl, s->cv.cost);
             pp.w = X.ws[sl];
             pp.h = X.hs[sl];
             const int in = q.cur[d], out = in ^ 1;
@@ -361,8 +366,8 @@ ff_status tick(ff_server* s) {
         for (auto& pr : kv.second) hp[pi++] = pr.first;
         const size_t smem = prop_smem_bytes(k.tw, k.th, k.n_iter);
         const int nq = (int)(qi - q0);
-        pls.push_back({PropLaunch{k.tw, k.th, k.n_iter, k.threads, k.spec}, q0, nq,
-                       std::min(nq, prop_blocks_per_sm(smem, k.threads, k.spec != 0) * s->cv.n_sms)});
+        pls.push_back({PropLaunch{k.tw, k.th, k.n_iter, k.threads, k.spec, s->cv.cost}, q0, nq,
+                       std::min(nq, prop_blocks_per_sm(smem, k.threads, k.spec != 0, s->cv.cost) * s->cv.n_sms)});
     }
     cudaStream_t stm = s->cv.stream;
     if (cudaMemcpyAsync(r.dev, r.host, bytes, cudaMemcpyHostToDevice, stm) != cudaSuccess)
@@ -373,7 +378,8 @@ ff_status tick(ff_server* s) {
         nl++;
     }
     if (!hos.empty()) {
-        launch_handover(reinterpret_cast<const HandoverProblem*>(r.dev + o_ho), (int)hos.size(), ho_pix, stm);
+        launch_handover(reinterpret_cast<const HandoverProblem*>(r.dev + o_ho), (int)hos.size(), ho_pix, s->cv.cost,
+                        stm);
         nl++;
     }
     for (size_t g = 0; g < pls.size(); g++) {
@@ -437,7 +443,7 @@ ff_status ff_server_submit(ff_server* s, uint64_t id, const ff_request* req) {
     auto q = std::make_unique<Req>();
     q->id = id;
     q->io = *req;
-    q->footprint = 2 * pyr_bytes(req->w, req->h, s->cv.n_scales) +
+    q->footprint = 2 * pyr_bytes(req->w, req->h, s->cv.n_scales, s->cv.cost == FF_COST_CENSUS) +
                    (int64_t)scratch_need(req->w, req->h, s->cv.n_scales);
     if (q->footprint > s->budget) return srv_fail(s, FF_ERR_ARG, "request larger than the memory budget");
     s->queued.push_back(std::move(q));

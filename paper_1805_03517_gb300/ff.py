@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "ff.h")
 FF_OK, FF_ERR_ARG, FF_ERR_OOM, FF_ERR_CUDA, FF_ERR_TIMEOUT, FF_ERR_BUSY = range(6)
 FF_OPT_SEED_KERNEL, FF_OPT_WAIT_LIMIT, FF_OPT_TEST_WITHHOLD_COPIES = 1, 2, 3
 FF_SEED_MMA_SYNC, FF_SEED_TCGEN05 = 0, 1
+FF_COST_WHT_SAD, FF_COST_CENSUS = 0, 1
 STATUS_NAMES = {0: "FF_OK", 1: "FF_ERR_ARG", 2: "FF_ERR_OOM", 3: "FF_ERR_CUDA", 4: "FF_ERR_TIMEOUT", 5: "FF_ERR_BUSY"}
 PHASES = ("features", "seed", "handover", "propagate", "consistency")
 
@@ -34,7 +35,7 @@ class FFError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("n_scales", ctypes.c_int), ("iters", ctypes.c_int), ("patch", ctypes.c_int),
                 ("n_coef", ctypes.c_int), ("rs_radius", ctypes.c_int), ("eps", ctypes.c_int),
-                ("seed", ctypes.c_uint32), ("rs_radius2", ctypes.c_int)]
+                ("seed", ctypes.c_uint32), ("rs_radius2", ctypes.c_int), ("cost", ctypes.c_int)]
 
 
 class PairJob(ctypes.Structure):
@@ -92,6 +93,7 @@ def lib():
         "ff_pyr_release": (S, [vp, vp]),
         "ff_pyr_level_dims": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "ff_pyr_features": (vp, [vp, i]),
+        "ff_pyr_census": (vp, [vp, i]),
         "ff_last_error": (ctypes.c_char_p, [vp]),
         "ff_sync": (S, [vp]),
         "ff_get_stats": (S, [vp, ctypes.POINTER(Stats)]),
@@ -196,6 +198,10 @@ def ff_pyr_features(pyr, level: int) -> int:
     return lib().ff_pyr_features(pyr, level) or 0
 
 
+def ff_pyr_census(pyr, level: int) -> int:
+    return lib().ff_pyr_census(pyr, level) or 0
+
+
 def ff_last_error(ctx) -> str:
     return lib().ff_last_error(ctx).decode()
 
@@ -282,7 +288,7 @@ def to_params(p) -> Params:
     if isinstance(p, Params):
         return p
     return Params(p.n_scales, p.iters, getattr(p, "patch", 8), getattr(p, "n_coef", 16), p.rs_radius, p.eps,
-                  p.seed & 0xFFFFFFFF, getattr(p, "rs_radius2", 4))
+                  p.seed & 0xFFFFFFFF, getattr(p, "rs_radius2", 4), getattr(p, "cost", FF_COST_WHT_SAD))
 
 
 @dataclass
@@ -338,6 +344,23 @@ class Matcher:
         self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
         src = _DevView(ptr, h * w * 96)
         split.view(-1).view(self.torch.uint8).copy_(self.torch.as_tensor(src, device=self.device))
+        return self._unsplit(split)
+
+    def level_census(self, pyr: Pyramid, level: int):
+        """Copy of the Census patterns of one level as uint64 [h][w][3] (48 bits per channel) in plain row order,
+        or None when the context does not match with the Census cost."""
+        w, h = ff_pyr_level_dims(pyr.handle, level)
+        ptr = ff_pyr_census(pyr.handle, level)
+        if not ptr:
+            return None
+        split = self._empty((h, w, 4), self.torch.int64)
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        src = _DevView(ptr, h * w * 32)
+        split.view(-1).view(self.torch.uint8).copy_(self.torch.as_tensor(src, device=self.device))
+        return self._unsplit(split)[:, :, :3]
+
+    def _unsplit(self, split):
+        w = split.shape[1]
         out = self.torch.empty_like(split)
         ne = (w + 1) // 2
         out[:, 0::2] = split[:, :ne]

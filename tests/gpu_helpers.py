@@ -7,7 +7,7 @@ import oracle
 
 
 def oracle_params(p):
-    return oracle.params(p.n_scales, p.iters, p.rs_radius, p.eps, p.seed)
+    return oracle.params(p.n_scales, p.iters, p.rs_radius, p.eps, p.seed, getattr(p, "cost", 0))
 
 
 def gpu_bidir(M, img_a, img_b, torch):

@@ -33,13 +33,14 @@ def test_binding_wraps_every_declared_symbol():
 
 def test_default_params(L):
     p = ff.ff_default_params()
-    assert (p.n_scales, p.iters, p.patch, p.n_coef, p.rs_radius, p.eps, p.seed, p.rs_radius2) == \
-        (5, 6, 8, 16, 2, 1, 0x20180503, 4)
+    assert (p.n_scales, p.iters, p.patch, p.n_coef, p.rs_radius, p.eps, p.seed, p.rs_radius2, p.cost) == \
+        (5, 6, 8, 16, 2, 1, 0x20180503, 4, ff.FF_COST_WHT_SAD)
 
 
 @pytest.mark.parametrize("field,value", [("n_scales", 0), ("n_scales", 9), ("iters", 0), ("iters", 256),
                                          ("patch", 7), ("n_coef", 12), ("rs_radius", -1), ("rs_radius", 17),
-                                         ("eps", -1), ("rs_radius2", -1), ("rs_radius2", 17)])
+                                         ("eps", -1), ("rs_radius2", -1), ("rs_radius2", 17), ("cost", -1),
+                                         ("cost", 2)])
 def test_create_rejects_bad_params(L, field, value):
     p = ff.ff_default_params()
     setattr(p, field, value)

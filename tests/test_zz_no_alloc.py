@@ -63,3 +63,24 @@ def test_noalloc_rejects_pyramids_beyond_its_scratch(ffm):
     assert e.value.status == ffm.FF_ERR_ARG
     M.release(pa)
     M.close()
+
+
+def test_noalloc_census_cost_equals_match_pair(ffm):
+    """Under the Census cost (Sec. 3.1) the entry point matches on the pyramids' Census patterns as well."""
+    prm = configs.MatchParams(n_scales=3, iters=2, eps=1, cost=1)
+    M = ffm.Matcher(prm, 0)
+    a, b = _pair(930, 90, 140, 4, -2)
+    pa = M.features(torch.from_numpy(a).cuda())
+    pb = M.features(torch.from_numpy(b).cuda())
+    for dir, (X, Y) in enumerate(((pa, pb), (pb, pa))):
+        ref_flow, ref_cost = M.match_pair(X, Y, dir)
+        with torch.cuda.stream(M.stream):
+            flow = torch.full((90, 140, 2), -7, dtype=torch.int16, device="cuda")
+            cost = torch.full((90, 140), -7, dtype=torch.int32, device="cuda")
+        ffm.ff_match_pair_noalloc(M.ctx, X.handle, Y.handle, dir, flow.data_ptr(), cost.data_ptr())
+        M.sync()
+        assert torch.equal(flow, ref_flow), dir
+        assert torch.equal(cost, ref_cost), dir
+    M.release(pa)
+    M.release(pb)
+    M.close()
