@@ -177,7 +177,8 @@ FF_API ff_status ff_pyr_release(ff_ctx* ctx, ff_pyr* pyr);
 /* Sizes of level `level` of a pyramid; FF_ERR_ARG if the level does not exist. */
 FF_API ff_status ff_pyr_level_dims(const ff_pyr* pyr, int level, int* w, int* h);
 
-/* Device pointer to the 48 int16 features per pixel of `level` (read-only view owned by the pyramid).  Rows are
+/* Device pointer to the 48 features per pixel of `level` (read-only view owned by the pyramid), 16 bits each in
+ * offset binary: the stored uint16 is the coefficient + 32768 (the int16 coefficient XOR 0x8000).  Rows are
  * stored colour-split: row y holds the descriptors of x = 0, 2, 4, ... followed by those of x = 1, 3, 5, ...,
  * i.e. pixel (x, y) is descriptor y*w + (x even ? x/2 : (w+1)/2 + x/2). */
 FF_API const int16_t* ff_pyr_features(const ff_pyr* pyr, int level);

@@ -36,7 +36,8 @@ void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* 
 // so the transform is separable: a row pass (4 outputs per patch row) then a column pass.
 // CTA = 32x16 output pixels: its 39x23 input window (clamped halo) is staged in shared memory, the row pass is
 // computed once per (window row, output column, channel) into shared memory (|value| <= 8*255 fits int16), and
-// each thread then runs the column pass for two output pixels.
+// each thread then runs the column pass for two output pixels.  Coefficients are stored in offset binary
+// (C ^ 0x8000), the form the SAD of the propagation kernels works on.
 constexpr int kWtx = 32, kWty = 16;
 constexpr int kWinX = kWtx + 7, kWinY = kWty + 7;
 
@@ -124,7 +125,8 @@ __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
             for (int u = 0; u < 4; u++)
 #pragma unroll
                 for (int v = 0; v < 4; v += 2)
-                    out[ch * 8 + u * 2 + v / 2] = (uint32_t)(C[u][v] & 0xffff) | ((uint32_t)C[u][v + 1] << 16);
+                    out[ch * 8 + u * 2 + v / 2] =
+                        ((uint32_t)(C[u][v] & 0xffff) | ((uint32_t)C[u][v + 1] << 16)) ^ 0x80008000u;  // offset binary
         }
         uint4* dst = reinterpret_cast<uint4*>(L.feat + (size_t)feat_index(x, y, L.w) * kNF);
 #pragma unroll
@@ -155,7 +157,7 @@ __global__ void k_seed_pack(const int16_t* __restrict__ feat, int n, int w, int 
             uint32_t wv = 0;
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                int q = ((int)f[4 * k + j]) >> 7;
+                int q = feature_coef(f[4 * k + j]) >> 7;
                 s += q * q;
                 wv |= ((uint32_t)(q & 0xff)) << (8 * j);
             }

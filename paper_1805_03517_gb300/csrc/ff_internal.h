@@ -2,7 +2,8 @@
 //
 // Device data layout (all row-major, pixel (x, y) at y*w + x):
 //   image     uint8 [h][w][3]
-//   features  int16 [h][w][48]  96 B per pixel: three 32-B sectors (R, G, B), coefficient u*4+v in each;
+//   features  int16 [h][w][48]  96 B per pixel: three 32-B sectors (R, G, B), coefficient u*4+v in each,
+//                               stored in offset binary (C ^ 0x8000, read back with feature_coef);
 //                               colour-split rows: within row y the descriptors of even x come first, then odd x
 //                               (feat_index), so the pixels of one red-black half-sweep are contiguous
 //   census    uint32 [h][w][8]  32 B per pixel (FF_COST_CENSUS only): words 2c, 2c+1 = channel c's 48-bit 7x7
@@ -172,6 +173,11 @@ struct TileChoice {
 
 // ---------------------------------------------------------------------------------------------------------
 // shared device helpers (library only)
+
+// Coefficient value of a stored feature (the maps hold offset binary: C ^ 0x8000).
+__host__ __device__ __forceinline__ int feature_coef(int16_t stored) {
+    return (int)(int16_t)((uint16_t)stored ^ 0x8000u);
+}
 
 // Position of pixel (x, y) in a colour-split feature map of width w.
 __host__ __device__ __forceinline__ int feat_index(int x, int y, int w) {

@@ -38,24 +38,17 @@ __device__ __forceinline__ void load_desc(const void* __restrict__ f, int idx, u
             : "l"(p + 32 * k));
 }
 
-// Exact SAD of the 48 int16 coefficients, two per 32-bit word.  Both operands are mapped to offset binary
-// (x ^ 0x8000 per half, which preserves order), so per half max - min is |a - b| in [0, 32640] and a plain
-// 32-bit subtraction of the packed max/min never borrows across halves.  Two packed differences add without
-// carrying (2 * 32640 < 65536); __dp2a_lo then adds both 16-bit halves into the int32 sum.
-constexpr uint32_t kBias = 0x80008000u;
-
-__device__ __forceinline__ void bias_desc(uint32_t (&d)[24]) {
-#pragma unroll
-    for (int k = 0; k < 24; k++) d[k] ^= kBias;
-}
-
-__device__ __forceinline__ int sad_biased(const uint32_t (&a)[24], const uint32_t (&b)[24]) {
+// Exact SAD of the 48 coefficients, two per 32-bit word.  The feature maps store every coefficient in offset
+// binary (C ^ 0x8000, i.e. C + 32768 as uint16, which preserves order), so per half max - min is |a - b| in
+// [0, 32640] and a plain 32-bit subtraction of the packed max/min never borrows across halves.  Two packed
+// differences add without carrying (2 * 32640 < 65536); __dp2a_lo then adds both 16-bit halves into the int32
+// sum.
+__device__ __forceinline__ int sad_words(const uint32_t (&a)[24], const uint32_t (&b)[24]) {
     unsigned s = 0;
 #pragma unroll
     for (int k = 0; k < 24; k += 2) {
-        uint32_t b0 = b[k] ^ kBias, b1 = b[k + 1] ^ kBias;
-        uint32_t d0 = __vmaxu2(a[k], b0) - __vminu2(a[k], b0);
-        uint32_t d1 = __vmaxu2(a[k + 1], b1) - __vminu2(a[k + 1], b1);
+        uint32_t d0 = __vmaxu2(a[k], b[k]) - __vminu2(a[k], b[k]);
+        uint32_t d1 = __vmaxu2(a[k + 1], b[k + 1]) - __vminu2(a[k + 1], b[k + 1]);
         s = __dp2a_lo(d0 + d1, 0x0101u, s);
     }
     return (int)s;
@@ -63,14 +56,14 @@ __device__ __forceinline__ int sad_biased(const uint32_t (&a)[24], const uint32_
 
 // The two matching costs (Sec. 3.1), as policies of the hand-over and propagation kernels: descriptor size in
 // 32-bit words, load of one pixel's descriptor, one-time preparation of the source pixel's descriptor, distance.
-struct CostSad {  // SAD of the 48 int16 WHT coefficients
+struct CostSad {  // SAD of the 48 WHT coefficients (stored in offset binary)
     static constexpr int kWords = 24;
     __device__ __forceinline__ static void load(const void* __restrict__ f, int idx, uint32_t (&d)[kWords]) {
         load_desc(f, idx, d);
     }
-    __device__ __forceinline__ static void prep(uint32_t (&a)[kWords]) { bias_desc(a); }
+    __device__ __forceinline__ static void prep(uint32_t (&)[kWords]) {}
     __device__ __forceinline__ static int dist(const uint32_t (&a)[kWords], const uint32_t (&b)[kWords]) {
-        return sad_biased(a, b);
+        return sad_words(a, b);
     }
 };
 

@@ -251,7 +251,7 @@ __global__ void k_seed_pack16(const int16_t* __restrict__ feat, int n, int w, in
     __half row[kTcK];
 #pragma unroll
     for (int k = 0; k < kTcK; k++) {
-        int q = (p < n && k < kNF) ? ((int)feat[(size_t)feat_index(p % w, p / w, w) * kNF + k]) >> 7 : 0;
+        int q = (p < n && k < kNF) ? feature_coef(feat[(size_t)feat_index(p % w, p / w, w) * kNF + k]) >> 7 : 0;
         row[k] = __int2half_rn(q);
     }
     uint4* dst = reinterpret_cast<uint4*>(desc + (size_t)p * kTcK);

@@ -336,14 +336,15 @@ class Matcher:
         ff_pyr_release(self.ctx, pyr.handle)
 
     def level_features(self, pyr: Pyramid, level: int):
-        """Copy of the features of one level as int16 [h][w][48] in plain row order (the library stores rows
-        colour-split: even x first, then odd x)."""
+        """Copy of the features of one level as int16 [h][w][48] coefficients in plain row order (the library
+        stores rows colour-split -- even x first, then odd x -- and coefficients in offset binary)."""
         w, h = ff_pyr_level_dims(pyr.handle, level)
         ptr = ff_pyr_features(pyr.handle, level)
         split = self._empty((h, w, 48), self.torch.int16)
         self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
         src = _DevView(ptr, h * w * 96)
         split.view(-1).view(self.torch.uint8).copy_(self.torch.as_tensor(src, device=self.device))
+        split.bitwise_xor_(-32768)
         return self._unsplit(split)
 
     def level_census(self, pyr: Pyramid, level: int):
