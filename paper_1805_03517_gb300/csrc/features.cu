@@ -1,5 +1,8 @@
 // features.cu -- image pyramid and Walsh-Hadamard patch descriptors (FlowFields++, arXiv 1805.03517, Sec. 3
-// and Sec. 3.1), plus the packed 8-bit descriptors of the coarsest level used by the initial matching.
+// and Sec. 3.1), plus the Census patterns (Census cost) and the packed descriptors of the coarsest level used by
+// the initial matching.
+#include <cuda_fp16.h>
+
 #include "ff_internal.h"
 
 namespace ff {
@@ -27,6 +30,59 @@ void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* 
                        cudaStream_t st) {
     dim3 grid((dw + 127) / 128, dh);
     k_downsample<<<grid, 128, 0, st>>>(src, sw, sh, spitch, dst, dw, dh);
+}
+
+// Levels 1..a.top of the pyramid of one frame in one launch (same arithmetic as k_downsample).  A CTA owns a
+// 32x32 block of level 1 (computed from level 0 in global memory) and derives the co-located blocks of the next
+// levels from it in shared memory: level sizes are floor(w/2), so both sources 2x, 2x+1 of a level-s pixel lie
+// in the parent block (the clamp only matters when the parent level is 1 pixel wide or high, and its single
+// pixel is in block 0).  A 32x32 level-1 block halves down to one pixel at level 6, hence a.top <= 6.
+__global__ __launch_bounds__(256) void k_pyramid(PyrArgs a) {
+    __shared__ uint8_t buf[2][kPyrBlock][kPyrBlock][3];
+    int size = kPyrBlock, ox = blockIdx.x * kPyrBlock, oy = blockIdx.y * kPyrBlock;
+    for (int i = threadIdx.x; i < size * size; i += blockDim.x) {
+        const int lx = i % size, ly = i / size, x = ox + lx, y = oy + ly;
+        if (x >= a.w[1] || y >= a.h[1]) continue;
+        const int x0 = min(2 * x, a.w[0] - 1), x1 = min(2 * x + 1, a.w[0] - 1);
+        const int y0 = min(2 * y, a.h[0] - 1), y1 = min(2 * y + 1, a.h[0] - 1);
+        const uint8_t* r0 = a.src + (size_t)y0 * a.spitch;
+        const uint8_t* r1 = a.src + (size_t)y1 * a.spitch;
+        uint8_t* o = a.dst[1] + ((size_t)y * a.w[1] + x) * 3;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const int v = (r0[x0 * 3 + c] + r0[x1 * 3 + c] + r1[x0 * 3 + c] + r1[x1 * 3 + c] + 2) >> 2;
+            o[c] = (uint8_t)v;
+            buf[0][ly][lx][c] = (uint8_t)v;
+        }
+    }
+    int cur = 0;
+    for (int s = 2; s <= a.top; s++) {
+        __syncthreads();
+        const int pox = ox, poy = oy;  // parent block origin (level s-1)
+        size >>= 1;
+        ox >>= 1;
+        oy >>= 1;
+        for (int i = threadIdx.x; i < size * size; i += blockDim.x) {
+            const int lx = i % size, ly = i / size, x = ox + lx, y = oy + ly;
+            if (x >= a.w[s] || y >= a.h[s]) continue;
+            const int x0 = min(2 * x, a.w[s - 1] - 1) - pox, x1 = min(2 * x + 1, a.w[s - 1] - 1) - pox;
+            const int y0 = min(2 * y, a.h[s - 1] - 1) - poy, y1 = min(2 * y + 1, a.h[s - 1] - 1) - poy;
+            uint8_t* o = a.dst[s] + ((size_t)y * a.w[s] + x) * 3;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const int v = (buf[cur][y0][x0][c] + buf[cur][y0][x1][c] + buf[cur][y1][x0][c] +
+                               buf[cur][y1][x1][c] + 2) >> 2;
+                o[c] = (uint8_t)v;
+                buf[cur ^ 1][ly][lx][c] = (uint8_t)v;
+            }
+        }
+        cur ^= 1;
+    }
+}
+
+void launch_pyramid(const PyrArgs& a, cudaStream_t st) {
+    dim3 grid((a.w[1] + kPyrBlock - 1) / kPyrBlock, (a.h[1] + kPyrBlock - 1) / kPyrBlock);
+    k_pyramid<<<grid, 256, 0, st>>>(a);
 }
 
 // Walsh-Hadamard descriptor (Sec. 3.1): for every pixel and channel, the 4x4 lowest-sequency coefficients of
@@ -78,6 +134,36 @@ __device__ __forceinline__ void census_pixel(const uint8_t (&win)[3][kWinY][kWin
     uint4* d = reinterpret_cast<uint4*>(dst);
     d[0] = make_uint4(w[0], w[1], w[2], w[3]);
     d[1] = make_uint4(w[4], w[5], 0u, 0u);
+}
+
+// The initial-matching descriptors of a coarsest-level pixel (row p = y*w + x), from its stored coefficient
+// words: 8-bit C >> 7 (floor, in [-128, 127]) zero-padded to 64 with its squared norm, and the same values as
+// f16 (exact) for the tensor-core seed.  Padding rows past the level's pixel count stay zero from allocation.
+__device__ __forceinline__ void seed_rows(const uint32_t (&out)[24], int p, const WhtLevel& L) {
+    uint32_t w8[16], w16[32];
+    int norm = 0;
+#pragma unroll
+    for (int k = 0; k < 24; k++) {
+        const int q0 = feature_coef((int16_t)(out[k] & 0xffffu)) >> 7;
+        const int q1 = feature_coef((int16_t)(out[k] >> 16)) >> 7;
+        norm += q0 * q0 + q1 * q1;
+        const uint32_t pair8 = (uint32_t)(q0 & 0xff) | ((uint32_t)(q1 & 0xff) << 8);
+        if (k & 1) w8[k >> 1] |= pair8 << 16;
+        else w8[k >> 1] = pair8;
+        const __half2 h = __halves2half2(__int2half_rn(q0), __int2half_rn(q1));
+        w16[k] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+#pragma unroll
+    for (int k = 12; k < 16; k++) w8[k] = 0u;
+#pragma unroll
+    for (int k = 24; k < 32; k++) w16[k] = 0u;
+    uint4* d8 = reinterpret_cast<uint4*>(L.seed_desc + (size_t)p * kSeedK);
+#pragma unroll
+    for (int k = 0; k < 4; k++) d8[k] = make_uint4(w8[4 * k], w8[4 * k + 1], w8[4 * k + 2], w8[4 * k + 3]);
+    uint4* d16 = reinterpret_cast<uint4*>(static_cast<char*>(L.desc16) + (size_t)p * kSeedK * 2);
+#pragma unroll
+    for (int k = 0; k < 8; k++) d16[k] = make_uint4(w16[4 * k], w16[4 * k + 1], w16[4 * k + 2], w16[4 * k + 3]);
+    L.seed_norm[p] = norm;
 }
 
 __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
@@ -132,6 +218,7 @@ __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
 #pragma unroll
         for (int k = 0; k < 6; k++) dst[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
         if (L.census) census_pixel(win, lx, ly, L.census + (size_t)feat_index(x, y, L.w) * (kCensusBytes / 4));
+        if (L.seed_desc) seed_rows(out, y * L.w + x, L);
     }
 }
 
@@ -140,43 +227,6 @@ int wht_tiles(int w, int h) { return wht_tiles_x(w) * ((h + kWty - 1) / kWty); }
 
 void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st) {
     k_wht<<<total_tiles, 256, 0, st>>>(a);
-}
-
-// 8-bit descriptor of the coarsest level: C >> 7 (arithmetic, i.e. floor(C / 128), in [-128, 127]) for the 48
-// coefficients, zero for the 16 padding lanes and for padding rows n..n8-1; norm = sum of squares.
-__global__ void k_seed_pack(const int16_t* __restrict__ feat, int n, int w, int n8, int8_t* __restrict__ desc,
-                            int32_t* __restrict__ norm) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n8) return;
-    uint32_t words[16];
-    int s = 0;
-    if (p < n) {
-        const int16_t* f = feat + (size_t)feat_index(p % w, p / w, w) * kNF;
-#pragma unroll
-        for (int k = 0; k < 12; k++) {
-            uint32_t wv = 0;
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                int q = feature_coef(f[4 * k + j]) >> 7;
-                s += q * q;
-                wv |= ((uint32_t)(q & 0xff)) << (8 * j);
-            }
-            words[k] = wv;
-        }
-        norm[p] = s;
-    } else {
-#pragma unroll
-        for (int k = 0; k < 12; k++) words[k] = 0;
-    }
-#pragma unroll
-    for (int k = 12; k < 16; k++) words[k] = 0;
-    uint4* dst = reinterpret_cast<uint4*>(desc + (size_t)p * kSeedK);
-#pragma unroll
-    for (int k = 0; k < 4; k++) dst[k] = make_uint4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
-}
-
-void launch_seed_pack(const int16_t* feat, int n, int w, int n8, int8_t* desc, int32_t* norm, cudaStream_t st) {
-    k_seed_pack<<<(n8 + 127) / 128, 128, 0, st>>>(feat, n, w, n8, desc, norm);
 }
 
 }  // namespace ff

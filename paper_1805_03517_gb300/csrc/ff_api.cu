@@ -969,6 +969,9 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
             return fail(c, FF_ERR_CUDA, "TMA tensor map encoding failed");
         }
         FF_CUDA(c, cudaMemcpy(np->tmap, map, sizeof map, cudaMemcpyHostToDevice));
+        // padding rows of the seed descriptors are never written: zero them once
+        FF_CUDA(c, cudaMemsetAsync(np->seed_desc, 0, (size_t)np->n_pad * kSeedK, c->stream));
+        FF_CUDA(c, cudaMemsetAsync(np->desc16, 0, (size_t)np->n_pad128 * 128, c->stream));
         P = np.get();
         c->pyrs.push_back(std::move(np));
     }
@@ -981,11 +984,23 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
         FF_CUDA(c, cudaEventRecord(ea, c->stream));
     }
     int nl = 0;
-    for (int s = 1; s < L; s++) {
-        const uint8_t* src = s == 1 ? rgb_dev : P->img[s - 1];
-        int spitch = s == 1 ? pitch_bytes : P->ws[s - 1] * 3;
-        launch_downsample(src, P->ws[s - 1], P->hs[s - 1], spitch, P->img[s], P->ws[s], P->hs[s], c->stream);
+    if (L > 1) {  // levels 1..min(L-1, 6) in one launch, deeper levels one launch each
+        PyrArgs pa{};
+        pa.src = rgb_dev;
+        pa.spitch = pitch_bytes;
+        for (int s = 0; s < L; s++) {
+            pa.dst[s] = P->img[s];
+            pa.w[s] = P->ws[s];
+            pa.h[s] = P->hs[s];
+        }
+        pa.top = std::min(L - 1, kPyrFusedTop);
+        launch_pyramid(pa, c->stream);
         nl++;
+        for (int s = pa.top + 1; s < L; s++) {
+            launch_downsample(P->img[s - 1], P->ws[s - 1], P->hs[s - 1], P->ws[s - 1] * 3, P->img[s], P->ws[s],
+                              P->hs[s], c->stream);
+            nl++;
+        }
     }
     WhtArgs wa{};
     wa.n = L;
@@ -998,14 +1013,17 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
         lv.h = P->hs[s];
         lv.feat = P->feat[s];
         lv.census = P->cen[s];
+        if (s == L - 1) {  // the coarsest level also writes the initial-matching descriptors
+            lv.seed_desc = P->seed_desc;
+            lv.seed_norm = P->seed_norm;
+            lv.desc16 = P->desc16;
+        }
         lv.tiles_x = wht_tiles_x(P->ws[s]);
         lv.tile_base = tiles;
         tiles += wht_tiles(P->ws[s], P->hs[s]);
     }
     launch_wht(wa, tiles, c->stream);
-    launch_seed_pack(P->feat[L - 1], P->n_coarse, P->ws[L - 1], P->n_pad, P->seed_desc, P->seed_norm, c->stream);
-    launch_seed_pack16(P->feat[L - 1], P->n_coarse, P->ws[L - 1], P->n_pad128, P->desc16, c->stream);
-    nl += 3;
+    nl++;
     c->launches += nl;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

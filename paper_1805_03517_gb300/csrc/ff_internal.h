@@ -36,6 +36,9 @@ struct WhtLevel {
     int w, h;
     int16_t* feat;       // [h][w][48]
     uint32_t* census;    // [h][w][8], or null: no Census patterns
+    int8_t* seed_desc;   // coarsest level only (else null): int8 [n_pad][64] rows y*w + x, padding rows zero
+    int32_t* seed_norm;  //   [w*h] squared norms
+    void* desc16;        //   f16 [n_pad128][64] rows y*w + x, padding rows zero
     int tiles_x;
     int tile_base;       // first CTA of this level in the fused launch
 };
@@ -46,10 +49,23 @@ struct WhtArgs {
 
 void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* dst, int dw, int dh,
                        cudaStream_t st);
+constexpr int kPyrBlock = 32;       // level-1 pixels per CTA side of the fused pyramid kernel
+constexpr int kPyrFusedTop = 6;     // deepest level it derives (32 >> 5 = 1 pixel per CTA)
+struct PyrArgs {
+    const uint8_t* src;             // level 0, rows spitch bytes apart
+    int spitch;
+    uint8_t* dst[kMaxLevels];       // level s >= 1, compact rows (3 * w[s] bytes)
+    int w[kMaxLevels], h[kMaxLevels];
+    int top;                        // last level computed (1..kPyrFusedTop)
+};
+void launch_pyramid(const PyrArgs& a, cudaStream_t st);
+// kernels ff_features launches for an L-level pyramid: the fused pyramid (+ one per level past kPyrFusedTop), WHT
+inline int features_launches(int L) {
+    return (L > 1 ? 1 + (L - 1 > kPyrFusedTop ? L - 1 - kPyrFusedTop : 0) : 0) + 1;
+}
 int wht_tiles_x(int w);
 int wht_tiles(int w, int h);
 void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st);
-void launch_seed_pack(const int16_t* feat, int n, int w, int n8, int8_t* desc, int32_t* norm, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------------------
 // initial matches (exact nearest neighbour at the coarsest level)
@@ -83,7 +99,6 @@ struct SeedTcProblem {
 };
 cudaError_t seed_tc_init_attributes();
 bool seed_tc_encode_map(void* map_host_128b, const void* desc16_dev, int n_pad);
-void launch_seed_pack16(const int16_t* feat, int n, int w, int n_pad, void* desc16, cudaStream_t st);
 // wait_limit: polls before a wait gives up (then *err_dev is set); withhold: issue no copies (test of the waits)
 void launch_seed_tc(const SeedTcProblem* probs_dev, int n_probs, int total_ctas, int64_t total_pix,
                     uint32_t wait_limit, int withhold, int* err_dev, cudaStream_t st);

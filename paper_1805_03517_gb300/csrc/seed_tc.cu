@@ -244,26 +244,6 @@ void launch_seed_tc(const SeedTcProblem* probs_dev, int n_probs, int total_ctas,
     k_seed_finish<<<(int)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(probs_dev, n_probs, total_pix);
 }
 
-// f16 copy of the 8-bit descriptors (C >> 7) for the tensor-core path: [n_pad][64], zero padded.
-__global__ void k_seed_pack16(const int16_t* __restrict__ feat, int n, int w, int n_pad, __half* __restrict__ desc) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pad) return;
-    __half row[kTcK];
-#pragma unroll
-    for (int k = 0; k < kTcK; k++) {
-        int q = (p < n && k < kNF) ? feature_coef(feat[(size_t)feat_index(p % w, p / w, w) * kNF + k]) >> 7 : 0;
-        row[k] = __int2half_rn(q);
-    }
-    uint4* dst = reinterpret_cast<uint4*>(desc + (size_t)p * kTcK);
-    const uint4* src = reinterpret_cast<const uint4*>(row);
-#pragma unroll
-    for (int k = 0; k < kRowBytes / 16; k++) dst[k] = src[k];
-}
-
-void launch_seed_pack16(const int16_t* feat, int n, int w, int n_pad, void* desc16, cudaStream_t st) {
-    k_seed_pack16<<<(n_pad + 127) / 128, 128, 0, st>>>(feat, n, w, n_pad, reinterpret_cast<__half*>(desc16));
-}
-
 // Tensor map of a [n_pad][64] f16 descriptor array: boxes of 64 x 128 (one 128-byte row per descriptor),
 // 128-byte swizzle, rows past n_pad read as zeros.
 bool seed_tc_encode_map(void* map_out, const void* desc16_dev, int n_pad) {

@@ -204,7 +204,7 @@ ff_status admit(ff_server* s) {
         q.chunk = 0;
         s->active.push_back(std::move(s->queued.front()));
         s->queued.pop_front();
-        s->launches += 2 * (q.L + 1);  // feature launches enqueued by ff_features
+        s->launches += 2 * features_launches(q.L);  // feature launches enqueued by ff_features
     }
     return FF_OK;
 }
