@@ -1002,11 +1002,13 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
             nl++;
         }
     }
+    // Levels in the launch from the coarsest up: its CTAs, which also write the seed rows, start first instead
+    // of forming the launch's tail.
     WhtArgs wa{};
     wa.n = L;
     int tiles = 0;
-    for (int s = 0; s < L; s++) {
-        WhtLevel& lv = wa.lv[s];
+    for (int s = L - 1; s >= 0; s--) {
+        WhtLevel& lv = wa.lv[L - 1 - s];
         lv.img = s == 0 ? rgb_dev : P->img[s];
         lv.pitch = s == 0 ? pitch_bytes : P->ws[s] * 3;
         lv.w = P->ws[s];

@@ -7,8 +7,8 @@
 // request advances by one propagation launch-chunk of its current level; a request's first tick also builds its
 // pyramids, finds its initial matches and does the first hand-over, the first chunk of every level carries that
 // level's hand-over, and the last chunk of level 0 is followed by the consistency check.  Work of all active
-// requests of a tick is merged into one launch per kernel kind (propagation: one per launch configuration), so
-// requests that arrive while others are on the GPU join the next tick.  Results depend only on the request
+// requests of a tick is merged into one launch per kernel kind (propagation: one per launch configuration, these
+// running concurrently on side streams), so requests that arrive while others are on the GPU join the next tick.  Results depend only on the request
 // (the random-search hash is keyed by pixel, level, iteration and direction), never on the mix.
 #include <cuda_runtime.h>
 
@@ -28,7 +28,8 @@ using namespace ff;
 
 namespace {
 
-constexpr int kRing = 4;  // ticks in flight before the host waits
+constexpr int kRing = 4;         // ticks in flight before the host waits
+constexpr int kSideStreams = 3;  // extra streams for the concurrent propagation launches of a tick
 
 size_t a256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -107,11 +108,25 @@ struct ff_server {
     RingSlot ring[kRing];
     int64_t tick = 0;
     int64_t launches = 0;
+    // side streams on which the propagation launches of one tick run concurrently (fork/join with events)
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t fork = nullptr, join[kSideStreams] = {};
 };
 
 namespace {
 
 ff_status srv_fail(ff_server* s, ff_status st, const char* msg) { return (ff_status)ctx_set_error(s->ctx, st, msg); }
+
+ff_status ensure_side_streams(ff_server* s) {
+    if (s->fork) return FF_OK;
+    for (int k = 0; k < kSideStreams; k++)
+        if (cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s->join[k], cudaEventDisableTiming) != cudaSuccess)
+            return srv_fail(s, FF_ERR_CUDA, "side stream creation failed");
+    if (cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) != cudaSuccess)
+        return srv_fail(s, FF_ERR_CUDA, "event creation failed");
+    return FF_OK;
+}
 
 ff_status ring_reserve(ff_server* s, RingSlot& r, size_t bytes) {
     if (r.done) {
@@ -382,11 +397,33 @@ ff_status tick(ff_server* s) {
                         stm);
         nl++;
     }
-    for (size_t g = 0; g < pls.size(); g++) {
+    // Propagation launches of different configurations are independent (disjoint problems, queues and
+    // counters): the largest runs on the main stream, the others on side streams, so small launches (coarse
+    // levels, other frame sizes) fill the SMs that the tail of a large one leaves idle.
+    std::vector<size_t> order(pls.size());
+    for (size_t g = 0; g < order.size(); g++) order[g] = g;
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return pls[a].nq > pls[b].nq; });
+    const int n_side = (int)std::min<size_t>(kSideStreams, pls.size() > 0 ? pls.size() - 1 : 0);
+    if (n_side > 0) {
+        st = ensure_side_streams(s);
+        if (st != FF_OK) return st;
+        if (cudaEventRecord(s->fork, stm) != cudaSuccess) return srv_fail(s, FF_ERR_CUDA, "event record failed");
+        for (int k = 0; k < n_side; k++)
+            if (cudaStreamWaitEvent(s->side[k], s->fork, 0) != cudaSuccess)
+                return srv_fail(s, FF_ERR_CUDA, "stream wait failed");
+    }
+    for (size_t i = 0; i < order.size(); i++) {
+        const size_t g = order[i];
+        cudaStream_t sg = i == 0 ? stm : s->side[(i - 1) % kSideStreams];
         launch_propagate(reinterpret_cast<const PropProblem*>(r.dev + o_prop),
                          reinterpret_cast<const int2*>(r.dev + o_q) + pls[g].q0, pls[g].nq,
-                         reinterpret_cast<int*>(r.dev + o_cnt) + g, pls[g].grid, pls[g].pl, stm);
+                         reinterpret_cast<int*>(r.dev + o_cnt) + g, pls[g].grid, pls[g].pl, sg);
         nl++;
+    }
+    for (int k = 0; k < n_side; k++) {
+        if (cudaEventRecord(s->join[k], s->side[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(stm, s->join[k], 0) != cudaSuccess)
+            return srv_fail(s, FF_ERR_CUDA, "stream join failed");
     }
     for (const Cons& cs : cons) {
         launch_consistency(cs.f, cs.b, nullptr, cs.w, cs.h, s->cv.eps, cs.mask, stm);
@@ -514,6 +551,14 @@ ff_status ff_server_destroy(ff_server* s) {
         if (r.dev) cudaFree(r.dev);
         if (r.done) cudaEventDestroy(r.done);
     }
+    for (int k = 0; k < kSideStreams; k++) {
+        if (s->side[k]) {
+            cudaStreamSynchronize(s->side[k]);
+            cudaStreamDestroy(s->side[k]);
+        }
+        if (s->join[k]) cudaEventDestroy(s->join[k]);
+    }
+    if (s->fork) cudaEventDestroy(s->fork);
     delete s;
     return FF_OK;
 }

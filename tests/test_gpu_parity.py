@@ -54,14 +54,17 @@ def check_pair(img_a, img_b, prm):
     return got
 
 
-def test_features_parity(lib_built):
+@pytest.mark.parametrize("L", [5, 7, 8])
+def test_features_parity(lib_built, L):
+    """Pyramid and WHT features of every level; L = 7 and 8 also take the per-level pyramid launches past the
+    six levels the fused pyramid kernel derives from one block."""
     o = oracle.default()
-    M = matcher(mp(5, 1))
-    for (h, w) in ((1, 1), (3, 2), (23, 37), (96, 128), (41, 300)):
+    M = matcher(mp(L, 1))
+    for (h, w) in ((1, 1), (3, 2), (23, 37), (96, 128), (41, 300), (130, 257)):
         img = P.rand_img(h * 131 + w, h, w)
         t = torch.from_numpy(img).cuda()
         pyr = M.features(t)
-        levels = o.pyramid(img, 5)
+        levels = o.pyramid(img, L)
         for s, lv in enumerate(levels):
             got = M.level_features(pyr, s)
             M.sync()
