@@ -128,7 +128,10 @@ const TileCfg kCands[] = {
     {32, 16, 1, 128, 0}, {16, 16, 1, 128, 0}, {16, 8, 2, 128, 0},  {8, 8, 3, 128, 0},   {32, 32, 1, 512, 0},
     {32, 16, 2, 512, 0}, {16, 16, 2, 512, 0}, {24, 24, 1, 512, 0}, {32, 16, 1, 128, 1}, {16, 16, 1, 128, 1},
     {16, 8, 2, 128, 1},  {8, 8, 3, 128, 1},   {32, 16, 1, 256, 1}, {16, 16, 1, 256, 1}, {16, 8, 2, 256, 1},
-    {8, 8, 3, 256, 1},   {32, 32, 1, 512, 1}, {16, 16, 2, 512, 1}, {24, 24, 1, 512, 1}};
+    {8, 8, 3, 256, 1},   {32, 32, 1, 512, 1}, {16, 16, 2, 512, 1}, {24, 24, 1, 512, 1},
+    // coarse levels: one pixel per thread per half-sweep (fewer dependent loads in a row)
+    {8, 8, 3, 512, 0},   {8, 8, 2, 512, 0},   {16, 8, 2, 512, 0},   {16, 16, 1, 512, 0}, {8, 8, 3, 512, 1},
+    {16, 8, 2, 512, 1},  {16, 16, 1, 512, 1}, {8, 8, 6, 512, 0},   {8, 8, 6, 512, 1}};
 constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
 
 // Tuning key: level index, level size of the first job, number of directions in the launch, iterations.
