@@ -29,6 +29,7 @@ METRIC = "Mpx/s bidirectional FF matching, batched/served vs single-pair; p50/p9
 UNIT = "Mpx/s"
 L2_FLUSH_BYTES = 512 << 20
 ALG_BYTES_PER_PIXEL_ITER = 11 * 96 + 96 + 8  # candidate gathers + own descriptor + flow/cost, per direction
+ALG_BYTES_PER_PIXEL_ITER_CENSUS = 11 * 32 + 32 + 8  # the same with 32-byte Census patterns
 
 
 def parse():
@@ -197,6 +198,7 @@ def measure_census(torch, ff, configs, stream, local_rank, steps, flush):
     with torch.cuda.stream(stream):
         d = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in imgs]
     stream.synchronize()
+    peak, _ = load_peaks()
     out = {"workload": wl.name, "px_per_step": wl.pixels, "eps": spec.params.eps, "steps": steps,
            "l2": "flushed before every timed step"}
     for name, cost in (("census", 1), ("wht_sad", 0)):
@@ -228,9 +230,34 @@ def measure_census(torch, ff, configs, stream, local_rank, steps, flush):
             ev.append((e0, e1))
         stream.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        # propagation roofline of this cost: algorithmic bytes per launch / device time per launch (profiling
+        # context with the same launch configuration)
+        P = ff.Matcher(dataclasses.replace(spec.params, cost=cost), local_rank, stream)
+        for lvl, cfg in enumerate(tuning):
+            ff.ff_set_tuning(P.ctx, lvl, cfg)
+        ff.ff_profile_enable(P.ctx, True)
+        n_prof = 10
+        for r in range(n_prof + 2):
+            if r == 2:
+                ff.ff_profile_read(P.ctx)
+            flush()
+            pyrs = [(P.features(a), P.features(b)) for a, b in d]
+            P.match_batch(pyrs, with_cost=False)
+            for pa, pb in pyrs:
+                P.release(pa)
+                P.release(pb)
+        prop_ms, prop_launches = ff.ff_profile_read(P.ctx)["propagate"]
+        P.close()
+        per_px_iter = ALG_BYTES_PER_PIXEL_ITER_CENSUS if cost else ALG_BYTES_PER_PIXEL_ITER
+        pix_iters = ff.ff_work_counts(M.ctx, spec.w, spec.h)[0]
+        bytes_per_launch = pix_iters * 2 * per_px_iter / (prop_launches / n_prof)
+        achieved = bytes_per_launch / (prop_ms / prop_launches / 1000.0) / 1e9
         M.close()
         out[name] = {"value": wl.pixels / (ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms,
-                     "tiles_per_level": [list(c) for c in tuning]}
+                     "tiles_per_level": [list(c) for c in tuning],
+                     "k_propagate": {"alg_bytes_per_pixel_iter": per_px_iter, "achieved_gbs": achieved,
+                                     "peak_gbs": peak, "frac": achieved / peak,
+                                     "avg_launch_ms": prop_ms / prop_launches}}
     return out
 
 

@@ -325,11 +325,22 @@ class Matcher:
         with self.torch.cuda.stream(self.stream):
             return self.torch.empty(shape, dtype=dtype, device=self.device)
 
+    def _uses(self, *tensors):
+        """The library reads these tensors on its stream: order that after the work already queued on the
+        caller's current stream, and keep torch's allocator from reusing their memory before it has run (the
+        call returns before the kernels do, so a temporary argument may be freed right away)."""
+        cur = self.torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+        for t in tensors:
+            t.record_stream(self.stream)
+
     def features(self, img) -> Pyramid:
         """img: uint8 [h][w][3] CUDA tensor (rows may be strided)."""
         assert img.dtype == self.torch.uint8 and img.is_cuda and img.dim() == 3 and img.shape[2] == 3
         assert img.stride(2) == 1 and img.stride(1) == 3
         h, w = int(img.shape[0]), int(img.shape[1])
+        self._uses(img)
         return Pyramid(ff_features(self.ctx, img.data_ptr(), w, h, img.stride(0)), w, h)
 
     def release(self, pyr: Pyramid):
@@ -416,12 +427,14 @@ class Matcher:
     def consistency(self, fwd, bwd, eps: int):
         h, w = int(fwd.shape[0]), int(fwd.shape[1])
         mask = self._empty((h, w), self.torch.uint8)
+        self._uses(fwd, bwd)
         ff_consistency(self.ctx, fwd.data_ptr(), bwd.data_ptr(), w, h, eps, mask.data_ptr())
         return mask
 
     def sparsify(self, fwd, bwd, eps: int, min_matches: int):
         h, w = int(fwd.shape[0]), int(fwd.shape[1])
         out = self._empty((h, w), self.torch.uint8)
+        self._uses(fwd, bwd)
         ff_sparsify(self.ctx, fwd.data_ptr(), bwd.data_ptr(), w, h, eps, min_matches, out.data_ptr())
         return out
 
