@@ -221,7 +221,8 @@ FF_API ff_status ff_work_counts(ff_ctx* ctx, int w, int h, int64_t* pixel_iters,
  * admitted first come first served while at most `max_active` are in flight and the device bytes of the
  * admitted requests (two feature pyramids + flow/cost scratch each) stay within `mem_budget_bytes`.  Each
  * ff_server_step enqueues one tick on the context's stream: every active request advances by one propagation
- * launch of its current level, with the work of all active requests merged into one launch per kernel kind;
+ * launch of its current level (by all of the level's launches while at most 8 requests are in flight), with the
+ * work of all active requests merged into one launch per kernel kind and launch configuration;
  * requests that arrive while others are on the GPU join at the next tick.  A request's results are identical
  * to matching it alone (ff_match_batch), whatever else is in flight.  Not thread-safe per server. */
 typedef struct ff_server ff_server;

@@ -4,12 +4,15 @@
 // Requests are queued by ff_server_submit and admitted, first come first served, while the number of active
 // requests stays below max_active and the device bytes of admitted requests (their two feature pyramids and
 // their flow/cost scratch) stay within the memory budget.  Every ff_server_step enqueues one tick: each active
-// request advances by one propagation launch-chunk of its current level; a request's first tick also builds its
-// pyramids, finds its initial matches and does the first hand-over, the first chunk of every level carries that
-// level's hand-over, and the last chunk of level 0 is followed by the consistency check.  Work of all active
-// requests of a tick is merged into one launch per kernel kind (propagation: one per launch configuration, these
-// running concurrently on side streams), so requests that arrive while others are on the GPU join the next tick.  Results depend only on the request
-// (the random-search hash is keyed by pixel, level, iteration and direction), never on the mix.
+// request advances by one propagation launch-chunk of its current level (by all remaining chunks of the level
+// while at most 8 requests are in flight, which cuts the ticks, and their overhead, on a request's latency at
+// light load); a request's first tick also builds its pyramids, finds its initial matches and does the first
+// hand-over, the first chunk of every level carries that level's hand-over, and the last chunk of level 0 is
+// followed by the consistency check.  Work of all active requests of a tick is merged into one launch per
+// kernel kind (propagation: one per launch configuration and chunk position, the configurations running
+// concurrently on side streams), so requests that arrive while others are on the GPU join the next tick.
+// Results depend only on the request (the random-search hash is keyed by pixel, level, iteration and
+// direction), never on the mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +33,7 @@ namespace {
 
 constexpr int kRing = 4;         // ticks in flight before the host waits
 constexpr int kSideStreams = 3;  // extra streams for the concurrent propagation launches of a tick
+constexpr int kWholeLevelMaxActive = 8;  // up to this many requests in flight, a tick runs a whole level
 
 size_t a256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -224,10 +228,13 @@ ff_status admit(ff_server* s) {
     return FF_OK;
 }
 
+// Propagation launches of a tick are grouped by phase (the position of a chunk among the chunks one request
+// runs in this tick: a request's chunk i + 1 reads what its chunk i wrote) and by launch configuration.
 struct PropGroupKey {
-    int tw, th, n_iter, threads, spec;
+    int phase, tw, th, n_iter, threads, spec;
     bool operator<(const PropGroupKey& o) const {
-        return std::tie(tw, th, n_iter, threads, spec) < std::tie(o.tw, o.th, o.n_iter, o.threads, o.spec);
+        return std::tie(phase, tw, th, n_iter, threads, spec) <
+               std::tie(o.phase, o.tw, o.th, o.n_iter, o.threads, o.spec);
     }
 };
 
@@ -248,6 +255,9 @@ ff_status tick(ff_server* s) {
     int seed_tiles = 0;
     int64_t ho_pix = 0;
     std::vector<size_t> finished;
+    // With few requests in flight a tick runs every remaining chunk of each request's level (fewer ticks, so
+    // less per-tick overhead on a request's latency); under load one chunk, so that arrivals join sooner.
+    const bool whole_level = (int)s->active.size() <= kWholeLevelMaxActive;
     for (size_t ri = 0; ri < s->active.size(); ri++) {
         Req& q = *s->active[ri];
         const int sl = q.level, L = q.L;
@@ -296,39 +306,44 @@ ff_status tick(ff_server* s) {
             }
         }
         const TileChoice c = q.cfg[sl];
-        const int t0 = q.chunk * c.k, n_iter = std::min(c.k, T - t0);
-        const bool last = sl == 0 && q.chunk == q.n_chunks[sl] - 1;
-        auto& grp = groups[PropGroupKey{c.tw, c.th, n_iter, c.threads, c.spec}];
-        for (int d = 0; d < 2; d++) {
-            const PyrView& X = d == 0 ? q.A : q.B;
-            const PyrView& Y = d == 0 ? q.B : q.A;
-            PropProblem pp{};
-            pp.fa = cost_desc(X, sl, s->cv.cost);
-            pp.fb = cost_desc(Y, sl, s->cv.cost);
-            pp.w = X.ws[sl];
-            pp.h = X.hs[sl];
-            const int in = q.cur[d], out = in ^ 1;
-            pp.flow_in = q.flow[d][sl][in];
-            pp.cost_in = q.cost[d][sl][in];
-            int32_t* user_cost = d == 0 ? q.io.cost_fwd : q.io.cost_bwd;
-            if (last) {
-                pp.flow_out = reinterpret_cast<uint32_t*>(d == 0 ? q.io.flow_fwd : q.io.flow_bwd);
-                pp.cost_out = user_cost ? user_cost : q.cost[d][sl][out];
-            } else {
-                pp.flow_out = q.flow[d][sl][out];
-                pp.cost_out = q.cost[d][sl][out];
+        const int n_run = whole_level ? q.n_chunks[sl] - q.chunk : 1;
+        for (int phase = 0; phase < n_run; phase++) {
+            const int chunk = q.chunk + phase;
+            const int t0 = chunk * c.k, n_iter = std::min(c.k, T - t0);
+            const bool last = sl == 0 && chunk == q.n_chunks[sl] - 1;
+            auto& grp = groups[PropGroupKey{phase, c.tw, c.th, n_iter, c.threads, c.spec}];
+            for (int d = 0; d < 2; d++) {
+                const PyrView& X = d == 0 ? q.A : q.B;
+                const PyrView& Y = d == 0 ? q.B : q.A;
+                PropProblem pp{};
+                pp.fa = cost_desc(X, sl, s->cv.cost);
+                pp.fb = cost_desc(Y, sl, s->cv.cost);
+                pp.w = X.ws[sl];
+                pp.h = X.hs[sl];
+                const int in = q.cur[d], out = in ^ 1;
+                pp.flow_in = q.flow[d][sl][in];
+                pp.cost_in = q.cost[d][sl][in];
+                int32_t* user_cost = d == 0 ? q.io.cost_fwd : q.io.cost_bwd;
+                if (last) {
+                    pp.flow_out = reinterpret_cast<uint32_t*>(d == 0 ? q.io.flow_fwd : q.io.flow_bwd);
+                    pp.cost_out = user_cost ? user_cost : q.cost[d][sl][out];
+                } else {
+                    pp.flow_out = q.flow[d][sl][out];
+                    pp.cost_out = q.cost[d][sl][out];
+                }
+                q.cur[d] = out;
+                pp.tiles_x = (pp.w + c.tw - 1) / c.tw;
+                pp.t0 = t0;
+                pp.n_iter = n_iter;
+                pp.level = sl;
+                pp.dir = d;
+                pp.seed = s->cv.seed;
+                pp.rs_radius = s->cv.rs_radius;
+                grp.push_back({pp, pp.tiles_x * ((pp.h + c.th - 1) / c.th)});
             }
-            q.cur[d] = out;
-            pp.tiles_x = (pp.w + c.tw - 1) / c.tw;
-            pp.t0 = t0;
-            pp.n_iter = n_iter;
-            pp.level = sl;
-            pp.dir = d;
-            pp.seed = s->cv.seed;
-            pp.rs_radius = s->cv.rs_radius;
-            grp.push_back({pp, pp.tiles_x * ((pp.h + c.th - 1) / c.th)});
         }
-        if (++q.chunk == q.n_chunks[sl]) {
+        q.chunk += n_run;
+        if (q.chunk == q.n_chunks[sl]) {
             if (sl == 0) {
                 cons.push_back({reinterpret_cast<const uint32_t*>(q.io.flow_fwd),
                                 reinterpret_cast<const uint32_t*>(q.io.flow_bwd), q.A.w, q.A.h, q.io.mask});
@@ -362,7 +377,7 @@ ff_status tick(ff_server* s) {
     struct PL {
         PropLaunch pl;
         size_t q0;
-        int nq, grid;
+        int nq, grid, phase;
     };
     std::vector<PL> pls;
     size_t pi = 0, qi = 0;
@@ -382,7 +397,8 @@ ff_status tick(ff_server* s) {
         const size_t smem = prop_smem_bytes(k.tw, k.th, k.n_iter);
         const int nq = (int)(qi - q0);
         pls.push_back({PropLaunch{k.tw, k.th, k.n_iter, k.threads, k.spec, s->cv.cost}, q0, nq,
-                       std::min(nq, prop_blocks_per_sm(smem, k.threads, k.spec != 0, s->cv.cost) * s->cv.n_sms)});
+                       std::min(nq, prop_blocks_per_sm(smem, k.threads, k.spec != 0, s->cv.cost) * s->cv.n_sms),
+                       k.phase});
     }
     cudaStream_t stm = s->cv.stream;
     if (cudaMemcpyAsync(r.dev, r.host, bytes, cudaMemcpyHostToDevice, stm) != cudaSuccess)
@@ -397,33 +413,39 @@ ff_status tick(ff_server* s) {
                         stm);
         nl++;
     }
-    // Propagation launches of different configurations are independent (disjoint problems, queues and
-    // counters): the largest runs on the main stream, the others on side streams, so small launches (coarse
-    // levels, other frame sizes) fill the SMs that the tail of a large one leaves idle.
-    std::vector<size_t> order(pls.size());
-    for (size_t g = 0; g < order.size(); g++) order[g] = g;
-    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return pls[a].nq > pls[b].nq; });
-    const int n_side = (int)std::min<size_t>(kSideStreams, pls.size() > 0 ? pls.size() - 1 : 0);
-    if (n_side > 0) {
-        st = ensure_side_streams(s);
-        if (st != FF_OK) return st;
-        if (cudaEventRecord(s->fork, stm) != cudaSuccess) return srv_fail(s, FF_ERR_CUDA, "event record failed");
-        for (int k = 0; k < n_side; k++)
-            if (cudaStreamWaitEvent(s->side[k], s->fork, 0) != cudaSuccess)
-                return srv_fail(s, FF_ERR_CUDA, "stream wait failed");
-    }
-    for (size_t i = 0; i < order.size(); i++) {
-        const size_t g = order[i];
-        cudaStream_t sg = i == 0 ? stm : s->side[(i - 1) % kSideStreams];
-        launch_propagate(reinterpret_cast<const PropProblem*>(r.dev + o_prop),
-                         reinterpret_cast<const int2*>(r.dev + o_q) + pls[g].q0, pls[g].nq,
-                         reinterpret_cast<int*>(r.dev + o_cnt) + g, pls[g].grid, pls[g].pl, sg);
-        nl++;
-    }
-    for (int k = 0; k < n_side; k++) {
-        if (cudaEventRecord(s->join[k], s->side[k]) != cudaSuccess ||
-            cudaStreamWaitEvent(stm, s->join[k], 0) != cudaSuccess)
-            return srv_fail(s, FF_ERR_CUDA, "stream join failed");
+    // Within a phase, propagation launches of different configurations are independent (disjoint problems,
+    // queues and counters): the largest runs on the main stream, the others on side streams, so small launches
+    // (coarse levels, other frame sizes) fill the SMs that the tail of a large one leaves idle.  Phases run one
+    // after the other (the groups map is ordered by phase).
+    for (size_t g0 = 0; g0 < pls.size();) {
+        size_t g1 = g0;
+        while (g1 < pls.size() && pls[g1].phase == pls[g0].phase) g1++;
+        std::vector<size_t> order;
+        for (size_t g = g0; g < g1; g++) order.push_back(g);
+        std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return pls[a].nq > pls[b].nq; });
+        const int n_side = (int)std::min<size_t>(kSideStreams, order.size() - 1);
+        if (n_side > 0) {
+            st = ensure_side_streams(s);
+            if (st != FF_OK) return st;
+            if (cudaEventRecord(s->fork, stm) != cudaSuccess) return srv_fail(s, FF_ERR_CUDA, "event record failed");
+            for (int k = 0; k < n_side; k++)
+                if (cudaStreamWaitEvent(s->side[k], s->fork, 0) != cudaSuccess)
+                    return srv_fail(s, FF_ERR_CUDA, "stream wait failed");
+        }
+        for (size_t i = 0; i < order.size(); i++) {
+            const size_t g = order[i];
+            cudaStream_t sg = i == 0 ? stm : s->side[(i - 1) % kSideStreams];
+            launch_propagate(reinterpret_cast<const PropProblem*>(r.dev + o_prop),
+                             reinterpret_cast<const int2*>(r.dev + o_q) + pls[g].q0, pls[g].nq,
+                             reinterpret_cast<int*>(r.dev + o_cnt) + g, pls[g].grid, pls[g].pl, sg);
+            nl++;
+        }
+        for (int k = 0; k < n_side; k++) {
+            if (cudaEventRecord(s->join[k], s->side[k]) != cudaSuccess ||
+                cudaStreamWaitEvent(stm, s->join[k], 0) != cudaSuccess)
+                return srv_fail(s, FF_ERR_CUDA, "stream join failed");
+        }
+        g0 = g1;
     }
     for (const Cons& cs : cons) {
         launch_consistency(cs.f, cs.b, nullptr, cs.w, cs.h, s->cv.eps, cs.mask, stm);

@@ -112,3 +112,35 @@ def test_server_rejects_and_bounds(ffm):
     assert sorted(done) == [10, 11, 12, 13]
     S.close()
     M.close()
+
+
+def test_many_in_flight_one_chunk_per_tick(ffm):
+    """More requests in flight than the whole-level threshold: ticks advance one chunk per request (and switch
+    to whole levels once few are left); every result equals matching the pair alone."""
+    prm = configs.MatchParams(n_scales=3, iters=3, eps=1)
+    M = ffm.Matcher(prm, 0)
+    sizes = [(40 + 4 * i, 56 + 6 * i) for i in range(14)]
+    pairs = [_pair(600 + i, h, w) for i, (h, w) in enumerate(sizes)]
+    dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in pairs]
+    torch.cuda.synchronize()
+    alone = []
+    for da, db in dev:
+        pa, pb = M.features(da), M.features(db)
+        o = M.match_batch([(pa, pb)])[0]
+        M.sync()
+        alone.append(tuple(o[k].cpu().numpy() for k in NAMES))
+        M.release(pa)
+        M.release(pb)
+    S = ffm.Server(M, mem_budget_bytes=1 << 30, max_active=14)
+    outs = {i: _outputs(M, h, w) for i, (h, w) in enumerate(sizes)}
+    for i in range(len(sizes)):
+        S.submit(i, dev[i][0], dev[i][1], outs[i])
+    done = []
+    while len(done) < len(sizes):
+        S.step()
+        done += S.poll(wait=True)
+    M.sync()
+    for i in range(len(sizes)):
+        G.assert_same(tuple(outs[i][k].cpu().numpy() for k in NAMES), alone[i])
+    S.close()
+    M.close()
