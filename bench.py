@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-pair batched measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream measurement")
     ap.add_argument("--no-census", action="store_true", help="skip the Census-cost measurement")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run the autotuner instead of the package's table of tuned configurations")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--tuning", default=None,
                     help="JSON list of per-level [tile_w, tile_h, iters_per_launch, threads, speculate] instead of "
@@ -60,8 +62,9 @@ def aggregate_ranks(torch, dist, dev, ms_local, px_per_step, world):
     return ms, px_per_step * world / (ms / 1000.0) / 1e6
 
 
-def propagate_traffic():
-    """DRAM bytes per k_propagate launch from the committed ncu capture, if the kernel source is unchanged."""
+def propagate_traffic(tuning):
+    """DRAM bytes per k_propagate launch from the committed ncu capture, if the kernel source and the per-level
+    launch configuration are the ones it was captured with."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "propagate_traffic_kitti_1242x375.json")
@@ -72,7 +75,11 @@ def propagate_traffic():
         rec = json.load(f)
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()
-    return rec["dram_bytes_per_launch"] if rec.get("propagate_cu_sha256") == sha else None
+    if rec.get("propagate_cu_sha256") != sha:
+        return None
+    if [list(c) for c in rec.get("tiles_per_level", [])] != [list(c) for c in tuning]:
+        return None
+    return rec["dram_bytes_per_launch"]
 
 
 def load_peaks():
@@ -418,9 +425,15 @@ def main():
         with torch.cuda.stream(stream):
             flush.fill_(1)
 
-    # per-level propagation configuration, chosen once by the library's autotuner on this workload
-    if args.tuning:
-        tuning = [tuple(c) for c in json.loads(args.tuning)]
+    # per-level propagation configuration: given, from the package's table of autotuned configurations for this
+    # workload, or chosen now by the library's autotuner (--autotune, or a workload without a table entry)
+    table = {}
+    with open(os.path.join(ROOT, "paper_1805_03517_gb300", "tuned.json")) as f:
+        table = json.load(f)
+    tuning_source = "autotuned in this run"
+    if args.tuning or (workload.name in table and not args.autotune):
+        tuning = [tuple(c) for c in (json.loads(args.tuning) if args.tuning else table[workload.name])]
+        tuning_source = "given" if args.tuning else "package table of ff_autotune results on GB300"
         for lvl, cfg in enumerate(tuning):
             ff.ff_set_tuning(M.ctx, lvl, cfg)
     else:
@@ -520,13 +533,14 @@ def main():
                        "px_per_step": px_per_step, "n_scales": prm.n_scales, "iters": prm.iters,
                        "rs_radius": prm.rs_radius, "eps": prm.eps, "parallelism": f"replicas x{world}",
                        "tiles_per_level": {str(l): list(c) for l, c in enumerate(tuning)},
+                       "tiles_from": tuning_source,
                        "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write, outside the events)"},
             "gpu_launches": launches,
             "clocks": clocks,
             "e2e": {"value": px_per_step * world / (e2e_ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "hbm", "kernel": "k_propagate", "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": propagate_traffic(),
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": propagate_traffic(tuning),
                          "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
                          "launches_per_step": launches_per_step},
             "phases_ms_per_step": {k: v[0] / n_prof for k, v in phases.items()},

@@ -131,7 +131,14 @@ const TileCfg kCands[] = {
     {8, 8, 3, 256, 1},   {32, 32, 1, 512, 1}, {16, 16, 2, 512, 1}, {24, 24, 1, 512, 1},
     // coarse levels: one pixel per thread per half-sweep (fewer dependent loads in a row)
     {8, 8, 3, 512, 0},   {8, 8, 2, 512, 0},   {16, 8, 2, 512, 0},   {16, 16, 1, 512, 0}, {8, 8, 3, 512, 1},
-    {16, 8, 2, 512, 1},  {16, 16, 1, 512, 1}, {8, 8, 6, 512, 0},   {8, 8, 6, 512, 1}};
+    {16, 8, 2, 512, 1},  {16, 16, 1, 512, 1}, {8, 8, 6, 512, 0},   {8, 8, 6, 512, 1},
+    // fine levels: larger tiles recompute a smaller share of halo pixels
+    {64, 32, 1, 128, 0}, {48, 32, 1, 128, 0}, {48, 32, 1, 256, 0}, {64, 16, 1, 128, 0}, {40, 24, 1, 128, 0},
+    {48, 24, 1, 128, 0}, {64, 24, 1, 256, 0}, {64, 24, 1, 128, 0}, {96, 24, 1, 256, 0}, {80, 24, 1, 256, 0},
+    {128, 16, 1, 256, 0}, {96, 32, 1, 256, 0}, {64, 24, 1, 512, 0}, {64, 20, 1, 256, 0}, {48, 24, 1, 256, 0},
+    {64, 16, 1, 256, 0}, {96, 16, 1, 256, 0}, {128, 24, 1, 512, 0}, {96, 24, 1, 128, 0}, {80, 24, 1, 128, 0},
+    {96, 32, 1, 128, 0}, {80, 32, 1, 128, 0}, {64, 28, 1, 128, 0}, {56, 24, 1, 128, 0}, {72, 24, 1, 128, 0},
+    {64, 20, 1, 128, 0}};
 constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
 
 // Tuning key: level index, level size of the first job, number of directions in the launch, iterations.
