@@ -332,8 +332,8 @@ const void* cost_desc(const ff_pyr* p, int level, int cost) {
     return cost == FF_COST_CENSUS ? static_cast<const void*>(p->cen[level]) : static_cast<const void*>(p->feat[level]);
 }
 
-// Build the launch sequence of a set of matching directions (+ consistency checks).  `force` (optional) imposes
-// one propagation configuration on every level (used by the autotuner).
+// Build the launch sequence of a set of matching directions (+ consistency checks).  `force` (optional, one entry
+// per level) imposes the propagation configuration of every level (used by the autotuner).
 ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons, Plan& P,
                      const TileCfg* force) {
     const int L = c->prm.n_scales, T = c->prm.iters, cost = c->prm.cost;
@@ -521,7 +521,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         for (int j = 0; j < nj; j++) level_pix += (int64_t)jobs[j].a->ws[s] * jobs[j].a->hs[s];
         TileCfg tc;
         if (force) {
-            tc = *force;
+            tc = force[s];
             tc.k = std::min(tc.k, T);
         } else if (c->forced[s].tw > 0) {
             tc = c->forced[s];
@@ -744,32 +744,71 @@ ff_status run_jobs(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
 
 // Time every candidate configuration on the given jobs and keep, per level, the fastest.  Runs the real
 // matching (outputs are overwritten by every trial; all configurations give identical results).
+// Tiles a launch of this configuration processes at level s (all jobs) and the CTAs resident at once.
+void wave_shape(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, const TileCfg& t, int64_t* tiles,
+                int64_t* slots) {
+    int64_t n = 0;
+    for (const DirJob& j : jobs)
+        n += (int64_t)((j.a->ws[s] + t.tw - 1) / t.tw) * ((j.a->hs[s] + t.th - 1) / t.th);
+    *tiles = n;
+    *slots = (int64_t)prop_blocks_per_sm(prop_smem_bytes(t.tw, t.th, t.k), t.threads, t.spec != 0, c->prm.cost) *
+             c->n_sms;
+}
+
+// A launch whose last wave is a small remainder of tiles runs at about the speed of one more full wave.  The
+// wave-fitted variant of a configuration grows the tile (height first, then width, by at most a quarter) just
+// enough that the tiles fill one wave fewer; it returns the configuration unchanged when none does.
+TileCfg wave_fitted(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, TileCfg t) {
+    int64_t tiles, slots;
+    wave_shape(c, jobs, s, t, &tiles, &slots);
+    if (slots < 1 || tiles <= slots) return t;
+    const int64_t waves = (tiles + slots - 1) / slots;
+    if (tiles - (waves - 1) * slots > slots / 2) return t;  // the last wave is at least half full
+    for (int grow = 1; grow <= std::max(1, t.th / 4) + std::max(1, t.tw / 4); grow++)
+        for (int dim = 0; dim < 2; dim++) {
+            TileCfg u = t;
+            if (dim == 0) {
+                if (grow > std::max(1, t.th / 4)) continue;
+                u.th += grow;
+            } else {
+                if (grow > std::max(1, t.tw / 4)) continue;
+                u.tw += grow;
+            }
+            if (!cfg_fits(u)) continue;
+            int64_t tu, su;
+            wave_shape(c, jobs, s, u, &tu, &su);
+            if (su > 0 && tu <= (waves - 1) * su) return u;
+        }
+    return t;
+}
+
 ff_status autotune(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons, int reps) {
     const int L = c->prm.n_scales, T = c->prm.iters, nj = (int)jobs.size();
-    std::vector<std::vector<double>> best_ms(L, std::vector<double>(kNCands, 1e30));
+    // per level, the best time and configuration seen; each candidate is timed as given and, where it leaves a
+    // short last wave at some level, once more with its wave-fitted variant at those levels
+    std::vector<double> best_ms(L, 1e30);
+    std::vector<TileCfg> best_cfg(L);
     ff_status s = drop_plans(c);
     if (s != FF_OK) return s;
     bool was_profiling = c->profiling;
-    for (int ci = 0; ci < kNCands; ci++) {
-        TileCfg cfg = kCands[ci];
-        cfg.k = std::min(cfg.k, T);
-        if (!cfg_fits(cfg)) continue;
+    auto time_plan = [&](const std::vector<TileCfg>& per_level) -> ff_status {
         Plan P;
-        s = build_plan(c, jobs, cons, P, &cfg);
-        if (s != FF_OK) {
+        ff_status st = build_plan(c, jobs, cons, P, per_level.data());
+        if (st != FF_OK) {
             free_plan(c, P);
-            return s;
+            return st;
         }
+        std::vector<double> lv_best(L, 1e30);
         for (int r = 0; r < reps + 1; r++) {
             c->events.clear();
-            s = run_launches(c, P.launches, true);
-            if (s == FF_OK) s = [&]() -> ff_status {
+            st = run_launches(c, P.launches, true);
+            if (st == FF_OK) st = [&]() -> ff_status {
                 FF_CUDA(c, cudaStreamSynchronize(c->stream));
                 return FF_OK;
             }();
-            if (s != FF_OK) {
+            if (st != FF_OK) {
                 free_plan(c, P);
-                return s;
+                return st;
             }
             std::vector<double> lv(L, 0.0);
             for (auto& e : c->events) {
@@ -781,21 +820,33 @@ ff_status autotune(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
             }
             c->events.clear();
             if (r > 0)  // the first run warms caches and clocks
-                for (int l = 0; l < L; l++) best_ms[l][ci] = std::min(best_ms[l][ci], lv[l]);
+                for (int l = 0; l < L; l++) lv_best[l] = std::min(lv_best[l], lv[l]);
         }
         free_plan(c, P);
+        for (int l = 0; l < L; l++)
+            if (lv_best[l] < best_ms[l]) {
+                best_ms[l] = lv_best[l];
+                best_cfg[l] = per_level[l];
+            }
+        return FF_OK;
+    };
+    for (int ci = 0; ci < kNCands; ci++) {
+        TileCfg cfg = kCands[ci];
+        cfg.k = std::min(cfg.k, T);
+        if (!cfg_fits(cfg)) continue;
+        std::vector<TileCfg> per_level(L, cfg), fitted(L, cfg);
+        bool any = false;
+        for (int l = 0; l < L; l++) {
+            fitted[l] = wave_fitted(c, jobs, l, cfg);
+            any = any || fitted[l].tw != cfg.tw || fitted[l].th != cfg.th;
+        }
+        s = time_plan(per_level);
+        if (s == FF_OK && any) s = time_plan(fitted);
+        if (s != FF_OK) return s;
     }
     c->profiling = was_profiling;
-    for (int l = 0; l < L; l++) {
-        int bi = -1;
-        for (int ci = 0; ci < kNCands; ci++)
-            if (best_ms[l][ci] < 1e29 && (bi < 0 || best_ms[l][ci] < best_ms[l][bi])) bi = ci;
-        if (bi >= 0) {
-            TileCfg cfg = kCands[bi];
-            cfg.k = std::min(cfg.k, T);
-            c->tuned[TuneKey{l, jobs[0].a->ws[l], jobs[0].a->hs[l], nj, T}] = cfg;
-        }
-    }
+    for (int l = 0; l < L; l++)
+        if (best_ms[l] < 1e29) c->tuned[TuneKey{l, jobs[0].a->ws[l], jobs[0].a->hs[l], nj, T}] = best_cfg[l];
     return FF_OK;
 }
 
