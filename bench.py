@@ -284,16 +284,18 @@ def measure_served(torch, ff, configs, stream, local_rank, n_req):
                 a, b, _ = synth.make_pair(kind, 5000 + 100 * len(pool) + k, w, h)
                 pool[(w, h)].append((torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)))
     stream.synchronize()
-    for (w, h), prs in pool.items():  # per-size launch configuration, as a deployment would tune once
-        pa, pb = M.features(prs[0][0]), M.features(prs[0][1])
-        M.autotune([(pa, pb)], reps=2)
-        M.release(pa)
-        M.release(pb)
+    for (w, h), prs in pool.items():  # per-size launch configurations, as a deployment would tune once:
+        pyrs = [(M.features(a), M.features(b)) for a, b in prs]
+        M.autotune(pyrs[:1], reps=2)  # for one pair in flight (light load)
+        M.autotune(pyrs, reps=2)      # for launches shared by many pairs (under load)
+        for pa, pb in pyrs:
+            M.release(pa)
+            M.release(pb)
     frames = []
     for i, (w, h, _) in enumerate(configs.serve_sizes(n_req)):
         frames.append(pool[(w, h)][i % 8])
     arrivals = serve.poisson_arrivals(n_req, 200.0, seed=5)
-    serve.serve(M, frames[:32], [0.0] * 32)  # warm-up: pools, plans and caches
+    serve.serve(M, frames[:512], [0.0] * 512)  # warm-up: pyramid and scratch pools at full occupancy, caches
     offered = serve.serve(M, frames, arrivals, mem_budget_bytes=60 << 30)
     saturated = serve.serve(M, frames, [0.0] * n_req, mem_budget_bytes=60 << 30)
     M.close()

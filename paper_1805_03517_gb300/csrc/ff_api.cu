@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -899,8 +900,20 @@ TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs
     if (c->forced[level].tw > 0) {
         tc = c->forced[level];
     } else {
-        auto it = c->tuned.find(TuneKey{level, w, h, n_dirs, T});
-        tc = it != c->tuned.end() ? it->second : default_cfg(c, level_pix_all, T);
+        // the configuration tuned for this level size with the nearest number of directions per launch
+        const TileCfg* best = nullptr;
+        int best_d = 0;
+        for (const auto& kv : c->tuned) {
+            if (std::get<0>(kv.first) != level || std::get<1>(kv.first) != w || std::get<2>(kv.first) != h ||
+                std::get<4>(kv.first) != T)
+                continue;
+            const int d = std::abs(std::get<3>(kv.first) - n_dirs);
+            if (!best || d < best_d) {
+                best = &kv.second;
+                best_d = d;
+            }
+        }
+        tc = best ? *best : default_cfg(c, level_pix_all, T);
     }
     return {tc.tw, tc.th, std::min(tc.k, T), tc.threads, tc.spec};
 }

@@ -34,6 +34,7 @@ namespace {
 constexpr int kRing = 4;         // ticks in flight before the host waits
 constexpr int kSideStreams = 3;  // extra streams for the concurrent propagation launches of a tick
 constexpr int kWholeLevelMaxActive = 8;  // up to this many requests in flight, a tick runs a whole level
+constexpr int kLoadedDirs = 16;          // directions per launch the configurations under load are looked up for
 
 size_t a256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -215,8 +216,11 @@ ff_status admit(ff_server* s) {
         }
         s->in_use += q.footprint;
         q.counted = true;
+        // launch configurations tuned for one pair at light load, for launches shared by many pairs under load
+        const int n_dirs = (int)s->active.size() + 1 > kWholeLevelMaxActive ? kLoadedDirs : 2;
         for (int l = 0; l < q.L; l++) {
-            q.cfg[l] = ctx_level_choice(s->ctx, l, q.A.ws[l], q.A.hs[l], 2, 2 * (int64_t)q.A.ws[l] * q.A.hs[l]);
+            q.cfg[l] = ctx_level_choice(s->ctx, l, q.A.ws[l], q.A.hs[l], n_dirs,
+                                        (int64_t)n_dirs * q.A.ws[l] * q.A.hs[l]);
             q.n_chunks[l] = (q.T + q.cfg[l].k - 1) / q.cfg[l].k;
         }
         q.level = q.L - 1;
