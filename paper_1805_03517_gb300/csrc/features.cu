@@ -11,6 +11,7 @@ namespace ff {
 // that a 1-pixel-wide or -high level averages its only column/row.  One thread per output pixel.
 __global__ void k_downsample(const uint8_t* __restrict__ src, int sw, int sh, int spitch, uint8_t* __restrict__ dst,
                              int dw, int dh) {
+    grid_dependency_sync();
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
     if (x >= dw || y >= dh) return;
@@ -29,7 +30,7 @@ __global__ void k_downsample(const uint8_t* __restrict__ src, int sw, int sh, in
 void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* dst, int dw, int dh,
                        cudaStream_t st) {
     dim3 grid((dw + 127) / 128, dh);
-    k_downsample<<<grid, 128, 0, st>>>(src, sw, sh, spitch, dst, dw, dh);
+    launch_k(k_downsample, grid, dim3(128), 0, st, src, sw, sh, spitch, dst, dw, dh);
 }
 
 // Levels 1..a.top of the pyramid of one frame in one launch (same arithmetic as k_downsample).  A CTA owns a
@@ -38,6 +39,7 @@ void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* 
 // in the parent block (the clamp only matters when the parent level is 1 pixel wide or high, and its single
 // pixel is in block 0).  A 32x32 level-1 block halves down to one pixel at level 6, hence a.top <= 6.
 __global__ __launch_bounds__(256) void k_pyramid(PyrArgs a) {
+    grid_dependency_sync();
     __shared__ uint8_t buf[2][kPyrBlock][kPyrBlock][3];
     int size = kPyrBlock, ox = blockIdx.x * kPyrBlock, oy = blockIdx.y * kPyrBlock;
     for (int i = threadIdx.x; i < size * size; i += blockDim.x) {
@@ -82,7 +84,7 @@ __global__ __launch_bounds__(256) void k_pyramid(PyrArgs a) {
 
 void launch_pyramid(const PyrArgs& a, cudaStream_t st) {
     dim3 grid((a.w[1] + kPyrBlock - 1) / kPyrBlock, (a.h[1] + kPyrBlock - 1) / kPyrBlock);
-    k_pyramid<<<grid, 256, 0, st>>>(a);
+    launch_k(k_pyramid, grid, dim3(256), 0, st, a);
 }
 
 // Walsh-Hadamard descriptor (Sec. 3.1): for every pixel and channel, the 4x4 lowest-sequency coefficients of
@@ -167,6 +169,7 @@ __device__ __forceinline__ void seed_rows(const uint32_t (&out)[24], int p, cons
 }
 
 __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
+    grid_dependency_sync();
     __shared__ uint8_t win[3][kWinY][kWinX];
     __shared__ short4 rowt[3][kWinY][kWtx];  // row pass: 4 horizontal Walsh sums per window row and output column
     int b = blockIdx.x, li = 0;
@@ -226,7 +229,7 @@ int wht_tiles_x(int w) { return (w + kWtx - 1) / kWtx; }
 int wht_tiles(int w, int h) { return wht_tiles_x(w) * ((h + kWty - 1) / kWty); }
 
 void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st) {
-    k_wht<<<total_tiles, 256, 0, st>>>(a);
+    launch_k(k_wht, dim3(total_tiles), dim3(256), 0, st, a);
 }
 
 }  // namespace ff

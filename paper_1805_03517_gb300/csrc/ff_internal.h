@@ -209,6 +209,37 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     return x;
 }
 
+// ---------------------------------------------------------------------------------------------------------
+// Programmatic dependent launch: every kernel of the library is launched with programmatic stream serialization,
+// so the next kernel's CTAs are launched while the last CTAs of the previous one finish, and starts with
+// grid_dependency_sync(), which waits until the previous grid has completed and its memory is visible (hence
+// also every grid before it) before anything it produced is read; it then lets its own dependent launch.
+#ifndef FF_PDL
+#define FF_PDL 1
+#endif
+
+__device__ __forceinline__ void grid_dependency_sync() {
+#if FF_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = FF_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 }  // namespace ff
 
 // Accessors implemented in ff_api.cu (ff_ctx and ff_pyr are opaque outside it).

@@ -15,6 +15,7 @@ __device__ __forceinline__ bool in_level(int x, int y, int w, int h) {
 // row-major order on ties).  One thread per block.
 __global__ void k_sparsify(const uint32_t* __restrict__ fwd, const uint32_t* __restrict__ bwd, int w, int h, int eps,
                            int s, uint8_t* __restrict__ out) {
+    grid_dependency_sync();
     const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y;
     if (3 * bx >= w) return;
     const int x0 = 3 * bx, y0 = 3 * by, x1 = min(x0 + 3, w), y1 = min(y0 + 3, h);
@@ -42,7 +43,7 @@ void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int
                      cudaStream_t st) {
     const int nbx = (w + 2) / 3, nby = (h + 2) / 3;
     dim3 grid((nbx + 127) / 128, nby);
-    k_sparsify<<<grid, 128, 0, st>>>(fwd, bwd, w, h, eps, s, out);
+    launch_k(k_sparsify, grid, dim3(128), 0, st, fwd, bwd, w, h, eps, s, out);
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -60,6 +61,7 @@ __device__ __forceinline__ bool consistent(uint32_t f, const uint32_t* __restric
 
 __global__ void k_consistency(const uint32_t* __restrict__ fwd, const uint32_t* __restrict__ bwd,
                               const uint32_t* __restrict__ bwd2, int w, int h, int eps, uint8_t* __restrict__ mask) {
+    grid_dependency_sync();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w * h) return;
     const int x = i % w, y = i / w;
@@ -72,7 +74,7 @@ __global__ void k_consistency(const uint32_t* __restrict__ fwd, const uint32_t* 
 void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, const uint32_t* bwd2, int w, int h, int eps,
                         uint8_t* mask, cudaStream_t st) {
     int n = w * h;
-    k_consistency<<<(n + 255) / 256, 256, 0, st>>>(fwd, bwd, bwd2, w, h, eps, mask);
+    launch_k(k_consistency, dim3((n + 255) / 256), dim3(256), 0, st, fwd, bwd, bwd2, w, h, eps, mask);
 }
 
 }  // namespace ff

@@ -101,6 +101,7 @@ __device__ __forceinline__ int cost_at(const void* __restrict__ fa, const void* 
 template <class C>
 __global__ __launch_bounds__(256) void k_handover(const HandoverProblem* __restrict__ probs, int n_probs,
                                                   int64_t total) {
+    grid_dependency_sync();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         int lo = 0, hi = n_probs - 1;
         while (lo < hi) {  // last problem with pix_base <= i
@@ -131,9 +132,9 @@ void launch_handover(const HandoverProblem* probs_dev, int n_probs, int64_t tota
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
     if (cost == FF_COST_CENSUS)
-        k_handover<CostCensus><<<(int)blocks, 256, 0, st>>>(probs_dev, n_probs, total_pix);
+        launch_k(k_handover<CostCensus>, dim3((int)blocks), dim3(256), 0, st, probs_dev, n_probs, total_pix);
     else
-        k_handover<CostSad><<<(int)blocks, 256, 0, st>>>(probs_dev, n_probs, total_pix);
+        launch_k(k_handover<CostSad>, dim3((int)blocks), dim3(256), 0, st, probs_dev, n_probs, total_pix);
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -306,6 +307,7 @@ template <int THREADS, bool SPEC, class C>
 __global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate(
     const PropProblem* __restrict__ probs, const int2* __restrict__ queue, int n_tiles, int* __restrict__ counter,
     PropLaunch L) {
+    grid_dependency_sync();
     extern __shared__ uint32_t smem[];
     __shared__ int s_next;
     for (;;) {
@@ -358,8 +360,8 @@ int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost) {
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st) {
     size_t smem = prop_smem_bytes(L.tw, L.th, L.max_iter);
-    prop_kernel(L.threads, L.spec != 0, L.cost)<<<grid, L.threads, smem, st>>>(probs_dev, queue_dev, n_tiles,
-                                                                                counter_dev, L);
+    launch_k(prop_kernel(L.threads, L.spec != 0, L.cost), dim3(grid), dim3(L.threads), smem, st, probs_dev, queue_dev,
+             n_tiles, counter_dev, L);
 }
 
 }  // namespace ff

@@ -35,6 +35,7 @@ constexpr int kSeedWarps = 8;
 
 __global__ __launch_bounds__(32 * kSeedWarps) void k_seed(const SeedProblem* __restrict__ probs, int n_probs,
                                                           int total_tiles) {
+    grid_dependency_sync();
     __shared__ int s_best[kSeedWarps][16], s_idx[kSeedWarps][16];
     const int tile = blockIdx.x;
     int pi = 0;
@@ -103,7 +104,7 @@ __global__ __launch_bounds__(32 * kSeedWarps) void k_seed(const SeedProblem* __r
 }
 
 void launch_seed(const SeedProblem* probs_dev, int n_probs, int total_row_tiles, cudaStream_t st) {
-    k_seed<<<total_row_tiles, 32 * kSeedWarps, 0, st>>>(probs_dev, n_probs, total_row_tiles);
+    launch_k(k_seed, dim3(total_row_tiles), dim3(32 * kSeedWarps), 0, st, probs_dev, n_probs, total_row_tiles);
 }
 
 }  // namespace ff

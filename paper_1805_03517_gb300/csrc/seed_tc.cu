@@ -116,6 +116,7 @@ constexpr size_t kSeedTcSmem = 1024 /*alignment slack*/ + kABytes + kBBytes + kT
 // probs[i] covers CTAs [cta_base, cta_base + row_tiles * col_tiles).
 __global__ __launch_bounds__(128) void k_seed_tc(const SeedTcProblem* __restrict__ probs, int n_probs,
                                                  uint32_t wait_limit, int withhold, int* __restrict__ err) {
+    grid_dependency_sync();
     extern __shared__ uint8_t smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int pi = 0;
@@ -215,6 +216,7 @@ __global__ __launch_bounds__(128) void k_seed_tc(const SeedTcProblem* __restrict
 
 // keys -> packed flow q - p and squared distance |a_p|^2 + min score.
 __global__ void k_seed_finish(const SeedTcProblem* __restrict__ probs, int n_probs, int64_t total) {
+    grid_dependency_sync();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         int lo = 0, hi = n_probs - 1;
         while (lo < hi) {
@@ -238,10 +240,10 @@ cudaError_t seed_tc_init_attributes() {
 
 void launch_seed_tc(const SeedTcProblem* probs_dev, int n_probs, int total_ctas, int64_t total_pix, uint32_t wait_limit,
                     int withhold, int* err_dev, cudaStream_t st) {
-    k_seed_tc<<<total_ctas, 128, kSeedTcSmem, st>>>(probs_dev, n_probs, wait_limit, withhold, err_dev);
+    launch_k(k_seed_tc, dim3(total_ctas), dim3(128), kSeedTcSmem, st, probs_dev, n_probs, wait_limit, withhold, err_dev);
     int64_t blocks = (total_pix + 255) / 256;
     if (blocks > 1024) blocks = 1024;
-    k_seed_finish<<<(int)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(probs_dev, n_probs, total_pix);
+    launch_k(k_seed_finish, dim3((int)(blocks < 1 ? 1 : blocks)), dim3(256), 0, st, probs_dev, n_probs, total_pix);
 }
 
 // Tensor map of a [n_pad][64] f16 descriptor array: boxes of 64 x 128 (one 128-byte row per descriptor),
