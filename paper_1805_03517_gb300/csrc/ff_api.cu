@@ -139,7 +139,7 @@ const TileCfg kCands[] = {
     {128, 16, 1, 256, 0}, {96, 32, 1, 256, 0}, {64, 24, 1, 512, 0}, {64, 20, 1, 256, 0}, {48, 24, 1, 256, 0},
     {64, 16, 1, 256, 0}, {96, 16, 1, 256, 0}, {128, 24, 1, 512, 0}, {96, 24, 1, 128, 0}, {80, 24, 1, 128, 0},
     {96, 32, 1, 128, 0}, {80, 32, 1, 128, 0}, {64, 28, 1, 128, 0}, {56, 24, 1, 128, 0}, {72, 24, 1, 128, 0},
-    {64, 20, 1, 128, 0}};
+    {64, 20, 1, 128, 0}, {24, 16, 1, 512, 0}, {32, 16, 1, 512, 0}, {20, 16, 1, 512, 0}, {26, 16, 1, 512, 0}};
 constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
 
 // Tuning key: level index, level size of the first job, number of directions in the launch, iterations.
