@@ -30,6 +30,7 @@ UNIT = "Mpx/s"
 L2_FLUSH_BYTES = 512 << 20
 ALG_BYTES_PER_PIXEL_ITER = 11 * 96 + 96 + 8  # candidate gathers + own descriptor + flow/cost, per direction
 ALG_BYTES_PER_PIXEL_ITER_CENSUS = 11 * 32 + 32 + 8  # the same with 32-byte Census patterns
+COSTS = {"wht_sad": 0, "census": 1}
 
 
 def parse():
@@ -38,6 +39,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default="kitti_1242x375")
+    ap.add_argument("--cost", default="wht_sad", choices=["wht_sad", "census"],
+                    help="matching cost of the timed workload (Census: 7x7 patterns, Hamming distance)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-pair batched measurement")
@@ -305,7 +308,7 @@ def measure_served(torch, ff, configs, stream, local_rank, n_req):
     return out
 
 
-def cpu_baseline(workload, imgs):
+def cpu_baseline(workload, imgs, cost_id=0):
     """The oracle as it stands, single-threaded, on one pair of the workload (a bounded sample)."""
     import oracle
 
@@ -314,7 +317,7 @@ def cpu_baseline(workload, imgs):
     p = spec.params
     o = oracle.default()
     t = time.perf_counter()
-    o.match_bidir(a, b, oracle.params(p.n_scales, p.iters, p.rs_radius, p.eps, p.seed))
+    o.match_bidir(a, b, oracle.params(p.n_scales, p.iters, p.rs_radius, p.eps, p.seed, cost_id))
     dt = time.perf_counter() - t
     return {"value": spec.pixels / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"one {spec.w}x{spec.h} pair of the workload, full bidirectional matching, "
@@ -346,7 +349,7 @@ def run_reference(args, rank, world):
     oracle.build()
     spec = workload.pairs[0]
     p = spec.params
-    task = (imgs[0][0], imgs[0][1], (p.n_scales, p.iters, p.rs_radius, p.eps, p.seed))
+    task = (imgs[0][0], imgs[0][1], (p.n_scales, p.iters, p.rs_radius, p.eps, p.seed, COSTS[args.cost]))
     cores = max(1, min(os.cpu_count() or 1, args.steps))
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
@@ -360,7 +363,8 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": dt * 1000 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int16", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload.name, "pairs_per_step": 1, "n_scales": p.n_scales, "iters": p.iters},
+            "config": {"workload": workload.name, "pairs_per_step": 1, "n_scales": p.n_scales, "iters": p.iters,
+                       "cost": args.cost},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full {spec.w}x{spec.h} pairs over {cores} single-threaded "
                                        "oracle processes"},
@@ -393,7 +397,10 @@ def main():
     imgs = make_inputs(workload)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    prm = workload.pairs[0].params
+    import dataclasses
+
+    cost_id = COSTS[args.cost]
+    prm = dataclasses.replace(workload.pairs[0].params, cost=cost_id)
     M = ff.Matcher(prm, local_rank, stream)
     with torch.cuda.stream(stream):
         dev_imgs = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in imgs]
@@ -433,7 +440,7 @@ def main():
     with open(os.path.join(ROOT, "paper_1805_03517_gb300", "tuned.json")) as f:
         table = json.load(f)
     tuning_source = "autotuned in this run"
-    if args.tuning or (workload.name in table and not args.autotune):
+    if args.tuning or (workload.name in table and not args.autotune and cost_id == 0):
         tuning = [tuple(c) for c in (json.loads(args.tuning) if args.tuning else table[workload.name])]
         tuning_source = "given" if args.tuning else "package table of ff_autotune results on GB300"
         for lvl, cfg in enumerate(tuning):
@@ -519,7 +526,7 @@ def main():
     P.close()
     pix_iters = sum(ff.ff_work_counts(M.ctx, p.w, p.h)[0] for p in workload.pairs)
     prop_ms, prop_launches = phases["propagate"]
-    alg_bytes_per_step = pix_iters * 2 * ALG_BYTES_PER_PIXEL_ITER
+    alg_bytes_per_step = pix_iters * 2 * (ALG_BYTES_PER_PIXEL_ITER_CENSUS if cost_id else ALG_BYTES_PER_PIXEL_ITER)
     launches_per_step = prop_launches / n_prof
     avg_launch_ms = prop_ms / prop_launches
     bytes_per_launch = alg_bytes_per_step / launches_per_step
@@ -533,7 +540,8 @@ def main():
             "vs_baseline": None, "dtype": "int16", "data": "synthetic",
             "config": {"workload": workload.name, "pairs_per_step": len(workload.pairs),
                        "px_per_step": px_per_step, "n_scales": prm.n_scales, "iters": prm.iters,
-                       "rs_radius": prm.rs_radius, "eps": prm.eps, "parallelism": f"replicas x{world}",
+                       "rs_radius": prm.rs_radius, "eps": prm.eps, "cost": args.cost,
+                       "parallelism": f"replicas x{world}",
                        "tiles_per_level": {str(l): list(c) for l, c in enumerate(tuning)},
                        "tiles_from": tuning_source,
                        "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write, outside the events)"},
@@ -542,13 +550,13 @@ def main():
             "e2e": {"value": px_per_step * world / (e2e_ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "hbm", "kernel": "k_propagate", "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": propagate_traffic(tuning),
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": propagate_traffic(tuning) if cost_id == 0 else None,
                          "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
                          "launches_per_step": launches_per_step},
             "phases_ms_per_step": {k: v[0] / n_prof for k, v in phases.items()},
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(workload, imgs)
+            line["cpu_baseline"] = cpu_baseline(workload, imgs, cost_id)
     if not args.no_census:
         census = measure_census(torch, ff, configs, stream, local_rank, max(10, min(100, args.steps // 3)), flush_l2)
         if rank == 0:
