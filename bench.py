@@ -148,10 +148,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(workload):
+def make_inputs(workload, with_gt=False):
     from paper_1805_03517_gb300 import synth
 
-    return [synth.make_pair(p.kind, p.seed, p.w, p.h)[:2] for p in workload.pairs]
+    pairs = [synth.make_pair(p.kind, p.seed, p.w, p.h) for p in workload.pairs]
+    return pairs if with_gt else [pr[:2] for pr in pairs]
+
+
+def flow_accuracy(flow, mask, gt):
+    """End-point error of the forward field against the generated (integer) ground truth, as context: mean EPE
+    over all pixels and over the matches kept by the consistency check, the share kept, and the share of
+    outliers (EPE > 3 px and > 5 % of the ground-truth length, the KITTI 2015 rule)."""
+    import numpy as np
+
+    e = np.hypot(*(flow.astype(np.float64) - gt.astype(np.float64)).transpose(2, 0, 1))
+    g = np.hypot(*gt.astype(np.float64).transpose(2, 0, 1))
+    out = (e > 3.0) & (e > 0.05 * g)
+    k = mask.astype(bool)
+    return {"epe_all_px": float(e.mean()), "epe_kept_px": float(e[k].mean()) if k.any() else None,
+            "kept_frac": float(k.mean()), "outliers_all": float(out.mean()),
+            "outliers_kept": float(out[k].mean()) if k.any() else None}
 
 
 def measure_batched(torch, ff, configs, stream, local_rank, steps):
@@ -394,7 +410,8 @@ def main():
 
     B.build()
     workload = configs.workload(args.workload)
-    imgs = make_inputs(workload)
+    imgs_gt = make_inputs(workload, with_gt=True)
+    imgs = [pr[:2] for pr in imgs_gt]
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     import dataclasses
@@ -554,6 +571,8 @@ def main():
                          "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
                          "launches_per_step": launches_per_step},
             "phases_ms_per_step": {k: v[0] / n_prof for k, v in phases.items()},
+            "accuracy_context": flow_accuracy(outs[0]["flow_fwd"].cpu().numpy(), outs[0]["mask"].cpu().numpy(),
+                                              imgs_gt[0][2]),
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(workload, imgs, cost_id)
