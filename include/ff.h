@@ -20,8 +20,9 @@
  *   - Pointers marked "device" must point to memory of the context's device; the caller owns them.
  *     Calls only enqueue work on the context's stream and return; a device buffer handed in must stay
  *     valid until that work has run (ff_sync waits for it).
- *   - Sizes: 1 <= w, h <= 8192; n_scales 1..8 (every level is at least 1x1).  A violation returns
- *     FF_ERR_ARG and launches nothing.
+ *   - Sizes: 1 <= w, h <= 8192; n_scales 1..8 (every level is at least 1x1); the coarsest level has at most
+ *     2^20 pixels (the initial matching is exhaustive, its work grows with the square of that count).  A
+ *     violation returns FF_ERR_ARG and launches nothing.
  *   - Errors: every call returns an ff_status; ff_last_error() gives a message for the last failure.  A
  *     CUDA failure (including one from earlier asynchronous work) returns FF_ERR_CUDA.
  *   - A context is not thread-safe: use one context per host thread (or serialise calls).

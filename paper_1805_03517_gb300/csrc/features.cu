@@ -94,8 +94,8 @@ void launch_pyramid(const PyrArgs& a, cudaStream_t st) {
 // so the transform is separable: a row pass (4 outputs per patch row) then a column pass.
 // CTA = 32x16 output pixels: its 39x23 input window (clamped halo) is staged in shared memory, the row pass is
 // computed once per (window row, output column, channel) into shared memory (|value| <= 8*255 fits int16), and
-// each thread then runs the column pass for two output pixels.  Coefficients are stored in offset binary
-// (C ^ 0x8000), the form the SAD of the propagation kernels works on.
+// the column pass slides down each column (per channel, half a tile at a time).  Coefficients are stored in
+// offset binary (C ^ 0x8000), the form the SAD of the propagation kernels works on.
 constexpr int kWtx = 32, kWty = 16;
 constexpr int kWinX = kWtx + 7, kWinY = kWty + 7;
 
@@ -195,33 +195,60 @@ __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
         rowt[ch][r][c] = make_short4((short)v0, (short)v1, (short)v2, (short)v3);
     }
     __syncthreads();
-    const int lx = threadIdx.x % kWtx;
-    for (int ly = threadIdx.x / kWtx; ly < kWty; ly += blockDim.x / kWtx) {
-        const int x = tx0 + lx, y = ty0 + ly;
-        if (x >= L.w || y >= L.h) continue;
-        uint32_t out[24];
+    // Column pass: one thread per (channel, output column, half of the tile's rows) slides down 8 output rows,
+    // loading each row-pass value once (15 per 8 outputs) and writing the channel's 32-B sector of each pixel.
+    for (int i = threadIdx.x; i < 3 * kWtx * 2; i += blockDim.x) {
+        const int col = i % kWtx, rest = i / kWtx, seg = rest & 1, ch = rest >> 1;
+        const int x = tx0 + col;
+        if (x >= L.w) continue;
+        short4 R[kWty / 2 + 7];
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) {
-            short4 R[8];
+        for (int k = 0; k < kWty / 2 + 7; k++) R[k] = rowt[ch][seg * (kWty / 2) + k][col];
 #pragma unroll
-            for (int i = 0; i < 8; i++) R[i] = rowt[ch][ly + i][lx];
+        for (int rr = 0; rr < kWty / 2; rr++) {
+            const int y = ty0 + seg * (kWty / 2) + rr;
+            if (y >= L.h) break;
             int C[4][4];
-            walsh4(R[0].x, R[1].x, R[2].x, R[3].x, R[4].x, R[5].x, R[6].x, R[7].x, C[0][0], C[1][0], C[2][0], C[3][0]);
-            walsh4(R[0].y, R[1].y, R[2].y, R[3].y, R[4].y, R[5].y, R[6].y, R[7].y, C[0][1], C[1][1], C[2][1], C[3][1]);
-            walsh4(R[0].z, R[1].z, R[2].z, R[3].z, R[4].z, R[5].z, R[6].z, R[7].z, C[0][2], C[1][2], C[2][2], C[3][2]);
-            walsh4(R[0].w, R[1].w, R[2].w, R[3].w, R[4].w, R[5].w, R[6].w, R[7].w, C[0][3], C[1][3], C[2][3], C[3][3]);
+            walsh4(R[rr].x, R[rr + 1].x, R[rr + 2].x, R[rr + 3].x, R[rr + 4].x, R[rr + 5].x, R[rr + 6].x, R[rr + 7].x,
+                   C[0][0], C[1][0], C[2][0], C[3][0]);
+            walsh4(R[rr].y, R[rr + 1].y, R[rr + 2].y, R[rr + 3].y, R[rr + 4].y, R[rr + 5].y, R[rr + 6].y, R[rr + 7].y,
+                   C[0][1], C[1][1], C[2][1], C[3][1]);
+            walsh4(R[rr].z, R[rr + 1].z, R[rr + 2].z, R[rr + 3].z, R[rr + 4].z, R[rr + 5].z, R[rr + 6].z, R[rr + 7].z,
+                   C[0][2], C[1][2], C[2][2], C[3][2]);
+            walsh4(R[rr].w, R[rr + 1].w, R[rr + 2].w, R[rr + 3].w, R[rr + 4].w, R[rr + 5].w, R[rr + 6].w, R[rr + 7].w,
+                   C[0][3], C[1][3], C[2][3], C[3][3]);
+            uint32_t out[8];
 #pragma unroll
             for (int u = 0; u < 4; u++)
 #pragma unroll
                 for (int v = 0; v < 4; v += 2)
-                    out[ch * 8 + u * 2 + v / 2] =
+                    out[u * 2 + v / 2] =
                         ((uint32_t)(C[u][v] & 0xffff) | ((uint32_t)C[u][v + 1] << 16)) ^ 0x80008000u;  // offset binary
+            uint4* dst = reinterpret_cast<uint4*>(L.feat + (size_t)feat_index(x, y, L.w) * kNF + ch * 16);
+            dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
+            dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
         }
-        uint4* dst = reinterpret_cast<uint4*>(L.feat + (size_t)feat_index(x, y, L.w) * kNF);
-#pragma unroll
-        for (int k = 0; k < 6; k++) dst[k] = make_uint4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+    }
+    if (!L.census && !L.seed_desc) return;
+    __syncthreads();  // the tile's descriptors written above are visible to the whole CTA
+    const int lx = threadIdx.x % kWtx;
+    for (int ly = threadIdx.x / kWtx; ly < kWty; ly += blockDim.x / kWtx) {
+        const int x = tx0 + lx, y = ty0 + ly;
+        if (x >= L.w || y >= L.h) continue;
         if (L.census) census_pixel(win, lx, ly, L.census + (size_t)feat_index(x, y, L.w) * (kCensusBytes / 4));
-        if (L.seed_desc) seed_rows(out, y * L.w + x, L);
+        if (L.seed_desc) {
+            uint32_t out[24];
+            const uint4* src = reinterpret_cast<const uint4*>(L.feat + (size_t)feat_index(x, y, L.w) * kNF);
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                const uint4 v = src[k];
+                out[4 * k] = v.x;
+                out[4 * k + 1] = v.y;
+                out[4 * k + 2] = v.z;
+                out[4 * k + 3] = v.w;
+            }
+            seed_rows(out, y * L.w + x, L);
+        }
     }
 }
 

@@ -22,6 +22,9 @@ using namespace ff;
 namespace {
 
 constexpr int kMaxDim = 8192;
+// The initial matching compares every pixel of the coarsest level with every other one (work and CTA counts grow
+// with the square of its pixel count), so the coarsest level is limited to 2^20 pixels.
+constexpr int kMaxCoarsePixels = 1 << 20;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
@@ -988,8 +991,16 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
     if (!rgb_dev) return fail(c, FF_ERR_ARG, "rgb_dev is NULL");
     if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim) return fail(c, FF_ERR_ARG, "size %dx%d outside 1..%d", w, h, kMaxDim);
     if (pitch_bytes < 3 * w) return fail(c, FF_ERR_ARG, "pitch %d < 3*w", pitch_bytes);
-    FF_CUDA(c, cudaSetDevice(c->device));
     const int L = c->prm.n_scales;
+    {
+        int ws[kMaxLevels], hs[kMaxLevels];
+        level_dims(w, h, L, ws, hs);
+        if ((int64_t)ws[L - 1] * hs[L - 1] > kMaxCoarsePixels)
+            return fail(c, FF_ERR_ARG,
+                        "coarsest level %dx%d has more than %d pixels for the exhaustive initial matching: use more "
+                        "scales for a %dx%d frame", ws[L - 1], hs[L - 1], kMaxCoarsePixels, w, h);
+    }
+    FF_CUDA(c, cudaSetDevice(c->device));
     const bool census = c->prm.cost == FF_COST_CENSUS;
     ff_pyr* P = nullptr;
     for (auto& q : c->pyrs)

@@ -503,6 +503,15 @@ ff_status ff_server_submit(ff_server* s, uint64_t id, const ff_request* req) {
     if (((uintptr_t)req->flow_fwd & 3) || ((uintptr_t)req->flow_bwd & 3) || ((uintptr_t)req->cost_fwd & 3) ||
         ((uintptr_t)req->cost_bwd & 3))
         return srv_fail(s, FF_ERR_ARG, "request outputs must be 4-byte aligned");
+    {  // the same limit ff_features applies: at most 2^20 pixels at the coarsest level
+        int cw = req->w, ch = req->h;
+        for (int l = 1; l < s->cv.n_scales; l++) {
+            cw = std::max(1, cw / 2);
+            ch = std::max(1, ch / 2);
+        }
+        if ((int64_t)cw * ch > (1 << 20))
+            return srv_fail(s, FF_ERR_ARG, "coarsest level too large for the exhaustive initial matching");
+    }
     auto q = std::make_unique<Req>();
     q->id = id;
     q->io = *req;

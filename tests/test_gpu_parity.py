@@ -224,6 +224,10 @@ def test_errors_are_reported(lib_built):
         ff.ff_features(M.ctx, img.data_ptr(), 12, 10, 20)  # pitch < 3w
     with pytest.raises(ff.FFError):
         ff.ff_features(M.ctx, img.data_ptr(), 9000, 10, 27000)
+    M1 = matcher(mp(1, 1))  # one level: the exhaustive seed would run over all 2048*1024 pixels
+    with pytest.raises(ff.FFError) as e:
+        ff.ff_features(M1.ctx, img.data_ptr(), 2048, 1024, 3 * 2048)
+    assert e.value.status == ff.FF_ERR_ARG and "coarsest level" in ff.ff_last_error(M1.ctx)
     pa = M.features(img)
     pb = M.features(torch.zeros((10, 14, 3), dtype=torch.uint8, device="cuda"))
     flow = torch.zeros((10, 12, 2), dtype=torch.int16, device="cuda")
