@@ -97,7 +97,7 @@ void launch_pyramid(const PyrArgs& a, cudaStream_t st) {
 // the column pass slides down each column (per channel, half a tile at a time).  Coefficients are stored in
 // offset binary (C ^ 0x8000), the form the SAD of the propagation kernels works on.
 constexpr int kWtx = 32, kWty = 16;
-constexpr int kWinX = kWtx + 7, kWinY = kWty + 7;
+constexpr int kWinX = kWtx + 8, kWinY = kWty + 7;  // 39 window columns used, one more keeps rows word-aligned
 
 __device__ __forceinline__ void walsh4(int a0, int a1, int a2, int a3, int a4, int a5, int a6, int a7, int& c0,
                                        int& c1, int& c2, int& c3) {
@@ -170,7 +170,7 @@ __device__ __forceinline__ void seed_rows(const uint32_t (&out)[24], int p, cons
 
 __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
     grid_dependency_sync();
-    __shared__ uint8_t win[3][kWinY][kWinX];
+    __shared__ __align__(16) uint8_t win[3][kWinY][kWinX];
     __shared__ short4 rowt[3][kWinY][kWtx];  // row pass: 4 horizontal Walsh sums per window row and output column
     int b = blockIdx.x, li = 0;
     while (li + 1 < args.n && b >= args.lv[li + 1].tile_base) li++;
@@ -189,9 +189,13 @@ __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * kWinY * kWtx; i += blockDim.x) {
         const int ch = i / (kWinY * kWtx), rem = i - ch * kWinY * kWtx, r = rem / kWtx, c = rem - r * kWtx;
-        const uint8_t* row = &win[ch][r][c];
+        // bytes c..c+7 of the window row from three aligned words
+        const uint32_t* rw = reinterpret_cast<const uint32_t*>(&win[ch][r][0]) + (c >> 2);
+        const uint32_t sh = 8u * (uint32_t)(c & 3);
+        const uint32_t lo = __funnelshift_r(rw[0], rw[1], sh), hi = __funnelshift_r(rw[1], rw[2], sh);
         int v0, v1, v2, v3;
-        walsh4(row[0], row[1], row[2], row[3], row[4], row[5], row[6], row[7], v0, v1, v2, v3);
+        walsh4(lo & 0xff, (lo >> 8) & 0xff, (lo >> 16) & 0xff, lo >> 24, hi & 0xff, (hi >> 8) & 0xff,
+               (hi >> 16) & 0xff, hi >> 24, v0, v1, v2, v3);
         rowt[ch][r][c] = make_short4((short)v0, (short)v1, (short)v2, (short)v3);
     }
     __syncthreads();
