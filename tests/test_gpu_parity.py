@@ -244,6 +244,17 @@ def test_errors_are_reported(lib_built):
     M.sync()
 
 
+def test_empty_batch_launches_nothing(lib_built):
+    from paper_1805_03517_gb300 import ff
+
+    M = matcher(mp(3, 1))
+    s0 = M.stats()
+    assert M.match_batch([]) == []
+    M.sync()
+    assert M.stats()["kernel_launches"] == s0["kernel_launches"]
+    assert ff.lib().ff_match_batch(M.ctx, -1, None) == ff.FF_ERR_ARG
+
+
 def test_sparsify_parity(lib_built):
     """Sparsification (Sec. 3.1) of random flows (ragged edge blocks) and of real matches, against the oracle."""
     o = oracle.default()
