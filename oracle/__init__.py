@@ -102,7 +102,7 @@ def _declare(lib):
     lib.ffo_propagate_census.argtypes = [u64p, u64p, c_int, c_int, i16p, i32p, c_int, c_int, c_u32, c_int, c_int,
                                          c_long]
     lib.ffo_propagate_census.restype = c_long
-    lib.ffo_sparsify.argtypes = [i16p, i16p, c_int, c_int, c_int, c_int, u8p]
+    lib.ffo_sparsify.argtypes = [i16p, i16p, ctypes.c_void_p, c_int, c_int, c_int, c_int, u8p]
     lib.ffo_sparsify.restype = None
     lib.ffo_match_bidir.argtypes = [u8p, u8p, c_int, c_int, ctypes.POINTER(Params), i16p, i16p, i32p, i32p, u8p]
     lib.ffo_match_bidir.restype = c_int
@@ -256,10 +256,14 @@ class Oracle:
             raise MemoryError("ffo_propagate_census")
         return flow, cost
 
-    def sparsify(self, fwd, bwd, eps, s):
+    def sparsify(self, fwd, bwd, eps, s, keep=None):
+        """keep: optional uint8 [h][w] mask of the matches left by the consistency checks (None: all)."""
         h, w, _ = fwd.shape
         out = np.empty((h, w), np.uint8)
-        self.L.ffo_sparsify(_i16(fwd), _i16(bwd), w, h, eps, s, out)
+        if keep is not None:
+            keep = np.ascontiguousarray(keep, dtype=np.uint8)
+            assert keep.shape == (h, w)
+        self.L.ffo_sparsify(_i16(fwd), _i16(bwd), None if keep is None else keep.ctypes.data, w, h, eps, s, out)
         return out
 
     def match_bidir(self, img_a, img_b, params: Params):

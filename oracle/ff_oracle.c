@@ -491,8 +491,11 @@ int ffo_match_bidir2(const uint8_t* rgb_a, const uint8_t* rgb_b, int w, int h, c
  * consistency check, keep only the match with the lowest consistency error; drop every other match.
  * Reading: blocks tile the image from (0, 0) (blocks at the right and bottom edges may be smaller); the error is
  * the squared Euclidean consistency error |f(p) + b(p + f(p))|^2; ties go to the first pixel in row-major order
- * within the block.  out[p] = 1 for kept matches, 0 elsewhere. */
-void ffo_sparsify(const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, int s, uint8_t* out) {
+ * within the block.  The paper sparsifies what is left after both consistency checks: `keep` (may be NULL) is
+ * that filter's mask, and a match counts only where keep[p] != 0 as well.  out[p] = 1 for kept matches, 0
+ * elsewhere. */
+void ffo_sparsify(const int16_t* fwd, const int16_t* bwd, const uint8_t* keep, int w, int h, int eps, int s,
+                  uint8_t* out) {
     for (long p = 0; p < (long)w * h; p++) out[p] = 0;
     for (int by = 0; by < h; by += 3)
         for (int bx = 0; bx < w; bx += 3) {
@@ -501,6 +504,7 @@ void ffo_sparsify(const int16_t* fwd, const int16_t* bwd, int w, int h, int eps,
             for (int y = by; y < by + 3 && y < h; y++)
                 for (int x = bx; x < bx + 3 && x < w; x++) {
                     long p = (long)y * w + x;
+                    if (keep && !keep[p]) continue;
                     int fx = fwd[2 * p], fy = fwd[2 * p + 1];
                     int qx = x + fx, qy = y + fy;
                     if (qx < 0 || qx >= w || qy < 0 || qy >= h) continue;

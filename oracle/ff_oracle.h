@@ -62,7 +62,8 @@ int ffo_match_dir(const int16_t* const* feat_a, const int16_t* const* feat_b, co
 void ffo_consistency(const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, uint8_t* mask);
 int ffo_match_bidir2(const uint8_t* rgb_a, const uint8_t* rgb_b, int w, int h, const ffo_params* prm, int rs_radius2,
                      int16_t* flow_fwd, int16_t* flow_bwd, int16_t* flow_bwd2, uint8_t* mask);
-void ffo_sparsify(const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, int s, uint8_t* out);
+void ffo_sparsify(const int16_t* fwd, const int16_t* bwd, const uint8_t* keep, int w, int h, int eps, int s,
+                  uint8_t* out);
 int ffo_match_bidir(const uint8_t* rgb_a, const uint8_t* rgb_b, int w, int h, const ffo_params* prm,
                     int16_t* flow_fwd, int16_t* flow_bwd, int32_t* cost_fwd, int32_t* cost_bwd, uint8_t* mask);
 

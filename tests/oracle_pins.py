@@ -432,8 +432,9 @@ def check_consistency(o):
     assert o.consistency(fwd, bwd, 1).tolist() == [[1, 0]]
 
 
-def sparsify_numpy(fwd, bwd, eps, s):
-    """Brute-force restatement: per 3x3 block, the lowest-error inlier if the block has >= s inliers."""
+def sparsify_numpy(fwd, bwd, eps, s, keep=None):
+    """Brute-force restatement: per 3x3 block, the lowest-error inlier if the block has >= s inliers (an inlier
+    passes the consistency check and, when a filter mask `keep` is given, is set in it)."""
     h, w, _ = fwd.shape
     ys, xs = np.mgrid[0:h, 0:w]
     qx = xs + fwd[..., 0].astype(np.int64)
@@ -442,6 +443,8 @@ def sparsify_numpy(fwd, bwd, eps, s):
     qxc, qyc = np.clip(qx, 0, w - 1), np.clip(qy, 0, h - 1)
     e = (fwd[..., 0] + bwd[qyc, qxc, 0].astype(np.int64)) ** 2 + (fwd[..., 1] + bwd[qyc, qxc, 1].astype(np.int64)) ** 2
     ok = inside & (e <= eps * eps)
+    if keep is not None:
+        ok &= keep.astype(bool)
     out = np.zeros((h, w), np.uint8)
     for by in range(0, h, 3):
         for bx in range(0, w, 3):
@@ -476,6 +479,23 @@ def check_sparsify(o):
                 for bx in range(0, w, 3):
                     assert got[by:by + 3, bx:bx + 3].sum() <= 1
             assert np.all(got <= o.consistency(fwd, bwd, eps))
+            # a filter mask: all ones changes nothing, all zeros keeps nothing, a random one is brute force
+            assert np.array_equal(o.sparsify(fwd, bwd, eps, s, np.ones((h, w), np.uint8)), got)
+            assert o.sparsify(fwd, bwd, eps, s, np.zeros((h, w), np.uint8)).sum() == 0
+            keep = (rng.random((h, w)) < 0.7).astype(np.uint8)
+            got_k = o.sparsify(fwd, bwd, eps, s, keep)
+            assert np.array_equal(got_k, sparsify_numpy(fwd, bwd, eps, s, keep)), (h, w, eps, s)
+            assert np.all(got_k <= keep)
+    # hand example with a mask: the error-0 match (1,1) is filtered out, so (2,2) (error 0) wins
+    fwd = np.zeros((3, 3, 2), np.int16)
+    bwd = np.zeros((3, 3, 2), np.int16)
+    bwd[..., 0] = 1
+    bwd[1, 1] = (0, 0)
+    bwd[2, 2] = (0, 0)
+    keep = np.ones((3, 3), np.uint8)
+    keep[1, 1] = 0
+    assert o.sparsify(fwd, bwd, 1, 8, keep).tolist() == [[0, 0, 0], [0, 0, 0], [0, 0, 1]]
+    assert o.sparsify(fwd, bwd, 1, 9, keep).sum() == 0  # 8 matches left < s
 
 
 def check_second_consistency(o):

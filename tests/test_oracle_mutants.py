@@ -54,6 +54,7 @@ MUTANTS = {
     "sparsify_last_tie_wins": ("if (best_p < 0 || e < best_e) {", "if (best_p < 0 || e <= best_e) {"),
     "sparsify_count_off": ("if (count >= s && best_p >= 0)", "if (count > s && best_p >= 0)"),
     "sparsify_block_4": ("for (int bx = 0; bx < w; bx += 3) {", "for (int bx = 0; bx < w; bx += 4) {"),
+    "sparsify_mask_ignored": ("if (keep && !keep[p]) continue;", "(void)keep;"),
 }
 
 
