@@ -12,7 +12,7 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
-__all__ = ["MatchParams", "PairSpec", "Workload", "WORKLOADS", "workload"]
+__all__ = ["MatchParams", "PairSpec", "Workload", "WORKLOADS", "TABLE3", "workload"]
 
 HASH_SEED = 0x2018_0503
 
@@ -54,9 +54,13 @@ class Workload:
         return sum(p.pixels for p in self.pairs)
 
 
+# Table 3: consistency threshold eps (px) and the number of consistent matches s a 3x3 block needs for its
+# best match to survive sparsification, per dataset
+TABLE3 = {"kitti": {"eps": 1, "min_matches": 7}, "sintel": {"eps": 7, "min_matches": 4}}
+
 SMALL = MatchParams(n_scales=3, iters=4, eps=1)
-KITTI = MatchParams(n_scales=5, iters=6, eps=1)
-SINTEL = MatchParams(n_scales=5, iters=6, eps=7)
+KITTI = MatchParams(n_scales=5, iters=6, eps=TABLE3["kitti"]["eps"])
+SINTEL = MatchParams(n_scales=5, iters=6, eps=TABLE3["sintel"]["eps"])
 
 SERVE_SIZES = ((320, 240, "rects"), (640, 480, "rects"), (1024, 436, "sintel"), (1242, 375, "kitti"))
 
