@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-pair batched measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream measurement")
     ap.add_argument("--no-census", action="store_true", help="skip the Census-cost measurement")
+    ap.add_argument("--no-filtered", action="store_true",
+                    help="skip the measurement with two consistency checks and sparsification")
     ap.add_argument("--autotune", action="store_true",
                     help="run the autotuner instead of the package's table of tuned configurations")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -285,6 +287,70 @@ def measure_census(torch, ff, configs, stream, local_rank, steps, flush):
                                      "peak_gbs": peak, "frac": achieved / peak,
                                      "avg_launch_ms": prop_ms / prop_launches}}
     return out
+
+
+def measure_filtered(torch, ff, configs, stream, local_rank, steps, flush, tuning):
+    """The whole filter of Sec. 3.1 on the KITTI-shaped pair: forward field, two inverse fields (the second with
+    its own random-search radius and hash stream), both consistency checks, then sparsification of what they
+    left (3x3 blocks, s = 7 of Table 3); L2 flushed per step.  Also the sparsification kernel alone."""
+    wl = configs.workload("kitti_1242x375")
+    spec = wl.pairs[0]
+    s_min = configs.TABLE3["kitti"]["min_matches"]
+    imgs = make_inputs(wl)
+    dev = torch.device("cuda", local_rank)
+    with torch.cuda.stream(stream):
+        d = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in imgs]
+    stream.synchronize()
+    M = ff.Matcher(spec.params, local_rank, stream)
+    for lvl, cfg in enumerate(tuning):
+        ff.ff_set_tuning(M.ctx, lvl, cfg)
+    outs, sparse = None, None
+
+    def step():
+        nonlocal outs, sparse
+        pyrs = [(M.features(a), M.features(b)) for a, b in d]
+        outs = M.match_batch(pyrs, outs=outs, with_cost=False, second_check=True)
+        with torch.cuda.stream(stream):
+            sparse = [M.sparsify(o["flow_fwd"], o["flow_bwd"], spec.params.eps, s_min, keep=o["mask"]) for o in outs]
+        for pa, pb in pyrs:
+            M.release(pa)
+            M.release(pb)
+
+    for _ in range(3):
+        step()
+    ev = []
+    for _ in range(steps):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        ev.append((e0, e1))
+    stream.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    o = outs[0]
+    # the sparsification kernel alone (inputs resident in L2: 10 algorithmic bytes per pixel -- forward flow,
+    # the inverse flow at the target, the filter mask, the output)
+    n_sp = 200
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_sp):
+            M.sparsify(o["flow_fwd"], o["flow_bwd"], spec.params.eps, s_min, keep=o["mask"])
+        e1.record(stream)
+    stream.synchronize()
+    sp_ms = e0.elapsed_time(e1) / n_sp
+    peak, _ = load_peaks()
+    sp_gbs = 10 * wl.pixels / (sp_ms / 1000.0) / 1e9
+    kept_two = float(o["mask"].float().mean().item())
+    kept_sparse = float(sparse[0].float().mean().item())
+    M.close()
+    return {"workload": wl.name, "px_per_step": wl.pixels, "eps": spec.params.eps, "min_matches": s_min,
+            "rs_radius2": spec.params.rs_radius2, "steps": steps, "value": wl.pixels / (ms / 1000.0) / 1e6,
+            "unit": UNIT, "ms_per_step": ms, "l2": "flushed before every timed step",
+            "kept_after_two_checks": kept_two, "kept_after_sparsification": kept_sparse,
+            "k_sparsify": {"ms": sp_ms, "alg_bytes_per_px": 10, "achieved_gbs": sp_gbs, "peak_gbs": peak,
+                           "frac": sp_gbs / peak, "note": "inputs L2-resident; a launch of ~4.7 MB is latency-bound"}}
 
 
 def measure_served(torch, ff, configs, stream, local_rank, n_req):
@@ -576,6 +642,11 @@ def main():
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(workload, imgs, cost_id)
+    if not args.no_filtered and workload.name == "kitti_1242x375" and cost_id == 0:
+        filtered = measure_filtered(torch, ff, configs, stream, local_rank, max(10, min(100, args.steps // 3)),
+                                    flush_l2, tuning)
+        if rank == 0:
+            line["filtered"] = filtered
     if not args.no_census:
         census = measure_census(torch, ff, configs, stream, local_rank, max(10, min(100, args.steps // 3)), flush_l2)
         if rank == 0:

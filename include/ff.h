@@ -166,11 +166,16 @@ FF_API ff_status ff_consistency(ff_ctx* ctx, const int16_t* fwd, const int16_t* 
 
 /* Sparsification of the consistent matches (Sec. 3.1; s in Table 3: 7 for KITTI, 4 for Sintel): the image is
  * tiled by 3x3 blocks from (0, 0) (blocks at the right and bottom edges may be smaller); in every block with at
- * least `min_matches` (1..9) matches that pass the consistency check with `eps`, only the match with the
- * lowest squared consistency error is kept (the first in row-major order on ties).  sparse_dev[p] = 1 for kept
- * matches, 0 elsewhere.  fwd/bwd: device int16 [h][w][2] flows; sparse_dev: device uint8 [h][w]. */
-FF_API ff_status ff_sparsify(ff_ctx* ctx, const int16_t* fwd, const int16_t* bwd, int w, int h, int eps,
-                             int min_matches, uint8_t* sparse_dev);
+ * least `min_matches` (1..9) matches that pass the consistency check with `eps` -- and, when `keep_dev` is not
+ * NULL, are set in that mask (the paper sparsifies what both consistency checks left: pass the `mask` of an
+ * ff_pair_job matched with a second inverse field) -- only the match with the lowest squared consistency error
+ * against `bwd` is kept (the first in row-major order on ties).  sparse_dev[p] = 1 for kept matches, 0
+ * elsewhere.  fwd/bwd: device int16 [h][w][2] flows (4-byte aligned); keep_dev: device uint8 [h][w] or NULL;
+ * sparse_dev: device uint8 [h][w], written.  Asynchronous on the context's stream; FF_ERR_ARG (nothing
+ * launched) for null or misaligned flow pointers, sizes outside 1..8192, eps outside 0..32767 or min_matches
+ * outside 1..9. */
+FF_API ff_status ff_sparsify(ff_ctx* ctx, const int16_t* fwd, const int16_t* bwd, const uint8_t* keep_dev, int w,
+                             int h, int eps, int min_matches, uint8_t* sparse_dev);
 
 /* Return a pyramid to the context's pool (its memory is reused by a later ff_features of the same size). */
 FF_API ff_status ff_pyr_release(ff_ctx* ctx, ff_pyr* pyr);

@@ -1242,16 +1242,16 @@ ff_status ff_consistency(ff_ctx* c, const int16_t* fwd, const int16_t* bwd, int 
     return run_launches(c, {l}, c->profiling);
 }
 
-ff_status ff_sparsify(ff_ctx* c, const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, int min_matches,
-                      uint8_t* sparse_dev) {
+ff_status ff_sparsify(ff_ctx* c, const int16_t* fwd, const int16_t* bwd, const uint8_t* keep_dev, int w, int h,
+                      int eps, int min_matches, uint8_t* sparse_dev) {
     if (!c) return FF_ERR_ARG;
     if (!fwd || !bwd || !sparse_dev || !aligned4(fwd) || !aligned4(bwd)) return fail(c, FF_ERR_ARG, "bad pointer");
     if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim) return fail(c, FF_ERR_ARG, "size %dx%d outside 1..%d", w, h, kMaxDim);
     if (eps < 0 || eps > 32767) return fail(c, FF_ERR_ARG, "eps must be 0..32767");
     if (min_matches < 1 || min_matches > 9) return fail(c, FF_ERR_ARG, "min_matches must be 1..9");
     FF_CUDA(c, cudaSetDevice(c->device));
-    launch_sparsify(reinterpret_cast<const uint32_t*>(fwd), reinterpret_cast<const uint32_t*>(bwd), w, h, eps,
-                    min_matches, sparse_dev, c->stream);
+    launch_sparsify(reinterpret_cast<const uint32_t*>(fwd), reinterpret_cast<const uint32_t*>(bwd), keep_dev, w, h,
+                    eps, min_matches, sparse_dev, c->stream);
     FF_CUDA(c, cudaGetLastError());
     c->launches += 1;
     return FF_OK;

@@ -160,8 +160,8 @@ void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n
 
 void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, const uint32_t* bwd2, int w, int h, int eps,
                         uint8_t* mask, cudaStream_t st);  // bwd2 may be null
-void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int eps, int s, uint8_t* out,
-                     cudaStream_t st);
+void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, const uint8_t* keep, int w, int h, int eps, int s,
+                     uint8_t* out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------------------
 // read-only views of context and pyramid internals for other translation units of the library

@@ -12,9 +12,10 @@ __device__ __forceinline__ bool in_level(int x, int y, int w, int h) {
 
 // Sparsification (Sec. 3.1; s in Table 3): per 3x3 block (tiling from (0, 0), partial blocks at the edges)
 // holding at least s consistent matches, keep the one with the lowest squared consistency error (first in
-// row-major order on ties).  One thread per block.
-__global__ void k_sparsify(const uint32_t* __restrict__ fwd, const uint32_t* __restrict__ bwd, int w, int h, int eps,
-                           int s, uint8_t* __restrict__ out) {
+// row-major order on ties).  A match counts only where the filter mask `keep` (may be null) is set.  One
+// thread per block.
+__global__ void k_sparsify(const uint32_t* __restrict__ fwd, const uint32_t* __restrict__ bwd,
+                           const uint8_t* __restrict__ keep, int w, int h, int eps, int s, uint8_t* __restrict__ out) {
     grid_dependency_sync();
     const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y;
     if (3 * bx >= w) return;
@@ -23,6 +24,7 @@ __global__ void k_sparsify(const uint32_t* __restrict__ fwd, const uint32_t* __r
     long long best_e = 0;
     for (int y = y0; y < y1; y++)
         for (int x = x0; x < x1; x++) {
+            if (keep && !keep[y * w + x]) continue;
             const uint32_t f = fwd[y * w + x];
             const int fx = flow_x(f), fy = flow_y(f), qx = x + fx, qy = y + fy;
             if (!in_level(qx, qy, w, h)) continue;
@@ -39,11 +41,11 @@ __global__ void k_sparsify(const uint32_t* __restrict__ fwd, const uint32_t* __r
         for (int x = x0; x < x1; x++) out[y * w + x] = (count >= s && y * w + x == best_p) ? 1 : 0;
 }
 
-void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, int w, int h, int eps, int s, uint8_t* out,
-                     cudaStream_t st) {
+void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, const uint8_t* keep, int w, int h, int eps, int s,
+                     uint8_t* out, cudaStream_t st) {
     const int nbx = (w + 2) / 3, nby = (h + 2) / 3;
     dim3 grid((nbx + 127) / 128, nby);
-    launch_k(k_sparsify, grid, dim3(128), 0, st, fwd, bwd, w, h, eps, s, out);
+    launch_k(k_sparsify, grid, dim3(128), 0, st, fwd, bwd, keep, w, h, eps, s, out);
 }
 
 // ---------------------------------------------------------------------------------------------------------

@@ -89,7 +89,7 @@ def lib():
         "ff_set_tuning": (S, [vp, i, ctypes.POINTER(Tuning)]),
         "ff_get_tuning": (S, [vp, i, ctypes.POINTER(Tuning)]),
         "ff_consistency": (S, [vp, vp, vp, i, i, i, vp]),
-        "ff_sparsify": (S, [vp, vp, vp, i, i, i, i, vp]),
+        "ff_sparsify": (S, [vp, vp, vp, vp, i, i, i, i, vp]),
         "ff_pyr_release": (S, [vp, vp]),
         "ff_pyr_level_dims": (S, [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "ff_pyr_features": (vp, [vp, i]),
@@ -180,8 +180,8 @@ def ff_consistency(ctx, fwd: int, bwd: int, w: int, h: int, eps: int, mask_dev: 
     _check(ctx, lib().ff_consistency(ctx, fwd, bwd, w, h, eps, mask_dev))
 
 
-def ff_sparsify(ctx, fwd: int, bwd: int, w: int, h: int, eps: int, min_matches: int, sparse_dev: int):
-    _check(ctx, lib().ff_sparsify(ctx, fwd, bwd, w, h, eps, min_matches, sparse_dev))
+def ff_sparsify(ctx, fwd: int, bwd: int, keep, w: int, h: int, eps: int, min_matches: int, sparse_dev: int):
+    _check(ctx, lib().ff_sparsify(ctx, fwd, bwd, keep, w, h, eps, min_matches, sparse_dev))
 
 
 def ff_pyr_release(ctx, pyr):
@@ -431,11 +431,18 @@ class Matcher:
         ff_consistency(self.ctx, fwd.data_ptr(), bwd.data_ptr(), w, h, eps, mask.data_ptr())
         return mask
 
-    def sparsify(self, fwd, bwd, eps: int, min_matches: int):
+    def sparsify(self, fwd, bwd, eps: int, min_matches: int, keep=None):
+        """keep: optional uint8 [h][w] CUDA mask of the matches the consistency checks left (e.g. the 'mask' of
+        match_batch with second_check); None counts every match that passes the check against bwd."""
         h, w = int(fwd.shape[0]), int(fwd.shape[1])
         out = self._empty((h, w), self.torch.uint8)
-        self._uses(fwd, bwd)
-        ff_sparsify(self.ctx, fwd.data_ptr(), bwd.data_ptr(), w, h, eps, min_matches, out.data_ptr())
+        if keep is not None:
+            assert keep.dtype == self.torch.uint8 and keep.is_cuda and keep.is_contiguous() and keep.numel() == h * w
+            self._uses(fwd, bwd, keep)
+        else:
+            self._uses(fwd, bwd)
+        ff_sparsify(self.ctx, fwd.data_ptr(), bwd.data_ptr(), keep.data_ptr() if keep is not None else None, w, h, eps,
+                    min_matches, out.data_ptr())
         return out
 
     def sync(self):

@@ -263,10 +263,14 @@ def test_sparsify_parity(lib_built):
     for (h, w) in ((1, 1), (7, 8), (31, 47), (96, 128)):
         fwd = rng.integers(-2, 3, size=(h, w, 2)).astype(np.int16)
         bwd = rng.integers(-2, 3, size=(h, w, 2)).astype(np.int16)
+        keep = (rng.random((h, w)) < 0.7).astype(np.uint8)
         for eps, s in ((1, 1), (2, 4), (3, 7), (0, 9)):
             got = M.sparsify(torch.from_numpy(fwd).cuda(), torch.from_numpy(bwd).cuda(), eps, s)
+            got_k = M.sparsify(torch.from_numpy(fwd).cuda(), torch.from_numpy(bwd).cuda(), eps, s,
+                               keep=torch.from_numpy(keep).cuda())
             M.sync()
             assert np.array_equal(got.cpu().numpy(), o.sparsify(fwd, bwd, eps, s)), (h, w, eps, s)
+            assert np.array_equal(got_k.cpu().numpy(), o.sparsify(fwd, bwd, eps, s, keep)), (h, w, eps, s)
     spec = configs.workload("small_128x96").pairs[0]
     a, b, _ = synth.make_pair(spec.kind, spec.seed, spec.w, spec.h)
     ff_, fb_, _, _, _ = check_pair(a, b, spec.params)
@@ -287,8 +291,14 @@ def test_two_consistency_checks(lib_built, h, w, L, T):
     pa, pb = M.features(torch.from_numpy(a).cuda()), M.features(torch.from_numpy(b).cuda())
     out = M.match_batch([(pa, pb)], second_check=True)[0]
     M.sync()
-    want = oracle.default().match_bidir2(a, b, G.oracle_params(prm), prm.rs_radius2)
+    o = oracle.default()
+    want = o.match_bidir2(a, b, G.oracle_params(prm), prm.rs_radius2)
     for k, wv in zip(("flow_fwd", "flow_bwd", "flow_bwd2", "mask"), want):
         assert np.array_equal(out[k].cpu().numpy(), wv), k
+    # the whole filter of Sec. 3.1: sparsification of what both checks left (s of Table 3)
+    for s in (4, 7):
+        got = M.sparsify(out["flow_fwd"], out["flow_bwd"], prm.eps, s, keep=out["mask"])
+        M.sync()
+        assert np.array_equal(got.cpu().numpy(), o.sparsify(want[0], want[1], prm.eps, s, want[3])), s
     M.release(pa)
     M.release(pb)
