@@ -12,40 +12,51 @@ __device__ __forceinline__ bool in_level(int x, int y, int w, int h) {
 
 // Sparsification (Sec. 3.1; s in Table 3): per 3x3 block (tiling from (0, 0), partial blocks at the edges)
 // holding at least s consistent matches, keep the one with the lowest squared consistency error (first in
-// row-major order on ties).  A match counts only where the filter mask `keep` (may be null) is set.  One
-// thread per block.
-__global__ void k_sparsify(const uint32_t* __restrict__ fwd, const uint32_t* __restrict__ bwd,
-                           const uint8_t* __restrict__ keep, int w, int h, int eps, int s, uint8_t* __restrict__ out) {
+// row-major order on ties).  A match counts only where the filter mask `keep` (may be null) is set.
+// One thread per pixel: every pixel's loads are in flight at once.  A CTA covers 32 x 2 whole blocks; each pixel
+// posts a key (error << 4 | its row-major index in the block, or ~0 if it does not count) to shared memory, and
+// every pixel then reads its block's nine keys: the count, and whether its own key is the block's minimum.
+constexpr int kSparsePx = 96, kSparsePy = 6;
+
+__global__ void __launch_bounds__(kSparsePx* kSparsePy)
+    k_sparsify(const uint32_t* __restrict__ fwd, const uint32_t* __restrict__ bwd, const uint8_t* __restrict__ keep,
+               int w, int h, int eps, int s, uint8_t* __restrict__ out) {
     grid_dependency_sync();
-    const int bx = blockIdx.x * blockDim.x + threadIdx.x, by = blockIdx.y;
-    if (3 * bx >= w) return;
-    const int x0 = 3 * bx, y0 = 3 * by, x1 = min(x0 + 3, w), y1 = min(y0 + 3, h);
-    int count = 0, best_p = -1;
-    long long best_e = 0;
-    for (int y = y0; y < y1; y++)
-        for (int x = x0; x < x1; x++) {
-            if (keep && !keep[y * w + x]) continue;
-            const uint32_t f = fwd[y * w + x];
-            const int fx = flow_x(f), fy = flow_y(f), qx = x + fx, qy = y + fy;
-            if (!in_level(qx, qy, w, h)) continue;
+    __shared__ unsigned long long key[kSparsePy][kSparsePx];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = blockIdx.x * kSparsePx + tx, y = blockIdx.y * kSparsePy + ty;
+    const bool inside = x < w && y < h;
+    unsigned long long k = ~0ull;
+    if (inside && (!keep || keep[y * w + x])) {
+        const uint32_t f = fwd[y * w + x];
+        const int fx = flow_x(f), fy = flow_y(f), qx = x + fx, qy = y + fy;
+        if (in_level(qx, qy, w, h)) {
             const uint32_t b = bwd[qy * w + qx];
             const long long ex = fx + flow_x(b), ey = fy + flow_y(b), e = ex * ex + ey * ey;
-            if (e > (long long)eps * eps) continue;
-            count++;
-            if (best_p < 0 || e < best_e) {
-                best_p = y * w + x;
-                best_e = e;
-            }
+            if (e <= (long long)eps * eps) k = ((unsigned long long)e << 4) | (unsigned)((ty % 3) * 3 + tx % 3);
         }
-    for (int y = y0; y < y1; y++)
-        for (int x = x0; x < x1; x++) out[y * w + x] = (count >= s && y * w + x == best_p) ? 1 : 0;
+    }
+    key[ty][tx] = k;
+    __syncthreads();
+    if (!inside) return;
+    const int bx0 = tx - tx % 3, by0 = ty - ty % 3;
+    int count = 0;
+    unsigned long long best = ~0ull;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const unsigned long long kk = key[by0 + i][bx0 + j];
+            count += kk != ~0ull;
+            best = kk < best ? kk : best;
+        }
+    out[y * w + x] = (count >= s && k == best && k != ~0ull) ? 1 : 0;
 }
 
 void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, const uint8_t* keep, int w, int h, int eps, int s,
                      uint8_t* out, cudaStream_t st) {
-    const int nbx = (w + 2) / 3, nby = (h + 2) / 3;
-    dim3 grid((nbx + 127) / 128, nby);
-    launch_k(k_sparsify, grid, dim3(128), 0, st, fwd, bwd, keep, w, h, eps, s, out);
+    dim3 grid((w + kSparsePx - 1) / kSparsePx, (h + kSparsePy - 1) / kSparsePy);
+    launch_k(k_sparsify, grid, dim3(kSparsePx, kSparsePy), 0, st, fwd, bwd, keep, w, h, eps, s, out);
 }
 
 // ---------------------------------------------------------------------------------------------------------

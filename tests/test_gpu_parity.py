@@ -244,6 +244,35 @@ def test_errors_are_reported(lib_built):
     M.sync()
 
 
+def test_filter_argument_errors_launch_nothing(lib_built):
+    """ff_consistency and ff_sparsify reject bad arguments with FF_ERR_ARG before launching anything."""
+    from paper_1805_03517_gb300 import ff
+
+    M = matcher(mp(3, 1))
+    f = torch.zeros((6, 9, 2), dtype=torch.int16, device="cuda")
+    out = torch.zeros((6, 9), dtype=torch.uint8, device="cuda")
+    L = ff.lib()
+    fp, op = f.data_ptr(), out.data_ptr()
+    M.sync()
+    s0 = M.stats()["kernel_launches"]
+    bad_sparsify = [(fp, fp, None, 9, 6, 1, 0, op), (fp, fp, None, 9, 6, 1, 10, op), (fp, fp, None, 9, 6, -1, 7, op),
+                    (fp, fp, None, 0, 6, 1, 7, op), (fp, fp, None, 9, 9000, 1, 7, op), (None, fp, None, 9, 6, 1, 7, op),
+                    (fp + 2, fp, None, 9, 6, 1, 7, op), (fp, fp, None, 9, 6, 1, 7, None)]
+    for args in bad_sparsify:
+        assert L.ff_sparsify(M.ctx, *args) == ff.FF_ERR_ARG, args
+    bad_consistency = [(fp, fp, 0, 6, 1, op), (fp, fp, 9, 6, -1, op), (None, fp, 9, 6, 1, op), (fp, fp + 2, 9, 6, 1, op),
+                       (fp, fp, 9, 6, 1, None)]
+    for args in bad_consistency:
+        assert L.ff_consistency(M.ctx, *args) == ff.FF_ERR_ARG, args
+    M.sync()
+    assert M.stats()["kernel_launches"] == s0
+    keep = torch.ones((6, 9), dtype=torch.uint8, device="cuda")
+    assert L.ff_sparsify(M.ctx, fp, fp, keep.data_ptr(), 9, 6, 1, 7, op) == ff.FF_OK
+    M.sync()
+    assert M.stats()["kernel_launches"] == s0 + 1
+    assert out.cpu().numpy().sum() == 3 * 2  # zero flows: every full 3x3 block keeps its first pixel
+
+
 def test_empty_batch_launches_nothing(lib_built):
     from paper_1805_03517_gb300 import ff
 
