@@ -113,25 +113,34 @@ __device__ __forceinline__ void walsh4(int a0, int a1, int a2, int a3, int a4, i
 // window: the 7x7 neighbourhood is window rows ly..ly+6, columns lx..lx+6 (the WHT window reaches one row and
 // column further).  Bit k of channel c: the k-th neighbour in row-major order, centre skipped, is strictly
 // darker than the centre.  Written as 8 words: (low, high) 32 bits of channels 0, 1, 2, then two zero words.
+// Per window row, the eight bytes at columns lx..lx+7 come from three aligned words and two funnel shifts; a
+// per-byte compare against the replicated centre gives 0xff / 0x00 bytes, and one multiply gathers the four
+// byte flags of a word into four adjacent bits (flag bits 0, 8, 16, 24 land on 28..31, every cross product
+// on a distinct lower bit, so nothing carries).
+__device__ __forceinline__ uint32_t darker_bits4(uint32_t v, uint32_t centre4) {
+    return ((__vcmpltu4(v, centre4) & 0x01010101u) * 0x10204080u) >> 28;
+}
+
 __device__ __forceinline__ void census_pixel(const uint8_t (&win)[3][kWinY][kWinX], int lx, int ly,
                                              uint32_t* __restrict__ dst) {
     uint32_t w[6];
+    const int wx = lx >> 2, sh = 8 * (lx & 3);
 #pragma unroll
     for (int ch = 0; ch < 3; ch++) {
-        const int centre = win[ch][ly + 3][lx + 3];
-        uint32_t lo = 0, hi = 0;
+        const uint32_t centre4 = (uint32_t)win[ch][ly + 3][lx + 3] * 0x01010101u;
+        unsigned long long bits = 0;
 #pragma unroll
-        for (int r = 0; r < 7; r++)
-#pragma unroll
-            for (int c = 0; c < 7; c++) {
-                if (r == 3 && c == 3) continue;
-                const int k = r * 7 + c - (r * 7 + c > 24 ? 1 : 0);
-                const uint32_t bit = win[ch][ly + r][lx + c] < centre ? 1u : 0u;
-                if (k < 32) lo |= bit << k;
-                else hi |= bit << (k - 32);
-            }
-        w[2 * ch] = lo;
-        w[2 * ch + 1] = hi;
+        for (int r = 0; r < 7; r++) {
+            const uint32_t* row = reinterpret_cast<const uint32_t*>(&win[ch][ly + r][0]);
+            const uint32_t a = row[wx], b = row[wx + 1], c = row[wx + 2];
+            const uint32_t m = darker_bits4(__funnelshift_r(a, b, sh), centre4) |
+                               (darker_bits4(__funnelshift_r(b, c, sh), centre4) << 4);  // columns lx..lx+7
+            if (r < 3) bits |= (unsigned long long)(m & 0x7fu) << (7 * r);
+            else if (r == 3) bits |= (unsigned long long)((m & 0x7u) | ((m >> 1) & 0x38u)) << 21;
+            else bits |= (unsigned long long)(m & 0x7fu) << (7 * r - 1);
+        }
+        w[2 * ch] = (uint32_t)bits;
+        w[2 * ch + 1] = (uint32_t)(bits >> 32);
     }
     uint4* d = reinterpret_cast<uint4*>(dst);
     d[0] = make_uint4(w[0], w[1], w[2], w[3]);
