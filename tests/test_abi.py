@@ -59,3 +59,20 @@ def test_null_arguments(L):
 
 def test_library_is_in_tree():
     assert os.path.commonpath([ff.LIB_PATH, os.path.dirname(ff.__file__)]) == os.path.dirname(ff.__file__)
+
+
+def test_tuned_table_is_well_formed():
+    """The package table of tuned launch configurations: one valid [tile_w, tile_h, iterations per launch,
+    threads, speculate] per level of each listed workload."""
+    import json
+
+    from paper_1805_03517_gb300 import configs
+
+    table = json.load(open(os.path.join(os.path.dirname(ff.__file__), "tuned.json")))
+    names = [k for k in table if k != "note"]
+    assert names and all(k in configs.WORKLOADS for k in names)
+    for name in names:
+        prm = configs.workload(name).pairs[0].params
+        assert len(table[name]) == prm.n_scales
+        for tw, th, k, threads, spec in table[name]:
+            assert tw >= 1 and th >= 1 and 1 <= k <= prm.iters and threads in (128, 256, 512) and spec in (0, 1)

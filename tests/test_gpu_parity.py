@@ -212,6 +212,29 @@ def test_full_size_configs(lib_built, name):
     check_pair(a, b, spec.params)
 
 
+def test_full_size_in_the_benchmark_configuration(lib_built):
+    """Every workload in the package table of tuned launch configurations (the per-level configurations the
+    benchmark times), matched with exactly those configurations: every output bit-exact."""
+    import json
+    import os
+
+    from paper_1805_03517_gb300 import ff
+
+    table = json.load(open(os.path.join(os.path.dirname(ff.__file__), "tuned.json")))
+    names = [k for k in table if k in configs.WORKLOADS]
+    assert names
+    for name in names:
+        spec = configs.workload(name).pairs[0]
+        a, b, _ = synth.make_pair(spec.kind, spec.seed, spec.w, spec.h)
+        M = ff.Matcher(spec.params, 0)
+        for lvl, cfg in enumerate(table[name]):
+            ff.ff_set_tuning(M.ctx, lvl, tuple(cfg))
+        assert [list(ff.ff_get_tuning(M.ctx, lvl)) for lvl in range(spec.params.n_scales)] == table[name]
+        got = G.gpu_bidir(M, a, b, torch)
+        G.assert_same(got, oracle.default().match_bidir(a, b, G.oracle_params(spec.params)))
+        M.close()
+
+
 def test_errors_are_reported(lib_built):
     from paper_1805_03517_gb300 import ff
 
