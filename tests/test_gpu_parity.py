@@ -102,6 +102,36 @@ def test_tiny_and_ragged(lib_built, h, w, L, T):
     check_pair(a, b, mp(L, T))
 
 
+def test_random_parameter_sweep(lib_built):
+    """Seeded draws over sizes, scales, iterations, random-search radius (0 disables the random candidates),
+    eps, hash seed and cost, on textured pairs with a random shift: every output bit-exact."""
+    from paper_1805_03517_gb300 import ff
+
+    rng = np.random.default_rng(2024)
+    for k in range(12):
+        h, w = int(rng.integers(1, 90)), int(rng.integers(1, 140))
+        max_l = 1
+        while max_l < 8 and (h >> max_l) >= 1 and (w >> max_l) >= 1:
+            max_l += 1
+        prm = configs.MatchParams(n_scales=int(rng.integers(1, max_l + 1)), iters=int(rng.integers(1, 5)),
+                                  rs_radius=int(rng.integers(0, 17)), eps=int(rng.integers(0, 8)),
+                                  seed=int(rng.integers(0, 2**32)), cost=int(rng.integers(0, 2)))
+        a = P.smooth_texture(100 + k, h, w)
+        b = P.shifted(a, int(rng.integers(-6, 7)), int(rng.integers(-6, 7)), 200 + k)
+        M = ff.Matcher(prm, 0)
+        got = G.gpu_bidir(M, a, b, torch)
+        M.close()
+        G.assert_same(got, oracle.default().match_bidir(a, b, G.oracle_params(prm)))
+    # radius 0: the random candidate is always the current flow, so only the neighbours can move a match
+    prm = configs.MatchParams(n_scales=3, iters=3, rs_radius=0, eps=1)
+    a = P.smooth_texture(300, 45, 61)
+    b = P.shifted(a, 4, -3, 301)
+    M = ff.Matcher(prm, 0)
+    got = G.gpu_bidir(M, a, b, torch)
+    M.close()
+    G.assert_same(got, oracle.default().match_bidir(a, b, G.oracle_params(prm)))
+
+
 def test_random_images_radius(lib_built):
     a = P.rand_img(1, 40, 52)
     b = P.rand_img(2, 40, 52)
