@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -571,31 +572,57 @@ def main():
     ms, value = aggregate_ranks(torch, dist, dev, sum(times) / len(times), px_per_step, world)
     launches = int(s1["kernel_launches"] - s0["kernel_launches"])
 
-    # end to end through the public API: pinned host frames in, flows and mask out, copies inside the timing
-    host_in = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in imgs]
-    host_out = None
+    # end to end through the public API, copies inside the timing: every step's frames go from one pinned host
+    # buffer to the device in one copy, and its result (forward and inverse flows and mask of every pair) comes
+    # back in one copy (each frame and output starts on a 256-byte boundary of its buffer)
+    def packed(sizes):
+        offs, total = [], 0
+        for n in sizes:
+            offs.append(total)
+            total += (n + 255) // 256 * 256
+        return offs, total
+
+    in_offs, in_total = packed([x.nbytes for pr in imgs for x in pr])
+    h_in = torch.empty(in_total, dtype=torch.uint8).pin_memory()
+    d_in = torch.empty(in_total, dtype=torch.uint8, device=dev)
+    e2e_imgs = []
+    for i, (a, b) in enumerate(imgs):
+        views = []
+        for x, off in zip((a, b), in_offs[2 * i:2 * i + 2]):
+            h_in[off:off + x.nbytes].copy_(torch.from_numpy(x).reshape(-1))
+            views.append(d_in[off:off + x.nbytes].view(x.shape))
+        e2e_imgs.append(tuple(views))
+    out_shapes = []
+    for p in workload.pairs:
+        out_shapes += [("flow_fwd", (p.h, p.w, 2), torch.int16), ("flow_bwd", (p.h, p.w, 2), torch.int16),
+                       ("mask", (p.h, p.w), torch.uint8)]
+    out_bytes = [math.prod(sh) * torch.tensor([], dtype=dt).element_size() for _, sh, dt in out_shapes]
+    out_offs, out_total = packed(out_bytes)
+    d_out = torch.empty(out_total, dtype=torch.uint8, device=dev)
+    h_out = torch.empty(out_total, dtype=torch.uint8).pin_memory()
+    e2e_outs = [{} for _ in workload.pairs]
+    for j, ((k, sh, dt), off, nb) in enumerate(zip(out_shapes, out_offs, out_bytes)):
+        e2e_outs[j // 3][k] = d_out[off:off + nb].view(dt).view(sh)
 
     def e2e_step():
-        nonlocal host_out
         with torch.cuda.stream(stream):
-            for (ha, hb), (da, db) in zip(host_in, dev_imgs):
-                da.copy_(ha, non_blocking=True)
-                db.copy_(hb, non_blocking=True)
-        step()
+            d_in.copy_(h_in, non_blocking=True)
+        pyrs = [(M.features(a), M.features(b)) for a, b in e2e_imgs]
+        M.match_batch(pyrs, outs=e2e_outs, with_cost=False)
+        for pa, pb in pyrs:
+            M.release(pa)
+            M.release(pb)
         with torch.cuda.stream(stream):
-            if host_out is None:
-                host_out = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items()}
-                            for o in outs]
-            for ho, o in zip(host_out, outs):
-                for k in ("flow_fwd", "flow_bwd", "mask"):
-                    ho[k].copy_(o[k], non_blocking=True)
+            h_out.copy_(d_out, non_blocking=True)
 
     for _ in range(3):
         e2e_step()
     e2e_times = timed(max(10, args.steps // 4), e2e_step, pre=flush_l2)
     e2e_ms = sum(e2e_times) / len(e2e_times)
-    h2d = sum(a.numel() + b.numel() for a, b in host_in)
-    d2h = sum(o[k].numel() * o[k].element_size() for o in outs for k in ("flow_fwd", "flow_bwd", "mask"))
+    h2d, d2h = in_total, out_total
+    for o, eo in zip(outs, e2e_outs):  # the end-to-end result equals the device-timed one
+        for k in ("flow_fwd", "flow_bwd", "mask"):
+            assert torch.equal(o[k], eo[k]), k
 
     # per-phase device time (profiling context: same kernels and launch shapes, phases bracketed by events)
     P = ff.Matcher(prm, local_rank, stream)
