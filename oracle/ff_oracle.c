@@ -18,7 +18,8 @@
  * The paper leaves the cost, descriptor size, filter, schedule and tie rules to cited work that is not
  * restated here; the readings taken are listed beside each function.  Parity of the end-to-end schedule is
  * pinned only through invariants (monotone cost, exact seed, exact translation recovery), since the paper
- * prints no matching output to compare with.
+ * prints no matching output to compare with: for the composed stage (ffo_match_dir, ffo_match_bidir,
+ * ffo_match_bidir2) parity is unpinned beyond those invariants; every step it composes is pinned on its own.
  */
 #include "ff_oracle.h"
 
