@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-pair batched measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream measurement")
     ap.add_argument("--no-census", action="store_true", help="skip the Census-cost measurement")
+    ap.add_argument("--settle-s", type=float, default=2.0,
+                    help="seconds of untimed steps before the warm-up steps, so the clocks have settled")
     ap.add_argument("--no-filtered", action="store_true",
                     help="skip the measurement with two consistency checks and sparsification")
     ap.add_argument("--autotune", action="store_true",
@@ -551,6 +553,14 @@ def main():
             M.release(pb)
     stream.synchronize()
 
+    # untimed steps until the GPU has been busy for --settle-s seconds (its clocks ramp up under sustained load
+    # on a freshly started process), then the W warm-up steps
+    t_settle = time.perf_counter()
+    while time.perf_counter() - t_settle < args.settle_s:
+        for _ in range(50):
+            flush_l2()
+            step()
+        stream.synchronize()
     for _ in range(args.warmup):
         flush_l2()
         step()
@@ -668,7 +678,8 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "tiles_per_level": {str(l): list(c) for l, c in enumerate(tuning)},
                        "tiles_from": tuning_source,
-                       "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write, outside the events)"},
+                       "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write, outside the events)",
+                       "settle_s": args.settle_s},
             "gpu_launches": launches,
             "clocks": clocks,
             "e2e": {"value": px_per_step * world / (e2e_ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
