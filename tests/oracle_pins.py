@@ -14,8 +14,16 @@ What pins what (FlowFields++, arXiv 1805.03517, Sec. 3.1, under the readings in 
   * SAD/cost       -- NumPy sum of absolute differences; out-of-level targets rejected;
   * propagation    -- invariants: cost never rises, cost == SAD(flow), flows stay in the level, only the
                       active colour changes, the result is no worse than every neighbour candidate, a changed
-                      flow strictly lowers the cost; plus an independent pure-Python restatement of the
-                      schedule on tiny inputs (a cross-check, not a pin to something outside);
+                      flow strictly lowers the cost;
+  * random search  -- where every move comes from: at d = 0 only an upstream neighbour's flow, at d >= 1 a
+                      neighbour's flow or a base plus this pixel's hashed offset in [-R, R]^2 (never (0, 0)),
+                      and no untaken random candidate was strictly cheaper; a (-1, -2) shift that only the random
+                      search can reach is recovered exactly, and nothing moves with R = 0; the same content at
+                      two levels, or as forward vs inverse field, draws different offsets (level and direction
+                      are in the key of the whole stage);
+  * cross-checks   -- a pure-Python restatement of the schedule on tiny inputs and the stage recomposed from its
+                      steps (checks against the oracle's own loop, not pins: every planted mistake must also be
+                      caught by a pin above, tests/test_oracle_mutants.py);
   * hash           -- a NumPy restatement of the published lowbias32 finaliser, and uniformity of offsets;
   * translation    -- exact recovery (cost 0, consistent) of known integer translations of a texture;
   * consistency    -- NumPy restatement, the f = -b case, and the eps boundary.
@@ -389,6 +397,136 @@ def check_propagation_schedule(o):
             assert np.array_equal(f_o, f_p) and np.array_equal(c_o, c_p), (h, w, k)
 
 
+def hashed_offset(seed, dir, level, t, d, x, y, R):
+    """The random-search offset of pixel (x, y) at (level, iteration t, direction step d): each component uniform in
+    [-R, R] from the published lowbias32 finaliser keyed as in the reading of Sec. 3.1 (Python integers)."""
+    span = 2 * R + 1
+    return (hash_py(seed, dir, level, t, d, x, y, 0) % span - R, hash_py(seed, dir, level, t, d, x, y, 1) % span - R)
+
+
+def _upstream_flows(f, x, y, d):
+    h, w, _ = f.shape
+    out = []
+    for ox, oy in UPSTREAM[d]:
+        nx, ny = x + ox, y + oy
+        if 0 <= nx < w and 0 <= ny < h:
+            out.append((int(f[ny, nx, 0]), int(f[ny, nx, 1])))
+    return out
+
+
+def check_random_search_moves(o):
+    """Where every move of a half-sweep comes from (Sec. 3.1: propagation towards the four quadrants, then a random
+    search after each of the last three propagation steps of an iteration):
+      * d = 0 (the first propagation step): a pixel that changes takes the flow one of its two upstream
+        neighbours held when the half-sweep started -- never a random candidate;
+      * d >= 1: a changed flow is an upstream neighbour's flow, or a base (the pixel's own flow or a neighbour's)
+        plus this pixel's hashed offset for (level, t, d), which lies in [-R, R]^2 and is not (0, 0);
+      * a pixel whose random candidate was not taken could not have lowered its cost with it.
+    Random initial flows, so that every kind of move happens (the counts are checked)."""
+    h, w = 12, 14
+    ia = smooth_texture(401, h, w)
+    ib = shifted(ia, 2, -1, 402)
+    fa, fb = o.wht(ia), o.wht(ib)
+    rng = np.random.default_rng(403)
+    flow0 = np.zeros((h, w, 2), np.int16)
+    for y in range(h):
+        for x in range(w):
+            flow0[y, x] = (rng.integers(-x, w - x), rng.integers(-y, h - y))
+    cost0 = o.init_cost(fa, fb, flow0)
+    iters, R, seed, dir, level = 2, 2, 4242, 1, 2
+    states = [(flow0, cost0)]
+    for k in range(1, iters * 8 + 1):
+        states.append(o.propagate(fa, fb, flow0, cost0, iters, R, seed, dir, level, max_halfsweeps=k))
+    moves = {"neighbour_d0": 0, "neighbour": 0, "random": [0, 0, 0, 0]}
+    for k in range(1, len(states)):
+        (f0, c0), (f1, c1) = states[k - 1], states[k]
+        t, d, colour = (k - 1) // 8, ((k - 1) // 2) % 4, (k - 1) % 2
+        for y in range(h):
+            for x in range(w):
+                if (x + y) % 2 != colour:
+                    continue
+                old = (int(f0[y, x, 0]), int(f0[y, x, 1]))
+                new = (int(f1[y, x, 0]), int(f1[y, x, 1]))
+                nbs = _upstream_flows(f0, x, y, d)
+                off = hashed_offset(seed, dir, level, t, d, x, y, R)
+                assert -R <= off[0] <= R and -R <= off[1] <= R
+                bases = [old] + nbs
+                if new != old:
+                    if d == 0:
+                        assert new in nbs, ("d=0 move that is no neighbour's flow", k, x, y, old, new, nbs)
+                        moves["neighbour_d0"] += 1
+                    elif new in nbs:
+                        moves["neighbour"] += 1
+                    else:
+                        assert off != (0, 0), (k, x, y)
+                        assert (new[0] - off[0], new[1] - off[1]) in bases, \
+                            ("move that is neither a neighbour's flow nor a base plus the hashed offset", k, x, y,
+                             old, new, nbs, off)
+                        moves["random"][d] += 1
+                if d >= 1 and off != (0, 0) and new in bases and (new[0] - off[0], new[1] - off[1]) not in bases:
+                    # the random candidate was not taken: it must not have been strictly cheaper
+                    c = sad_numpy(fa, fb, x, y, new[0] + off[0], new[1] + off[1])
+                    assert c < 0 or c >= int(c1[y, x]), ("missed random improvement", k, x, y)
+    assert moves["neighbour_d0"] > 0 and moves["neighbour"] > 0, moves
+    assert all(moves["random"][d] > 0 for d in (1, 2, 3)), moves
+
+
+def check_random_search_finds_negative_offset(o):
+    """Only the random search can move a pixel whose upstream neighbours hold its own flow (they are skipped):
+    from an all-zero field, a target shifted by (-1, -2) -- inside the radius, negative in both components -- is
+    recovered exactly (cost 0) on every pixel whose patch lies inside both frames; with R = 0 (no random
+    candidate) nothing moves at all.  Offsets drawn from [0, 2R] instead of [-R, R] could never reach it."""
+    h, w = 24, 28
+    ia = smooth_texture(410, h, w)
+    ib = shifted(ia, -1, -2, 411)
+    fa, fb = o.wht(ia), o.wht(ib)
+    flow0 = np.zeros((h, w, 2), np.int16)
+    cost0 = o.init_cost(fa, fb, flow0)
+    assert cost0.min() > 0
+    f, c = o.propagate(fa, fb, flow0, cost0, 2, 2, 1234, 0, 0)
+    inner = np.zeros((h, w), bool)
+    inner[4 + 2:h - 4, 4 + 1:w - 4] = True  # patch margin (3 above/left, 4 below/right) plus the shift
+    assert np.all(f[inner] == (-1, -2)), "random search did not recover a negative shift"
+    assert np.all(c[inner] == 0)
+    f0, c0 = o.propagate(fa, fb, flow0, cost0, 2, 0, 1234, 0, 0)
+    assert np.array_equal(f0, flow0) and np.array_equal(c0, cost0), "something moved without a random candidate"
+
+
+def check_stream_keys(o):
+    """The level and the matching direction are part of the random-search key of the whole stage (reading of
+    Sec. 3.1: one counter-based stream per (direction, level, iteration)).
+      * Level: the same content placed at level 1 of a 2-level pyramid and at level 2 of a 3-level one, under
+        finer levels whose target frame is constant (every candidate ties there, so nothing moves and the
+        level-0 field is the coarse result doubled at each hand-over), must come out different.
+      * Direction: the inverse field of (A, B) matches B to A on the inverse stream, so it must differ from the
+        forward field of (B, A), which matches the same content on the forward stream."""
+    import oracle as _o
+
+    w1, h1 = 12, 10
+    xa = o.wht(smooth_texture(500, h1, w1))
+    xb = o.wht(smooth_texture(501, h1, w1))  # unrelated content: the random search keeps finding better targets
+    flat = lambda hh, ww: o.wht(np.full((hh, ww, 3), 90, np.uint8))
+
+    def prm(L):
+        return _o.params(n_scales=L, iters=2, rs_radius=2, eps=1, seed=31)
+
+    f2, _ = o.match_dir([o.wht(smooth_texture(502, 2 * h1, 2 * w1)), xa], [flat(2 * h1, 2 * w1), xb], prm(2), 0)
+    f3, _ = o.match_dir([o.wht(smooth_texture(503, 4 * h1, 4 * w1)), o.wht(smooth_texture(504, 2 * h1, 2 * w1)), xa],
+                        [flat(4 * h1, 4 * w1), flat(2 * h1, 2 * w1), xb], prm(3), 0)
+    r1 = f2[::2, ::2] // 2
+    r2 = f3[::4, ::4] // 4
+    # the finer levels were frozen: the outputs are the coarse results, doubled per level and repeated
+    assert np.array_equal(f2, 2 * np.repeat(np.repeat(r1, 2, 0), 2, 1))
+    assert np.array_equal(f3, 4 * np.repeat(np.repeat(r2, 4, 0), 4, 1))
+    assert not np.array_equal(r1, r2), "the same content drew the same offsets at levels 1 and 2"
+    a = smooth_texture(510, 30, 40)
+    b = smooth_texture(511, 30, 40)
+    p = _o.params(n_scales=2, iters=2, rs_radius=2, eps=1, seed=32)
+    inv_ab = o.match_bidir(a, b, p)[1]
+    fwd_ba = o.match_bidir(b, a, p)[0]
+    assert not np.array_equal(inv_ab, fwd_ba), "the inverse field drew the forward field's offsets"
+
+
 def check_translation(o):
     """Known integer translations are recovered exactly (cost 0) and pass the consistency check."""
     prm_cls = __import__("oracle").params
@@ -639,6 +777,9 @@ ALL_CHECKS = [
     check_seed,
     check_upsample,
     check_propagation_invariants,
+    check_random_search_moves,
+    check_random_search_finds_negative_offset,
+    check_stream_keys,
     check_propagation_schedule,
     check_translation,
     check_consistency,
