@@ -92,7 +92,9 @@ enum { FF_COST_WHT_SAD = 0, FF_COST_CENSUS = 1 };
 FF_API void ff_default_params(ff_params* p);
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a cudaStream_t; NULL
- * means the legacy default stream).  The parameters are copied.  *out receives the context. */
+ * means the legacy default stream).  The parameters are copied.  *out receives the context.  The first context
+ * on a device also reserves there the fixed scratch array of ff_match_pair_noalloc (FF_NOALLOC_SCRATCH_BYTES,
+ * held until the process exits) and loads the kernels that entry point launches; FF_ERR_OOM if that fails. */
 FF_API ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* cuda_stream);
 
 /* Build the feature pyramid of one frame (Sec. 3 and 3.1): L pyramid levels (2x2 box average, rounded half
@@ -266,14 +268,17 @@ FF_API ff_status ff_server_destroy(ff_server* srv);
 /* ff_match_pair without any memory allocation.  The paper has no counterpart: this serves callers that must
  * not allocate device memory while they run -- a real-time frame loop (cudaMalloc/cudaFree may synchronise the
  * device and stall other streams), code whose device memory belongs to another framework's fixed pool, or a
- * hot path that must not hit out-of-memory half way.  Same arguments, semantics and results as
- * ff_match_pair (the caller still passes the pyramids, built beforehand by ff_features, and the outputs); all
- * scratch lives in one file-scope device array of FF_NOALLOC_SCRATCH_BYTES that every device loading the
- * library keeps until the process exits.  Pyramids needing more scratch than that return FF_ERR_ARG.
- * The first call on a device looks up the array's device address (a one-time set-up per device), so make it
- * before any stream capture.  Every call reuses the same array, which keeps the last call's contents (the call
- * clears what must start at zero); calls whose work overlaps on the GPU -- on different streams or contexts of
- * the same device -- race on the array and must be serialised by the caller. */
+ * hot path that must not hit out-of-memory half way.  Same arguments and results as ff_match_pair (the caller
+ * still passes the pyramids, built beforehand by ff_features, and the outputs).  All scratch lives in one
+ * file-scope device array of FF_NOALLOC_SCRATCH_BYTES; pyramids needing more than that return FF_ERR_ARG.
+ * The array is reserved on a device, and its address looked up, when the first context is created there
+ * (ff_create loads this entry point's module and kernels, which lazy module loading would otherwise do on its
+ * first call); it stays reserved until the process exits.  So a call allocates nothing and loads no code.  A
+ * context, and these calls, must not outlive a reset of its device.  Every call reuses the same array, which
+ * keeps the last call's contents (the call clears what must start at zero); calls whose work overlaps on the
+ * GPU -- on different streams or contexts of the same device -- race on the array and must be serialised by
+ * the caller.  The initial matches always come from the mma.sync kernel (FF_OPT_SEED_KERNEL is not consulted;
+ * both kernels give identical results). */
 FF_API ff_status ff_match_pair_noalloc(ff_ctx* ctx, const ff_pyr* a, const ff_pyr* b, int dir, int16_t* flow_dev,
                                        int32_t* cost_dev);
 

@@ -163,6 +163,7 @@ struct ff_ctx {
     uint32_t wait_limit = 1u << 22;    // polls before a device-side wait gives up (~1 s)
     int withhold = 0;                  // test of the bounded waits: the tensor-core seed issues no copies
     int* d_err = nullptr;              // device error word of bounded waits
+    void* noalloc_scratch = nullptr;   // device address of ff_match_pair_noalloc's fixed scratch array
     std::string err;
     int64_t launches = 0, replays = 0, plans_built = 0, bytes = 0;
     bool profiling = false;
@@ -869,6 +870,7 @@ bool ctx_view(const ff_ctx* c, CtxView* out) {
     out->eps = c->prm.eps;
     out->seed = c->prm.seed;
     out->cost = c->prm.cost;
+    out->noalloc_scratch = c->noalloc_scratch;
     return true;
 }
 
@@ -973,12 +975,17 @@ ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* cuda_str
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->prm = *p;
-    if (cudaSetDevice(device) != cudaSuccess || init_kernel_attributes() != cudaSuccess ||
-        seed_tc_init_attributes() != cudaSuccess ||
-        cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    // with the device current: kernel attributes, and the set-up of ff_match_pair_noalloc (its scratch array and
+    // kernels are loaded here, so that its calls never load code or reserve memory)
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = init_kernel_attributes();
+    if (e == cudaSuccess) e = seed_tc_init_attributes();
+    if (e == cudaSuccess) e = noalloc_prepare(&c->noalloc_scratch);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         delete c;
-        return FF_ERR_CUDA;
+        return e == cudaErrorMemoryAllocation ? FF_ERR_OOM : FF_ERR_CUDA;
     }
     *out = c;
     return FF_OK;

@@ -148,7 +148,11 @@ struct PropLaunch {
 };
 constexpr size_t kMaxPropSmem = 200 * 1024;
 size_t prop_smem_bytes(int tw, int th, int n_iter);
-cudaError_t init_kernel_attributes();  // once per device, before the first launch
+cudaError_t init_kernel_attributes();  // once per device, before the first launch (also loads k_handover)
+cudaError_t seed_load_kernel();        // loads k_seed onto the current device (lazy module loading)
+// Set-up of ff_match_pair_noalloc on the current device, run by ff_create: loads its module (which reserves the
+// fixed scratch array) and the kernels it launches, and returns the array's device address.
+cudaError_t noalloc_prepare(void** scratch);
 bool prop_threads_ok(int threads);
 int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost);  // resident CTAs per SM of the kernel
 // queue_dev[i] = (problem index, tile index); counter_dev must be zero when the launch starts
@@ -181,6 +185,7 @@ struct CtxView {
     int n_scales, iters, rs_radius, eps;
     uint32_t seed;
     int cost;
+    void* noalloc_scratch;  // device address of ff_match_pair_noalloc's scratch array on this device
 };
 struct TileChoice {
     int tw, th, k, threads, spec;

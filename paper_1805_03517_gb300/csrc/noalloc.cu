@@ -10,7 +10,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "ff.h"
 #include "ff_internal.h"
@@ -21,33 +20,11 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[FF_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device ordinal
-
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // The descriptors a level is matched with (WHT features, or Census patterns under the Census cost).
 const void* cost_desc(const PyrView& v, int level, int cost) {
     return cost == FF_COST_CENSUS ? static_cast<const void*>(v.cen[level]) : static_cast<const void*>(v.feat[level]);
-}
-
-// Set-up, once per device, with that device current: the device address of the scratch array.  (In host code
-// the array's name is only a host-side stand-in; kernels must be given this address.)
-ff_status scratch_address(int device, void** out) {
-    if (device < 0 || device >= kMaxDevices) return FF_ERR_ARG;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return FF_ERR_CUDA;
-        }
-        g_scratch_ptr[device] = p;
-    }
-    *out = g_scratch_ptr[device];
-    return FF_OK;
 }
 
 // Everything the device-side set-up writes into the scratch array, passed by value.
@@ -100,6 +77,25 @@ __global__ void k_noalloc_setup(SetupArgs a) {
 
 }  // namespace
 
+namespace ff {
+
+// Set-up on the current device, run once per context by ff_create.  With lazy module loading (the default) this
+// file's module -- and with it the scratch array -- is loaded on a device only when something of it is first
+// used there, and each kernel's code on its first use; doing both here keeps ff_match_pair_noalloc from loading
+// code or reserving memory.  In host code the array's name is only a host-side stand-in: kernels are given the
+// device address cudaGetSymbolAddress returns.
+cudaError_t noalloc_prepare(void** scratch) {
+    *scratch = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(scratch, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_noalloc_setup);
+    if (e != cudaSuccess) return e;
+    return seed_load_kernel();  // k_handover and k_propagate are loaded by init_kernel_attributes
+}
+
+}  // namespace ff
+
 extern "C" ff_status ff_match_pair_noalloc(ff_ctx* c, const ff_pyr* a, const ff_pyr* b, int dir, int16_t* flow_dev,
                                            int32_t* cost_dev) {
     CtxView cv;
@@ -115,8 +111,8 @@ extern "C" ff_status ff_match_pair_noalloc(ff_ctx* c, const ff_pyr* a, const ff_
     if (!flow_dev || ((uintptr_t)flow_dev & 3) || ((uintptr_t)cost_dev & 3))
         return err(FF_ERR_ARG, "flow_dev / cost_dev must be 4-byte aligned device pointers");
     if (cudaSetDevice(cv.device) != cudaSuccess) return err(FF_ERR_CUDA, "cudaSetDevice failed");
-    void* base = nullptr;
-    if (scratch_address(cv.device, &base) != FF_OK) return err(FF_ERR_CUDA, "cudaGetSymbolAddress failed");
+    void* base = cv.noalloc_scratch;  // looked up by ff_create on this device
+    if (!base) return err(FF_ERR_CUDA, "the scratch array of ff_match_pair_noalloc was not set up");
 
     const int L = A.L, T = cv.iters;
     SetupArgs sa{};

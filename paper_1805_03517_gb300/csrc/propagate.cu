@@ -334,13 +334,16 @@ PropKernel prop_kernel(int threads, bool spec, int cost) {
 }
 
 cudaError_t init_kernel_attributes() {
+    cudaFuncAttributes fa;
+    cudaError_t e0 = cudaFuncGetAttributes(&fa, k_handover<CostSad>);
+    if (e0 == cudaSuccess) e0 = cudaFuncGetAttributes(&fa, k_handover<CostCensus>);
+    if (e0 != cudaSuccess) return e0;
     for (int cost : {FF_COST_WHT_SAD, FF_COST_CENSUS})
         for (int t : {128, 256, 512})
             for (bool sp : {false, true}) {
                 cudaError_t e = cudaFuncSetAttribute(prop_kernel(t, sp, cost),
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
                 if (e != cudaSuccess) return e;
-
             }
     return cudaSuccess;
 }

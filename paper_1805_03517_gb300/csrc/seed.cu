@@ -103,6 +103,11 @@ __global__ __launch_bounds__(32 * kSeedWarps) void k_seed(const SeedProblem* __r
     }
 }
 
+cudaError_t seed_load_kernel() {
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, k_seed);
+}
+
 void launch_seed(const SeedProblem* probs_dev, int n_probs, int total_row_tiles, cudaStream_t st) {
     launch_k(k_seed, dim3(total_row_tiles), dim3(32 * kSeedWarps), 0, st, probs_dev, n_probs, total_row_tiles);
 }

@@ -1,8 +1,12 @@
-"""ff_match_pair_noalloc, the entry point for callers that must not allocate device memory while they run.
+"""ff_match_pair_noalloc, the entry point for callers that must not allocate device memory while they run
+(a real-time frame loop that cudaMalloc/cudaFree would stall, memory owned by another framework's fixed pool,
+a hot path that must not run out of memory half way).
 
-It must give exactly what ff_match_pair gives (the matching is integer, so the tolerance is zero), on two
-calls in a row: the second call reuses the fixed scratch array the first one left behind.  This file is
-named so that pytest collects it last.
+It must give exactly what ff_match_pair gives (the matching is integer, so the tolerance is zero), on calls in
+a row that carve the shared scratch array differently (a smaller pair after a larger one), and at the
+1242x375 size of the KITTI-shaped workload against the oracle itself.  Across every call the device's free
+memory and the library's count of the bytes it holds must not change: the array and the kernels were set up
+when the context was created.  This file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -32,24 +36,59 @@ def _pair(seed, h, w, dx, dy):
     return a, b
 
 
-def test_noalloc_equals_match_pair_on_two_calls_in_a_row(ffm):
+def _noalloc_call(ffm, M, X, Y, dir, h, w):
+    """One call into fresh poisoned outputs; asserts that it allocated nothing on the device."""
+    with torch.cuda.stream(M.stream):  # poison the outputs on the stream the library uses
+        flow = torch.full((h, w, 2), -7, dtype=torch.int16, device="cuda")
+        cost = torch.full((h, w), -7, dtype=torch.int32, device="cuda")
+    M.sync()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    held0 = ffm.ff_get_stats(M.ctx)["scratch_bytes"]
+    ffm.ff_match_pair_noalloc(M.ctx, X.handle, Y.handle, dir, flow.data_ptr(), cost.data_ptr())
+    M.sync()
+    assert ffm.ff_get_stats(M.ctx)["scratch_bytes"] == held0, "the library allocated during the call"
+    assert torch.cuda.mem_get_info()[0] == free0, "device memory was allocated during the call"
+    return flow, cost
+
+
+def test_noalloc_equals_match_pair_on_calls_in_a_row(ffm):
     prm = configs.MatchParams(n_scales=4, iters=3, eps=1)
     M = ffm.Matcher(prm, 0)
-    pairs = [_pair(900, 150, 230, 7, -3), _pair(910, 150, 230, -5, 4)]  # same size: the second call reuses it all
+    # two pairs of one size (the second call reuses the first one's carving), then a smaller one (a new carving)
+    pairs = [_pair(900, 150, 230, 7, -3), _pair(910, 150, 230, -5, 4), _pair(920, 70, 96, 3, 2)]
     for call, (a, b) in enumerate(pairs):
+        h, w, _ = a.shape
         pa = M.features(torch.from_numpy(a).cuda())
         pb = M.features(torch.from_numpy(b).cuda())
         for dir, (X, Y) in enumerate(((pa, pb), (pb, pa))):
             ref_flow, ref_cost = M.match_pair(X, Y, dir)
-            with torch.cuda.stream(M.stream):  # poison the outputs on the stream the library uses
-                flow = torch.full((150, 230, 2), -7, dtype=torch.int16, device="cuda")
-                cost = torch.full((150, 230), -7, dtype=torch.int32, device="cuda")
-            ffm.ff_match_pair_noalloc(M.ctx, X.handle, Y.handle, dir, flow.data_ptr(), cost.data_ptr())
-            M.sync()
+            flow, cost = _noalloc_call(ffm, M, X, Y, dir, h, w)
             assert torch.equal(flow, ref_flow), (call, dir)
             assert torch.equal(cost, ref_cost), (call, dir)
         M.release(pa)
         M.release(pb)
+    M.close()
+
+
+def test_noalloc_kitti_size_against_the_oracle(ffm, orc):
+    """The 1242x375 pair of the KITTI-shaped workload (L=5, T=6), each direction against the oracle."""
+    import oracle
+    from paper_1805_03517_gb300 import synth
+
+    spec = configs.workload("kitti_1242x375").pairs[0]
+    a, b, _ = synth.make_pair(spec.kind, spec.seed, spec.w, spec.h)
+    p = spec.params
+    want = orc.match_bidir(a, b, oracle.params(p.n_scales, p.iters, p.rs_radius, p.eps, p.seed))
+    M = ffm.Matcher(p, 0)
+    pa = M.features(torch.from_numpy(a).cuda())
+    pb = M.features(torch.from_numpy(b).cuda())
+    for dir, (X, Y) in enumerate(((pa, pb), (pb, pa))):
+        flow, cost = _noalloc_call(ffm, M, X, Y, dir, spec.h, spec.w)
+        assert np.array_equal(flow.cpu().numpy(), want[dir]), dir
+        assert np.array_equal(cost.cpu().numpy(), want[2 + dir]), dir
+    M.release(pa)
+    M.release(pb)
     M.close()
 
 
@@ -74,11 +113,7 @@ def test_noalloc_census_cost_equals_match_pair(ffm):
     pb = M.features(torch.from_numpy(b).cuda())
     for dir, (X, Y) in enumerate(((pa, pb), (pb, pa))):
         ref_flow, ref_cost = M.match_pair(X, Y, dir)
-        with torch.cuda.stream(M.stream):
-            flow = torch.full((90, 140, 2), -7, dtype=torch.int16, device="cuda")
-            cost = torch.full((90, 140), -7, dtype=torch.int32, device="cuda")
-        ffm.ff_match_pair_noalloc(M.ctx, X.handle, Y.handle, dir, flow.data_ptr(), cost.data_ptr())
-        M.sync()
+        flow, cost = _noalloc_call(ffm, M, X, Y, dir, 90, 140)
         assert torch.equal(flow, ref_flow), dir
         assert torch.equal(cost, ref_cost), dir
     M.release(pa)
