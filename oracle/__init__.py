@@ -37,6 +37,7 @@ class Params(ctypes.Structure):
         ("eps", ctypes.c_int),
         ("seed", ctypes.c_uint32),
         ("cost", ctypes.c_int),
+        ("sub_scales", ctypes.c_int),
     ]
 
 
@@ -85,6 +86,13 @@ def _declare(lib):
     lib.ffo_init_cost.restype = None
     lib.ffo_upsample.argtypes = [i16p, i16p, c_int, c_int, i16p, c_int, c_int, i16p, i32p]
     lib.ffo_upsample.restype = c_int
+    lib.ffo_upsample_grid.argtypes = [i16p, i16p, c_int, c_int, c_int, i16p, c_int, c_int, i16p, i32p]
+    lib.ffo_upsample_grid.restype = c_int
+    lib.ffo_grid_handover.argtypes = [i16p, i16p, c_int, c_int, c_int, i16p, c_int, c_int, i16p, i32p]
+    lib.ffo_grid_handover.restype = None
+    lib.ffo_propagate_grid.argtypes = [i16p, i16p, c_int, c_int, c_int, i16p, i32p, c_int, c_int, c_u32, c_int, c_int,
+                                       c_long]
+    lib.ffo_propagate_grid.restype = c_long
     lib.ffo_propagate.argtypes = [i16p, i16p, c_int, c_int, i16p, i32p, c_int, c_int, c_u32, c_int, c_int, c_long]
     lib.ffo_propagate.restype = c_long
     pp = ctypes.POINTER(ctypes.c_void_p)
@@ -185,6 +193,43 @@ class Oracle:
         rc = self.L.ffo_upsample(_i16(fa), _i16(fb), w, h, _i16(flow_coarse), wc, hc, flow, cost)
         if rc != 0:
             raise RuntimeError(f"ffo_upsample failed: {rc}")
+        return flow, cost
+
+    @staticmethod
+    def grid_dims(w, h, g):
+        return (w + g - 1) // g, (h + g - 1) // g
+
+    def upsample_grid(self, fa, fb, g, flow_coarse):
+        """Hand-over from the level above onto the grid of every g-th pixel of this level."""
+        h, w, _ = fa.shape
+        gw, gh = self.grid_dims(w, h, g)
+        hc, wc, _ = flow_coarse.shape
+        flow = np.empty((gh, gw, 2), np.int16)
+        cost = np.empty((gh, gw), np.int32)
+        rc = self.L.ffo_upsample_grid(_i16(fa), _i16(fb), w, h, g, _i16(flow_coarse), wc, hc, flow, cost)
+        if rc != 0:
+            raise RuntimeError(f"ffo_upsample_grid failed: {rc}")
+        return flow, cost
+
+    def grid_handover(self, fa, fb, g, flow_parent):
+        """Hand-over from the grid of every 2g-th pixel to the grid of every g-th pixel of the same level."""
+        h, w, _ = fa.shape
+        gw, gh = self.grid_dims(w, h, g)
+        ph, pw, _ = flow_parent.shape
+        flow = np.empty((gh, gw, 2), np.int16)
+        cost = np.empty((gh, gw), np.int32)
+        self.L.ffo_grid_handover(_i16(fa), _i16(fb), w, h, g, _i16(flow_parent), pw, ph, flow, cost)
+        return flow, cost
+
+    def propagate_grid(self, fa, fb, g, flow, cost, iters, rs_radius, seed, dir, stream, max_halfsweeps=-1):
+        """Propagation with random search on the grid of every g-th pixel (stream = the hash's level id)."""
+        h, w, _ = fa.shape
+        flow = np.array(flow, dtype=np.int16, order="C", copy=True)
+        cost = np.array(cost, dtype=np.int32, order="C", copy=True)
+        n = self.L.ffo_propagate_grid(_i16(fa), _i16(fb), w, h, g, flow, cost, iters, rs_radius, seed & 0xFFFFFFFF,
+                                      dir, stream, max_halfsweeps)
+        if n < 0:
+            raise MemoryError("ffo_propagate_grid")
         return flow, cost
 
     def propagate(self, fa, fb, flow, cost, iters, rs_radius, seed, dir, level, max_halfsweeps=-1):
@@ -293,8 +338,8 @@ def _u64(a):
 COST_WHT_SAD, COST_CENSUS = 0, 1
 
 
-def params(n_scales, iters, rs_radius=2, eps=1, seed=0, cost=COST_WHT_SAD) -> Params:
-    return Params(n_scales, iters, rs_radius, eps, seed & 0xFFFFFFFF, cost)
+def params(n_scales, iters, rs_radius=2, eps=1, seed=0, cost=COST_WHT_SAD, sub_scales=0) -> Params:
+    return Params(n_scales, iters, rs_radius, eps, seed & 0xFFFFFFFF, cost, sub_scales)
 
 
 _default = None

@@ -175,18 +175,25 @@ int32_t ffo_hamming(const uint64_t* ca, const uint64_t* cb, int w, int h, int x,
 }
 
 /* The descriptors a level is matched with: WHT coefficients (cost = SAD) or, if ca is set, Census patterns
- * (cost = Hamming distance). */
+ * (cost = Hamming distance), and the grid of source pixels a flow field lives on: every g-th pixel of the level
+ * in both directions (g = 1: every pixel; g = 2, 4: a sub-scale or sub-sub-scale, see match_dir_c).  Grid pixel
+ * (x, y) is level pixel (g*x, g*y); flows are in level pixels and may point to any pixel of the target level. */
 typedef struct {
     const int16_t* fa;
     const int16_t* fb;
     const uint64_t* ca;
     const uint64_t* cb;
-    int w, h;
+    int w, h; /* the level */
+    int g;    /* grid stride */
 } costsrc;
 
+static int grid_w(const costsrc* cs) { return (cs->w + cs->g - 1) / cs->g; }
+static int grid_h(const costsrc* cs) { return (cs->h + cs->g - 1) / cs->g; }
+
+/* Cost of grid pixel (x, y) with flow (fx, fy); -1 when the target lies outside the level. */
 static int32_t cost_of(const costsrc* cs, int x, int y, int fx, int fy) {
-    return cs->ca ? ffo_hamming(cs->ca, cs->cb, cs->w, cs->h, x, y, fx, fy)
-                  : ffo_sad(cs->fa, cs->fb, cs->w, cs->h, x, y, fx, fy);
+    return cs->ca ? ffo_hamming(cs->ca, cs->cb, cs->w, cs->h, cs->g * x, cs->g * y, fx, fy)
+                  : ffo_sad(cs->fa, cs->fb, cs->w, cs->h, cs->g * x, cs->g * y, fx, fy);
 }
 
 /* floor(c / 128), the arithmetic shift C >> 7 written without relying on signed shifts. */
@@ -220,31 +227,33 @@ void ffo_seed(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* flow,
 
 /* cost(p) = matching cost of p's current flow; every flow handed in must point inside the level. */
 static void init_cost_c(const costsrc* cs, const int16_t* flow, int32_t* cost) {
-    for (int y = 0; y < cs->h; y++)
-        for (int x = 0; x < cs->w; x++) {
-            long p = (long)y * cs->w + x;
+    for (int y = 0; y < grid_h(cs); y++)
+        for (int x = 0; x < grid_w(cs); x++) {
+            long p = (long)y * grid_w(cs) + x;
             cost[p] = cost_of(cs, x, y, flow[2 * p], flow[2 * p + 1]);
         }
 }
 
 void ffo_init_cost(const int16_t* fa, const int16_t* fb, int w, int h, const int16_t* flow, int32_t* cost) {
-    costsrc cs = {fa, fb, NULL, NULL, w, h};
+    costsrc cs = {fa, fb, NULL, NULL, w, h, 1};
     init_cost_c(&cs, flow, cost);
 }
 
 /* Coarse-to-fine hand-over (Sec. 3): a pixel starts from twice the flow of its parent pixel one level up,
- * parent = (min(x/2, wc-1), min(y/2, hc-1)), and its cost is recomputed at the finer level.  Such a flow
- * always lands inside the finer level; returns -2 if one does not (a broken assertion). */
+ * parent = (min(x/2, wc-1), min(y/2, hc-1)), and its cost is recomputed at the finer level.  (x, y) are level
+ * coordinates: on a grid of stride g, grid pixel (u, v) is level pixel (g*u, g*v).  Such a flow always lands
+ * inside the finer level; returns -2 if one does not (a broken assertion). */
 static int upsample_c(const costsrc* cs, const int16_t* flow_coarse, int wc, int hc, int16_t* flow, int32_t* cost) {
-    const int w = cs->w, h = cs->h;
-    for (int y = 0; y < h; y++)
-        for (int x = 0; x < w; x++) {
+    const int gw = grid_w(cs), gh = grid_h(cs);
+    for (int v = 0; v < gh; v++)
+        for (int u = 0; u < gw; u++) {
+            int x = cs->g * u, y = cs->g * v;
             int px = mini(x / 2, wc - 1), py = mini(y / 2, hc - 1);
-            long pc = (long)py * wc + px, p = (long)y * w + x;
+            long pc = (long)py * wc + px, p = (long)v * gw + u;
             int fx = 2 * flow_coarse[2 * pc], fy = 2 * flow_coarse[2 * pc + 1];
             flow[2 * p] = (int16_t)fx;
             flow[2 * p + 1] = (int16_t)fy;
-            cost[p] = cost_of(cs, x, y, fx, fy);
+            cost[p] = cost_of(cs, u, v, fx, fy);
             if (cost[p] < 0) return -2;
         }
     return 0;
@@ -252,8 +261,40 @@ static int upsample_c(const costsrc* cs, const int16_t* flow_coarse, int wc, int
 
 int ffo_upsample(const int16_t* fa, const int16_t* fb, int w, int h, const int16_t* flow_coarse, int wc, int hc,
                  int16_t* flow, int32_t* cost) {
-    costsrc cs = {fa, fb, NULL, NULL, w, h};
+    costsrc cs = {fa, fb, NULL, NULL, w, h, 1};
     return upsample_c(&cs, flow_coarse, wc, hc, flow, cost);
+}
+
+int ffo_upsample_grid(const int16_t* fa, const int16_t* fb, int w, int h, int g, const int16_t* flow_coarse, int wc,
+                      int hc, int16_t* flow, int32_t* cost) {
+    costsrc cs = {fa, fb, NULL, NULL, w, h, g};
+    return upsample_c(&cs, flow_coarse, wc, hc, flow, cost);
+}
+
+/* Hand-over between two grids of one level (reading of the sub-scales of Sec. 3.1, see match_dir_c): grid pixel
+ * (u, v) of stride g starts from the flow of grid pixel (min(u/2, pw-1), min(v/2, ph-1)) of the grid of stride 2g
+ * (pw x ph), unchanged (both are in level pixels), except that its target is clamped into the level: the child
+ * pixel lies up to g pixels right of / below its parent, so the parent's flow may point past the edge.  The cost
+ * is recomputed. */
+static void grid_handover_c(const costsrc* cs, const int16_t* flow_parent, int pw, int ph, int16_t* flow,
+                            int32_t* cost) {
+    const int gw = grid_w(cs), gh = grid_h(cs);
+    for (int v = 0; v < gh; v++)
+        for (int u = 0; u < gw; u++) {
+            long pp = (long)mini(v / 2, ph - 1) * pw + mini(u / 2, pw - 1), p = (long)v * gw + u;
+            int x = cs->g * u, y = cs->g * v;
+            int fx = clampi(x + flow_parent[2 * pp], 0, cs->w - 1) - x;
+            int fy = clampi(y + flow_parent[2 * pp + 1], 0, cs->h - 1) - y;
+            flow[2 * p] = (int16_t)fx;
+            flow[2 * p + 1] = (int16_t)fy;
+            cost[p] = cost_of(cs, u, v, fx, fy);
+        }
+}
+
+void ffo_grid_handover(const int16_t* fa, const int16_t* fb, int w, int h, int g, const int16_t* flow_parent, int pw,
+                       int ph, int16_t* flow, int32_t* cost) {
+    costsrc cs = {fa, fb, NULL, NULL, w, h, g};
+    grid_handover_c(&cs, flow_parent, pw, ph, flow, cost);
 }
 
 /* The two neighbours a pixel looks at in propagation direction d (one direction per quadrant, Sec. 3.1).
@@ -266,7 +307,10 @@ static void neighbours(int d, int x, int y, int* n1x, int* n1y, int* n2x, int* n
     *n2y = (d == 0 || d == 1) ? y - 1 : y + 1;
 }
 
-/* Propagation with random search at one level (Sec. 3.1).  For t = 0..iters-1, for each direction d = 0..3,
+/* Propagation with random search at one level (Sec. 3.1), on the grid of cs (every pixel, or every g-th pixel
+ * of a sub-scale; x, y below are grid coordinates, neighbours are grid neighbours, flows and offsets are in level
+ * pixels, and the hash is keyed with the level coordinates (g*x, g*y) and the stream id `level`).  For
+ * t = 0..iters-1, for each direction d = 0..3,
  * two half-sweeps (pixels with (x+y) even, then odd); within a half-sweep every pixel of that colour is
  * updated from the state at the start of the half-sweep, so their order does not matter.
  * A pixel tries, in order: the flow of neighbour 1, the flow of neighbour 2 (neighbours outside the level
@@ -276,7 +320,7 @@ static void neighbours(int d, int x, int y, int* n1x, int* n1y, int* n2x, int* n
  * Stops after max_halfsweeps half-sweeps if max_halfsweeps >= 0; returns the number run. */
 static long propagate_c(const costsrc* cs, int16_t* flow, int32_t* cost, int iters, int rs_radius, uint32_t seed,
                         int dir, int level, long max_halfsweeps) {
-    const int w = cs->w, h = cs->h;
+    const int w = grid_w(cs), h = grid_h(cs);
     long n = (long)w * h, done = 0;
     int16_t* prev = (int16_t*)malloc(sizeof(int16_t) * 2 * (size_t)n);
     if (!prev) return -1;
@@ -309,8 +353,9 @@ static long propagate_c(const costsrc* cs, int16_t* flow, int32_t* cost, int ite
                             }
                         }
                         if (d >= 1) {
-                            int ox = (int)(ffo_hash(seed, dir, level, t, d, x, y, 0) % (uint32_t)span) - rs_radius;
-                            int oy = (int)(ffo_hash(seed, dir, level, t, d, x, y, 1) % (uint32_t)span) - rs_radius;
+                            int lx = cs->g * x, ly = cs->g * y;
+                            int ox = (int)(ffo_hash(seed, dir, level, t, d, lx, ly, 0) % (uint32_t)span) - rs_radius;
+                            int oy = (int)(ffo_hash(seed, dir, level, t, d, lx, ly, 1) % (uint32_t)span) - rs_radius;
                             if (ox != 0 || oy != 0) {
                                 int32_t cc = cost_of(cs, x, y, fx + ox, fy + oy);
                                 if (cc >= 0 && cc < c) {
@@ -335,57 +380,80 @@ static long propagate_c(const costsrc* cs, int16_t* flow, int32_t* cost, int ite
 
 long ffo_propagate(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* flow, int32_t* cost, int iters,
                    int rs_radius, uint32_t seed, int dir, int level, long max_halfsweeps) {
-    costsrc cs = {fa, fb, NULL, NULL, w, h};
+    costsrc cs = {fa, fb, NULL, NULL, w, h, 1};
     return propagate_c(&cs, flow, cost, iters, rs_radius, seed, dir, level, max_halfsweeps);
+}
+
+long ffo_propagate_grid(const int16_t* fa, const int16_t* fb, int w, int h, int g, int16_t* flow, int32_t* cost,
+                        int iters, int rs_radius, uint32_t seed, int dir, int stream, long max_halfsweeps) {
+    costsrc cs = {fa, fb, NULL, NULL, w, h, g};
+    return propagate_c(&cs, flow, cost, iters, rs_radius, seed, dir, stream, max_halfsweeps);
 }
 
 long ffo_propagate_census(const uint64_t* ca, const uint64_t* cb, int w, int h, int16_t* flow, int32_t* cost,
                           int iters, int rs_radius, uint32_t seed, int dir, int level, long max_halfsweeps) {
-    costsrc cs = {NULL, NULL, ca, cb, w, h};
+    costsrc cs = {NULL, NULL, ca, cb, w, h, 1};
     return propagate_c(&cs, flow, cost, iters, rs_radius, seed, dir, level, max_halfsweeps);
 }
 
 /* One matching direction over a prepared pyramid of features (Sec. 3.1): exact seed at the coarsest level,
  * then for every level from coarse to fine: hand-over from the level above (except the coarsest), cost,
  * propagation with random search.  Writes the level-0 flow and cost.  feat_a/feat_b[s] are the level-s
- * feature maps of the source and target frames; both frames have the sizes ws[s] x hs[s]. */
+ * feature maps of the source and target frames; both frames have the sizes ws[s] x hs[s].
+ *
+ * Sub-scales and sub-sub-scales (Sec. 3.1 uses them "as in" Flow Fields+, which is not restated; reading):
+ * with prm->sub_scales = n (0, 1 or 2), every level below the coarsest is first matched on the grid of every
+ * 2^n-th pixel, then of every 2^(n-1)-th, ..., then on every pixel -- the same descriptors, so a sparse grid
+ * reaches across 2^k level pixels per propagation step with the fine level's detail.  The first grid of a level
+ * takes the hand-over from the level above; each later grid takes its parent grid pixel's flow (clamped into the
+ * level, grid_handover_c).  Every grid runs the level's whole propagation schedule on its own random stream,
+ * stream id s + 8k for the grid of stride 2^k (k = 0: the level itself, as without sub-scales).  The coarsest
+ * level starts from exact matches and has no sub-scales. */
 static int match_dir_c(const int16_t* const* feat_a, const int16_t* const* feat_b, const uint64_t* const* cen_a,
                        const uint64_t* const* cen_b, const int* ws, const int* hs, const ffo_params* prm, int dir,
                        int16_t* flow, int32_t* cost) {
-    int L = prm->n_scales;
-    int16_t* f_prev = NULL;
-    int w_prev = 0, h_prev = 0;
+    int L = prm->n_scales, n_sub = prm->sub_scales;
+    if (n_sub < 0 || n_sub > 2) return -1;
+    int16_t* f_prev = NULL; /* the last field: of the level above, or of a sparser grid of this level */
+    int w_prev = 0, h_prev = 0; /* its grid size */
     for (int s = L - 1; s >= 0; s--) {
-        int w = ws[s], h = hs[s];
-        long n = (long)w * h;
-        int16_t* f = (int16_t*)malloc(sizeof(int16_t) * 2 * (size_t)n);
-        int32_t* c = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-        if (!f || !c) {
-            free(f);
-            free(c);
+        const int k_first = s == L - 1 ? 0 : n_sub;
+        for (int k = k_first; k >= 0; k--) {
+            costsrc cs = {feat_a[s], feat_b[s], cen_a ? cen_a[s] : NULL, cen_b ? cen_b[s] : NULL, ws[s], hs[s], 1 << k};
+            int gw = grid_w(&cs), gh = grid_h(&cs);
+            long n = (long)gw * gh;
+            int16_t* f = (int16_t*)malloc(sizeof(int16_t) * 2 * (size_t)n);
+            int32_t* c = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+            if (!f || !c) {
+                free(f);
+                free(c);
+                free(f_prev);
+                return -1;
+            }
+            if (s == L - 1) {
+                ffo_seed(feat_a[s], feat_b[s], gw, gh, f, c);  /* initial matches on the WHT descriptors in both modes */
+                init_cost_c(&cs, f, c);
+            } else if (k == k_first) {
+                if (upsample_c(&cs, f_prev, w_prev, h_prev, f, c) != 0) {
+                    free(f);
+                    free(c);
+                    free(f_prev);
+                    return -2;
+                }
+            } else {
+                grid_handover_c(&cs, f_prev, w_prev, h_prev, f, c);
+            }
+            propagate_c(&cs, f, c, prm->iters, prm->rs_radius, prm->seed, dir, s + 8 * k, -1);
             free(f_prev);
-            return -1;
-        }
-        costsrc cs = {feat_a[s], feat_b[s], cen_a ? cen_a[s] : NULL, cen_b ? cen_b[s] : NULL, w, h};
-        if (s == L - 1) {
-            ffo_seed(feat_a[s], feat_b[s], w, h, f, c);  /* initial matches on the WHT descriptors in both modes */
-            init_cost_c(&cs, f, c);
-        } else if (upsample_c(&cs, f_prev, w_prev, h_prev, f, c) != 0) {
-            free(f);
+            f_prev = f;
+            w_prev = gw;
+            h_prev = gh;
+            if (s == 0 && k == 0) {
+                memcpy(flow, f, sizeof(int16_t) * 2 * (size_t)n);
+                memcpy(cost, c, sizeof(int32_t) * (size_t)n);
+            }
             free(c);
-            free(f_prev);
-            return -2;
         }
-        propagate_c(&cs, f, c, prm->iters, prm->rs_radius, prm->seed, dir, s, -1);
-        free(f_prev);
-        f_prev = f;
-        w_prev = w;
-        h_prev = h;
-        if (s == 0) {
-            memcpy(flow, f, sizeof(int16_t) * 2 * (size_t)n);
-            memcpy(cost, c, sizeof(int32_t) * (size_t)n);
-        }
-        free(c);
     }
     free(f_prev);
     return 0;

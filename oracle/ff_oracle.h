@@ -35,6 +35,7 @@ typedef struct {
     int eps;       /* consistency threshold in pixels */
     uint32_t seed; /* random-search hash seed */
     int cost;      /* 0: SAD of the WHT descriptors, 1: Hamming distance of the Census patterns */
+    int sub_scales; /* 0: none; 1: sub-scales; 2: sub-scales and sub-sub-scales (grids of every 2nd / 4th pixel) */
 } ffo_params;
 
 /* 0 on success; negative on an argument error or a broken internal assertion. */
@@ -57,6 +58,12 @@ int ffo_upsample(const int16_t* fa, const int16_t* fb, int w, int h, const int16
                  int16_t* flow, int32_t* cost);
 long ffo_propagate(const int16_t* fa, const int16_t* fb, int w, int h, int16_t* flow, int32_t* cost, int iters,
                    int rs_radius, uint32_t seed, int dir, int level, long max_halfsweeps);
+int ffo_upsample_grid(const int16_t* fa, const int16_t* fb, int w, int h, int g, const int16_t* flow_coarse, int wc,
+                      int hc, int16_t* flow, int32_t* cost);
+void ffo_grid_handover(const int16_t* fa, const int16_t* fb, int w, int h, int g, const int16_t* flow_parent, int pw,
+                       int ph, int16_t* flow, int32_t* cost);
+long ffo_propagate_grid(const int16_t* fa, const int16_t* fb, int w, int h, int g, int16_t* flow, int32_t* cost,
+                        int iters, int rs_radius, uint32_t seed, int dir, int stream, long max_halfsweeps);
 int ffo_match_dir(const int16_t* const* feat_a, const int16_t* const* feat_b, const int* ws, const int* hs,
                   const ffo_params* prm, int dir, int16_t* flow, int32_t* cost);
 void ffo_consistency(const int16_t* fwd, const int16_t* bwd, int w, int h, int eps, uint8_t* mask);

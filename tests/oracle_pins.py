@@ -21,6 +21,11 @@ What pins what (FlowFields++, arXiv 1805.03517, Sec. 3.1, under the readings in 
                       search can reach is recovered exactly, and nothing moves with R = 0; the same content at
                       two levels, or as forward vs inverse field, draws different offsets (level and direction
                       are in the key of the whole stage);
+  * sub-scales     -- (reading: grids of every 2nd / 4th pixel of a level, matched before the level itself)
+                      hand-overs against their definitions (twice the parent flow onto a grid; the parent grid
+                      pixel's flow clamped into the level), grid propagation moves and costs at the strided level
+                      pixels with the hash keyed by level coordinates and the grid's stream, exact recovery of
+                      translations through sub-scales and sub-sub-scales;
   * cross-checks   -- a pure-Python restatement of the schedule on tiny inputs and the stage recomposed from its
                       steps (checks against the oracle's own loop, not pins: every planted mistake must also be
                       caught by a pin above, tests/test_oracle_mutants.py);
@@ -527,6 +532,121 @@ def check_stream_keys(o):
     assert not np.array_equal(inv_ab, fwd_ba), "the inverse field drew the forward field's offsets"
 
 
+def check_sub_scale_handovers(o):
+    """Hand-overs of the sub-scale reading (Sec. 3.1 defers sub-scales to Flow Fields+): onto the grid of every
+    g-th pixel of a level from the level above, twice the flow of the parent of level pixel (g*u, g*v), always
+    inside the level; and from the grid of stride 2g to the grid of stride g of the same level, the parent grid
+    pixel's flow unchanged but with its target clamped into the level; the cost is the SAD at (g*u, g*v)."""
+    rng = np.random.default_rng(61)
+    for (h, w) in ((17, 23), (16, 20), (9, 5)):
+        fa = o.wht(rand_img(62, h, w))
+        fb = o.wht(rand_img(63, h, w))
+        hc, wc = max(1, h // 2), max(1, w // 2)
+        fc = np.zeros((hc, wc, 2), np.int16)
+        for y in range(hc):
+            for x in range(wc):
+                fc[y, x] = (rng.integers(-x, wc - x), rng.integers(-y, hc - y))
+        for g in (2, 4):
+            gw, gh = -(-w // g), -(-h // g)
+            flow, cost = o.upsample_grid(fa, fb, g, fc)
+            assert flow.shape == (gh, gw, 2)
+            for v in range(gh):
+                for u in range(gw):
+                    x, y = g * u, g * v
+                    want = 2 * fc[min(y // 2, hc - 1), min(x // 2, wc - 1)]
+                    assert flow[v, u].tolist() == want.tolist(), (g, u, v)
+                    assert 0 <= x + want[0] < w and 0 <= y + want[1] < h
+                    assert cost[v, u] == sad_numpy(fa, fb, x, y, *want.tolist())
+            # the next finer grid of the same level: parent pixel's flow, target clamped into the level
+            pw, ph = gw, gh
+            fp = np.zeros((ph, pw, 2), np.int16)
+            for v in range(ph):
+                for u in range(pw):
+                    x, y = g * u, g * v
+                    fp[v, u] = (rng.integers(-x, w - x), rng.integers(-y, h - y))
+            g2 = g // 2
+            cw, ch = -(-w // g2), -(-h // g2)
+            flow, cost = o.grid_handover(fa, fb, g2, fp)
+            assert flow.shape == (ch, cw, 2)
+            clamped = 0
+            for v in range(ch):
+                for u in range(cw):
+                    x, y = g2 * u, g2 * v
+                    f = fp[min(v // 2, ph - 1), min(u // 2, pw - 1)].astype(int)
+                    tx, ty = min(max(x + f[0], 0), w - 1), min(max(y + f[1], 0), h - 1)
+                    clamped += (tx, ty) != (x + f[0], y + f[1])
+                    assert flow[v, u].tolist() == [tx - x, ty - y], (g2, u, v)
+                    assert cost[v, u] == sad_numpy(fa, fb, x, y, tx - x, ty - y)
+            assert clamped > 0  # the case the clamp exists for did occur
+
+
+def check_sub_scale_propagation(o):
+    """Propagation on the grid of every second or fourth pixel of a level: the cost of grid pixel (u, v) is the
+    SAD at level pixel (g*u, g*v), never rises and only the active colour (u + v parity) moves; at d = 0 a changed
+    pixel takes a grid neighbour's snapshot flow; at d >= 1 a changed flow is a grid neighbour's flow or a base
+    plus the offset hashed with the level coordinates (g*u, g*v) and the grid's stream id, in [-R, R]^2."""
+    h, w = 26, 30
+    ia = smooth_texture(420, h, w)
+    ib = shifted(ia, 3, -2, 421)
+    fa, fb = o.wht(ia), o.wht(ib)
+    rng = np.random.default_rng(422)
+    for g in (2, 4):
+        gw, gh = -(-w // g), -(-h // g)
+        flow0 = np.zeros((gh, gw, 2), np.int16)
+        for v in range(gh):
+            for u in range(gw):
+                flow0[v, u] = (rng.integers(-g * u, w - g * u), rng.integers(-g * v, h - g * v))
+        cost0 = np.array([[sad_numpy(fa, fb, g * u, g * v, *flow0[v, u].tolist()) for u in range(gw)]
+                          for v in range(gh)], np.int64)
+        iters, R, seed, dir, stream = 2, 2, 99, 1, 3 + 8 * (g.bit_length() - 1)
+        states = [(flow0, cost0)]
+        for k in range(1, iters * 8 + 1):
+            states.append(o.propagate_grid(fa, fb, g, flow0, cost0, iters, R, seed, dir, stream, max_halfsweeps=k))
+        rnd = 0
+        for k in range(1, len(states)):
+            (f0, c0), (f1, c1) = states[k - 1], states[k]
+            t, d, colour = (k - 1) // 8, ((k - 1) // 2) % 4, (k - 1) % 2
+            assert np.all(c1 <= c0), (g, k)
+            for v in range(gh):
+                for u in range(gw):
+                    new = (int(f1[v, u, 0]), int(f1[v, u, 1]))
+                    assert c1[v, u] == sad_numpy(fa, fb, g * u, g * v, *new), (g, k, u, v)
+                    old = (int(f0[v, u, 0]), int(f0[v, u, 1]))
+                    if new == old:
+                        continue
+                    assert (u + v) % 2 == colour, (g, k, u, v)
+                    nbs = _upstream_flows(f0, u, v, d)
+                    if d == 0:
+                        assert new in nbs, (g, k, u, v)
+                    elif new not in nbs:
+                        off = hashed_offset(seed, dir, stream, t, d, g * u, g * v, R)
+                        assert off != (0, 0) and (new[0] - off[0], new[1] - off[1]) in [old] + nbs, (g, k, u, v)
+                        rnd += 1
+        assert rnd > 0, g
+
+
+def check_sub_scale_translation(o):
+    """With sub-scales (and sub-sub-scales), known integer translations are still recovered exactly (cost 0,
+    consistent), and the sub-scales change the schedule (the fields differ from those without them)."""
+    import oracle as _o
+
+    for (h, w, L, dx, dy, n_sub) in ((64, 72, 3, 8, -4, 1), (48, 56, 2, -6, 4, 2), (64, 72, 3, -5, 7, 2)):
+        ia = smooth_texture(700 + L + n_sub, h, w)
+        ib = shifted(ia, dx, dy, 710 + L)
+        prm = _o.params(n_scales=L, iters=3, rs_radius=2, eps=0, seed=9, sub_scales=n_sub)
+        ff, fb, cf, cb, mask = o.match_bidir(ia, ib, prm)
+        m = 4 + 2 ** (L - 1)
+        ys, xs = np.mgrid[0:h, 0:w]
+        inner = (xs >= m + max(0, -dx)) & (xs < w - m - max(0, dx)) & (ys >= m + max(0, -dy)) & (ys < h - m - max(0, dy))
+        assert np.all(ff[inner] == (dx, dy)), (L, n_sub, dx, dy)
+        assert np.all(cf[inner] == 0) and np.all(mask[inner] == 1)
+    ia = smooth_texture(730, 40, 52)
+    ib = smooth_texture(731, 40, 52)
+    plain = o.match_bidir(ia, ib, _o.params(n_scales=2, iters=2, seed=4))
+    sub = o.match_bidir(ia, ib, _o.params(n_scales=2, iters=2, seed=4, sub_scales=1))
+    assert not np.array_equal(plain[0], sub[0])
+
+
 def check_translation(o):
     """Known integer translations are recovered exactly (cost 0) and pass the consistency check."""
     prm_cls = __import__("oracle").params
@@ -780,6 +900,9 @@ ALL_CHECKS = [
     check_random_search_moves,
     check_random_search_finds_negative_offset,
     check_stream_keys,
+    check_sub_scale_handovers,
+    check_sub_scale_propagation,
+    check_sub_scale_translation,
     check_propagation_schedule,
     check_translation,
     check_consistency,

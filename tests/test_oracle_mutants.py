@@ -37,11 +37,21 @@ MUTANTS = {
     "random_offset_not_centred": ("% (uint32_t)span) - rs_radius;\n                            int oy",
                                   "% (uint32_t)span);\n                            int oy"),
     "random_cost_wrong_component": ("x, y, fx + ox, fy + oy);", "x, y, fx + ox, fy + ox);"),
-    "random_iteration_not_in_hash": ("ffo_hash(seed, dir, level, t, d, x, y, 0)", "ffo_hash(seed, dir, level, 0, d, x, y, 0)"),
-    "random_direction_not_in_hash": ("ffo_hash(seed, dir, level, t, d, x, y, 1)", "ffo_hash(seed, 0, level, t, d, x, y, 1)"),
+    "random_iteration_not_in_hash": ("ffo_hash(seed, dir, level, t, d, lx, ly, 0)", "ffo_hash(seed, dir, level, 0, d, lx, ly, 0)"),
+    "random_direction_not_in_hash": ("ffo_hash(seed, dir, level, t, d, lx, ly, 1)", "ffo_hash(seed, 0, level, t, d, lx, ly, 1)"),
     "random_base_before_neighbours": ("int32_t cc = cost_of(cs, x, y, fx + ox, fy + oy);",
                                       "int32_t cc = cost_of(cs, x, y, flow[2 * p] + ox, flow[2 * p + 1] + oy);"),
-    "level_not_in_hash": ("prm->rs_radius, prm->seed, dir, s, -1)", "prm->rs_radius, prm->seed, dir, 0, -1)"),
+    "grid_source_not_strided": ("ffo_sad(cs->fa, cs->fb, cs->w, cs->h, cs->g * x, cs->g * y, fx, fy)",
+                                "ffo_sad(cs->fa, cs->fb, cs->w, cs->h, x, y, fx, fy)"),
+    "grid_hash_in_grid_coordinates": ("int lx = cs->g * x, ly = cs->g * y;", "int lx = x, ly = y;"),
+    "grid_handover_not_clamped": ("int fx = clampi(x + flow_parent[2 * pp], 0, cs->w - 1) - x;",
+                                  "int fx = flow_parent[2 * pp];"),
+    "grid_handover_wrong_parent": ("long pp = (long)mini(v / 2, ph - 1) * pw + mini(u / 2, pw - 1)",
+                                   "long pp = (long)mini(v, ph - 1) * pw + mini(u, pw - 1)"),
+    "upsample_grid_parent_in_grid_coordinates": ("int x = cs->g * u, y = cs->g * v;\n            int px",
+                                                 "int x = u, y = v;\n            int px"),
+    "sub_scales_skipped": ("const int k_first = s == L - 1 ? 0 : n_sub;", "const int k_first = 0;"),
+    "level_not_in_hash": ("prm->rs_radius, prm->seed, dir, s + 8 * k, -1)", "prm->rs_radius, prm->seed, dir, 8 * k, -1)"),
     "inverse_same_direction_key": ("ws, hs, prm, 1,", "ws, hs, prm, 0,"),
     "consistency_strict": ("<= (long)eps * eps", "< (long)eps * eps"),
     "consistency_sign": ("long ex = fx + bwd[2 * q]", "long ex = fx - bwd[2 * q]"),
@@ -67,7 +77,8 @@ MUTANTS = {
 CROSS_CHECKS = {"check_propagation_schedule", "check_pipeline_composition"}
 PINS = [c for c in P.ALL_CHECKS if c.__name__ not in CROSS_CHECKS]
 
-# Mistakes in the random search and in its key, with the pin (derived from the definition) that must catch each.
+# Mistakes in the random search, its key and the sub-scale grids, with the pin (derived from the definition)
+# that must catch each.
 EXPECTED_PIN = {
     "random_search_on_all_steps": "check_random_search_moves",
     "random_offset_not_centred": "check_random_search_finds_negative_offset",
@@ -75,6 +86,12 @@ EXPECTED_PIN = {
     "random_iteration_not_in_hash": "check_random_search_moves",
     "random_direction_not_in_hash": "check_random_search_moves",
     "inverse_same_direction_key": "check_stream_keys",
+    "grid_source_not_strided": "check_sub_scale_propagation",
+    "grid_hash_in_grid_coordinates": "check_sub_scale_propagation",
+    "grid_handover_not_clamped": "check_sub_scale_handovers",
+    "grid_handover_wrong_parent": "check_sub_scale_handovers",
+    "upsample_grid_parent_in_grid_coordinates": "check_sub_scale_handovers",
+    "sub_scales_skipped": "check_sub_scale_translation",
 }
 
 
