@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-pair batched measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served-stream measurement")
     ap.add_argument("--no-census", action="store_true", help="skip the Census-cost measurement")
+    ap.add_argument("--no-sub-scales", action="store_true", help="skip the measurement with sub-scale grids")
     ap.add_argument("--settle-s", type=float, default=2.0,
                     help="seconds of untimed steps before the warm-up steps, so the clocks have settled")
     ap.add_argument("--no-filtered", action="store_true",
@@ -54,6 +55,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="run the autotuner instead of the package's table of tuned configurations")
     ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--features", default="frame", choices=["frame", "batch"],
+                    help="features of the step's frames: one ff_features call per frame, or ff_features_batch")
     ap.add_argument("--tuning", default=None,
                     help="JSON list of per-level [tile_w, tile_h, iters_per_launch, threads, speculate] instead of "
                          "autotuning (for reproducible profiler captures)")
@@ -68,6 +71,26 @@ def aggregate_ranks(torch, dist, dev, ms_local, px_per_step, world):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms = float(t.item())
     return ms, px_per_step * world / (ms / 1000.0) / 1e6
+
+
+def propagate_l1_record(tuning):
+    """The committed ncu capture of a level-0 k_propagate launch of the 1242x375 pair (L1 LSU data-pipe wavefronts,
+    their peak per cycle, DRAM bytes), if the kernel source and the launch configuration are the ones it was
+    captured with."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "propagate_l1_kitti_1242x375.json")
+    src = os.path.join(ROOT, "paper_1805_03517_gb300", "csrc", "propagate.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    with open(src, "rb") as f:
+        if rec.get("propagate_cu_sha256") != hashlib.sha256(f.read()).hexdigest():
+            return None
+    if [list(c) for c in rec.get("tiles_per_level", [])] != [list(c) for c in tuning]:
+        return None
+    return rec
 
 
 def propagate_traffic(tuning):
@@ -88,6 +111,23 @@ def propagate_traffic(tuning):
     if [list(c) for c in rec.get("tiles_per_level", [])] != [list(c) for c in tuning]:
         return None
     return rec["dram_bytes_per_launch"]
+
+
+def batch_traffic():
+    """DRAM bytes per algorithmic byte of k_propagate in a batch whose features exceed L2, from the committed ncu
+    capture of an 8-pair KITTI batch, if the kernel source is the one it was captured with."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "propagate_traffic_batch8_kitti_1242x375.json")
+    src = os.path.join(ROOT, "paper_1805_03517_gb300", "csrc", "propagate.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    with open(src, "rb") as f:
+        if rec.get("propagate_cu_sha256") != hashlib.sha256(f.read()).hexdigest():
+            return None
+    return rec
 
 
 def load_peaks():
@@ -191,13 +231,15 @@ def measure_batched(torch, ff, configs, stream, local_rank, steps):
         M.release(pb)
     outs = None
 
-    def step():
+    frames = [x for pr in d for x in pr]
+
+    def step():  # features of all 96 frames in one launch per kernel, then the merged matching launches
         nonlocal outs
-        pyrs = [(M.features(a), M.features(b)) for a, b in d]
+        fp = M.features_batch(frames)
+        pyrs = list(zip(fp[0::2], fp[1::2]))
         outs = M.match_batch(pyrs, outs=outs, with_cost=False)
-        for pa, pb in pyrs:
-            M.release(pa)
-            M.release(pb)
+        for p in fp:
+            M.release(p)
 
     for _ in range(3):
         step()
@@ -212,11 +254,41 @@ def measure_batched(torch, ff, configs, stream, local_rank, steps):
     stream.synchronize()
     ms = e0.elapsed_time(e1) / steps
     launches = M.stats()["kernel_launches"] - s0["kernel_launches"]
+    # propagation roofline of the batched step: here the features (5 GB) exceed L2, so HBM is the bound; device
+    # time per launch from a profiling context with the same launch configurations
+    P = ff.Matcher(wl.pairs[0].params, local_rank, stream)
+    for lvl, cfg in enumerate(tuning):
+        ff.ff_set_tuning(P.ctx, lvl, cfg)
+    ff.ff_profile_enable(P.ctx, True)
+    n_prof = 3
+    for r in range(n_prof + 1):
+        if r == 1:
+            ff.ff_profile_read(P.ctx)
+        fp = P.features_batch(frames)
+        P.match_batch(list(zip(fp[0::2], fp[1::2])), with_cost=False)
+        for p in fp:
+            P.release(p)
+    prop_ms, prop_launches = ff.ff_profile_read(P.ctx)["propagate"]
+    pix_iters = sum(ff.ff_work_counts(P.ctx, p.w, p.h)[0] for p in wl.pairs)
+    P.close()
     M.close()
+    peak, peak_kind = load_peaks()
+    bytes_per_launch = pix_iters * 2 * ALG_BYTES_PER_PIXEL_ITER / (prop_launches / n_prof)
+    achieved = bytes_per_launch / (prop_ms / prop_launches / 1000.0) / 1e9
+    traffic = batch_traffic()
+    roof = {"bound": "hbm", "kernel": "k_propagate", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+            "unit": "GB/s", "frac": achieved / peak, "alg_bytes_per_launch": bytes_per_launch,
+            "avg_launch_ms": prop_ms / prop_launches, "launches_per_step": prop_launches / n_prof,
+            "traffic": None, "traffic_note": None}
+    if traffic:
+        # DRAM bytes per algorithmic byte of the captured level-0 launches of an 8-pair KITTI batch, scaled to this
+        # batch's average launch
+        roof["traffic"] = traffic["dram_per_alg_byte"] * bytes_per_launch
+        roof["traffic_note"] = traffic["note"]
     return {"workload": wl.name, "pairs_per_step": len(wl.pairs), "px_per_step": wl.pixels,
             "value": wl.pixels / (ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "gpu_launches_per_step": launches / steps, "tiles_per_level": [list(c) for c in tuning],
-            "l2": "not flushed: 5 GB of features per step exceed L2"}
+            "l2": "not flushed: 5 GB of features per step exceed L2", "roofline": roof}
 
 
 def measure_census(torch, ff, configs, stream, local_rank, steps, flush):
@@ -372,39 +444,104 @@ def measure_filtered(torch, ff, configs, stream, local_rank, steps, flush, tunin
                            "note": "device time per launch from a CUDA graph of 100 launches; inputs L2-resident"}}
 
 
+def measure_sub_scales(torch, ff, configs, stream, local_rank, steps, flush, tuning):
+    """The KITTI-shaped pair matched with sub-scales and sub-sub-scales (every level below the coarsest first on
+    the grids of every 4th and every 2nd pixel, then on every pixel; the reading of Sec. 3.1 the library takes),
+    levels in the package table's configurations, grid passes autotuned; L2 flushed per step.  Mpx/s counts level-0 pixels, as for the
+    plain schedule, so the two are comparable per frame pair."""
+    import dataclasses
+
+    wl = configs.workload("kitti_1242x375")
+    spec = wl.pairs[0]
+    imgs = make_inputs(wl)
+    dev = torch.device("cuda", local_rank)
+    with torch.cuda.stream(stream):
+        d = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in imgs]
+    stream.synchronize()
+    out = {"workload": wl.name, "px_per_step": wl.pixels, "steps": steps, "l2": "flushed before every timed step"}
+    for n_sub in (1, 2):
+        M = ff.Matcher(dataclasses.replace(spec.params, sub_scales=n_sub), local_rank, stream)
+        for lvl, cfg in enumerate(tuning):
+            ff.ff_set_tuning(M.ctx, lvl, cfg)
+        pyrs = [(M.features(a), M.features(b)) for a, b in d]
+        M.autotune(pyrs, reps=2)  # configurations of the grid passes (the levels keep the table's)
+        for pa, pb in pyrs:
+            M.release(pa)
+            M.release(pb)
+        outs = None
+
+        def step():
+            nonlocal outs
+            pyrs = [(M.features(a), M.features(b)) for a, b in d]
+            outs = M.match_batch(pyrs, outs=outs, with_cost=False)
+            for pa, pb in pyrs:
+                M.release(pa)
+                M.release(pb)
+
+        for _ in range(3):
+            step()
+        ev = []
+        for _ in range(steps):
+            flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            ev.append((e0, e1))
+        stream.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        pix_iters = ff.ff_work_counts(M.ctx, spec.w, spec.h)[0]
+        M.close()
+        out[f"sub_scales_{n_sub}"] = {"value": wl.pixels / (ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                                      "pixel_iters_per_direction": pix_iters}
+    return out
+
+
+def _make_pair_task(spec):
+    from paper_1805_03517_gb300 import synth
+
+    kind, seed, w, h = spec
+    a, b, _ = synth.make_pair(kind, seed, w, h)
+    return a, b
+
+
 def measure_served(torch, ff, configs, stream, local_rank, n_req):
-    """Served stream: Poisson arrivals (200 pairs/s) of frame pairs of four sizes, continuous batching under a
-    60 GB device budget; latency from arrival to completion.  Also the same requests all arriving at once."""
-    from paper_1805_03517_gb300 import serve, synth
+    """Served stream: Poisson arrivals (200 pairs/s) of n_req distinct frame pairs, each generated from its own seed
+    with a size drawn uniformly from four sizes, continuous batching under a 60 GB device budget; latency from
+    arrival to completion.  Also the same requests all arriving at once."""
+    import multiprocessing as mp
+
+    from paper_1805_03517_gb300 import serve
 
     dev = torch.device("cuda", local_rank)
     prm = configs.KITTI
     M = ff.Matcher(prm, local_rank, stream)
-    pool = {}
-    with torch.cuda.stream(stream):
-        for (w, h, kind) in configs.SERVE_SIZES:
-            pool[(w, h)] = []
-            for k in range(8):
-                a, b, _ = synth.make_pair(kind, 5000 + 100 * len(pool) + k, w, h)
-                pool[(w, h)].append((torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)))
+    specs = [configs.serve_pair(i) for i in range(n_req)]
+    t_gen = time.perf_counter()
+    frames = []
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        for a, b in pool.imap(_make_pair_task, [(p.kind, p.seed, p.w, p.h) for p in specs], chunksize=4):
+            with torch.cuda.stream(stream):
+                frames.append((torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)))
     stream.synchronize()
-    for (w, h), prs in pool.items():  # per-size launch configurations, as a deployment would tune once:
-        pyrs = [(M.features(a), M.features(b)) for a, b in prs]
+    gen_s = time.perf_counter() - t_gen
+    for (w, h, _) in configs.SERVE_SIZES:  # per-size launch configurations, as a deployment would tune once:
+        same = [f for f, p in zip(frames, specs) if (p.w, p.h) == (w, h)][:8]
+        pyrs = [(M.features(a), M.features(b)) for a, b in same]
         M.autotune(pyrs[:1], reps=2)  # for one pair in flight (light load)
         M.autotune(pyrs, reps=2)      # for launches shared by many pairs (under load)
         for pa, pb in pyrs:
             M.release(pa)
             M.release(pb)
-    frames = []
-    for i, (w, h, _) in enumerate(configs.serve_sizes(n_req)):
-        frames.append(pool[(w, h)][i % 8])
     arrivals = serve.poisson_arrivals(n_req, 200.0, seed=5)
     serve.serve(M, frames[:512], [0.0] * 512)  # warm-up: pyramid and scratch pools at full occupancy, caches
     offered = serve.serve(M, frames, arrivals, mem_budget_bytes=60 << 30)
     saturated = serve.serve(M, frames, [0.0] * n_req, mem_budget_bytes=60 << 30)
     M.close()
     out = {"requests": n_req, "arrival_rate_per_s": 200.0, "sizes": [f"{w}x{h}" for w, h, _ in configs.SERVE_SIZES],
-           "mem_budget_gb": 60, "inputs": "32 distinct synthetic pairs (8 per size) cycled over the stream",
+           "mem_budget_gb": 60,
+           "inputs": f"{n_req} distinct synthetic pairs, pair i from seed 5000 + i (generated in {gen_s:.0f} s on "
+                     "the host, resident on the device before the stream starts)",
            "offered_load": offered.as_dict(), "saturated": saturated.as_dict()}
     return out
 
@@ -511,9 +648,15 @@ def main():
     px_per_step = workload.pixels
     outs = None
 
+    def features(m, imgs):
+        if args.features == "batch":
+            fp = m.features_batch([x for pr in imgs for x in pr])
+            return list(zip(fp[0::2], fp[1::2]))
+        return [(m.features(a), m.features(b)) for a, b in imgs]
+
     def step():
         nonlocal outs
-        pyrs = [(M.features(a), M.features(b)) for a, b in dev_imgs]
+        pyrs = features(M, dev_imgs)
         outs = M.match_batch(pyrs, outs=outs, with_cost=False)
         for pa, pb in pyrs:
             M.release(pa)
@@ -619,7 +762,7 @@ def main():
     def e2e_step():
         with torch.cuda.stream(stream):
             d_in.copy_(h_in, non_blocking=True)
-        pyrs = [(M.features(a), M.features(b)) for a, b in e2e_imgs]
+        pyrs = features(M, e2e_imgs)
         M.match_batch(pyrs, outs=e2e_outs, with_cost=False)
         for pa, pb in pyrs:
             M.release(pa)
@@ -645,7 +788,7 @@ def main():
 
     def prof_step():
         nonlocal prof_outs
-        pyrs = [(P.features(a), P.features(b)) for a, b in dev_imgs]
+        pyrs = features(P, dev_imgs)
         prof_outs = P.match_batch(pyrs, outs=prof_outs, with_cost=False)
         for pa, pb in pyrs:
             P.release(pa)
@@ -659,6 +802,10 @@ def main():
         flush_l2()
         prof_step()
     phases = ff.ff_profile_read(P.ctx)
+    for _ in range(n_prof):
+        flush_l2()
+        prof_step()
+    passes = ff.ff_profile_read_passes(P.ctx)
     P.close()
     pix_iters = sum(ff.ff_work_counts(M.ctx, p.w, p.h)[0] for p in workload.pairs)
     prop_ms, prop_launches = phases["propagate"]
@@ -668,6 +815,37 @@ def main():
     bytes_per_launch = alg_bytes_per_step / launches_per_step
     achieved = bytes_per_launch / (avg_launch_ms / 1000.0) / 1e9
     peak, peak_kind = load_peaks()
+    # level 0, the dominant launches: algorithmic bytes and live device time per launch
+    l0_ms, l0_launches = passes.get(0, (0.0, 0))
+    l0_px_iters = sum(p.w * p.h for p in workload.pairs) * prm.iters * 2
+    l0_launch_ms = l0_ms / l0_launches if l0_launches else None
+    l0_alg = l0_px_iters * (ALG_BYTES_PER_PIXEL_ITER_CENSUS if cost_id else ALG_BYTES_PER_PIXEL_ITER) / (
+        l0_launches / n_prof) if l0_launches else None
+    hbm_roof = {"bound": "hbm", "kernel": "k_propagate", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": achieved / peak,
+                "traffic": propagate_traffic(tuning) if cost_id == 0 else None,
+                "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
+                "launches_per_step": launches_per_step}
+    rec = propagate_l1_record(tuning) if cost_id == 0 and workload.name == "kitti_1242x375" else None
+    if rec and l0_launch_ms and clocks.get("sm_mhz"):
+        # what binds (ncu): the L1 LSU data-pipe wavefront rate of the scattered 32-byte descriptor gathers; peak =
+        # ncu's sustained wavefronts per cycle (whole GPU) x the SM clock sampled during the timed steps
+        wf_peak = rec["wavefronts_peak_per_cycle"] * clocks["sm_mhz"] * 1e6
+        wf_achieved = rec["wavefronts_per_launch"] / (l0_launch_ms / 1000.0)
+        roofline = {"bound": "l1", "kernel": "k_propagate (level-0 launches, 57 % of a step)",
+                    "unit": "wavefronts/s", "achieved": wf_achieved, "peak": wf_peak,
+                    "peak_kind": "ncu peak_sustained of l1tex__data_pipe_lsu_wavefronts x sampled SM clock",
+                    "frac": wf_achieved / wf_peak, "traffic": rec["dram_bytes_per_launch"],
+                    "traffic_unit": "DRAM bytes per level-0 launch (ncu)", "avg_launch_ms": l0_launch_ms,
+                    "alg_bytes_per_launch": l0_alg,
+                    "ncu": {k: rec[k] for k in ("l1_wavefront_pct", "l1_hit_pct", "l2_hit_pct", "capture")},
+                    "hbm": {"achieved": l0_alg / (l0_launch_ms / 1000.0) / 1e9, "peak": peak, "peak_kind": peak_kind,
+                            "unit": "GB/s", "frac": l0_alg / (l0_launch_ms / 1000.0) / 1e9 / peak,
+                            "dram_gbs": rec["dram_bytes_per_launch"] / (l0_launch_ms / 1000.0) / 1e9,
+                            "dram_frac": rec["dram_bytes_per_launch"] / (l0_launch_ms / 1000.0) / 1e9 / peak},
+                    "all_levels": hbm_roof}
+    else:
+        roofline = hbm_roof
 
     if rank == 0:
         line = {
@@ -681,15 +859,15 @@ def main():
                        "tiles_per_level": {str(l): list(c) for l, c in enumerate(tuning)},
                        "tiles_from": tuning_source,
                        "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write, outside the events)",
+                       "features": "ff_features_batch (one launch per kernel for all frames)" if args.features == "batch"
+                                   else "ff_features per frame",
                        "settle_s": args.settle_s},
             "gpu_launches": launches,
             "clocks": clocks,
             "e2e": {"value": px_per_step * world / (e2e_ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": {"bound": "hbm", "kernel": "k_propagate", "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": propagate_traffic(tuning) if cost_id == 0 else None,
-                         "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
-                         "launches_per_step": launches_per_step},
+            "roofline": roofline,
+            "propagate_ms_per_pass": {str(k): v[0] / n_prof for k, v in sorted(passes.items())},
             "phases_ms_per_step": {k: v[0] / n_prof for k, v in phases.items()},
             "accuracy_context": flow_accuracy(outs[0]["flow_fwd"].cpu().numpy(), outs[0]["mask"].cpu().numpy(),
                                               imgs_gt[0][2]),
@@ -704,6 +882,14 @@ def main():
             filtered = {"error": repr(e)}
         if rank == 0:
             line["filtered"] = filtered
+    if not args.no_sub_scales and workload.name == "kitti_1242x375" and cost_id == 0:
+        try:  # an auxiliary measurement: report its failure in the line instead of losing the line
+            sub = measure_sub_scales(torch, ff, configs, stream, local_rank, max(10, min(100, args.steps // 3)),
+                                     flush_l2, tuning)
+        except Exception as e:  # noqa: BLE001
+            sub = {"error": repr(e)}
+        if rank == 0:
+            line["sub_scales"] = sub
     if not args.no_census:
         census = measure_census(torch, ff, configs, stream, local_rank, max(10, min(100, args.steps // 3)), flush_l2)
         if rank == 0:

@@ -77,6 +77,16 @@ typedef struct {
     int cost;        /* matching cost of propagation and random search: FF_COST_WHT_SAD (default) or
                         FF_COST_CENSUS (see below); the coarsest-level initial matches use the WHT descriptors
                         either way */
+    int sub_scales;  /* 0 (default), 1 or 2.  Sec. 3.1 matches on "sub-scales and sub-sub-scales" as in Flow
+                        Fields+, which it does not restate; this library's reading: every level below the
+                        coarsest is first matched on the grid of every 2^n-th pixel of the level (n = sub_scales),
+                        then of every 2^(n-1)-th, ..., then on every pixel.  A grid pixel (u, v) is level pixel
+                        (g*u, g*v) with the level's own descriptors; flows are in level pixels and may point to
+                        any level pixel; each grid runs the level's whole propagation schedule (neighbours one grid
+                        step apart) on its own random stream.  The first grid takes the usual hand-over from the
+                        level above; each later grid takes its parent grid pixel's flow with the target clamped
+                        into the level.  Supported by ff_match_pair, ff_match_batch, ff_autotune and the server;
+                        ff_match_pair_noalloc rejects it (FF_ERR_ARG). */
 } ff_params;
 
 /* Matching costs (Sec. 3.1 matches with a Census cost or SIFT descriptors; Sec. 4.1 takes Census for Sintel).
@@ -88,7 +98,7 @@ typedef struct {
 enum { FF_COST_WHT_SAD = 0, FF_COST_CENSUS = 1 };
 
 /* Default parameters: L=5, iters=6, patch=8, n_coef=16, rs_radius=2, eps=1, seed=0x20180503, rs_radius2=4,
- * cost=FF_COST_WHT_SAD. */
+ * cost=FF_COST_WHT_SAD, sub_scales=0. */
 FF_API void ff_default_params(ff_params* p);
 
 /* Create a context on CUDA device `device` that enqueues all work on `cuda_stream` (a cudaStream_t; NULL
@@ -105,6 +115,21 @@ FF_API ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* c
  * *out receives a pyramid owned by the context; it stays valid until ff_pyr_release or ff_destroy.
  * Released pyramids of the same size are recycled, so steady-state calls allocate nothing. */
 FF_API ff_status ff_features(ff_ctx* ctx, const uint8_t* rgb_dev, int w, int h, int pitch_bytes, ff_pyr** out);
+
+/* One frame of ff_features_batch: device image uint8 [h][w][3], rows pitch_bytes apart. */
+typedef struct {
+    const uint8_t* rgb_dev;
+    int w, h, pitch_bytes;
+} ff_frame;
+
+/* ff_features for n frames of any sizes in one launch per kernel (Sec. 3 and 3.1, as ff_features): the pyramid
+ * levels 1..6 of every frame in one launch and the Walsh-Hadamard descriptors, Census patterns and seed rows of
+ * every level of every frame in another (frames with 8 levels add one launch per frame for the last level).
+ * out[i] (n entries) receives frame i's pyramid, identical to ff_features on that frame alone.  The launches read
+ * a table of the frames that the call copies to a context-owned device buffer on the context's stream (grown,
+ * after waiting for the stream, when a larger batch needs it).  On an error no pyramid is taken and out[] is
+ * all NULL. */
+FF_API ff_status ff_features_batch(ff_ctx* ctx, int n, const ff_frame* frames, ff_pyr** out);
 
 /* Match one direction (Sec. 3.1): dir 0 matches frame a to frame b, dir 1 computes the inverse field (the
  * caller passes the pyramids swapped; dir only selects the random-search stream).  Exact nearest-neighbour
@@ -219,9 +244,15 @@ enum { FF_PHASE_FEATURES = 0, FF_PHASE_SEED = 1, FF_PHASE_HANDOVER = 2, FF_PHASE
        FF_PHASE_CONSISTENCY = 4, FF_N_PHASES = 5 };
 FF_API ff_status ff_profile_enable(ff_ctx* ctx, int on);
 FF_API ff_status ff_profile_read(ff_ctx* ctx, double* ms /* [FF_N_PHASES] */, int64_t* launches /* [FF_N_PHASES] */);
+/* The propagation phase split by pass (the same events, read and cleared the same way; use instead of
+ * ff_profile_read): entry s is level s, entry s + 8k its sub-scale grid of stride 2^k (k = 1, 2).  ms and launches
+ * have FF_N_PASSES entries. */
+#define FF_N_PASSES 24
+FF_API ff_status ff_profile_read_passes(ff_ctx* ctx, double* ms /* [FF_N_PASSES] */, int64_t* launches /* [FF_N_PASSES] */);
 
 /* Algorithmic work of a plan for pyramids of size w x h with the context's parameters: per direction, the
- * number of (pixel, iteration) updates summed over all levels, and the number of level-0 pixels. */
+ * number of (pixel, iteration) updates summed over all levels and sub-scale grids, and the number of level-0
+ * pixels. */
 FF_API ff_status ff_work_counts(ff_ctx* ctx, int w, int h, int64_t* pixel_iters, int64_t* pixels);
 
 /* ---- continuous-batching server ------------------------------------------------------------------------
@@ -256,6 +287,10 @@ FF_API ff_status ff_server_submit(ff_server* srv, uint64_t id, const ff_request*
 FF_API ff_status ff_server_step(ff_server* srv, int* n_active, int* n_queued);
 /* Ids (up to max_ids) of requests whose outputs are complete; with wait != 0 blocks until at least one is. */
 FF_API ff_status ff_server_poll(ff_server* srv, int wait, uint64_t* ids, int max_ids, int* n_done);
+/* Withdraw a request that is still queued (not yet admitted): FF_OK, and its id is never reported by
+ * ff_server_poll; nothing of it was on the device, so its buffers are the caller's again at once.  FF_ERR_BUSY if
+ * the request has been admitted (it completes normally and is reported by poll); FF_ERR_ARG for an unknown id. */
+FF_API ff_status ff_server_cancel(ff_server* srv, uint64_t id);
 /* Ticks enqueued, kernel launches enqueued, and device bytes of the admitted requests. */
 FF_API ff_status ff_server_stats(ff_server* srv, int64_t* ticks, int64_t* launches, int64_t* bytes_in_use);
 /* Wait for the stream, release every resource of the server (not the context). */
@@ -290,8 +325,13 @@ FF_API ff_status ff_match_pair_noalloc(ff_ctx* ctx, const ff_pyr* a, const ff_py
  *                                up; the kernel then records the failure, cleans up and returns, and the next
  *                                ff_sync reports FF_ERR_TIMEOUT with the context still usable.
  *   FF_OPT_TEST_WITHHOLD_COPIES  1: the tensor-core seed issues no copies, so its waits can only expire (a test of
- *                                the bounded waits); 0 (default) normal operation. */
-enum { FF_OPT_SEED_KERNEL = 1, FF_OPT_WAIT_LIMIT = 2, FF_OPT_TEST_WITHHOLD_COPIES = 3 };
+ *                                the bounded waits); 0 (default) normal operation.
+ *   FF_OPT_TEST_FAIL_ALLOCS      n >= 0: the next n device allocations made for this context (pyramids, plans, the
+ *                                server's scratch and tables) fail as on an exhausted device, without calling the
+ *                                allocator, so the calls that need them return FF_ERR_OOM and launch nothing (a test
+ *                                of the out-of-memory paths); 0 (default) normal operation.  Unlike the other
+ *                                options it keeps the cached plans. */
+enum { FF_OPT_SEED_KERNEL = 1, FF_OPT_WAIT_LIMIT = 2, FF_OPT_TEST_WITHHOLD_COPIES = 3, FF_OPT_TEST_FAIL_ALLOCS = 4 };
 enum { FF_SEED_MMA_SYNC = 0, FF_SEED_TCGEN05 = 1 };
 FF_API ff_status ff_set_option(ff_ctx* ctx, int option, int64_t value);
 

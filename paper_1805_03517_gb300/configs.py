@@ -28,6 +28,7 @@ class MatchParams:
     seed: int = HASH_SEED
     rs_radius2: int = 4  # random-search radius of the second inverse field (two-check mode)
     cost: int = 0        # 0: SAD of the WHT descriptors, 1: Hamming distance of 7x7 Census patterns
+    sub_scales: int = 0  # 0: none, 1: sub-scales, 2: sub-scales and sub-sub-scales (grids of every 2nd/4th pixel)
 
 
 @dataclass(frozen=True)
@@ -86,6 +87,10 @@ WORKLOADS = {
                                 "Sintel-shaped 1024x436 pair, L=5, T=6, eps=7"),
     "batch48_mixed": Workload("batch48_mixed", _batch48(),
                               "48 pairs: 16x 1242x375, 16x 1024x436, 16x 640x480, L=5, T=6, eps=1"),
+    # the first eight pairs of the batch: a batch whose features (0.95 GB) exceed L2 but that a profiler can
+    # replay in a few GB of device memory
+    "batch8_kitti_1242x375": Workload("batch8_kitti_1242x375", _batch48()[:8],
+                                      "8 KITTI-shaped 1242x375 pairs of the batch, L=5, T=6, eps=1"),
 }
 
 

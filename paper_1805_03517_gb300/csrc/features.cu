@@ -38,10 +38,9 @@ void launch_downsample(const uint8_t* src, int sw, int sh, int spitch, uint8_t* 
 // levels from it in shared memory: level sizes are floor(w/2), so both sources 2x, 2x+1 of a level-s pixel lie
 // in the parent block (the clamp only matters when the parent level is 1 pixel wide or high, and its single
 // pixel is in block 0).  A 32x32 level-1 block halves down to one pixel at level 6, hence a.top <= 6.
-__global__ __launch_bounds__(256) void k_pyramid(PyrArgs a) {
-    grid_dependency_sync();
-    __shared__ uint8_t buf[2][kPyrBlock][kPyrBlock][3];
-    int size = kPyrBlock, ox = blockIdx.x * kPyrBlock, oy = blockIdx.y * kPyrBlock;
+__device__ __forceinline__ void pyramid_block(const PyrArgs& a, int bx, int by,
+                                              uint8_t (&buf)[2][kPyrBlock][kPyrBlock][3]) {
+    int size = kPyrBlock, ox = bx * kPyrBlock, oy = by * kPyrBlock;
     for (int i = threadIdx.x; i < size * size; i += blockDim.x) {
         const int lx = i % size, ly = i / size, x = ox + lx, y = oy + ly;
         if (x >= a.w[1] || y >= a.h[1]) continue;
@@ -82,9 +81,37 @@ __global__ __launch_bounds__(256) void k_pyramid(PyrArgs a) {
     }
 }
 
+__global__ __launch_bounds__(256) void k_pyramid(PyrArgs a) {
+    grid_dependency_sync();
+    __shared__ uint8_t buf[2][kPyrBlock][kPyrBlock][3];
+    pyramid_block(a, blockIdx.x, blockIdx.y, buf);
+}
+
+// The pyramids of many frames in one launch: CTA b works on frame f (the last with cta_base <= b), block
+// b - cta_base of its level-1 block grid (bx blocks per row).
+__global__ __launch_bounds__(256) void k_pyramid_tab(const PyrArgs* __restrict__ tab, int n) {
+    grid_dependency_sync();
+    __shared__ uint8_t buf[2][kPyrBlock][kPyrBlock][3];
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].cta_base <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const PyrArgs& a = tab[lo];
+    const int b = (int)blockIdx.x - a.cta_base;
+    pyramid_block(a, b % a.bx, b / a.bx, buf);
+}
+
+int pyramid_blocks_x(int w1) { return (w1 + kPyrBlock - 1) / kPyrBlock; }
+int pyramid_blocks(int w1, int h1) { return pyramid_blocks_x(w1) * ((h1 + kPyrBlock - 1) / kPyrBlock); }
+
 void launch_pyramid(const PyrArgs& a, cudaStream_t st) {
     dim3 grid((a.w[1] + kPyrBlock - 1) / kPyrBlock, (a.h[1] + kPyrBlock - 1) / kPyrBlock);
     launch_k(k_pyramid, grid, dim3(256), 0, st, a);
+}
+
+void launch_pyramid_tab(const PyrArgs* tab_dev, int n, int total_ctas, cudaStream_t st) {
+    launch_k(k_pyramid_tab, dim3(total_ctas), dim3(256), 0, st, tab_dev, n);
 }
 
 // Walsh-Hadamard descriptor (Sec. 3.1): for every pixel and channel, the 4x4 lowest-sequency coefficients of
@@ -177,14 +204,9 @@ __device__ __forceinline__ void seed_rows(const uint32_t (&out)[24], int p, cons
     L.seed_norm[p] = norm;
 }
 
-__global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
-    grid_dependency_sync();
-    __shared__ __align__(16) uint8_t win[3][kWinY][kWinX];
-    __shared__ short4 rowt[3][kWinY][kWtx];  // row pass: 4 horizontal Walsh sums per window row and output column
-    int b = blockIdx.x, li = 0;
-    while (li + 1 < args.n && b >= args.lv[li + 1].tile_base) li++;
-    const WhtLevel L = args.lv[li];
-    int t = b - L.tile_base;
+// One 32x16 tile t of one level (shared memory: the clamped input window and the row pass).
+__device__ __forceinline__ void wht_tile(const WhtLevel& L, int t, uint8_t (&win)[3][kWinY][kWinX],
+                                         short4 (&rowt)[3][kWinY][kWtx]) {
     int tx0 = (t % L.tiles_x) * kWtx, ty0 = (t / L.tiles_x) * kWty;
     for (int i = threadIdx.x; i < kWinX * kWinY; i += blockDim.x) {
         int r = i / kWinX, c = i - r * kWinX;
@@ -265,11 +287,39 @@ __global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
     }
 }
 
+__global__ __launch_bounds__(256) void k_wht(WhtArgs args) {
+    grid_dependency_sync();
+    __shared__ __align__(16) uint8_t win[3][kWinY][kWinX];
+    __shared__ short4 rowt[3][kWinY][kWtx];  // row pass: 4 horizontal Walsh sums per window row and output column
+    int b = blockIdx.x, li = 0;
+    while (li + 1 < args.n && b >= args.lv[li + 1].tile_base) li++;
+    const WhtLevel L = args.lv[li];
+    wht_tile(L, b - L.tile_base, win, rowt);
+}
+
+// The levels of many frames in one launch: CTA b works on entry e (the last with tile_base <= b).
+__global__ __launch_bounds__(256) void k_wht_tab(const WhtLevel* __restrict__ tab, int n) {
+    grid_dependency_sync();
+    __shared__ __align__(16) uint8_t win[3][kWinY][kWinX];
+    __shared__ short4 rowt[3][kWinY][kWtx];
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].tile_base <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const WhtLevel L = tab[lo];
+    wht_tile(L, (int)blockIdx.x - L.tile_base, win, rowt);
+}
+
 int wht_tiles_x(int w) { return (w + kWtx - 1) / kWtx; }
 int wht_tiles(int w, int h) { return wht_tiles_x(w) * ((h + kWty - 1) / kWty); }
 
 void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st) {
     launch_k(k_wht, dim3(total_tiles), dim3(256), 0, st, a);
+}
+
+void launch_wht_tab(const WhtLevel* tab_dev, int n, int total_tiles, cudaStream_t st) {
+    launch_k(k_wht_tab, dim3(total_tiles), dim3(256), 0, st, tab_dev, n);
 }
 
 }  // namespace ff

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -145,8 +146,15 @@ const TileCfg kCands[] = {
     {64, 20, 1, 128, 0}, {24, 16, 1, 512, 0}, {32, 16, 1, 512, 0}, {20, 16, 1, 512, 0}, {26, 16, 1, 512, 0}};
 constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
 
-// Tuning key: level index, level size of the first job, number of directions in the launch, iterations.
+// Tuning key: pass index, grid size of the first job, number of directions in the launch, iterations.  A pass is
+// a level (index s) or one of its sub-scale grids of stride 2^k (index s + 8k).
 using TuneKey = std::tuple<int, int, int, int, int>;
+constexpr int kMaxPasses = 3 * kMaxLevels;
+static_assert(kMaxPasses == FF_N_PASSES, "pass indices of the profile readout");
+int pass_index(int s, int k) { return s + kMaxLevels * k; }
+int grid_dim(int v, int k) { return (v + (1 << k) - 1) >> k; }
+// sub-scale grids of level s (the coarsest level has none)
+int grids_of(const ff_params& p, int s) { return s == p.n_scales - 1 ? 0 : p.sub_scales; }
 
 }  // namespace
 
@@ -164,6 +172,8 @@ struct ff_ctx {
     int withhold = 0;                  // test of the bounded waits: the tensor-core seed issues no copies
     int* d_err = nullptr;              // device error word of bounded waits
     void* noalloc_scratch = nullptr;   // device address of ff_match_pair_noalloc's fixed scratch array
+    int64_t fail_allocs = 0;           // test of the out-of-memory paths: device allocations still to fail
+    DevBuf feat_tab;                   // device table of ff_features_batch (frames' pyramid and WHT launch entries)
     std::string err;
     int64_t launches = 0, replays = 0, plans_built = 0, bytes = 0;
     bool profiling = false;
@@ -204,7 +214,7 @@ ff_status dev_alloc(ff_ctx* c, DevBuf& b, size_t bytes) {
         b.p = nullptr;
         return FF_OK;
     }
-    cudaError_t e = cudaMalloc(&b.p, bytes);
+    cudaError_t e = ctx_malloc(c, &b.p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
@@ -235,6 +245,7 @@ ff_status check_params(const ff_params* p, ff_ctx* c) {
     if (p->rs_radius2 < 0 || p->rs_radius2 > 16) return fail(c, FF_ERR_ARG, "rs_radius2 must be 0..16");
     if (p->cost != FF_COST_WHT_SAD && p->cost != FF_COST_CENSUS)
         return fail(c, FF_ERR_ARG, "cost must be FF_COST_WHT_SAD or FF_COST_CENSUS");
+    if (p->sub_scales < 0 || p->sub_scales > 2) return fail(c, FF_ERR_ARG, "sub_scales must be 0, 1 or 2");
     return FF_OK;
 }
 
@@ -283,7 +294,7 @@ int kernels_of(const Launch& l) { return l.kind == Kind::Memset ? 0 : l.kind == 
 
 ff_status ensure_err_word(ff_ctx* c) {
     if (c->d_err) return FF_OK;
-    if (cudaMalloc(&c->d_err, 256) != cudaSuccess) {
+    if (ctx_malloc(c, reinterpret_cast<void**>(&c->d_err), 256) != cudaSuccess) {
         cudaGetLastError();
         c->d_err = nullptr;
         return fail(c, FF_ERR_OOM, "error word allocation failed");
@@ -338,17 +349,20 @@ const void* cost_desc(const ff_pyr* p, int level, int cost) {
 }
 
 // Build the launch sequence of a set of matching directions (+ consistency checks).  `force` (optional, one entry
-// per level) imposes the propagation configuration of every level (used by the autotuner).
+// per pass index) imposes the propagation configuration of every level and grid (used by the autotuner).
 ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons, Plan& P,
                      const TileCfg* force) {
     const int L = c->prm.n_scales, T = c->prm.iters, cost = c->prm.cost;
     const int nj = (int)jobs.size();
     // per job and level: two flow and two cost buffers (ping-pong) + seed distances
+    // per job, level and grid (k = 0: the level; k = 1, 2: its sub-scale grids of stride 2^k)
     struct LevelBufs {
         uint32_t* flow[2];
         int32_t* cost[2];
     };
-    std::vector<std::vector<LevelBufs>> lb(nj, std::vector<LevelBufs>(L));
+    auto gdim = grid_dim;
+    auto k_first = [&](int s) { return grids_of(c->prm, s); };
+    std::vector<std::vector<std::array<LevelBufs, 3>>> lb(nj, std::vector<std::array<LevelBufs, 3>>(L));
     std::vector<int32_t*> seed_dist(nj);
     std::vector<unsigned long long*> seed_keys(nj);
     const bool tc = c->seed_kernel == FF_SEED_TCGEN05;
@@ -358,7 +372,9 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     }
     size_t scratch = 0, keys_bytes = 0;
     for (int j = 0; j < nj; j++) {
-        for (int s = 0; s < L; s++) scratch += 4 * align_up((size_t)jobs[j].a->ws[s] * jobs[j].a->hs[s] * 4);
+        for (int s = 0; s < L; s++)
+            for (int k = 0; k <= k_first(s); k++)
+                scratch += 4 * align_up((size_t)gdim(jobs[j].a->ws[s], k) * gdim(jobs[j].a->hs[s], k) * 4);
         scratch += align_up((size_t)jobs[j].a->n_coarse * 4);
         if (tc) keys_bytes += (size_t)jobs[j].a->n_coarse * 8;
     }
@@ -369,15 +385,16 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     char* base = static_cast<char*>(P.bufs.back().p);
     size_t off = 0;
     for (int j = 0; j < nj; j++) {
-        for (int s = 0; s < L; s++) {
-            size_t n = (size_t)jobs[j].a->ws[s] * jobs[j].a->hs[s];
-            for (int k = 0; k < 2; k++) {
-                lb[j][s].flow[k] = reinterpret_cast<uint32_t*>(base + off);
-                off += align_up(n * 4);
-                lb[j][s].cost[k] = reinterpret_cast<int32_t*>(base + off);
-                off += align_up(n * 4);
+        for (int s = 0; s < L; s++)
+            for (int k = 0; k <= k_first(s); k++) {
+                size_t n = (size_t)gdim(jobs[j].a->ws[s], k) * gdim(jobs[j].a->hs[s], k);
+                for (int b = 0; b < 2; b++) {
+                    lb[j][s][k].flow[b] = reinterpret_cast<uint32_t*>(base + off);
+                    off += align_up(n * 4);
+                    lb[j][s][k].cost[b] = reinterpret_cast<int32_t*>(base + off);
+                    off += align_up(n * 4);
+                }
             }
-        }
         seed_dist[j] = reinterpret_cast<int32_t*>(base + off);
         off += align_up((size_t)jobs[j].a->n_coarse * 4);
     }
@@ -447,7 +464,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             sp.cta_base = ctas;
             ctas += sp.row_tiles * sp.col_tiles;
             sp.keys = seed_keys[j];
-            sp.flow = lb[j][L - 1].flow[0];
+            sp.flow = lb[j][L - 1][0].flow[0];
             sp.dist = seed_dist[j];
             sp.pix_base = pix;
             pix += sp.n;
@@ -476,7 +493,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             sp.normB = B->seed_norm;
             sp.n = A->n_coarse;
             sp.w = A->ws[L - 1];
-            sp.flow = lb[j][L - 1].flow[0];
+            sp.flow = lb[j][L - 1][0].flow[0];
             sp.dist = seed_dist[j];
             sp.warp_base = tiles;
             tiles += (sp.n + 15) / 16;
@@ -486,9 +503,11 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         l.total = tiles;
         pend.push_back({l, o, 0, -1});
     }
-    // 2. per level: hand-over (the cost of the seed at the coarsest level), then the propagation launches
+    // 2. per level, and before it per sub-scale grid (sparsest first): hand-over (the cost of the seed at the
+    //    coarsest level), then the propagation launches
     std::vector<int> cur_buf(nj, 0);
     for (int s = L - 1; s >= 0; s--) {
+      for (int k = k_first(s); k >= 0; k--) {
         {
             Launch l{};
             l.kind = Kind::Handover;
@@ -500,18 +519,26 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
                 HandoverProblem hp{};
                 hp.fa = cost_desc(A, s, cost);
                 hp.fb = cost_desc(jobs[j].b, s, cost);
-                hp.w = A->ws[s];
-                hp.h = A->hs[s];
+                hp.w = gdim(A->ws[s], k);
+                hp.h = gdim(A->hs[s], k);
+                hp.g = 1 << k;
+                hp.lw = A->ws[s];
+                hp.lh = A->hs[s];
                 if (s == L - 1) {
                     hp.parent = nullptr;
-                    hp.flow_in = lb[j][s].flow[0];
-                } else {
-                    hp.parent = lb[j][s + 1].flow[cur_buf[j]];
+                    hp.flow_in = lb[j][s][0].flow[0];
+                } else if (k == k_first(s)) {  // from the level above
+                    hp.parent = lb[j][s + 1][0].flow[cur_buf[j]];
                     hp.pw = A->ws[s + 1];
                     hp.ph = A->hs[s + 1];
+                } else {  // from the sparser grid of this level
+                    hp.parent = lb[j][s][k + 1].flow[cur_buf[j]];
+                    hp.pw = gdim(A->ws[s], k + 1);
+                    hp.ph = gdim(A->hs[s], k + 1);
+                    hp.same_level = 1;
                 }
-                hp.flow_out = lb[j][s].flow[0];
-                hp.cost_out = lb[j][s].cost[0];
+                hp.flow_out = lb[j][s][k].flow[0];
+                hp.cost_out = lb[j][s][k].cost[0];
                 hp.pix_base = pix;
                 pix += (int64_t)hp.w * hp.h;
                 hos.push_back(hp);
@@ -523,33 +550,35 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             pend.push_back({l, o, 0, -1});
         }
         int64_t level_pix = 0;
-        for (int j = 0; j < nj; j++) level_pix += (int64_t)jobs[j].a->ws[s] * jobs[j].a->hs[s];
+        for (int j = 0; j < nj; j++) level_pix += (int64_t)gdim(jobs[j].a->ws[s], k) * gdim(jobs[j].a->hs[s], k);
+        const int pass = pass_index(s, k);
         TileCfg tc;
         if (force) {
-            tc = force[s];
+            tc = force[pass];
             tc.k = std::min(tc.k, T);
-        } else if (c->forced[s].tw > 0) {
+        } else if (k == 0 && c->forced[s].tw > 0) {
             tc = c->forced[s];
             tc.k = std::min(tc.k, T);
         } else {
-            auto it = c->tuned.find(TuneKey{s, jobs[0].a->ws[s], jobs[0].a->hs[s], nj, T});
+            auto it = c->tuned.find(TuneKey{pass, gdim(jobs[0].a->ws[s], k), gdim(jobs[0].a->hs[s], k), nj, T});
             tc = it != c->tuned.end() ? it->second : default_cfg(c, level_pix, T);
         }
         const size_t smem = prop_smem_bytes(tc.tw, tc.th, tc.k);
-        const int blocks = prop_blocks_per_sm(smem, tc.threads, tc.spec != 0, cost) * c->n_sms;
+        const int blocks = prop_blocks_per_sm(smem, tc.threads, tc.spec != 0, cost, k > 0) * c->n_sms;
         for (int t0 = 0; t0 < T; t0 += tc.k) {
             int n_iter = std::min(tc.k, T - t0);
             bool last = t0 + n_iter == T;
             Launch l{};
             l.kind = Kind::Propagate;
             l.phase = FF_PHASE_PROPAGATE;
-            l.level = s;
+            l.level = pass;
             l.prop.tw = tc.tw;
             l.prop.th = tc.th;
             l.prop.max_iter = n_iter;
             l.prop.threads = tc.threads;
             l.prop.spec = tc.spec;
             l.prop.cost = cost;
+            l.prop.grid = k > 0;
             size_t oq = queue.size();
             std::vector<int> pidx(nj), ntiles(nj);
             for (int j = 0; j < nj; j++) {
@@ -557,24 +586,28 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
                 PropProblem pp{};
                 pp.fa = cost_desc(A, s, cost);
                 pp.fb = cost_desc(jobs[j].b, s, cost);
-                pp.w = A->ws[s];
-                pp.h = A->hs[s];
+                pp.w = gdim(A->ws[s], k);
+                pp.h = gdim(A->hs[s], k);
+                pp.g = 1 << k;
+                pp.lw = A->ws[s];
+                pp.lh = A->hs[s];
                 int in = cur_buf[j], out = in ^ 1;
-                pp.flow_in = lb[j][s].flow[in];
-                pp.cost_in = lb[j][s].cost[in];
-                if (last && s == 0) {  // the final launch writes the caller's buffers (cost to scratch if NULL)
+                const LevelBufs& B = lb[j][s][k];
+                pp.flow_in = B.flow[in];
+                pp.cost_in = B.cost[in];
+                if (last && s == 0 && k == 0) {  // the final launch writes the caller's buffers (cost to scratch if NULL)
                     pp.flow_out = jobs[j].flow_out;
-                    pp.cost_out = jobs[j].cost_out ? jobs[j].cost_out : lb[j][s].cost[out];
+                    pp.cost_out = jobs[j].cost_out ? jobs[j].cost_out : B.cost[out];
                 } else {
-                    pp.flow_out = lb[j][s].flow[out];
-                    pp.cost_out = lb[j][s].cost[out];
+                    pp.flow_out = B.flow[out];
+                    pp.cost_out = B.cost[out];
                 }
                 cur_buf[j] = out;
                 pp.tiles_x = (pp.w + tc.tw - 1) / tc.tw;
                 ntiles[j] = pp.tiles_x * ((pp.h + tc.th - 1) / tc.th);
                 pp.t0 = t0;
                 pp.n_iter = n_iter;
-                pp.level = s;
+                pp.level = s + 8 * k;  // the hash stream of this level or grid
                 pp.dir = jobs[j].dir;
                 pp.seed = c->prm.seed;
                 pp.rs_radius = jobs[j].rs_radius;
@@ -584,15 +617,16 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             for (const std::vector<int>& g : groups) {
                 int most = 0;
                 for (int j : g) most = std::max(most, ntiles[j]);
-                for (int k = 0; k < most; k++)
+                for (int q = 0; q < most; q++)
                     for (int j : g)
-                        if (k < ntiles[j]) queue.push_back(make_int2(pidx[j], k));
+                        if (q < ntiles[j]) queue.push_back(make_int2(pidx[j], q));
             }
             l.n_probs = nj;
             l.total = (int)(queue.size() - oq);
             l.grid = std::min(l.total, blocks);
             pend.push_back({l, 0, oq, n_counters++});
         }
+      }
     }
     // 3. consistency of each pair: the forward flow and the inverse flow, both at level 0
     for (const ConsJob& cj : cons) {
@@ -749,23 +783,24 @@ ff_status run_jobs(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
 
 // Time every candidate configuration on the given jobs and keep, per level, the fastest.  Runs the real
 // matching (outputs are overwritten by every trial; all configurations give identical results).
-// Tiles a launch of this configuration processes at level s (all jobs) and the CTAs resident at once.
-void wave_shape(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, const TileCfg& t, int64_t* tiles,
+// Tiles a launch of this configuration processes in pass (s, k) (all jobs) and the CTAs resident at once.
+void wave_shape(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, int k, const TileCfg& t, int64_t* tiles,
                 int64_t* slots) {
     int64_t n = 0;
     for (const DirJob& j : jobs)
-        n += (int64_t)((j.a->ws[s] + t.tw - 1) / t.tw) * ((j.a->hs[s] + t.th - 1) / t.th);
+        n += (int64_t)((grid_dim(j.a->ws[s], k) + t.tw - 1) / t.tw) * ((grid_dim(j.a->hs[s], k) + t.th - 1) / t.th);
     *tiles = n;
-    *slots = (int64_t)prop_blocks_per_sm(prop_smem_bytes(t.tw, t.th, t.k), t.threads, t.spec != 0, c->prm.cost) *
+    *slots = (int64_t)prop_blocks_per_sm(prop_smem_bytes(t.tw, t.th, t.k), t.threads, t.spec != 0, c->prm.cost,
+                                         k > 0) *
              c->n_sms;
 }
 
 // A launch whose last wave is a small remainder of tiles runs at about the speed of one more full wave.  The
 // wave-fitted variant of a configuration grows the tile (height first, then width, by at most a quarter) just
 // enough that the tiles fill one wave fewer; it returns the configuration unchanged when none does.
-TileCfg wave_fitted(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, TileCfg t) {
+TileCfg wave_fitted(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, int k, TileCfg t) {
     int64_t tiles, slots;
-    wave_shape(c, jobs, s, t, &tiles, &slots);
+    wave_shape(c, jobs, s, k, t, &tiles, &slots);
     if (slots < 1 || tiles <= slots) return t;
     const int64_t waves = (tiles + slots - 1) / slots;
     if (tiles - (waves - 1) * slots > slots / 2) return t;  // the last wave is at least half full
@@ -781,7 +816,7 @@ TileCfg wave_fitted(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, Til
             }
             if (!cfg_fits(u)) continue;
             int64_t tu, su;
-            wave_shape(c, jobs, s, u, &tu, &su);
+            wave_shape(c, jobs, s, k, u, &tu, &su);
             if (su > 0 && tu <= (waves - 1) * su) return u;
         }
     return t;
@@ -789,21 +824,25 @@ TileCfg wave_fitted(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, Til
 
 ff_status autotune(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons, int reps) {
     const int L = c->prm.n_scales, T = c->prm.iters, nj = (int)jobs.size();
-    // per level, the best time and configuration seen; each candidate is timed as given and, where it leaves a
-    // short last wave at some level, once more with its wave-fitted variant at those levels
-    std::vector<double> best_ms(L, 1e30);
-    std::vector<TileCfg> best_cfg(L);
+    // the passes of a plan: every level and, with sub-scales, its grids
+    std::vector<std::pair<int, int>> passes;
+    for (int s = 0; s < L; s++)
+        for (int k = 0; k <= grids_of(c->prm, s); k++) passes.push_back({s, k});
+    // per pass, the best time and configuration seen; each candidate is timed as given and, where it leaves a
+    // short last wave in some pass, once more with its wave-fitted variant in those passes
+    std::vector<double> best_ms(kMaxPasses, 1e30);
+    std::vector<TileCfg> best_cfg(kMaxPasses);
     ff_status s = drop_plans(c);
     if (s != FF_OK) return s;
     bool was_profiling = c->profiling;
-    auto time_plan = [&](const std::vector<TileCfg>& per_level) -> ff_status {
+    auto time_plan = [&](const std::vector<TileCfg>& per_pass) -> ff_status {
         Plan P;
-        ff_status st = build_plan(c, jobs, cons, P, per_level.data());
+        ff_status st = build_plan(c, jobs, cons, P, per_pass.data());
         if (st != FF_OK) {
             free_plan(c, P);
             return st;
         }
-        std::vector<double> lv_best(L, 1e30);
+        std::vector<double> pass_best(kMaxPasses, 1e30);
         for (int r = 0; r < reps + 1; r++) {
             c->events.clear();
             st = run_launches(c, P.launches, true);
@@ -815,43 +854,52 @@ ff_status autotune(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
                 free_plan(c, P);
                 return st;
             }
-            std::vector<double> lv(L, 0.0);
+            std::vector<double> lv(kMaxPasses, 0.0);
             for (auto& e : c->events) {
                 float t = 0.f;
                 cudaEventElapsedTime(&t, e.a, e.b);
-                if (e.phase == FF_PHASE_PROPAGATE && e.level >= 0) lv[e.level] += t;
+                if (e.phase == FF_PHASE_PROPAGATE && e.level >= 0 && e.level < kMaxPasses) lv[e.level] += t;
                 c->event_pool.push_back(e.a);
                 c->event_pool.push_back(e.b);
             }
             c->events.clear();
             if (r > 0)  // the first run warms caches and clocks
-                for (int l = 0; l < L; l++) lv_best[l] = std::min(lv_best[l], lv[l]);
+                for (auto [ps, pk] : passes) {
+                    const int p = pass_index(ps, pk);
+                    pass_best[p] = std::min(pass_best[p], lv[p]);
+                }
         }
         free_plan(c, P);
-        for (int l = 0; l < L; l++)
-            if (lv_best[l] < best_ms[l]) {
-                best_ms[l] = lv_best[l];
-                best_cfg[l] = per_level[l];
+        for (auto [ps, pk] : passes) {
+            const int p = pass_index(ps, pk);
+            if (pass_best[p] < best_ms[p]) {
+                best_ms[p] = pass_best[p];
+                best_cfg[p] = per_pass[p];
             }
+        }
         return FF_OK;
     };
     for (int ci = 0; ci < kNCands; ci++) {
         TileCfg cfg = kCands[ci];
         cfg.k = std::min(cfg.k, T);
         if (!cfg_fits(cfg)) continue;
-        std::vector<TileCfg> per_level(L, cfg), fitted(L, cfg);
+        std::vector<TileCfg> per_pass(kMaxPasses, cfg), fitted(kMaxPasses, cfg);
         bool any = false;
-        for (int l = 0; l < L; l++) {
-            fitted[l] = wave_fitted(c, jobs, l, cfg);
-            any = any || fitted[l].tw != cfg.tw || fitted[l].th != cfg.th;
+        for (auto [ps, pk] : passes) {
+            const int p = pass_index(ps, pk);
+            fitted[p] = wave_fitted(c, jobs, ps, pk, cfg);
+            any = any || fitted[p].tw != cfg.tw || fitted[p].th != cfg.th;
         }
-        s = time_plan(per_level);
+        s = time_plan(per_pass);
         if (s == FF_OK && any) s = time_plan(fitted);
         if (s != FF_OK) return s;
     }
     c->profiling = was_profiling;
-    for (int l = 0; l < L; l++)
-        if (best_ms[l] < 1e29) c->tuned[TuneKey{l, jobs[0].a->ws[l], jobs[0].a->hs[l], nj, T}] = best_cfg[l];
+    for (auto [ps, pk] : passes) {
+        const int p = pass_index(ps, pk);
+        if (best_ms[p] < 1e29)
+            c->tuned[TuneKey{p, grid_dim(jobs[0].a->ws[ps], pk), grid_dim(jobs[0].a->hs[ps], pk), nj, T}] = best_cfg[p];
+    }
     return FF_OK;
 }
 
@@ -871,6 +919,7 @@ bool ctx_view(const ff_ctx* c, CtxView* out) {
     out->seed = c->prm.seed;
     out->cost = c->prm.cost;
     out->noalloc_scratch = c->noalloc_scratch;
+    out->sub_scales = c->prm.sub_scales;
     return true;
 }
 
@@ -927,6 +976,15 @@ int ctx_set_error(ff_ctx* c, int status, const char* msg) {
     return (int)fail(c, (ff_status)status, "%s", msg);
 }
 
+cudaError_t ctx_malloc(ff_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (c->fail_allocs > 0) {  // FF_OPT_TEST_FAIL_ALLOCS: behave as an exhausted device, allocate nothing
+        c->fail_allocs--;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 }  // namespace ff
 
 namespace {
@@ -943,58 +1001,9 @@ ff_status check_pyr(ff_ctx* c, const ff_pyr* p, const char* what) {
     return FF_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-void ff_default_params(ff_params* p) {
-    if (!p) return;
-    p->n_scales = 5;
-    p->iters = 6;
-    p->patch = 8;
-    p->n_coef = 16;
-    p->rs_radius = 2;
-    p->eps = 1;
-    p->seed = 0x20180503u;
-    p->rs_radius2 = 4;
-    p->cost = FF_COST_WHT_SAD;
-}
-
-ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* cuda_stream) {
-    if (!out) return FF_ERR_ARG;
-    *out = nullptr;
-    ff_status s = check_params(p, nullptr);
-    if (s != FF_OK) return s;
-    int n = 0;
-    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
-        cudaGetLastError();
-        return FF_ERR_ARG;
-    }
-    ff_ctx* c = new (std::nothrow) ff_ctx();
-    if (!c) return FF_ERR_OOM;
-    c->device = device;
-    c->stream = static_cast<cudaStream_t>(cuda_stream);
-    c->prm = *p;
-    // with the device current: kernel attributes, and the set-up of ff_match_pair_noalloc (its scratch array and
-    // kernels are loaded here, so that its calls never load code or reserve memory)
-    cudaError_t e = cudaSetDevice(device);
-    if (e == cudaSuccess) e = init_kernel_attributes();
-    if (e == cudaSuccess) e = seed_tc_init_attributes();
-    if (e == cudaSuccess) e = noalloc_prepare(&c->noalloc_scratch);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        delete c;
-        return e == cudaErrorMemoryAllocation ? FF_ERR_OOM : FF_ERR_CUDA;
-    }
-    *out = c;
-    return FF_OK;
-}
-
-ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch_bytes, ff_pyr** out) {
-    if (!c) return FF_ERR_ARG;
-    if (!out) return fail(c, FF_ERR_ARG, "out is NULL");
-    *out = nullptr;
+// A frame's pyramid from the context's pool (allocated if no free one of its size exists), after validating the
+// frame.  Launches nothing except, for a new pyramid, the zeroing of its seed rows' padding.
+ff_status acquire_pyr(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch_bytes, ff_pyr** out) {
     if (!rgb_dev) return fail(c, FF_ERR_ARG, "rgb_dev is NULL");
     if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim) return fail(c, FF_ERR_ARG, "size %dx%d outside 1..%d", w, h, kMaxDim);
     if (pitch_bytes < 3 * w) return fail(c, FF_ERR_ARG, "pitch %d < 3*w", pitch_bytes);
@@ -1068,6 +1077,112 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
         c->pyrs.push_back(std::move(np));
     }
     P->in_use = true;
+    *out = P;
+    return FF_OK;
+}
+
+// Arguments of the fused pyramid launch of a frame (levels 1..min(L-1, 6)).
+PyrArgs pyramid_args(const ff_pyr* P, const uint8_t* rgb_dev, int pitch_bytes) {
+    PyrArgs pa{};
+    pa.src = rgb_dev;
+    pa.spitch = pitch_bytes;
+    for (int s = 0; s < P->L; s++) {
+        pa.dst[s] = P->img[s];
+        pa.w[s] = P->ws[s];
+        pa.h[s] = P->hs[s];
+    }
+    pa.top = std::min(P->L - 1, kPyrFusedTop);
+    return pa;
+}
+
+// Levels past the fused pyramid launch (L = 8 only): one launch each; returns the number of launches.
+int deep_levels(const ff_pyr* P, cudaStream_t st) {
+    int nl = 0;
+    for (int s = kPyrFusedTop + 1; s < P->L; s++) {
+        launch_downsample(P->img[s - 1], P->ws[s - 1], P->hs[s - 1], P->ws[s - 1] * 3, P->img[s], P->ws[s], P->hs[s],
+                          st);
+        nl++;
+    }
+    return nl;
+}
+
+// WHT launch entry of level s of a frame; *tiles is the first CTA of the entry and is advanced past it.
+WhtLevel wht_level(const ff_pyr* P, int s, const uint8_t* rgb_dev, int pitch_bytes, int* tiles) {
+    WhtLevel lv{};
+    lv.img = s == 0 ? rgb_dev : P->img[s];
+    lv.pitch = s == 0 ? pitch_bytes : P->ws[s] * 3;
+    lv.w = P->ws[s];
+    lv.h = P->hs[s];
+    lv.feat = P->feat[s];
+    lv.census = P->cen[s];
+    if (s == P->L - 1) {  // the coarsest level also writes the initial-matching descriptors
+        lv.seed_desc = P->seed_desc;
+        lv.seed_norm = P->seed_norm;
+        lv.desc16 = P->desc16;
+    }
+    lv.tiles_x = wht_tiles_x(P->ws[s]);
+    lv.tile_base = *tiles;
+    *tiles += wht_tiles(P->ws[s], P->hs[s]);
+    return lv;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ff_default_params(ff_params* p) {
+    if (!p) return;
+    p->n_scales = 5;
+    p->iters = 6;
+    p->patch = 8;
+    p->n_coef = 16;
+    p->rs_radius = 2;
+    p->eps = 1;
+    p->seed = 0x20180503u;
+    p->rs_radius2 = 4;
+    p->cost = FF_COST_WHT_SAD;
+    p->sub_scales = 0;
+}
+
+ff_status ff_create(ff_ctx** out, const ff_params* p, int device, void* cuda_stream) {
+    if (!out) return FF_ERR_ARG;
+    *out = nullptr;
+    ff_status s = check_params(p, nullptr);
+    if (s != FF_OK) return s;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return FF_ERR_ARG;
+    }
+    ff_ctx* c = new (std::nothrow) ff_ctx();
+    if (!c) return FF_ERR_OOM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->prm = *p;
+    // with the device current: kernel attributes, and the set-up of ff_match_pair_noalloc (its scratch array and
+    // kernels are loaded here, so that its calls never load code or reserve memory)
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = init_kernel_attributes();
+    if (e == cudaSuccess) e = seed_tc_init_attributes();
+    if (e == cudaSuccess) e = noalloc_prepare(&c->noalloc_scratch);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return e == cudaErrorMemoryAllocation ? FF_ERR_OOM : FF_ERR_CUDA;
+    }
+    *out = c;
+    return FF_OK;
+}
+
+ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch_bytes, ff_pyr** out) {
+    if (!c) return FF_ERR_ARG;
+    if (!out) return fail(c, FF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    ff_pyr* P = nullptr;
+    ff_status s = acquire_pyr(c, rgb_dev, w, h, pitch_bytes, &P);
+    if (s != FF_OK) return s;
+    const int L = P->L;
 
     cudaEvent_t ea = nullptr, eb = nullptr;
     if (c->profiling) {
@@ -1077,45 +1192,15 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
     }
     int nl = 0;
     if (L > 1) {  // levels 1..min(L-1, 6) in one launch, deeper levels one launch each
-        PyrArgs pa{};
-        pa.src = rgb_dev;
-        pa.spitch = pitch_bytes;
-        for (int s = 0; s < L; s++) {
-            pa.dst[s] = P->img[s];
-            pa.w[s] = P->ws[s];
-            pa.h[s] = P->hs[s];
-        }
-        pa.top = std::min(L - 1, kPyrFusedTop);
+        PyrArgs pa = pyramid_args(P, rgb_dev, pitch_bytes);
         launch_pyramid(pa, c->stream);
         nl++;
-        for (int s = pa.top + 1; s < L; s++) {
-            launch_downsample(P->img[s - 1], P->ws[s - 1], P->hs[s - 1], P->ws[s - 1] * 3, P->img[s], P->ws[s],
-                              P->hs[s], c->stream);
-            nl++;
-        }
+        nl += deep_levels(P, c->stream);
     }
-    // Levels in the launch from the coarsest up: its CTAs, which also write the seed rows, start first instead
-    // of forming the launch's tail.
     WhtArgs wa{};
     wa.n = L;
     int tiles = 0;
-    for (int s = L - 1; s >= 0; s--) {
-        WhtLevel& lv = wa.lv[L - 1 - s];
-        lv.img = s == 0 ? rgb_dev : P->img[s];
-        lv.pitch = s == 0 ? pitch_bytes : P->ws[s] * 3;
-        lv.w = P->ws[s];
-        lv.h = P->hs[s];
-        lv.feat = P->feat[s];
-        lv.census = P->cen[s];
-        if (s == L - 1) {  // the coarsest level also writes the initial-matching descriptors
-            lv.seed_desc = P->seed_desc;
-            lv.seed_norm = P->seed_norm;
-            lv.desc16 = P->desc16;
-        }
-        lv.tiles_x = wht_tiles_x(P->ws[s]);
-        lv.tile_base = tiles;
-        tiles += wht_tiles(P->ws[s], P->hs[s]);
-    }
+    for (int s = L - 1; s >= 0; s--) wa.lv[L - 1 - s] = wht_level(P, s, rgb_dev, pitch_bytes, &tiles);
     launch_wht(wa, tiles, c->stream);
     nl++;
     c->launches += nl;
@@ -1129,6 +1214,99 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
         c->events.push_back({FF_PHASE_FEATURES, -1, ea, eb, nl});
     }
     *out = P;
+    return FF_OK;
+}
+
+ff_status ff_features_batch(ff_ctx* c, int n, const ff_frame* frames, ff_pyr** out) {
+    if (!c) return FF_ERR_ARG;
+    if (n < 0 || (n > 0 && (!frames || !out))) return fail(c, FF_ERR_ARG, "bad frame list");
+    for (int i = 0; i < n; i++) out[i] = nullptr;
+    if (n == 0) return FF_OK;
+    for (int i = 0; i < n; i++) {
+        ff_status s = acquire_pyr(c, frames[i].rgb_dev, frames[i].w, frames[i].h, frames[i].pitch_bytes, &out[i]);
+        if (s != FF_OK) {  // give back what this call took; nothing was launched
+            for (int j = 0; j < i; j++) {
+                out[j]->in_use = false;
+                out[j] = nullptr;
+            }
+            return s;
+        }
+    }
+    // tables: one pyramid entry per frame with more than one level; the WHT levels of all frames, coarsest levels
+    // first (their CTAs also write the seed rows, the longest tiles)
+    std::vector<PyrArgs> pyr_tab;
+    std::vector<WhtLevel> wht_tab;
+    int ctas = 0, tiles = 0, max_L = 0;
+    for (int i = 0; i < n; i++) {
+        max_L = std::max(max_L, out[i]->L);
+        if (out[i]->L > 1) {
+            PyrArgs pa = pyramid_args(out[i], frames[i].rgb_dev, frames[i].pitch_bytes);
+            pa.cta_base = ctas;
+            pa.bx = pyramid_blocks_x(out[i]->ws[1]);
+            ctas += pyramid_blocks(out[i]->ws[1], out[i]->hs[1]);
+            pyr_tab.push_back(pa);
+        }
+    }
+    for (int up = 0; up < max_L; up++)  // up = levels above the finest: 0 is each frame's coarsest level
+        for (int i = 0; i < n; i++) {
+            const int L = out[i]->L;
+            if (up < L) wht_tab.push_back(wht_level(out[i], L - 1 - up, frames[i].rgb_dev, frames[i].pitch_bytes, &tiles));
+        }
+    const size_t o_wht = align_up(pyr_tab.size() * sizeof(PyrArgs));
+    const size_t bytes = o_wht + wht_tab.size() * sizeof(WhtLevel);
+    auto give_back = [&]() {
+        for (int i = 0; i < n; i++) {
+            out[i]->in_use = false;
+            out[i] = nullptr;
+        }
+    };
+    if (c->feat_tab.bytes < bytes) {  // grow the context's table buffer (after the work that still reads it)
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            give_back();
+            return fail(c, FF_ERR_CUDA, "cudaStreamSynchronize failed: %s", cudaGetErrorString(e));
+        }
+        dev_free(c, c->feat_tab);
+        ff_status s = dev_alloc(c, c->feat_tab, std::max(bytes, (size_t)64 << 10));
+        if (s != FF_OK) {
+            give_back();
+            return s;
+        }
+    }
+    std::vector<char> host(bytes);
+    memcpy(host.data(), pyr_tab.data(), pyr_tab.size() * sizeof(PyrArgs));
+    memcpy(host.data() + o_wht, wht_tab.data(), wht_tab.size() * sizeof(WhtLevel));
+    char* dev = static_cast<char*>(c->feat_tab.p);
+
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (c->profiling) {
+        ea = get_event(c);
+        eb = get_event(c);
+        FF_CUDA(c, cudaEventRecord(ea, c->stream));
+    }
+    // from pageable memory: the copy is staged before the call returns, so the host table can go at once; it runs
+    // after the work already on the stream (which may still read the previous table)
+    cudaError_t e = cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, c->stream);
+    int nl = 0;
+    if (e == cudaSuccess && !pyr_tab.empty()) {
+        launch_pyramid_tab(reinterpret_cast<const PyrArgs*>(dev), (int)pyr_tab.size(), ctas, c->stream);
+        nl++;
+        for (int i = 0; i < n; i++) nl += deep_levels(out[i], c->stream);
+    }
+    if (e == cudaSuccess) {
+        launch_wht_tab(reinterpret_cast<const WhtLevel*>(dev + o_wht), (int)wht_tab.size(), tiles, c->stream);
+        nl++;
+        e = cudaGetLastError();
+    }
+    c->launches += nl;
+    if (e != cudaSuccess) {
+        give_back();
+        return fail(c, FF_ERR_CUDA, "feature launch failed: %s", cudaGetErrorString(e));
+    }
+    if (c->profiling) {
+        FF_CUDA(c, cudaEventRecord(eb, c->stream));
+        c->events.push_back({FF_PHASE_FEATURES, -1, ea, eb, nl});
+    }
     return FF_OK;
 }
 
@@ -1296,6 +1474,17 @@ ff_status ff_sync(ff_ctx* c) {
     FF_CUDA(c, cudaSetDevice(c->device));
     FF_CUDA(c, cudaStreamSynchronize(c->stream));
     FF_CUDA(c, cudaGetLastError());
+#if FF_DEBUG_BOUNDS
+    {  // a debug-bounds build: an index check failed since the last check
+        int rec[3];
+        for (int tu = 0; tu < 2; tu++) {
+            FF_CUDA(c, tu == 0 ? bounds_take_propagate(rec) : bounds_take_filter(rec));
+            if (rec[0] != 0)
+                return fail(c, FF_ERR_CUDA, "bounds check %d failed: index %d outside 0..%d (access skipped)", rec[0],
+                            rec[1], rec[2] - 1);
+        }
+    }
+#endif
     if (c->d_err) {  // a bounded device-side wait gave up since the last check
         int e = 0;
         FF_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
@@ -1319,6 +1508,10 @@ ff_status ff_set_option(ff_ctx* c, int option, int64_t value) {
         case FF_OPT_TEST_WITHHOLD_COPIES:
             if (value != 0 && value != 1) return fail(c, FF_ERR_ARG, "withhold must be 0 or 1");
             break;
+        case FF_OPT_TEST_FAIL_ALLOCS:
+            if (value < 0 || value > (1ll << 30)) return fail(c, FF_ERR_ARG, "allocation failures must be 0..2^30");
+            c->fail_allocs = value;  // takes effect at once and keeps the cached plans
+            return FF_OK;
         default:
             return fail(c, FF_ERR_ARG, "unknown option %d", option);
     }
@@ -1367,12 +1560,39 @@ ff_status ff_profile_read(ff_ctx* c, double* ms, int64_t* launches) {
     return FF_OK;
 }
 
+ff_status ff_profile_read_passes(ff_ctx* c, double* ms, int64_t* launches) {
+    if (!c) return FF_ERR_ARG;
+    FF_CUDA(c, cudaStreamSynchronize(c->stream));
+    double acc[FF_N_PASSES] = {0};
+    int64_t cnt[FF_N_PASSES] = {0};
+    for (auto& e : c->events) {
+        float t = 0.f;
+        FF_CUDA(c, cudaEventElapsedTime(&t, e.a, e.b));
+        if (e.phase == FF_PHASE_PROPAGATE && e.level >= 0 && e.level < FF_N_PASSES) {
+            acc[e.level] += t;
+            cnt[e.level] += e.n;
+        }
+        c->event_pool.push_back(e.a);
+        c->event_pool.push_back(e.b);
+    }
+    c->events.clear();
+    for (int i = 0; i < FF_N_PASSES; i++) {
+        if (ms) ms[i] = acc[i];
+        if (launches) launches[i] = cnt[i];
+    }
+    return FF_OK;
+}
+
 ff_status ff_work_counts(ff_ctx* c, int w, int h, int64_t* pixel_iters, int64_t* pixels) {
     if (!c || w < 1 || h < 1 || w > kMaxDim || h > kMaxDim) return FF_ERR_ARG;
     int ws[kMaxLevels], hs[kMaxLevels];
     level_dims(w, h, c->prm.n_scales, ws, hs);
     int64_t pi = 0;
-    for (int s = 0; s < c->prm.n_scales; s++) pi += (int64_t)ws[s] * hs[s] * c->prm.iters;
+    for (int s = 0; s < c->prm.n_scales; s++)
+        for (int k = 0; k <= (s == c->prm.n_scales - 1 ? 0 : c->prm.sub_scales); k++) {
+            const int g = 1 << k;
+            pi += (int64_t)((ws[s] + g - 1) / g) * ((hs[s] + g - 1) / g) * c->prm.iters;
+        }
     if (pixel_iters) *pixel_iters = pi;
     if (pixels) *pixels = (int64_t)w * h;
     return FF_OK;
@@ -1384,6 +1604,7 @@ ff_status ff_destroy(ff_ctx* c) {
     cudaStreamSynchronize(c->stream);
     for (auto& kv : c->plans) free_plan(c, *kv.second);
     for (auto& p : c->pyrs) dev_free(c, p->mem);
+    dev_free(c, c->feat_tab);
     if (c->d_err) cudaFree(c->d_err);
     for (auto& e : c->events) {
         cudaEventDestroy(e.a);

@@ -57,8 +57,13 @@ struct PyrArgs {
     uint8_t* dst[kMaxLevels];       // level s >= 1, compact rows (3 * w[s] bytes)
     int w[kMaxLevels], h[kMaxLevels];
     int top;                        // last level computed (1..kPyrFusedTop)
+    int cta_base, bx;               // table launches: first CTA of this frame, level-1 blocks per row
 };
 void launch_pyramid(const PyrArgs& a, cudaStream_t st);
+// many frames in one launch (tab_dev: n entries in device memory, cta_base ascending)
+void launch_pyramid_tab(const PyrArgs* tab_dev, int n, int total_ctas, cudaStream_t st);
+int pyramid_blocks_x(int w1);        // level-1 blocks per row / in all of a frame with level 1 of size w1 x h1
+int pyramid_blocks(int w1, int h1);
 // kernels ff_features launches for an L-level pyramid: the fused pyramid (+ one per level past kPyrFusedTop), WHT
 inline int features_launches(int L) {
     return (L > 1 ? 1 + (L - 1 > kPyrFusedTop ? L - 1 - kPyrFusedTop : 0) : 0) + 1;
@@ -66,6 +71,8 @@ inline int features_launches(int L) {
 int wht_tiles_x(int w);
 int wht_tiles(int w, int h);
 void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st);
+// the levels of many frames in one launch (tab_dev: n entries in device memory, tile_base ascending)
+void launch_wht_tab(const WhtLevel* tab_dev, int n, int total_tiles, cudaStream_t st);
 
 // ---------------------------------------------------------------------------------------------------------
 // initial matches (exact nearest neighbour at the coarsest level)
@@ -106,12 +113,18 @@ void launch_seed_tc(const SeedTcProblem* probs_dev, int n_probs, int total_ctas,
 // ---------------------------------------------------------------------------------------------------------
 // hand-over (coarse-to-fine initialisation) and cost initialisation
 
+// A flow field lives on a grid of source pixels of its level: every pixel (g = 1), or every g-th pixel in both
+// directions (g = 2, 4: the sub-scale grids).  Grid pixel (u, v) is level pixel (g*u, g*v); flows are in level
+// pixels and may point to any pixel of the target level (lw x lh).
 struct HandoverProblem {
     const void* fa;          // cost descriptors of the source frame (WHT features or Census patterns)
     const void* fb;          // and of the target frame
-    int w, h;
-    const uint32_t* parent;  // flow of the level above (pw x ph), or null: take flow_in as is
+    int w, h;                // the grid this hand-over fills
+    int g, lw, lh;           // its stride and level size (g <= 1: every pixel, lw x lh = w x h)
+    const uint32_t* parent;  // flow of the level above or of the grid of stride 2g (pw x ph), or null: flow_in
     int pw, ph;
+    int same_level;          // 1: parent is the grid of stride 2g of this level (flow copied, target clamped);
+                             // 0: parent is the level above (flow doubled)
     const uint32_t* flow_in;
     uint32_t* flow_out;
     int32_t* cost_out;
@@ -130,11 +143,12 @@ struct PropProblem {  // one (pair, direction, level) of a propagation launch
     const int32_t* cost_in;
     uint32_t* flow_out;
     int32_t* cost_out;
-    int w, h;
+    int w, h;        // the grid propagated (the level itself unless g > 1)
+    int g, lw, lh;   // grid stride and level size (used by the grid kernels only, g > 1)
     int tiles_x;
     int t0;          // first iteration index (for the random-search hash)
     int n_iter;      // iterations fused into this launch
-    int level;
+    int level;       // stream id of the random-search hash: the level, + 8 * log2(g) on a sub-scale grid
     int dir;
     uint32_t seed;
     int rs_radius;
@@ -145,6 +159,7 @@ struct PropLaunch {
     int threads;     // CTA size: 128, 256 or 512
     int spec;        // 1: load the random candidate together with the neighbour candidates
     int cost;        // FF_COST_WHT_SAD or FF_COST_CENSUS
+    int grid;        // 1: the problems are sub-scale grids (g > 1)
 };
 constexpr size_t kMaxPropSmem = 200 * 1024;
 size_t prop_smem_bytes(int tw, int th, int n_iter);
@@ -154,7 +169,7 @@ cudaError_t seed_load_kernel();        // loads k_seed onto the current device (
 // fixed scratch array) and the kernels it launches, and returns the array's device address.
 cudaError_t noalloc_prepare(void** scratch);
 bool prop_threads_ok(int threads);
-int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost);  // resident CTAs per SM of the kernel
+int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost, bool grid = false);  // resident CTAs per SM
 // queue_dev[i] = (problem index, tile index); counter_dev must be zero when the launch starts
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st);
@@ -186,6 +201,7 @@ struct CtxView {
     uint32_t seed;
     int cost;
     void* noalloc_scratch;  // device address of ff_match_pair_noalloc's scratch array on this device
+    int sub_scales;
 };
 struct TileChoice {
     int tw, th, k, threads, spec;
@@ -230,6 +246,40 @@ __device__ __forceinline__ void grid_dependency_sync() {
 #endif
 }
 
+// Debug-bounds build (compiled with -DFF_DEBUG_BOUNDS=1; a stand-in for a memory checker): the propagation,
+// hand-over and filter kernels check every gather and shared-memory index against its buffer before the access;
+// the first violation (code, index, limit) is recorded in its translation unit's record, the access is skipped
+// (a load reads zeros) and nothing traps.  ff_sync reports a recorded violation as FF_ERR_CUDA and clears it.
+// Release builds compile every check away.
+#ifndef FF_DEBUG_BOUNDS
+#define FF_DEBUG_BOUNDS 0
+#endif
+
+__device__ __forceinline__ bool idx_ok(int* rec, int code, long long idx, long long lim) {
+#if FF_DEBUG_BOUNDS
+    if (idx >= 0 && idx < lim) return true;
+    if (atomicCAS(rec, 0, code) == 0) {
+        rec[1] = (int)idx;
+        rec[2] = (int)lim;
+    }
+    return false;
+#else
+    (void)rec, (void)code, (void)idx, (void)lim;
+    return true;
+#endif
+}
+
+// Bytes of dynamic shared memory the running launch was given (read only by debug-bounds checks).
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+    unsigned n;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(n));
+    return n;
+}
+
+// Take (read and clear) the bounds record of propagate.cu / filter.cu; rec[0] == 0: no violation.
+cudaError_t bounds_take_propagate(int rec[3]);
+cudaError_t bounds_take_filter(int rec[3]);
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -255,5 +305,7 @@ bool ctx_view(const ff_ctx* c, CtxView* out);
 bool ctx_owns_live_pyr(const ff_ctx* c, const ff_pyr* p);
 bool pyr_view(const ff_pyr* p, PyrView* out);
 TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all);
+// cudaMalloc on behalf of a context; fails as out of memory while the context's FF_OPT_TEST_FAIL_ALLOCS count lasts
+cudaError_t ctx_malloc(ff_ctx* c, void** p, size_t bytes);
 int ctx_set_error(ff_ctx* c, int status, const char* msg);
 }  // namespace ff

@@ -4,6 +4,21 @@
 
 namespace ff {
 
+// first index violation of a debug-bounds build (see idx_ok): code, index, limit
+static __device__ int g_bounds[4];
+enum : int { kBoundsBwd = 20, kBoundsSparseBwd, kBoundsSparseKey };
+
+cudaError_t bounds_take_filter(int rec[3]) {
+    int h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyFromSymbol(h, g_bounds, sizeof h);
+    if (e == cudaSuccess && h[0] != 0) {
+        const int z[4] = {0, 0, 0, 0};
+        e = cudaMemcpyToSymbol(g_bounds, z, sizeof z);
+    }
+    rec[0] = h[0], rec[1] = h[1], rec[2] = h[2];
+    return e;
+}
+
 __device__ __forceinline__ int flow_x(uint32_t f) { return (int)(int16_t)(f & 0xffffu); }
 __device__ __forceinline__ int flow_y(uint32_t f) { return ((int)f) >> 16; }
 __device__ __forceinline__ bool in_level(int x, int y, int w, int h) {
@@ -30,7 +45,7 @@ __global__ void __launch_bounds__(kSparsePx* kSparsePy)
     if (inside && (!keep || keep[y * w + x])) {
         const uint32_t f = fwd[y * w + x];
         const int fx = flow_x(f), fy = flow_y(f), qx = x + fx, qy = y + fy;
-        if (in_level(qx, qy, w, h)) {
+        if (in_level(qx, qy, w, h) && idx_ok(g_bounds, kBoundsSparseBwd, qy * w + qx, w * h)) {
             const uint32_t b = bwd[qy * w + qx];
             const long long ex = fx + flow_x(b), ey = fy + flow_y(b), e = ex * ex + ey * ey;
             if (e <= (long long)eps * eps) k = ((unsigned long long)e << 4) | (unsigned)((ty % 3) * 3 + tx % 3);
@@ -46,6 +61,7 @@ __global__ void __launch_bounds__(kSparsePx* kSparsePy)
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
+            if (!idx_ok(g_bounds, kBoundsSparseKey, (by0 + i) * kSparsePx + bx0 + j, kSparsePx * kSparsePy)) continue;
             const unsigned long long kk = key[by0 + i][bx0 + j];
             count += kk != ~0ull;
             best = kk < best ? kk : best;
@@ -66,7 +82,7 @@ void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, const uint8_t* ke
 __device__ __forceinline__ bool consistent(uint32_t f, const uint32_t* __restrict__ bwd, int x, int y, int w, int h,
                                            int eps) {
     const int fx = flow_x(f), fy = flow_y(f), qx = x + fx, qy = y + fy;
-    if (!in_level(qx, qy, w, h)) return false;
+    if (!in_level(qx, qy, w, h) || !idx_ok(g_bounds, kBoundsBwd, qy * w + qx, w * h)) return false;
     const uint32_t b = bwd[qy * w + qx];
     const long long ex = fx + flow_x(b), ey = fy + flow_y(b);
     return ex * ex + ey * ey <= (long long)eps * eps;

@@ -110,6 +110,7 @@ extern "C" ff_status ff_match_pair_noalloc(ff_ctx* c, const ff_pyr* a, const ff_
     if (dir != 0 && dir != 1) return err(FF_ERR_ARG, "dir must be 0 or 1");
     if (!flow_dev || ((uintptr_t)flow_dev & 3) || ((uintptr_t)cost_dev & 3))
         return err(FF_ERR_ARG, "flow_dev / cost_dev must be 4-byte aligned device pointers");
+    if (cv.sub_scales != 0) return err(FF_ERR_ARG, "ff_match_pair_noalloc does not run sub-scale grids");
     if (cudaSetDevice(cv.device) != cudaSuccess) return err(FF_ERR_CUDA, "cudaSetDevice failed");
     void* base = cv.noalloc_scratch;  // looked up by ff_create on this device
     if (!base) return err(FF_ERR_CUDA, "the scratch array of ff_match_pair_noalloc was not set up");

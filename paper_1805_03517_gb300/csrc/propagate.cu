@@ -20,6 +20,24 @@
 
 namespace ff {
 
+// first index violation of a debug-bounds build (see idx_ok): code, index, limit
+static __device__ int g_bounds[4];
+
+cudaError_t bounds_take_propagate(int rec[3]) {
+    int h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyFromSymbol(h, g_bounds, sizeof h);
+    if (e == cudaSuccess && h[0] != 0) {
+        const int z[4] = {0, 0, 0, 0};
+        e = cudaMemcpyToSymbol(g_bounds, z, sizeof z);
+    }
+    rec[0] = h[0], rec[1] = h[1], rec[2] = h[2];
+    return e;
+}
+
+// Bounds codes of this file's checks.
+enum : int { kBoundsOwn = 1, kBoundsCand1, kBoundsCand2, kBoundsRandom, kBoundsSpec, kBoundsSmemOwn, kBoundsSmemN1,
+             kBoundsSmemN2, kBoundsTileRead, kBoundsTileSmem, kBoundsTileWrite, kBoundsParent, kBoundsHandoverDesc };
+
 __device__ __forceinline__ int flow_x(uint32_t f) { return (int)(int16_t)(f & 0xffffu); }
 __device__ __forceinline__ int flow_y(uint32_t f) { return ((int)f) >> 16; }
 __device__ __forceinline__ uint32_t pack_flow(int dx, int dy) { return (uint32_t)(dx & 0xffff) | ((uint32_t)dy << 16); }
@@ -84,13 +102,24 @@ struct CostCensus {  // Hamming distance of the three 48-bit Census patterns (on
     }
 };
 
-// Cost of the descriptor at (x, y) of fa against (tx, ty) of fb (both inside the level).
+// A descriptor load that a debug-bounds build checks against the map's n descriptors (zeros if outside).
 template <class C>
-__device__ __forceinline__ int cost_at(const void* __restrict__ fa, const void* __restrict__ fb, int w, int x, int y,
-                                       int tx, int ty) {
+__device__ __forceinline__ void load_chk(const void* __restrict__ f, int idx, int n, int code, uint32_t (&d)[C::kWords]) {
+    if (idx_ok(g_bounds, code, idx, n)) {
+        C::load(f, idx, d);
+    } else {
+#pragma unroll
+        for (int k = 0; k < C::kWords; k++) d[k] = 0;
+    }
+}
+
+// Cost of the descriptor at (x, y) of fa against (tx, ty) of fb (both inside the w x h level).
+template <class C>
+__device__ __forceinline__ int cost_at(const void* __restrict__ fa, const void* __restrict__ fb, int w, int h, int x,
+                                       int y, int tx, int ty) {
     uint32_t a[C::kWords], b[C::kWords];
-    C::load(fa, feat_index(x, y, w), a);
-    C::load(fb, feat_index(tx, ty, w), b);
+    load_chk<C>(fa, feat_index(x, y, w), w * h, kBoundsHandoverDesc, a);
+    load_chk<C>(fb, feat_index(tx, ty, w), w * h, kBoundsHandoverDesc, b);
     C::prep(a);
     return C::dist(a, b);
 }
@@ -110,18 +139,25 @@ __global__ __launch_bounds__(256) void k_handover(const HandoverProblem* __restr
         }
         const HandoverProblem& P = probs[lo];
         int p = (int)(i - P.pix_base);
-        int x = p % P.w, y = p / P.w;
+        const int u = p % P.w, v = p / P.w;
+        const bool grid = P.g > 1;
+        const int g = grid ? P.g : 1, lw = grid ? P.lw : P.w, lh = grid ? P.lh : P.h;
+        const int x = g * u, y = g * v;  // level coordinates
         uint32_t f;
-        if (P.parent) {
+        if (P.parent && P.same_level) {  // from the grid of stride 2g: the same flow, its target clamped
+            const int pi = min(v >> 1, P.ph - 1) * P.pw + min(u >> 1, P.pw - 1);
+            uint32_t pf = idx_ok(g_bounds, kBoundsParent, pi, P.pw * P.ph) ? P.parent[pi] : 0u;
+            f = pack_flow(min(max(x + flow_x(pf), 0), lw - 1) - x, min(max(y + flow_y(pf), 0), lh - 1) - y);
+        } else if (P.parent) {  // from the level above: twice the parent pixel's flow
             int px = min(x >> 1, P.pw - 1), py = min(y >> 1, P.ph - 1);
-            uint32_t pf = P.parent[py * P.pw + px];
+            uint32_t pf = idx_ok(g_bounds, kBoundsParent, py * P.pw + px, P.pw * P.ph) ? P.parent[py * P.pw + px] : 0u;
             f = pack_flow(2 * flow_x(pf), 2 * flow_y(pf));
         } else {
             f = P.flow_in[p];
         }
         int tx = x + flow_x(f), ty = y + flow_y(f);
         int c = INT_MAX;  // unreachable for valid inputs: a handed-over flow always lands inside the level
-        if (in_level(tx, ty, P.w, P.h)) c = cost_at<C>(P.fa, P.fb, P.w, x, y, tx, ty);
+        if (in_level(tx, ty, lw, lh)) c = cost_at<C>(P.fa, P.fb, lw, lh, x, y, tx, ty);
         P.flow_out[p] = f;
         P.cost_out[p] = c;
     }
@@ -180,10 +216,12 @@ __device__ __forceinline__ bool region_pixel(int i, int HW, int rx0, int ry0, in
 // from the new flow.  Either way the candidate evaluated is the one the schedule defines, so results are
 // identical.  (Fetching it early only into a buffer no neighbour needs, without SPEC, measured 16 % slower on
 // the 1242x375 pair.)
-template <class C, bool SPEC>
+template <class C, bool SPEC, bool GRID>
 __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& G, uint32_t* sflow, int32_t* scost,
                                           int j, int rem, uint32_t k1) {
-    const int w = P.w, h = P.h;
+    const int w = P.w, h = P.h;  // the grid (the level itself unless GRID)
+    // GRID: grid pixel (x, y) is level pixel (g*x, g*y) of a lw x lh level; flows and targets are in level pixels
+    const int g = GRID ? P.g : 1, lw = GRID ? P.lw : w, lh = GRID ? P.lh : h;
     const int d = j >> 1, colour = j & 1;
     int rx0, ry0, rx1, ry1;
     halfsweep_region(G, w, h, j, rem, rx0, ry0, rx1, ry1);
@@ -195,21 +233,25 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
         int x, y;
         if (!region_pixel(i, HW, rx0, ry0, rx1, colour, x, y)) continue;
         const int sidx = (y - G.ly0) * G.RW + (x - G.lx0);
+        const int n_s = G.RW * G.RH, n_d = lw * lh;  // shared-memory entries, descriptors of the level
+        if (!idx_ok(g_bounds, kBoundsSmemOwn, sidx, n_s)) continue;
         uint32_t cur = sflow[sidx];
         int c = scost[sidx];
         const int n1x = x + ((d & 1) ? 1 : -1);
         const int n2y = y + ((d & 2) ? 1 : -1);
         const bool v1 = (unsigned)n1x < (unsigned)w;
         const bool v2 = (unsigned)n2y < (unsigned)h;
-        const uint32_t f1 = v1 ? sflow[sidx + (n1x - x)] : 0u;
-        const uint32_t f2 = v2 ? sflow[sidx + (n2y - y) * G.RW] : 0u;
+        const uint32_t f1 = v1 && idx_ok(g_bounds, kBoundsSmemN1, sidx + (n1x - x), n_s) ? sflow[sidx + (n1x - x)] : 0u;
+        const uint32_t f2 =
+            v2 && idx_ok(g_bounds, kBoundsSmemN2, sidx + (n2y - y) * G.RW, n_s) ? sflow[sidx + (n2y - y) * G.RW] : 0u;
         // a candidate equal to the current flow (or to an already tried one) cannot be strictly cheaper
-        const bool e1 = v1 && f1 != cur && in_level(x + flow_x(f1), y + flow_y(f1), w, h);
-        const bool e2 = v2 && f2 != cur && !(v1 && f2 == f1) && in_level(x + flow_x(f2), y + flow_y(f2), w, h);
+        const int X = g * x, Y = g * y;  // level coordinates
+        const bool e1 = v1 && f1 != cur && in_level(X + flow_x(f1), Y + flow_y(f1), lw, lh);
+        const bool e2 = v2 && f2 != cur && !(v1 && f2 == f1) && in_level(X + flow_x(f2), Y + flow_y(f2), lw, lh);
         if (!(e1 || e2 || d >= 1)) continue;
         int ox = 0, oy = 0;
         if (d >= 1) {
-            const uint32_t k2 = mix32(k1 ^ ((uint32_t)y * 65536u + (uint32_t)x));
+            const uint32_t k2 = mix32(k1 ^ ((uint32_t)Y * 65536u + (uint32_t)X));
             ox = (int)(mix32(k2 ^ (uint32_t)(2 * d)) % span) - R;
             oy = (int)(mix32(k2 ^ (uint32_t)(2 * d + 1)) % span) - R;
         }
@@ -218,12 +260,13 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
         // issue every independent load (own descriptor, neighbour candidates, speculative random) before compute
         uint32_t a[C::kWords], b1[C::kWords], b2[C::kWords];
         uint32_t b3[SPEC ? C::kWords : 1];
-        C::load(P.fa, feat_index(x, y, w), a);
-        if (e1) C::load(P.fb, feat_index(x + flow_x(f1), y + flow_y(f1), w), b1);
-        if (e2) C::load(P.fb, feat_index(x + flow_x(f2), y + flow_y(f2), w), b2);
+        load_chk<C>(P.fa, feat_index(X, Y, lw), n_d, kBoundsOwn, a);
+        if (e1) load_chk<C>(P.fb, feat_index(X + flow_x(f1), Y + flow_y(f1), lw), n_d, kBoundsCand1, b1);
+        if (e2) load_chk<C>(P.fb, feat_index(X + flow_x(f2), Y + flow_y(f2), lw), n_d, kBoundsCand2, b2);
         if constexpr (SPEC) {
             const int sx = flow_x(cur) + ox, sy = flow_y(cur) + oy;
-            if (rnd && in_level(x + sx, y + sy, w, h)) C::load(P.fb, feat_index(x + sx, y + sy, w), b3);
+            if (rnd && in_level(X + sx, Y + sy, lw, lh))
+                load_chk<C>(P.fb, feat_index(X + sx, Y + sy, lw), n_d, kBoundsSpec, b3);
         }
         C::prep(a);
         if (e1) {
@@ -236,17 +279,17 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
         }
         if (rnd) {
             const int fx = flow_x(cur) + ox, fy = flow_y(cur) + oy;
-            if (in_level(x + fx, y + fy, w, h)) {
+            if (in_level(X + fx, Y + fy, lw, lh)) {
                 int s3;
                 if constexpr (SPEC) {
                     if (cur == cur0) {
                         s3 = C::dist(a, b3);  // same target as speculated (which was then in the level)
                     } else {
-                        C::load(P.fb, feat_index(x + fx, y + fy, w), b1);
+                        load_chk<C>(P.fb, feat_index(X + fx, Y + fy, lw), n_d, kBoundsRandom, b1);
                         s3 = C::dist(a, b1);
                     }
                 } else {
-                    C::load(P.fb, feat_index(x + fx, y + fy, w), b1);
+                    load_chk<C>(P.fb, feat_index(X + fx, Y + fy, lw), n_d, kBoundsRandom, b1);
                     s3 = C::dist(a, b1);
                 }
                 if (s3 < c) { cur = pack_flow(fx, fy); c = s3; }
@@ -258,7 +301,7 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
 }
 
 // One tile of one problem: load the tile and its halo, run n_iter iterations in shared memory, write the tile.
-template <class C, bool SPEC>
+template <class C, bool SPEC, bool GRID>
 __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, const PropLaunch& L, uint32_t* smem) {
     const int w = P.w, h = P.h;
     TileGeom G;
@@ -277,8 +320,11 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
     for (int i = threadIdx.x; i < G.RW * G.RH; i += blockDim.x) {
         int r = i / G.RW, c = i - r * G.RW;
         size_t g = (size_t)(G.ly0 + r) * w + G.lx0 + c;
-        sflow[i] = P.flow_in[g];
-        scost[i] = P.cost_in[g];
+        // flow and cost of the region (2 words per pixel) must fit the launch's dynamic shared memory
+        const bool ok = idx_ok(g_bounds, kBoundsTileRead, (long long)g, (long long)w * h) &&
+                        (!FF_DEBUG_BOUNDS || idx_ok(g_bounds, kBoundsTileSmem, 2 * G.RW * G.RH - 1, dyn_smem_bytes() / 4));
+        sflow[i] = ok ? P.flow_in[g] : 0u;
+        scost[i] = ok ? P.cost_in[g] : 0;
     }
     __syncthreads();
     for (int it = 0; it < P.n_iter; it++) {
@@ -286,7 +332,7 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
         const int rem = kHaloPerIter * (P.n_iter - 1 - it);
         const uint32_t k1 = mix32(P.seed ^ mix32((uint32_t)P.dir * 65536u + (uint32_t)P.level * 256u + (uint32_t)t));
         for (int j = 0; j < 8; j++) {
-            halfsweep<C, SPEC>(P, G, sflow, scost, j, rem, k1);
+            halfsweep<C, SPEC, GRID>(P, G, sflow, scost, j, rem, k1);
             __syncthreads();
         }
     }
@@ -295,6 +341,9 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
         int r = i / TW, c = i - r * TW;
         int sidx = (G.y0 + r - G.ly0) * G.RW + (G.x0 + c - G.lx0);
         size_t g = (size_t)(G.y0 + r) * w + G.x0 + c;
+        if (!idx_ok(g_bounds, kBoundsTileWrite, (long long)g, (long long)w * h) ||
+            !idx_ok(g_bounds, kBoundsTileSmem, sidx, G.RW * G.RH))
+            continue;
         P.flow_out[g] = sflow[sidx];
         P.cost_out[g] = scost[sidx];
     }
@@ -302,8 +351,9 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
 
 // Persistent launch: each CTA takes tiles from the launch's queue (an atomic counter, zeroed before the launch)
 // until it is empty, so the last wave has no idle tail.  queue[i] = (problem index, tile index in problem).
-// Instantiated for 128, 256 and 512 threads, with and without speculative random-candidate loads, per cost.
-template <int THREADS, bool SPEC, class C>
+// Instantiated for 128, 256 and 512 threads, with and without speculative random-candidate loads, per cost, for
+// levels and for sub-scale grids (GRID).
+template <int THREADS, bool SPEC, class C, bool GRID = false>
 __global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate(
     const PropProblem* __restrict__ probs, const int2* __restrict__ queue, int n_tiles, int* __restrict__ counter,
     PropLaunch L) {
@@ -316,21 +366,29 @@ __global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate
         const int q = s_next;
         if (q >= n_tiles) return;
         const int2 e = queue[q];
-        propagate_tile<C, SPEC>(probs[e.x], e.y, L, smem);
+        propagate_tile<C, SPEC, GRID>(probs[e.x], e.y, L, smem);
         __syncthreads();
     }
 }
 
 using PropKernel = void (*)(const PropProblem*, const int2*, int, int*, PropLaunch);
 
-template <class C>
-PropKernel prop_kernel_c(int threads, bool spec) {
-    if (spec) return threads == 128 ? k_propagate<128, true, C> : threads == 512 ? k_propagate<512, true, C> : k_propagate<256, true, C>;
-    return threads == 128 ? k_propagate<128, false, C> : threads == 512 ? k_propagate<512, false, C> : k_propagate<256, false, C>;
+template <class C, bool SPEC, bool GRID>
+PropKernel prop_kernel_t(int threads) {
+    return threads == 128   ? k_propagate<128, SPEC, C, GRID>
+           : threads == 512 ? k_propagate<512, SPEC, C, GRID>
+                            : k_propagate<256, SPEC, C, GRID>;
 }
 
-PropKernel prop_kernel(int threads, bool spec, int cost) {
-    return cost == FF_COST_CENSUS ? prop_kernel_c<CostCensus>(threads, spec) : prop_kernel_c<CostSad>(threads, spec);
+template <class C>
+PropKernel prop_kernel_c(int threads, bool spec, bool grid) {
+    if (grid) return spec ? prop_kernel_t<C, true, true>(threads) : prop_kernel_t<C, false, true>(threads);
+    return spec ? prop_kernel_t<C, true, false>(threads) : prop_kernel_t<C, false, false>(threads);
+}
+
+PropKernel prop_kernel(int threads, bool spec, int cost, bool grid = false) {
+    return cost == FF_COST_CENSUS ? prop_kernel_c<CostCensus>(threads, spec, grid)
+                                  : prop_kernel_c<CostSad>(threads, spec, grid);
 }
 
 cudaError_t init_kernel_attributes() {
@@ -340,19 +398,22 @@ cudaError_t init_kernel_attributes() {
     if (e0 != cudaSuccess) return e0;
     for (int cost : {FF_COST_WHT_SAD, FF_COST_CENSUS})
         for (int t : {128, 256, 512})
-            for (bool sp : {false, true}) {
-                cudaError_t e = cudaFuncSetAttribute(prop_kernel(t, sp, cost),
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
-                if (e != cudaSuccess) return e;
-            }
+            for (bool sp : {false, true})
+                for (bool grid : {false, true}) {
+                    cudaError_t e = cudaFuncSetAttribute(prop_kernel(t, sp, cost, grid),
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)kMaxPropSmem);
+                    if (e != cudaSuccess) return e;
+                }
     return cudaSuccess;
 }
 
 bool prop_threads_ok(int threads) { return threads == 128 || threads == 256 || threads == 512; }
 
-int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost) {
+int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost, bool grid) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prop_kernel(threads, spec, cost), threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prop_kernel(threads, spec, cost, grid),
+                                                      threads, smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -363,8 +424,8 @@ int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost) {
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st) {
     size_t smem = prop_smem_bytes(L.tw, L.th, L.max_iter);
-    launch_k(prop_kernel(L.threads, L.spec != 0, L.cost), dim3(grid), dim3(L.threads), smem, st, probs_dev, queue_dev,
-             n_tiles, counter_dev, L);
+    launch_k(prop_kernel(L.threads, L.spec != 0, L.cost, L.grid != 0), dim3(grid), dim3(L.threads),
+             smem, st, probs_dev, queue_dev, n_tiles, counter_dev, L);
 }
 
 }  // namespace ff

@@ -48,12 +48,13 @@ struct Req {
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
     int64_t footprint = 0;
-    uint32_t* flow[2][kMaxLevels][2] = {};
-    int32_t* cost[2][kMaxLevels][2] = {};
+    // per direction, level and grid (k = 0: the level; k = 1, 2: its sub-scale grids of stride 2^k), ping-pong
+    uint32_t* flow[2][kMaxLevels][3][2] = {};
+    int32_t* cost[2][kMaxLevels][3][2] = {};
     int32_t* dist[2] = {};
-    TileChoice cfg[kMaxLevels] = {};
-    int n_chunks[kMaxLevels] = {};
-    int level = 0, chunk = 0, cur[2] = {0, 0};
+    TileChoice cfg[kMaxLevels][3] = {};
+    int n_chunks[kMaxLevels][3] = {};
+    int level = 0, grid = 0, chunk = 0, cur[2] = {0, 0};  // the pass in progress: (level, grid), its next chunk
     bool started = false;
     int64_t done_tick = -1;
     bool counted = false;  // footprint added to the server's bytes in use
@@ -86,11 +87,16 @@ const void* cost_desc(const PyrView& v, int level, int cost) {
     return cost == FF_COST_CENSUS ? static_cast<const void*>(v.cen[level]) : static_cast<const void*>(v.feat[level]);
 }
 
-size_t scratch_need(int w, int h, int L) {
+int grid_dim(int v, int k) { return (v + (1 << k) - 1) >> k; }
+// sub-scale grids of level s of an L-level pyramid (the coarsest level has none)
+int grids_of(int s, int L, int sub_scales) { return s == L - 1 ? 0 : sub_scales; }
+
+size_t scratch_need(int w, int h, int L, int sub_scales) {
     size_t b = 0;
     int ws = w, hs = h;
     for (int s = 0; s < L; s++) {
-        b += 2 * 4 * a256((size_t)ws * hs * 4);
+        for (int k = 0; k <= grids_of(s, L, sub_scales); k++)
+            b += 2 * 4 * a256((size_t)grid_dim(ws, k) * grid_dim(hs, k) * 4);
         if (s + 1 < L) {
             ws = std::max(1, ws / 2);
             hs = std::max(1, hs / 2);
@@ -143,7 +149,8 @@ ff_status ring_reserve(ff_server* s, RingSlot& r, size_t bytes) {
     r.host = nullptr;
     r.dev = nullptr;
     size_t cap = std::max(bytes, (size_t)1 << 20) * 2;
-    if (cudaMallocHost(&r.host, cap) != cudaSuccess || cudaMalloc(&r.dev, cap) != cudaSuccess) {
+    if (cudaMallocHost(&r.host, cap) != cudaSuccess ||
+        ctx_malloc(s->ctx, reinterpret_cast<void**>(&r.dev), cap) != cudaSuccess) {
         cudaGetLastError();
         return srv_fail(s, FF_ERR_OOM, "tick table allocation failed");
     }
@@ -153,13 +160,13 @@ ff_status ring_reserve(ff_server* s, RingSlot& r, size_t bytes) {
 
 // Scratch of a request: per direction and level two flow and two cost buffers, plus seed distances.
 ff_status take_scratch(ff_server* s, Req& q) {
-    size_t need = scratch_need(q.A.w, q.A.h, q.L);
+    size_t need = scratch_need(q.A.w, q.A.h, q.L, s->cv.sub_scales);
     auto it = s->free_scratch.find(need);
     void* p = nullptr;
     if (it != s->free_scratch.end()) {
         p = it->second;
         s->free_scratch.erase(it);
-    } else if (cudaMalloc(&p, need) != cudaSuccess) {
+    } else if (ctx_malloc(s->ctx, &p, need) != cudaSuccess) {
         cudaGetLastError();
         return srv_fail(s, FF_ERR_OOM, "scratch allocation failed");
     }
@@ -168,15 +175,16 @@ ff_status take_scratch(ff_server* s, Req& q) {
     char* b = static_cast<char*>(p);
     size_t off = 0;
     for (int d = 0; d < 2; d++)
-        for (int l = 0; l < q.L; l++) {
-            size_t n = (size_t)q.A.ws[l] * q.A.hs[l];
-            for (int k = 0; k < 2; k++) {
-                q.flow[d][l][k] = reinterpret_cast<uint32_t*>(b + off);
-                off += a256(n * 4);
-                q.cost[d][l][k] = reinterpret_cast<int32_t*>(b + off);
-                off += a256(n * 4);
+        for (int l = 0; l < q.L; l++)
+            for (int g = 0; g <= grids_of(l, q.L, s->cv.sub_scales); g++) {
+                size_t n = (size_t)grid_dim(q.A.ws[l], g) * grid_dim(q.A.hs[l], g);
+                for (int k = 0; k < 2; k++) {
+                    q.flow[d][l][g][k] = reinterpret_cast<uint32_t*>(b + off);
+                    off += a256(n * 4);
+                    q.cost[d][l][g][k] = reinterpret_cast<int32_t*>(b + off);
+                    off += a256(n * 4);
+                }
             }
-        }
     for (int d = 0; d < 2; d++) {
         q.dist[d] = reinterpret_cast<int32_t*>(b + off);
         off += a256((size_t)q.A.n_coarse * 4);
@@ -218,12 +226,14 @@ ff_status admit(ff_server* s) {
         q.counted = true;
         // launch configurations tuned for one pair at light load, for launches shared by many pairs under load
         const int n_dirs = (int)s->active.size() + 1 > kWholeLevelMaxActive ? kLoadedDirs : 2;
-        for (int l = 0; l < q.L; l++) {
-            q.cfg[l] = ctx_level_choice(s->ctx, l, q.A.ws[l], q.A.hs[l], n_dirs,
-                                        (int64_t)n_dirs * q.A.ws[l] * q.A.hs[l]);
-            q.n_chunks[l] = (q.T + q.cfg[l].k - 1) / q.cfg[l].k;
-        }
+        for (int l = 0; l < q.L; l++)
+            for (int g = 0; g <= grids_of(l, q.L, s->cv.sub_scales); g++) {  // tuning entries: pass l + 8g
+                const int gw = grid_dim(q.A.ws[l], g), gh = grid_dim(q.A.hs[l], g);
+                q.cfg[l][g] = ctx_level_choice(s->ctx, l + kMaxLevels * g, gw, gh, n_dirs, (int64_t)n_dirs * gw * gh);
+                q.n_chunks[l][g] = (q.T + q.cfg[l][g].k - 1) / q.cfg[l][g].k;
+            }
         q.level = q.L - 1;
+        q.grid = 0;
         q.chunk = 0;
         s->active.push_back(std::move(s->queued.front()));
         s->queued.pop_front();
@@ -235,10 +245,10 @@ ff_status admit(ff_server* s) {
 // Propagation launches of a tick are grouped by phase (the position of a chunk among the chunks one request
 // runs in this tick: a request's chunk i + 1 reads what its chunk i wrote) and by launch configuration.
 struct PropGroupKey {
-    int phase, tw, th, n_iter, threads, spec;
+    int phase, tw, th, n_iter, threads, spec, grid;
     bool operator<(const PropGroupKey& o) const {
-        return std::tie(phase, tw, th, n_iter, threads, spec) <
-               std::tie(o.phase, o.tw, o.th, o.n_iter, o.threads, o.spec);
+        return std::tie(phase, tw, th, n_iter, threads, spec, grid) <
+               std::tie(o.phase, o.tw, o.th, o.n_iter, o.threads, o.spec, o.grid);
     }
 };
 
@@ -276,7 +286,7 @@ ff_status tick(ff_server* s) {
                 sp.normB = Y.seed_norm;
                 sp.n = X.n_coarse;
                 sp.w = X.ws[L - 1];
-                sp.flow = q.flow[d][L - 1][0];
+                sp.flow = q.flow[d][L - 1][0][0];
                 sp.dist = q.dist[d];
                 sp.warp_base = seed_tiles;
                 seed_tiles += (sp.n + 15) / 16;
@@ -284,62 +294,74 @@ ff_status tick(ff_server* s) {
             }
             q.started = true;
         }
-        if (q.chunk == 0) {  // hand-over into this level (the seed's cost at the coarsest level)
+        const int gk = q.grid, k_first = grids_of(sl, L, s->cv.sub_scales);
+        if (q.chunk == 0) {  // hand-over into this level or grid (the seed's cost at the coarsest level)
             for (int d = 0; d < 2; d++) {
                 const PyrView& X = d == 0 ? q.A : q.B;
                 const PyrView& Y = d == 0 ? q.B : q.A;
                 HandoverProblem hp{};
                 hp.fa = cost_desc(X, sl, s->cv.cost);
                 hp.fb = cost_desc(Y, sl, s->cv.cost);
-                hp.w = X.ws[sl];
-                hp.h = X.hs[sl];
+                hp.w = grid_dim(X.ws[sl], gk);
+                hp.h = grid_dim(X.hs[sl], gk);
+                hp.g = 1 << gk;
+                hp.lw = X.ws[sl];
+                hp.lh = X.hs[sl];
                 if (sl == L - 1) {
                     hp.parent = nullptr;
-                    hp.flow_in = q.flow[d][sl][0];
-                } else {
-                    hp.parent = q.flow[d][sl + 1][q.cur[d]];
+                    hp.flow_in = q.flow[d][sl][0][0];
+                } else if (gk == k_first) {  // from the level above
+                    hp.parent = q.flow[d][sl + 1][0][q.cur[d]];
                     hp.pw = X.ws[sl + 1];
                     hp.ph = X.hs[sl + 1];
+                } else {  // from the sparser grid of this level
+                    hp.parent = q.flow[d][sl][gk + 1][q.cur[d]];
+                    hp.pw = grid_dim(X.ws[sl], gk + 1);
+                    hp.ph = grid_dim(X.hs[sl], gk + 1);
+                    hp.same_level = 1;
                 }
-                hp.flow_out = q.flow[d][sl][0];
-                hp.cost_out = q.cost[d][sl][0];
+                hp.flow_out = q.flow[d][sl][gk][0];
+                hp.cost_out = q.cost[d][sl][gk][0];
                 hp.pix_base = ho_pix;
                 ho_pix += (int64_t)hp.w * hp.h;
                 hos.push_back(hp);
                 q.cur[d] = 0;
             }
         }
-        const TileChoice c = q.cfg[sl];
-        const int n_run = whole_level ? q.n_chunks[sl] - q.chunk : 1;
+        const TileChoice c = q.cfg[sl][gk];
+        const int n_run = whole_level ? q.n_chunks[sl][gk] - q.chunk : 1;
         for (int phase = 0; phase < n_run; phase++) {
             const int chunk = q.chunk + phase;
             const int t0 = chunk * c.k, n_iter = std::min(c.k, T - t0);
-            const bool last = sl == 0 && chunk == q.n_chunks[sl] - 1;
-            auto& grp = groups[PropGroupKey{phase, c.tw, c.th, n_iter, c.threads, c.spec}];
+            const bool last = sl == 0 && gk == 0 && chunk == q.n_chunks[sl][gk] - 1;
+            auto& grp = groups[PropGroupKey{phase, c.tw, c.th, n_iter, c.threads, c.spec, gk > 0 ? 1 : 0}];
             for (int d = 0; d < 2; d++) {
                 const PyrView& X = d == 0 ? q.A : q.B;
                 const PyrView& Y = d == 0 ? q.B : q.A;
                 PropProblem pp{};
                 pp.fa = cost_desc(X, sl, s->cv.cost);
                 pp.fb = cost_desc(Y, sl, s->cv.cost);
-                pp.w = X.ws[sl];
-                pp.h = X.hs[sl];
+                pp.w = grid_dim(X.ws[sl], gk);
+                pp.h = grid_dim(X.hs[sl], gk);
+                pp.g = 1 << gk;
+                pp.lw = X.ws[sl];
+                pp.lh = X.hs[sl];
                 const int in = q.cur[d], out = in ^ 1;
-                pp.flow_in = q.flow[d][sl][in];
-                pp.cost_in = q.cost[d][sl][in];
+                pp.flow_in = q.flow[d][sl][gk][in];
+                pp.cost_in = q.cost[d][sl][gk][in];
                 int32_t* user_cost = d == 0 ? q.io.cost_fwd : q.io.cost_bwd;
                 if (last) {
                     pp.flow_out = reinterpret_cast<uint32_t*>(d == 0 ? q.io.flow_fwd : q.io.flow_bwd);
-                    pp.cost_out = user_cost ? user_cost : q.cost[d][sl][out];
+                    pp.cost_out = user_cost ? user_cost : q.cost[d][sl][gk][out];
                 } else {
-                    pp.flow_out = q.flow[d][sl][out];
-                    pp.cost_out = q.cost[d][sl][out];
+                    pp.flow_out = q.flow[d][sl][gk][out];
+                    pp.cost_out = q.cost[d][sl][gk][out];
                 }
                 q.cur[d] = out;
                 pp.tiles_x = (pp.w + c.tw - 1) / c.tw;
                 pp.t0 = t0;
                 pp.n_iter = n_iter;
-                pp.level = sl;
+                pp.level = sl + kMaxLevels * gk;  // the hash stream of this level or grid
                 pp.dir = d;
                 pp.seed = s->cv.seed;
                 pp.rs_radius = s->cv.rs_radius;
@@ -347,13 +369,17 @@ ff_status tick(ff_server* s) {
             }
         }
         q.chunk += n_run;
-        if (q.chunk == q.n_chunks[sl]) {
+        if (q.chunk == q.n_chunks[sl][gk] && gk > 0) {  // on to the next finer grid of this level
+            q.grid--;
+            q.chunk = 0;
+        } else if (q.chunk == q.n_chunks[sl][gk]) {
             if (sl == 0) {
                 cons.push_back({reinterpret_cast<const uint32_t*>(q.io.flow_fwd),
                                 reinterpret_cast<const uint32_t*>(q.io.flow_bwd), q.A.w, q.A.h, q.io.mask});
                 finished.push_back(ri);
             } else {
                 q.level--;
+                q.grid = grids_of(q.level, L, s->cv.sub_scales);
                 q.chunk = 0;
             }
         }
@@ -400,8 +426,9 @@ ff_status tick(ff_server* s) {
         for (auto& pr : kv.second) hp[pi++] = pr.first;
         const size_t smem = prop_smem_bytes(k.tw, k.th, k.n_iter);
         const int nq = (int)(qi - q0);
-        pls.push_back({PropLaunch{k.tw, k.th, k.n_iter, k.threads, k.spec, s->cv.cost}, q0, nq,
-                       std::min(nq, prop_blocks_per_sm(smem, k.threads, k.spec != 0, s->cv.cost) * s->cv.n_sms),
+        pls.push_back({PropLaunch{k.tw, k.th, k.n_iter, k.threads, k.spec, s->cv.cost, k.grid}, q0, nq,
+                       std::min(nq, prop_blocks_per_sm(smem, k.threads, k.spec != 0, s->cv.cost, k.grid != 0) *
+                                        s->cv.n_sms),
                        k.phase});
     }
     cudaStream_t stm = s->cv.stream;
@@ -516,7 +543,7 @@ ff_status ff_server_submit(ff_server* s, uint64_t id, const ff_request* req) {
     q->id = id;
     q->io = *req;
     q->footprint = 2 * pyr_bytes(req->w, req->h, s->cv.n_scales, s->cv.cost == FF_COST_CENSUS) +
-                   (int64_t)scratch_need(req->w, req->h, s->cv.n_scales);
+                   (int64_t)scratch_need(req->w, req->h, s->cv.n_scales, s->cv.sub_scales);
     if (q->footprint > s->budget) return srv_fail(s, FF_ERR_ARG, "request larger than the memory budget");
     s->queued.push_back(std::move(q));
     return FF_OK;
@@ -564,6 +591,19 @@ ff_status ff_server_poll(ff_server* s, int wait, uint64_t* ids, int max_ids, int
     if (n_done) *n_done = n;
     if (e != cudaSuccess && e != cudaErrorNotReady) return srv_fail(s, FF_ERR_CUDA, cudaGetErrorString(e));
     return FF_OK;
+}
+
+ff_status ff_server_cancel(ff_server* s, uint64_t id) {
+    if (!s) return FF_ERR_ARG;
+    for (auto it = s->queued.begin(); it != s->queued.end(); ++it)
+        if ((*it)->id == id) {  // nothing of a queued request is on the device yet
+            s->queued.erase(it);
+            return FF_OK;
+        }
+    for (auto* list : {&s->active, &s->finishing})
+        for (auto& q : *list)
+            if (q->id == id) return srv_fail(s, FF_ERR_BUSY, "request already admitted: it completes normally");
+    return srv_fail(s, FF_ERR_ARG, "no such request");
 }
 
 ff_status ff_server_stats(ff_server* s, int64_t* ticks, int64_t* launches, int64_t* bytes_in_use) {

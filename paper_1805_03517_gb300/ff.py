@@ -16,10 +16,12 @@ from dataclasses import dataclass
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libff.so")
+# FF_LIBRARY selects another build of the same library (the debug-bounds build, _lib/libff_debug.so)
+LIB_PATH = os.environ.get("FF_LIBRARY", LIB_PATH)
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "ff.h")
 
 FF_OK, FF_ERR_ARG, FF_ERR_OOM, FF_ERR_CUDA, FF_ERR_TIMEOUT, FF_ERR_BUSY = range(6)
-FF_OPT_SEED_KERNEL, FF_OPT_WAIT_LIMIT, FF_OPT_TEST_WITHHOLD_COPIES = 1, 2, 3
+FF_OPT_SEED_KERNEL, FF_OPT_WAIT_LIMIT, FF_OPT_TEST_WITHHOLD_COPIES, FF_OPT_TEST_FAIL_ALLOCS = 1, 2, 3, 4
 FF_SEED_MMA_SYNC, FF_SEED_TCGEN05 = 0, 1
 FF_COST_WHT_SAD, FF_COST_CENSUS = 0, 1
 STATUS_NAMES = {0: "FF_OK", 1: "FF_ERR_ARG", 2: "FF_ERR_OOM", 3: "FF_ERR_CUDA", 4: "FF_ERR_TIMEOUT", 5: "FF_ERR_BUSY"}
@@ -35,7 +37,8 @@ class FFError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("n_scales", ctypes.c_int), ("iters", ctypes.c_int), ("patch", ctypes.c_int),
                 ("n_coef", ctypes.c_int), ("rs_radius", ctypes.c_int), ("eps", ctypes.c_int),
-                ("seed", ctypes.c_uint32), ("rs_radius2", ctypes.c_int), ("cost", ctypes.c_int)]
+                ("seed", ctypes.c_uint32), ("rs_radius2", ctypes.c_int), ("cost", ctypes.c_int),
+                ("sub_scales", ctypes.c_int)]
 
 
 class PairJob(ctypes.Structure):
@@ -48,6 +51,10 @@ class Request(ctypes.Structure):
     _fields_ = [("rgb_a", ctypes.c_void_p), ("rgb_b", ctypes.c_void_p), ("w", ctypes.c_int), ("h", ctypes.c_int),
                 ("pitch_bytes", ctypes.c_int), ("flow_fwd", ctypes.c_void_p), ("flow_bwd", ctypes.c_void_p),
                 ("cost_fwd", ctypes.c_void_p), ("cost_bwd", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("rgb_dev", ctypes.c_void_p), ("w", ctypes.c_int), ("h", ctypes.c_int), ("pitch_bytes", ctypes.c_int)]
 
 
 class Tuning(ctypes.Structure):
@@ -83,6 +90,7 @@ def lib():
         "ff_default_params": (None, [ctypes.POINTER(Params)]),
         "ff_create": (S, [ctypes.POINTER(vp), ctypes.POINTER(Params), i, vp]),
         "ff_features": (S, [vp, vp, i, i, i, ctypes.POINTER(vp)]),
+        "ff_features_batch": (S, [vp, i, ctypes.POINTER(Frame), ctypes.POINTER(vp)]),
         "ff_match_pair": (S, [vp, vp, vp, i, vp, vp]),
         "ff_match_batch": (S, [vp, i, ctypes.POINTER(PairJob)]),
         "ff_autotune": (S, [vp, i, ctypes.POINTER(PairJob), i]),
@@ -99,6 +107,7 @@ def lib():
         "ff_get_stats": (S, [vp, ctypes.POINTER(Stats)]),
         "ff_profile_enable": (S, [vp, i]),
         "ff_profile_read": (S, [vp, ctypes.POINTER(ctypes.c_double), i64p]),
+        "ff_profile_read_passes": (S, [vp, ctypes.POINTER(ctypes.c_double), i64p]),
         "ff_work_counts": (S, [vp, i, i, i64p, i64p]),
         "ff_match_pair_noalloc": (S, [vp, vp, vp, i, vp, vp]),
         "ff_server_create": (S, [vp, ctypes.c_int64, i, ctypes.POINTER(vp)]),
@@ -106,6 +115,7 @@ def lib():
         "ff_server_step": (S, [vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "ff_server_poll": (S, [vp, i, ctypes.POINTER(ctypes.c_uint64), i, ctypes.POINTER(i)]),
         "ff_server_stats": (S, [vp, i64p, i64p, i64p]),
+        "ff_server_cancel": (S, [vp, ctypes.c_uint64]),
         "ff_server_destroy": (S, [vp]),
         "ff_set_option": (S, [vp, i, ctypes.c_int64]),
         "ff_destroy": (S, [vp]),
@@ -144,6 +154,14 @@ def ff_features(ctx, rgb_dev: int, w: int, h: int, pitch_bytes: int):
     pyr = ctypes.c_void_p()
     _check(ctx, lib().ff_features(ctx, rgb_dev, w, h, pitch_bytes, ctypes.byref(pyr)))
     return pyr
+
+
+def ff_features_batch(ctx, frames):
+    """frames: list of (rgb_dev, w, h, pitch_bytes); returns the list of pyramid handles."""
+    arr = (Frame * len(frames))(*[Frame(*f) for f in frames])
+    out = (ctypes.c_void_p * len(frames))()
+    _check(ctx, lib().ff_features_batch(ctx, len(frames), arr, out))
+    return [ctypes.c_void_p(p) for p in out]
 
 
 def ff_match_pair(ctx, a, b, dir: int, flow_dev: int, cost_dev: int | None):
@@ -227,6 +245,17 @@ def ff_profile_read(ctx):
     return {p: (ms[i], n[i]) for i, p in enumerate(PHASES)}
 
 
+N_PASSES = 24
+
+
+def ff_profile_read_passes(ctx):
+    """Propagation time per pass: {pass index: (ms, launches)} for the passes that ran (level s, grid s + 8k)."""
+    ms = (ctypes.c_double * N_PASSES)()
+    n = (ctypes.c_int64 * N_PASSES)()
+    _check(ctx, lib().ff_profile_read_passes(ctx, ms, n))
+    return {i: (ms[i], n[i]) for i in range(N_PASSES) if n[i]}
+
+
 def ff_work_counts(ctx, w: int, h: int):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(ctx, lib().ff_work_counts(ctx, w, h, ctypes.byref(a), ctypes.byref(b)))
@@ -261,6 +290,10 @@ def ff_server_poll(ctx, srv, wait: bool = False, max_ids: int = 256):
     return list(ids[: n.value])
 
 
+def ff_server_cancel(ctx, srv, rid: int):
+    _check(ctx, lib().ff_server_cancel(srv, rid))
+
+
 def ff_server_stats(ctx, srv):
     t, l, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(ctx, lib().ff_server_stats(srv, ctypes.byref(t), ctypes.byref(l), ctypes.byref(b)))
@@ -288,7 +321,8 @@ def to_params(p) -> Params:
     if isinstance(p, Params):
         return p
     return Params(p.n_scales, p.iters, getattr(p, "patch", 8), getattr(p, "n_coef", 16), p.rs_radius, p.eps,
-                  p.seed & 0xFFFFFFFF, getattr(p, "rs_radius2", 4), getattr(p, "cost", FF_COST_WHT_SAD))
+                  p.seed & 0xFFFFFFFF, getattr(p, "rs_radius2", 4), getattr(p, "cost", FF_COST_WHT_SAD),
+                  getattr(p, "sub_scales", 0))
 
 
 @dataclass
@@ -342,6 +376,17 @@ class Matcher:
         h, w = int(img.shape[0]), int(img.shape[1])
         self._uses(img)
         return Pyramid(ff_features(self.ctx, img.data_ptr(), w, h, img.stride(0)), w, h)
+
+    def features_batch(self, imgs) -> list:
+        """Pyramids of many frames (uint8 [h][w][3] CUDA tensors of any sizes) in one launch per kernel."""
+        frames = []
+        for img in imgs:
+            assert img.dtype == self.torch.uint8 and img.is_cuda and img.dim() == 3 and img.shape[2] == 3
+            assert img.stride(2) == 1 and img.stride(1) == 3
+            frames.append((img.data_ptr(), int(img.shape[1]), int(img.shape[0]), img.stride(0)))
+        self._uses(*imgs)
+        hs = ff_features_batch(self.ctx, frames)
+        return [Pyramid(hd, f[1], f[2]) for hd, f in zip(hs, frames)]
 
     def release(self, pyr: Pyramid):
         ff_pyr_release(self.ctx, pyr.handle)
@@ -489,6 +534,11 @@ class Server:
 
     def stats(self):
         return ff_server_stats(self.m.ctx, self.srv)
+
+    def cancel(self, rid: int):
+        """Withdraw a request that has not been admitted yet (FFError FF_ERR_BUSY once it has)."""
+        ff_server_cancel(self.m.ctx, self.srv, rid)
+        self.keep.pop(rid, None)
 
     def close(self):
         if self.srv:

@@ -7,7 +7,8 @@ import oracle
 
 
 def oracle_params(p):
-    return oracle.params(p.n_scales, p.iters, p.rs_radius, p.eps, p.seed, getattr(p, "cost", 0))
+    return oracle.params(p.n_scales, p.iters, p.rs_radius, p.eps, p.seed, getattr(p, "cost", 0),
+                         getattr(p, "sub_scales", 0))
 
 
 def gpu_bidir(M, img_a, img_b, torch):
@@ -31,3 +32,22 @@ def assert_same(got, want, names=("flow_fwd", "flow_bwd", "cost_fwd", "cost_bwd"
             bad = np.argwhere(g != w)
             raise AssertionError(f"{n}: {len(bad)} mismatches, first at {bad[0].tolist()}: "
                                  f"gpu {g[tuple(bad[0])]} oracle {w[tuple(bad[0])]}")
+
+
+def _oracle_bidir_task(args):
+    img_a, img_b, prm = args
+    return oracle.default().match_bidir(img_a, img_b, oracle.params(*prm))
+
+
+def oracle_bidir_many(pairs, p):
+    """The oracle's whole stage for many pairs on the host cores (one single-threaded oracle per process).  The
+    pool is started with 'spawn': a process forked after CUDA has been initialised can hang."""
+    import multiprocessing as mp
+    import os
+
+    oracle.build()
+    prm = (p.n_scales, p.iters, p.rs_radius, p.eps, p.seed, getattr(p, "cost", 0), getattr(p, "sub_scales", 0))
+    tasks = [(np.ascontiguousarray(a), np.ascontiguousarray(b), prm) for a, b in pairs]
+    n = max(1, min(len(tasks), os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(_oracle_bidir_task, tasks, chunksize=1)

@@ -144,3 +144,43 @@ def test_many_in_flight_one_chunk_per_tick(ffm):
         G.assert_same(tuple(outs[i][k].cpu().numpy() for k in NAMES), alone[i])
     S.close()
     M.close()
+
+
+def test_served_workload_sizes_against_the_oracle(ffm):
+    """Requests of every size of the served workload (320x240, 640x480, 1024x436, 1242x375; L=5, T=6, eps=1)
+    through the server, twelve in flight at once, so that ticks advance one chunk per request with the launch
+    configurations tuned for eight pairs per launch; every result equals the oracle's."""
+    from paper_1805_03517_gb300 import synth
+
+    prm = configs.KITTI
+    M = ffm.Matcher(prm, 0)
+    specs = [(w, h, kind, 7000 + 10 * k + j) for k, (w, h, kind) in enumerate(configs.SERVE_SIZES) for j in range(3)]
+    pairs = [synth.make_pair(kind, seed, w, h)[:2] for (w, h, kind, seed) in specs]
+    dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in pairs]
+    torch.cuda.synchronize()
+    for k in range(len(configs.SERVE_SIZES)):  # launch configurations for many pairs per launch, per size
+        group = dev[3 * k:3 * k + 3] * 3  # eight or more pairs of one size
+        pyrs = [(M.features(a), M.features(b)) for a, b in group[:8]]
+        M.autotune(pyrs, reps=1)
+        for pa, pb in pyrs:
+            M.release(pa)
+            M.release(pb)
+    S = ffm.Server(M, mem_budget_bytes=60 << 30, max_active=len(dev))
+    outs = {i: _outputs(M, h, w) for i, (w, h, _, _) in enumerate(specs)}
+    for i in range(len(dev)):
+        S.submit(i, dev[i][0], dev[i][1], outs[i])
+    n_active, _ = S.step()
+    assert n_active > 8
+    done = []
+    while len(done) < len(dev):
+        S.step()
+        done += S.poll(wait=True)
+    M.sync()
+    want = G.oracle_bidir_many(pairs, prm)
+    for i, (w, h, _, _) in enumerate(specs):
+        try:
+            G.assert_same(tuple(outs[i][k].cpu().numpy() for k in NAMES), want[i])
+        except AssertionError as e:
+            raise AssertionError(f"request {i} ({w}x{h}): {e}") from None
+    S.close()
+    M.close()
