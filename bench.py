@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="run the autotuner instead of the package's table of tuned configurations")
     ap.add_argument("--serve-requests", type=int, default=2000)
-    ap.add_argument("--features", default="frame", choices=["frame", "batch"],
+    ap.add_argument("--features", default="batch", choices=["frame", "batch"],
                     help="features of the step's frames: one ff_features call per frame, or ff_features_batch")
     ap.add_argument("--tuning", default=None,
                     help="JSON list of per-level [tile_w, tile_h, iters_per_launch, threads, speculate] instead of "
@@ -254,8 +254,9 @@ def measure_batched(torch, ff, configs, stream, local_rank, steps):
     stream.synchronize()
     ms = e0.elapsed_time(e1) / steps
     launches = M.stats()["kernel_launches"] - s0["kernel_launches"]
-    # propagation roofline of the batched step: here the features (5 GB) exceed L2, so HBM is the bound; device
-    # time per launch from a profiling context with the same launch configurations
+    # propagation roofline of the batched step (its features, 5 GB, exceed L2): the level-0 launches, timed live in
+    # a profiling context with the same launch configurations; DRAM bytes and L1 wavefronts per algorithmic byte
+    # from the committed capture of an 8-pair KITTI batch (also beyond L2), scaled to this batch's launches
     P = ff.Matcher(wl.pairs[0].params, local_rank, stream)
     for lvl, cfg in enumerate(tuning):
         ff.ff_set_tuning(P.ctx, lvl, cfg)
@@ -268,23 +269,34 @@ def measure_batched(torch, ff, configs, stream, local_rank, steps):
         P.match_batch(list(zip(fp[0::2], fp[1::2])), with_cost=False)
         for p in fp:
             P.release(p)
-    prop_ms, prop_launches = ff.ff_profile_read(P.ctx)["propagate"]
-    pix_iters = sum(ff.ff_work_counts(P.ctx, p.w, p.h)[0] for p in wl.pairs)
+    passes = ff.ff_profile_read_passes(P.ctx)
     P.close()
     M.close()
     peak, peak_kind = load_peaks()
-    bytes_per_launch = pix_iters * 2 * ALG_BYTES_PER_PIXEL_ITER / (prop_launches / n_prof)
-    achieved = bytes_per_launch / (prop_ms / prop_launches / 1000.0) / 1e9
-    traffic = batch_traffic()
-    roof = {"bound": "hbm", "kernel": "k_propagate", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
-            "unit": "GB/s", "frac": achieved / peak, "alg_bytes_per_launch": bytes_per_launch,
-            "avg_launch_ms": prop_ms / prop_launches, "launches_per_step": prop_launches / n_prof,
-            "traffic": None, "traffic_note": None}
-    if traffic:
-        # DRAM bytes per algorithmic byte of the captured level-0 launches of an 8-pair KITTI batch, scaled to this
-        # batch's average launch
-        roof["traffic"] = traffic["dram_per_alg_byte"] * bytes_per_launch
-        roof["traffic_note"] = traffic["note"]
+    l0_ms, l0_n = passes.get(0, (0.0, 0))
+    l0_launch_ms = l0_ms / l0_n
+    l0_alg = sum(p.w * p.h for p in wl.pairs) * wl.pairs[0].params.iters * 2 * ALG_BYTES_PER_PIXEL_ITER / (l0_n / n_prof)
+    alg_gbs = l0_alg / (l0_launch_ms / 1000.0) / 1e9
+    roof = {"kernel": "k_propagate (level-0 launches)", "avg_launch_ms": l0_launch_ms, "alg_bytes_per_launch": l0_alg,
+            "alg_gbs": alg_gbs, "launches_per_step": l0_n / n_prof}
+    rec = batch_traffic()
+    if rec:
+        dram = rec["dram_per_alg_byte"] * l0_alg
+        dram_gbs = dram / (l0_launch_ms / 1000.0) / 1e9
+        roof.update({"traffic": dram, "traffic_note": rec["note"],
+                     "hbm": {"achieved": dram_gbs, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                             "frac": dram_gbs / peak}})
+        if rec.get("wavefronts_per_alg_byte") and rec.get("wavefronts_peak_per_cycle"):
+            clk = rec["sm_clock_hz"]
+            wf = rec["wavefronts_per_alg_byte"] * l0_alg / (l0_launch_ms / 1000.0)
+            roof.update({"bound": "l1", "unit": "wavefronts/s", "achieved": wf,
+                         "peak": rec["wavefronts_peak_per_cycle"] * clk, "frac": wf / (rec["wavefronts_peak_per_cycle"] * clk),
+                         "peak_kind": "ncu peak_sustained of l1tex__data_pipe_lsu_wavefronts x the captured SM clock"})
+        else:
+            roof.update({"bound": "hbm", "unit": "GB/s", "achieved": dram_gbs, "peak": peak, "frac": dram_gbs / peak})
+    else:
+        roof.update({"bound": "hbm", "unit": "GB/s", "achieved": alg_gbs, "peak": peak, "frac": alg_gbs / peak,
+                     "traffic": None, "note": "algorithmic bytes; no DRAM capture for this kernel source"})
     return {"workload": wl.name, "pairs_per_step": len(wl.pairs), "px_per_step": wl.pixels,
             "value": wl.pixels / (ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "gpu_launches_per_step": launches / steps, "tiles_per_level": [list(c) for c in tuning],

@@ -126,6 +126,13 @@ void launch_pyramid_tab(const PyrArgs* tab_dev, int n, int total_ctas, cudaStrea
 constexpr int kWtx = 32, kWty = 16;
 constexpr int kWinX = kWtx + 8, kWinY = kWty + 7;  // 39 window columns used, one more keeps rows word-aligned
 
+// One 32-byte sector with a single 256-bit store (the sector of a descriptor a thread writes).
+__device__ __forceinline__ void st_sector(void* p, const uint32_t (&v)[8]) {
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(v[0]), "r"(v[1]), "r"(v[2]),
+                 "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void walsh4(int a0, int a1, int a2, int a3, int a4, int a5, int a6, int a7, int& c0,
                                        int& c1, int& c2, int& c3) {
     int s01 = a0 + a1, s23 = a2 + a3, s45 = a4 + a5, s67 = a6 + a7;
@@ -169,9 +176,8 @@ __device__ __forceinline__ void census_pixel(const uint8_t (&win)[3][kWinY][kWin
         w[2 * ch] = (uint32_t)bits;
         w[2 * ch + 1] = (uint32_t)(bits >> 32);
     }
-    uint4* d = reinterpret_cast<uint4*>(dst);
-    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    d[1] = make_uint4(w[4], w[5], 0u, 0u);
+    const uint32_t sec[8] = {w[0], w[1], w[2], w[3], w[4], w[5], 0u, 0u};
+    st_sector(dst, sec);
 }
 
 // The initial-matching descriptors of a coarsest-level pixel (row p = y*w + x), from its stored coefficient
@@ -259,9 +265,7 @@ __device__ __forceinline__ void wht_tile(const WhtLevel& L, int t, uint8_t (&win
                 for (int v = 0; v < 4; v += 2)
                     out[u * 2 + v / 2] =
                         ((uint32_t)(C[u][v] & 0xffff) | ((uint32_t)C[u][v + 1] << 16)) ^ 0x80008000u;  // offset binary
-            uint4* dst = reinterpret_cast<uint4*>(L.feat + (size_t)feat_index(x, y, L.w) * kNF + ch * 16);
-            dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
-            dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+            st_sector(L.feat + (size_t)feat_index(x, y, L.w) * kNF + ch * 16, out);
         }
     }
     if (!L.census && !L.seed_desc) return;

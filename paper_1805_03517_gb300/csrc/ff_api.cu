@@ -66,7 +66,7 @@ struct ff_pyr {
 
 namespace {
 
-enum class Kind { Memset, Seed, SeedTc, Handover, Propagate, Consistency };
+enum class Kind { Memset, Seed, SeedTc, Handover, Propagate, Consistency, ConsistencyTab };
 
 struct Launch {
     Kind kind;
@@ -283,6 +283,9 @@ ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
             break;
         case Kind::Consistency:
             launch_consistency(L.fwd, L.bwd, L.bwd2, L.w, L.h, L.eps, L.mask, st);
+            break;
+        case Kind::ConsistencyTab:
+            launch_consistency_tab(static_cast<const ConsProblem*>(L.probs), L.n_probs, L.total_pix, L.eps, st);
             break;
     }
     cudaError_t e = cudaGetLastError();
@@ -629,7 +632,10 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
       }
     }
     // 3. consistency of each pair: the forward flow and the inverse flow, both at level 0
-    for (const ConsJob& cj : cons) {
+    //    (one launch for a single pair; the pairs of a batch share one launch over a table)
+    std::vector<ConsProblem> cps;
+    if (cons.size() == 1) {
+        const ConsJob& cj = cons[0];
         Launch l{};
         l.kind = Kind::Consistency;
         l.phase = FF_PHASE_CONSISTENCY;
@@ -641,6 +647,27 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         l.eps = c->prm.eps;
         l.mask = cj.mask;
         pend.push_back({l, 0, 0, -1});
+    } else if (cons.size() > 1) {
+        Launch l{};
+        l.kind = Kind::ConsistencyTab;
+        l.phase = FF_PHASE_CONSISTENCY;
+        int64_t pix = 0;
+        for (const ConsJob& cj : cons) {
+            ConsProblem cp{};
+            cp.fwd = jobs[cj.dj_fwd].flow_out;
+            cp.bwd = jobs[cj.dj_bwd].flow_out;
+            cp.bwd2 = cj.dj_bwd2 >= 0 ? jobs[cj.dj_bwd2].flow_out : nullptr;
+            cp.w = jobs[cj.dj_fwd].a->w;
+            cp.h = jobs[cj.dj_fwd].a->h;
+            cp.mask = cj.mask;
+            cp.pix_base = pix;
+            pix += (int64_t)cp.w * cp.h;
+            cps.push_back(cp);
+        }
+        l.n_probs = (int)cps.size();
+        l.total_pix = pix;
+        l.eps = c->prm.eps;
+        pend.push_back({l, 0, 0, -1});
     }
 
     // upload the problem tables, queues and counters in one block
@@ -649,13 +676,15 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     size_t o_prop = o_ho + align_up(hos.size() * sizeof(HandoverProblem));
     size_t o_q = o_prop + align_up(props.size() * sizeof(PropProblem));
     size_t o_cnt = o_q + align_up(queue.size() * sizeof(int2));
-    size_t tbytes = o_cnt + align_up((size_t)std::max(n_counters, 1) * sizeof(int));
+    size_t o_cons = o_cnt + align_up((size_t)std::max(n_counters, 1) * sizeof(int));
+    size_t tbytes = o_cons + align_up(cps.size() * sizeof(ConsProblem));
     std::vector<char> host(tbytes, 0);
     memcpy(host.data() + o_seed, seeds.data(), seeds.size() * sizeof(SeedProblem));
     memcpy(host.data() + o_tc, tcseeds.data(), tcseeds.size() * sizeof(SeedTcProblem));
     memcpy(host.data() + o_ho, hos.data(), hos.size() * sizeof(HandoverProblem));
     memcpy(host.data() + o_prop, props.data(), props.size() * sizeof(PropProblem));
     memcpy(host.data() + o_q, queue.data(), queue.size() * sizeof(int2));
+    memcpy(host.data() + o_cons, cps.data(), cps.size() * sizeof(ConsProblem));
     P.bufs.emplace_back();
     st = dev_alloc(c, P.bufs.back(), tbytes);
     if (st != FF_OK) return st;
@@ -685,6 +714,9 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
                 l.counter = reinterpret_cast<int*>(tb + o_cnt) + pd.counter;
                 break;
             case Kind::Consistency:
+                break;
+            case Kind::ConsistencyTab:
+                l.probs = tb + o_cons;
                 break;
         }
         P.launches.push_back(l);
@@ -948,10 +980,11 @@ bool pyr_view(const ff_pyr* p, PyrView* out) {
 }
 
 // The configuration build_plan would use for this level (override, tuned, or default).
+// `level` is a pass index: a level (0..7, where a per-level override applies) or a sub-scale grid (s + 8k).
 TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all) {
     const int T = c->prm.iters;
     TileCfg tc;
-    if (c->forced[level].tw > 0) {
+    if (level >= 0 && level < kMaxLevels && c->forced[level].tw > 0) {
         tc = c->forced[level];
     } else {
         // the configuration tuned for this level size with the nearest number of directions per launch

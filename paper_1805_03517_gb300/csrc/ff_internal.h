@@ -179,6 +179,16 @@ void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n
 
 void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, const uint32_t* bwd2, int w, int h, int eps,
                         uint8_t* mask, cudaStream_t st);  // bwd2 may be null
+// The consistency checks of many pairs in one launch (a batch): one entry per pair, pix_base ascending.
+struct ConsProblem {
+    const uint32_t* fwd;
+    const uint32_t* bwd;
+    const uint32_t* bwd2;  // or null
+    int w, h;
+    uint8_t* mask;
+    int64_t pix_base;      // first pixel of this pair in the launch
+};
+void launch_consistency_tab(const ConsProblem* probs_dev, int n, int64_t total_pix, int eps, cudaStream_t st);
 void launch_sparsify(const uint32_t* fwd, const uint32_t* bwd, const uint8_t* keep, int w, int h, int eps, int s,
                      uint8_t* out, cudaStream_t st);
 
@@ -304,6 +314,7 @@ namespace ff {
 bool ctx_view(const ff_ctx* c, CtxView* out);
 bool ctx_owns_live_pyr(const ff_ctx* c, const ff_pyr* p);
 bool pyr_view(const ff_pyr* p, PyrView* out);
+// the launch configuration of a pass (level s, or its sub-scale grid s + 8k) of size w x h
 TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all);
 // cudaMalloc on behalf of a context; fails as out of memory while the context's FF_OPT_TEST_FAIL_ALLOCS count lasts
 cudaError_t ctx_malloc(ff_ctx* c, void** p, size_t bytes);

@@ -106,4 +106,30 @@ void launch_consistency(const uint32_t* fwd, const uint32_t* bwd, const uint32_t
     launch_k(k_consistency, dim3((n + 255) / 256), dim3(256), 0, st, fwd, bwd, bwd2, w, h, eps, mask);
 }
 
+// Every pair of a batch in one grid-stride launch: pixel i belongs to the last pair with pix_base <= i.
+__global__ void k_consistency_tab(const ConsProblem* __restrict__ probs, int n, int64_t total, int eps) {
+    grid_dependency_sync();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (probs[mid].pix_base <= i) lo = mid; else hi = mid - 1;
+        }
+        const ConsProblem& P = probs[lo];
+        const int p = (int)(i - P.pix_base);
+        const int x = p % P.w, y = p / P.w;
+        const uint32_t f = P.fwd[p];
+        bool ok = consistent(f, P.bwd, x, y, P.w, P.h, eps);
+        if (P.bwd2) ok = ok && consistent(f, P.bwd2, x, y, P.w, P.h, eps);
+        P.mask[p] = ok ? 1 : 0;
+    }
+}
+
+void launch_consistency_tab(const ConsProblem* probs_dev, int n, int64_t total_pix, int eps, cudaStream_t st) {
+    int64_t blocks = (total_pix + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    launch_k(k_consistency_tab, dim3((int)blocks), dim3(256), 0, st, probs_dev, n, total_pix, eps);
+}
+
 }  // namespace ff

@@ -230,7 +230,13 @@ ff_status admit(ff_server* s) {
             for (int g = 0; g <= grids_of(l, q.L, s->cv.sub_scales); g++) {  // tuning entries: pass l + 8g
                 const int gw = grid_dim(q.A.ws[l], g), gh = grid_dim(q.A.hs[l], g);
                 q.cfg[l][g] = ctx_level_choice(s->ctx, l + kMaxLevels * g, gw, gh, n_dirs, (int64_t)n_dirs * gw * gh);
-                q.n_chunks[l][g] = (q.T + q.cfg[l][g].k - 1) / q.cfg[l][g].k;
+                const TileChoice& t = q.cfg[l][g];
+                if (t.k < 1 || t.tw < 1 || t.th < 1 || !prop_threads_ok(t.threads) ||
+                    prop_smem_bytes(t.tw, t.th, t.k) > kMaxPropSmem) {
+                    release_req(s, q);
+                    return srv_fail(s, FF_ERR_CUDA, "invalid launch configuration");
+                }
+                q.n_chunks[l][g] = (q.T + t.k - 1) / t.k;
             }
         q.level = q.L - 1;
         q.grid = 0;
