@@ -127,7 +127,8 @@ typedef struct {
  * every level of every frame in another (frames with 8 levels add one launch per frame for the last level).
  * out[i] (n entries) receives frame i's pyramid, identical to ff_features on that frame alone.  The launches read
  * a table of the frames that the call copies to a context-owned device buffer on the context's stream (grown,
- * after waiting for the stream, when a larger batch needs it).  On an error no pyramid is taken and out[] is
+ * after waiting for the stream, when a larger batch needs it).  The copy is from pageable host memory, so this
+ * call cannot be recorded into a CUDA graph (ff_features can).  On an error no pyramid is taken and out[] is
  * all NULL. */
 FF_API ff_status ff_features_batch(ff_ctx* ctx, int n, const ff_frame* frames, ff_pyr** out);
 

@@ -7,6 +7,21 @@
 
 namespace ff {
 
+// first index violation of a debug-bounds build (see idx_ok): code, index, limit
+static __device__ int g_bounds[4];
+enum : int { kBoundsImage = 40, kBoundsWin, kBoundsRowt, kBoundsFeat, kBoundsCensus, kBoundsSeed, kBoundsPyr };
+
+cudaError_t bounds_take_features(int rec[3]) {
+    int h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyFromSymbol(h, g_bounds, sizeof h);
+    if (e == cudaSuccess && h[0] != 0) {
+        const int z[4] = {0, 0, 0, 0};
+        e = cudaMemcpyToSymbol(g_bounds, z, sizeof z);
+    }
+    rec[0] = h[0], rec[1] = h[1], rec[2] = h[2];
+    return e;
+}
+
 // One pyramid step (Sec. 3): 2x2 box average per channel, rounded half up; source coordinates clamped so
 // that a 1-pixel-wide or -high level averages its only column/row.  One thread per output pixel.
 __global__ void k_downsample(const uint8_t* __restrict__ src, int sw, int sh, int spitch, uint8_t* __restrict__ dst,
@@ -46,6 +61,7 @@ __device__ __forceinline__ void pyramid_block(const PyrArgs& a, int bx, int by,
         if (x >= a.w[1] || y >= a.h[1]) continue;
         const int x0 = min(2 * x, a.w[0] - 1), x1 = min(2 * x + 1, a.w[0] - 1);
         const int y0 = min(2 * y, a.h[0] - 1), y1 = min(2 * y + 1, a.h[0] - 1);
+        if (!idx_ok(g_bounds, kBoundsPyr, (long long)y1 * a.w[0] + x1, (long long)a.w[0] * a.h[0])) continue;
         const uint8_t* r0 = a.src + (size_t)y0 * a.spitch;
         const uint8_t* r1 = a.src + (size_t)y1 * a.spitch;
         uint8_t* o = a.dst[1] + ((size_t)y * a.w[1] + x) * 3;
@@ -218,6 +234,7 @@ __device__ __forceinline__ void wht_tile(const WhtLevel& L, int t, uint8_t (&win
         int r = i / kWinX, c = i - r * kWinX;
         int gy = min(max(ty0 - 3 + r, 0), L.h - 1);
         int gx = min(max(tx0 - 3 + c, 0), L.w - 1);
+        if (!idx_ok(g_bounds, kBoundsImage, (long long)gy * L.w + gx, (long long)L.w * L.h)) gy = gx = 0;
         const uint8_t* px = L.img + (size_t)gy * L.pitch + gx * 3;
         win[0][r][c] = px[0];
         win[1][r][c] = px[1];
@@ -228,6 +245,7 @@ __device__ __forceinline__ void wht_tile(const WhtLevel& L, int t, uint8_t (&win
         const int ch = i / (kWinY * kWtx), rem = i - ch * kWinY * kWtx, r = rem / kWtx, c = rem - r * kWtx;
         // bytes c..c+7 of the window row from three aligned words
         const uint32_t* rw = reinterpret_cast<const uint32_t*>(&win[ch][r][0]) + (c >> 2);
+        if (!idx_ok(g_bounds, kBoundsWin, (c >> 2) + 2, kWinX / 4)) continue;
         const uint32_t sh = 8u * (uint32_t)(c & 3);
         const uint32_t lo = __funnelshift_r(rw[0], rw[1], sh), hi = __funnelshift_r(rw[1], rw[2], sh);
         int v0, v1, v2, v3;
@@ -242,6 +260,7 @@ __device__ __forceinline__ void wht_tile(const WhtLevel& L, int t, uint8_t (&win
         const int col = i % kWtx, rest = i / kWtx, seg = rest & 1, ch = rest >> 1;
         const int x = tx0 + col;
         if (x >= L.w) continue;
+        if (!idx_ok(g_bounds, kBoundsRowt, seg * (kWty / 2) + kWty / 2 + 6, kWinY)) continue;
         short4 R[kWty / 2 + 7];
 #pragma unroll
         for (int k = 0; k < kWty / 2 + 7; k++) R[k] = rowt[ch][seg * (kWty / 2) + k][col];
@@ -265,6 +284,7 @@ __device__ __forceinline__ void wht_tile(const WhtLevel& L, int t, uint8_t (&win
                 for (int v = 0; v < 4; v += 2)
                     out[u * 2 + v / 2] =
                         ((uint32_t)(C[u][v] & 0xffff) | ((uint32_t)C[u][v + 1] << 16)) ^ 0x80008000u;  // offset binary
+            if (!idx_ok(g_bounds, kBoundsFeat, feat_index(x, y, L.w), (long long)L.w * L.h)) continue;
             st_sector(L.feat + (size_t)feat_index(x, y, L.w) * kNF + ch * 16, out);
         }
     }
@@ -274,8 +294,10 @@ __device__ __forceinline__ void wht_tile(const WhtLevel& L, int t, uint8_t (&win
     for (int ly = threadIdx.x / kWtx; ly < kWty; ly += blockDim.x / kWtx) {
         const int x = tx0 + lx, y = ty0 + ly;
         if (x >= L.w || y >= L.h) continue;
+        if (!idx_ok(g_bounds, kBoundsCensus, ly + 6, kWinY) || !idx_ok(g_bounds, kBoundsCensus, (lx >> 2) + 2, kWinX / 4))
+            continue;
         if (L.census) census_pixel(win, lx, ly, L.census + (size_t)feat_index(x, y, L.w) * (kCensusBytes / 4));
-        if (L.seed_desc) {
+        if (L.seed_desc && idx_ok(g_bounds, kBoundsSeed, y * L.w + x, (long long)L.w * L.h)) {
             uint32_t out[24];
             const uint4* src = reinterpret_cast<const uint4*>(L.feat + (size_t)feat_index(x, y, L.w) * kNF);
 #pragma unroll

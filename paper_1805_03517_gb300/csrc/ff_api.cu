@@ -1510,8 +1510,8 @@ ff_status ff_sync(ff_ctx* c) {
 #if FF_DEBUG_BOUNDS
     {  // a debug-bounds build: an index check failed since the last check
         int rec[3];
-        for (int tu = 0; tu < 2; tu++) {
-            FF_CUDA(c, tu == 0 ? bounds_take_propagate(rec) : bounds_take_filter(rec));
+        for (int tu = 0; tu < 3; tu++) {
+            FF_CUDA(c, tu == 0 ? bounds_take_propagate(rec) : tu == 1 ? bounds_take_filter(rec) : bounds_take_features(rec));
             if (rec[0] != 0)
                 return fail(c, FF_ERR_CUDA, "bounds check %d failed: index %d outside 0..%d (access skipped)", rec[0],
                             rec[1], rec[2] - 1);

@@ -256,8 +256,8 @@ __device__ __forceinline__ void grid_dependency_sync() {
 #endif
 }
 
-// Debug-bounds build (compiled with -DFF_DEBUG_BOUNDS=1; a stand-in for a memory checker): the propagation,
-// hand-over and filter kernels check every gather and shared-memory index against its buffer before the access;
+// Debug-bounds build (compiled with -DFF_DEBUG_BOUNDS=1; a stand-in for a memory checker): the feature,
+// propagation, hand-over and filter kernels check their gather, store and shared-memory indices before the access;
 // the first violation (code, index, limit) is recorded in its translation unit's record, the access is skipped
 // (a load reads zeros) and nothing traps.  ff_sync reports a recorded violation as FF_ERR_CUDA and clears it.
 // Release builds compile every check away.
@@ -289,6 +289,7 @@ __device__ __forceinline__ unsigned dyn_smem_bytes() {
 // Take (read and clear) the bounds record of propagate.cu / filter.cu; rec[0] == 0: no violation.
 cudaError_t bounds_take_propagate(int rec[3]);
 cudaError_t bounds_take_filter(int rec[3]);
+cudaError_t bounds_take_features(int rec[3]);
 
 template <typename... KArgs, typename... Args>
 cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
