@@ -202,50 +202,74 @@ void release_req(ff_server* s, Req& q) {
     q.counted = false;
 }
 
+// Admission: the queued requests that fit (first come first served, while slots and the memory budget allow) have
+// the features of all their frames built in one ff_features_batch call, then their scratch and launch
+// configurations set up in order.  If the features fail nothing is taken and the requests stay queued; if a later
+// step fails, that request and the ones after it stay queued (their pyramids are given back).
 ff_status admit(ff_server* s) {
-    while (!s->queued.empty() && (int)s->active.size() < s->max_active) {
-        Req& q = *s->queued.front();
-        const bool idle = s->active.empty() && s->finishing.empty();
-        if (s->in_use + q.footprint > s->budget && !idle) break;  // wait for memory
-        ff_status st = ff_features(s->ctx, q.io.rgb_a, q.io.w, q.io.h, q.io.pitch_bytes, &q.pa);
-        if (st == FF_OK) st = ff_features(s->ctx, q.io.rgb_b, q.io.w, q.io.h, q.io.pitch_bytes, &q.pb);
-        if (st != FF_OK) {
-            release_req(s, q);
-            return st;
-        }
+    size_t n_new = 0;
+    int64_t in_use = s->in_use;
+    bool idle = s->active.empty() && s->finishing.empty();
+    for (auto& qp : s->queued) {
+        if ((int)(s->active.size() + n_new) >= s->max_active) break;
+        if (in_use + qp->footprint > s->budget && !idle) break;  // wait for memory
+        in_use += qp->footprint;
+        idle = false;
+        n_new++;
+    }
+    if (n_new == 0) return FF_OK;
+    std::vector<ff_frame> frames;
+    for (size_t i = 0; i < n_new; i++) {
+        const ff_request& io = s->queued[i]->io;
+        frames.push_back({io.rgb_a, io.w, io.h, io.pitch_bytes});
+        frames.push_back({io.rgb_b, io.w, io.h, io.pitch_bytes});
+    }
+    std::vector<ff_pyr*> pyrs(frames.size(), nullptr);
+    ff_status st = ff_features_batch(s->ctx, (int)frames.size(), frames.data(), pyrs.data());
+    if (st != FF_OK) return st;
+    const int L = s->cv.n_scales;
+    const int deep = L - 1 > kPyrFusedTop ? L - 1 - kPyrFusedTop : 0;
+    s->launches += (L > 1 ? 1 : 0) + 1 + (int64_t)frames.size() * deep;  // the feature launches just enqueued
+    for (size_t i = 0; i < n_new; i++) {
+        s->queued[i]->pa = pyrs[2 * i];
+        s->queued[i]->pb = pyrs[2 * i + 1];
+    }
+    size_t admitted = 0;
+    for (; admitted < n_new && st == FF_OK; admitted++) {
+        Req& q = *s->queued[admitted];
         pyr_view(q.pa, &q.A);
         pyr_view(q.pb, &q.B);
         q.L = q.A.L;
         q.T = s->cv.iters;
         st = take_scratch(s, q);
-        if (st != FF_OK) {
-            release_req(s, q);
-            return st;
-        }
+        if (st != FF_OK) break;
         s->in_use += q.footprint;
         q.counted = true;
         // launch configurations tuned for one pair at light load, for launches shared by many pairs under load
-        const int n_dirs = (int)s->active.size() + 1 > kWholeLevelMaxActive ? kLoadedDirs : 2;
-        for (int l = 0; l < q.L; l++)
+        const int n_dirs = (int)(s->active.size() + admitted) + 1 > kWholeLevelMaxActive ? kLoadedDirs : 2;
+        for (int l = 0; l < q.L && st == FF_OK; l++)
             for (int g = 0; g <= grids_of(l, q.L, s->cv.sub_scales); g++) {  // tuning entries: pass l + 8g
                 const int gw = grid_dim(q.A.ws[l], g), gh = grid_dim(q.A.hs[l], g);
                 q.cfg[l][g] = ctx_level_choice(s->ctx, l + kMaxLevels * g, gw, gh, n_dirs, (int64_t)n_dirs * gw * gh);
                 const TileChoice& t = q.cfg[l][g];
                 if (t.k < 1 || t.tw < 1 || t.th < 1 || !prop_threads_ok(t.threads) ||
                     prop_smem_bytes(t.tw, t.th, t.k) > kMaxPropSmem) {
-                    release_req(s, q);
-                    return srv_fail(s, FF_ERR_CUDA, "invalid launch configuration");
+                    st = srv_fail(s, FF_ERR_CUDA, "invalid launch configuration");
+                    break;
                 }
                 q.n_chunks[l][g] = (q.T + t.k - 1) / t.k;
             }
+        if (st != FF_OK) break;
         q.level = q.L - 1;
         q.grid = 0;
         q.chunk = 0;
+    }
+    for (size_t i = admitted; i < n_new; i++) release_req(s, *s->queued[i]);  // stays queued, holds nothing
+    for (size_t i = 0; i < admitted; i++) {
         s->active.push_back(std::move(s->queued.front()));
         s->queued.pop_front();
-        s->launches += 2 * features_launches(q.L);  // feature launches enqueued by ff_features
     }
-    return FF_OK;
+    return st;
 }
 
 // Propagation launches of a tick are grouped by phase (the position of a chunk among the chunks one request

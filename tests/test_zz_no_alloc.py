@@ -3,10 +3,10 @@
 a hot path that must not run out of memory half way).
 
 It must give exactly what ff_match_pair gives (the matching is integer, so the tolerance is zero), on calls in
-a row that carve the shared scratch array differently (a smaller pair after a larger one), and at the
-1242x375 size of the KITTI-shaped workload against the oracle itself.  Across every call the device's free
-memory and the library's count of the bytes it holds must not change: the array and the kernels were set up
-when the context was created.  This file is named so that pytest collects it last.
+a row that carve the shared scratch array differently (a smaller pair after a larger one), at the 1242x375 size
+of the KITTI-shaped workload against the oracle itself, and near the array's size limit (1.41 Mpx).  Across
+every call the device's free memory and the library's count of the bytes it holds must not change: the array
+and the kernels were set up when the context was created.  This file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -87,6 +87,25 @@ def test_noalloc_kitti_size_against_the_oracle(ffm, orc):
         flow, cost = _noalloc_call(ffm, M, X, Y, dir, spec.h, spec.w)
         assert np.array_equal(flow.cpu().numpy(), want[dir]), dir
         assert np.array_equal(cost.cpu().numpy(), want[2 + dir]), dir
+    M.release(pa)
+    M.release(pb)
+    M.close()
+
+
+def test_noalloc_near_its_scratch_limit(ffm):
+    """A 1600x880 pair (1.41 Mpx, L=5, T=6): its per-level flow and cost buffers take about 30 MB of the
+    32 MiB array.  Each direction equals ff_match_pair, and nothing is allocated during the calls."""
+    from paper_1805_03517_gb300 import synth
+
+    M = ffm.Matcher(configs.KITTI, 0)
+    a, b, _ = synth.make_pair("kitti", 7700, 1600, 880)
+    pa = M.features(torch.from_numpy(a).cuda())
+    pb = M.features(torch.from_numpy(b).cuda())
+    for dir, (X, Y) in enumerate(((pa, pb), (pb, pa))):
+        ref_flow, ref_cost = M.match_pair(X, Y, dir)
+        flow, cost = _noalloc_call(ffm, M, X, Y, dir, 880, 1600)
+        assert torch.equal(flow, ref_flow), dir
+        assert torch.equal(cost, ref_cost), dir
     M.release(pa)
     M.release(pb)
     M.close()
