@@ -172,17 +172,24 @@ FF_API ff_status ff_autotune(ff_ctx* ctx, int n, const ff_pair_job* jobs, int re
 
 /* Propagation launch configuration of one level: tile interior (pixels), iterations fused per launch, threads
  * per CTA (128, 256 or 512), and whether the random candidate is fetched together with the neighbour candidates
- * (speculate = 1; refetched when a neighbour was taken).  None of these changes any result. */
+ * (speculate = 1; refetched when a neighbour was taken).  cluster = 0 is this tile form.  cluster = n (1..16)
+ * selects the cluster form instead: one thread-block cluster of n CTAs per direction of each pair covers the whole
+ * level without a halo, CTAs exchanging their block edges through distributed shared memory (threads 256 or 512,
+ * tile_w = tile_h = 0, speculate = 0); a plan falls back to the default tile form for a level the cluster form cannot take (a
+ * level narrower or lower than the partition, blocks beyond shared memory, or clusters this device cannot
+ * schedule).  The server (ff_server_*) and ff_match_pair_noalloc always launch the tile form.  None of these
+ * changes any result. */
 typedef struct {
-    int tile_w, tile_h, iters_per_launch, threads, speculate;
+    int tile_w, tile_h, iters_per_launch, threads, speculate, cluster;
 } ff_tuning;
 
-/* Impose the configuration of one level on every later plan of this context, overriding the autotuner;
- * NULL removes the override.  FF_ERR_ARG if the tile with its halo does not fit in shared memory or a field is
- * out of range.  Cached plans are dropped. */
+/* Impose the configuration of one pass on every later plan of this context, overriding the autotuner; NULL
+ * removes the override.  `level` is a pass index: 0..7 a pyramid level, s + 8k (k = 1, 2) the sub-scale grid of
+ * stride 2^k of level s (FF_N_PASSES in all).  FF_ERR_ARG if the tile with its halo does not fit in shared
+ * memory or a field is out of range.  Cached plans are dropped. */
 FF_API ff_status ff_set_tuning(ff_ctx* ctx, int level, const ff_tuning* cfg);
 
-/* The configuration in force for `level`: the override if set, else the autotuner's choice; FF_ERR_ARG if
+/* The configuration in force for pass `level`: the override if set, else the autotuner's choice; FF_ERR_ARG if
  * neither exists. */
 FF_API ff_status ff_get_tuning(ff_ctx* ctx, int level, ff_tuning* out);
 
@@ -235,6 +242,7 @@ typedef struct {
     int64_t graph_replays;     /* CUDA-graph launches since creation */
     int64_t plans_built;       /* distinct match plans built (each may be captured into a graph) */
     int64_t scratch_bytes;     /* device bytes currently held for plans, pyramids and staging */
+    int64_t cluster_launches;  /* of kernel_launches: propagation launches of the cluster form (ff_tuning) */
 } ff_stats;
 FF_API ff_status ff_get_stats(ff_ctx* ctx, ff_stats* out);
 
@@ -325,8 +333,9 @@ FF_API ff_status ff_match_pair_noalloc(ff_ctx* ctx, const ff_pyr* a, const ff_py
  *   FF_OPT_WAIT_LIMIT            polls (1..2^30, default 2^22, about a second) before a device-side wait gives
  *                                up; the kernel then records the failure, cleans up and returns, and the next
  *                                ff_sync reports FF_ERR_TIMEOUT with the context still usable.
- *   FF_OPT_TEST_WITHHOLD_COPIES  1: the tensor-core seed issues no copies, so its waits can only expire (a test of
- *                                the bounded waits); 0 (default) normal operation.
+ *   FF_OPT_TEST_WITHHOLD_COPIES  1: the tensor-core seed issues no copies and the cluster form of the propagation
+ *                                sends no block edges, so their waits can only expire (a test of the bounded
+ *                                waits); 0 (default) normal operation.
  *   FF_OPT_TEST_FAIL_ALLOCS      n >= 0: the next n device allocations made for this context (pyramids, plans, the
  *                                server's scratch and tables) fail as on an exhausted device, without calling the
  *                                allocator, so the calls that need them return FF_ERR_OOM and launch nothing (a test

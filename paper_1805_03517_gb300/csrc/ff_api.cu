@@ -120,10 +120,12 @@ struct Plan {
     std::vector<DevBuf> bufs;
     cudaGraphExec_t exec = nullptr;
     int graph_nodes = 0;
+    int cluster_nodes = 0;  // of graph_nodes: propagation launches of the cluster form
 };
 
 struct TileCfg {
     int tw, th, k, threads, spec;  // tile interior, iterations fused per launch, CTA size, speculative random
+    int cluster = 0;               // > 0: the cluster form with this many CTAs per problem (tw, th unused)
 };
 
 // Candidate propagation configurations (tile shape, fused iterations, CTA size) the autotuner times per level.
@@ -143,7 +145,9 @@ const TileCfg kCands[] = {
     {128, 16, 1, 256, 0}, {96, 32, 1, 256, 0}, {64, 24, 1, 512, 0}, {64, 20, 1, 256, 0}, {48, 24, 1, 256, 0},
     {64, 16, 1, 256, 0}, {96, 16, 1, 256, 0}, {128, 24, 1, 512, 0}, {96, 24, 1, 128, 0}, {80, 24, 1, 128, 0},
     {96, 32, 1, 128, 0}, {80, 32, 1, 128, 0}, {64, 28, 1, 128, 0}, {56, 24, 1, 128, 0}, {72, 24, 1, 128, 0},
-    {64, 20, 1, 128, 0}, {24, 16, 1, 512, 0}, {32, 16, 1, 512, 0}, {20, 16, 1, 512, 0}, {26, 16, 1, 512, 0}};
+    {64, 20, 1, 128, 0}, {24, 16, 1, 512, 0}, {32, 16, 1, 512, 0}, {20, 16, 1, 512, 0}, {26, 16, 1, 512, 0},
+    // the cluster form (every iteration in one launch, no halo): small levels of a few problems
+    {0, 0, 255, 256, 0, 16}, {0, 0, 255, 512, 0, 16}, {0, 0, 255, 256, 0, 8}, {0, 0, 255, 512, 0, 8}};
 constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
 
 // Tuning key: pass index, grid size of the first job, number of directions in the launch, iterations.  A pass is
@@ -166,7 +170,7 @@ struct ff_ctx {
     std::vector<std::unique_ptr<ff_pyr>> pyrs;
     std::map<std::vector<uintptr_t>, std::unique_ptr<Plan>> plans;
     std::map<TuneKey, TileCfg> tuned;
-    TileCfg forced[kMaxLevels] = {};  // per-level override (tw == 0: none)
+    TileCfg forced[kMaxPasses] = {};  // per-pass override (threads == 0: none)
     int seed_kernel = FF_SEED_TCGEN05;
     uint32_t wait_limit = 1u << 22;    // polls before a device-side wait gives up (~1 s)
     int withhold = 0;                  // test of the bounded waits: the tensor-core seed issues no copies
@@ -176,6 +180,7 @@ struct ff_ctx {
     DevBuf feat_tab;                   // device table of ff_features_batch (frames' pyramid and WHT launch entries)
     std::string err;
     int64_t launches = 0, replays = 0, plans_built = 0, bytes = 0;
+    int64_t cluster_launches = 0;      // of `launches`: propagation launches of the cluster form
     bool profiling = false;
     struct Ev {
         int phase, level;
@@ -249,7 +254,25 @@ ff_status check_params(const ff_params* p, ff_ctx* c) {
     return FF_OK;
 }
 
-bool cfg_fits(const TileCfg& t) { return prop_smem_bytes(t.tw, t.th, t.k) <= kMaxPropSmem; }
+// Whether a tile-form configuration's tile and halo fit in shared memory (a cluster-form configuration is
+// checked per pass by cluster_fits).
+bool cfg_fits(const TileCfg& t) { return t.cluster > 0 || prop_smem_bytes(t.tw, t.th, t.k) <= kMaxPropSmem; }
+
+// Whether the cluster form of `t` can run pass (s, k) of these jobs: a partition of every problem, its shared
+// memory within the limit, and clusters of that shape launchable on this device.  *smem: the largest CTA's bytes.
+bool cluster_fits(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, int k, const TileCfg& t, size_t* smem) {
+    size_t most = 0;
+    for (const DirJob& j : jobs) {
+        const int w = grid_dim(j.a->ws[s], k), h = grid_dim(j.a->hs[s], k);
+        int bx = 0, by = 0;
+        if (!cluster_partition(w, h, t.cluster, bx, by)) return false;
+        most = std::max(most, cluster_smem_bytes(w, h, bx, by));
+    }
+    if (most > kMaxPropSmem || prop_cluster_capacity(t.cluster, t.threads, c->prm.cost, k > 0, most) < 1)
+        return false;
+    *smem = most;
+    return true;
+}
 
 // Default propagation configuration of a level when it has not been tuned: large tiles with one iteration per
 // launch when the level fills the GPU, otherwise small tiles with fused iterations (idle SMs absorb the halo).
@@ -294,6 +317,7 @@ ff_status enqueue_launch(ff_ctx* c, const Launch& L) {
 }
 
 int kernels_of(const Launch& l) { return l.kind == Kind::Memset ? 0 : l.kind == Kind::SeedTc ? 2 : 1; }
+int clusters_of(const Launch& l) { return l.kind == Kind::Propagate && l.prop.cluster > 0 ? 1 : 0; }
 
 ff_status ensure_err_word(ff_ctx* c) {
     if (c->d_err) return FF_OK;
@@ -335,6 +359,7 @@ ff_status run_launches(ff_ctx* c, const std::vector<Launch>& ls, bool timed) {
             ff_status s = enqueue_launch(c, ls[k]);
             if (s != FF_OK) return s;
             nk += kernels_of(ls[k]);
+            c->cluster_launches += clusters_of(ls[k]);
         }
         c->launches += nk;
         if (timed) {
@@ -369,7 +394,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     std::vector<int32_t*> seed_dist(nj);
     std::vector<unsigned long long*> seed_keys(nj);
     const bool tc = c->seed_kernel == FF_SEED_TCGEN05;
-    if (tc) {
+    {  // the error word of the bounded waits (tensor-core seed, cluster-form propagation)
         ff_status se = ensure_err_word(c);
         if (se != FF_OK) return se;
     }
@@ -559,15 +584,18 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         if (force) {
             tc = force[pass];
             tc.k = std::min(tc.k, T);
-        } else if (k == 0 && c->forced[s].tw > 0) {
-            tc = c->forced[s];
+        } else if (c->forced[pass].threads > 0) {
+            tc = c->forced[pass];
             tc.k = std::min(tc.k, T);
         } else {
             auto it = c->tuned.find(TuneKey{pass, gdim(jobs[0].a->ws[s], k), gdim(jobs[0].a->hs[s], k), nj, T});
             tc = it != c->tuned.end() ? it->second : default_cfg(c, level_pix, T);
         }
-        const size_t smem = prop_smem_bytes(tc.tw, tc.th, tc.k);
-        const int blocks = prop_blocks_per_sm(smem, tc.threads, tc.spec != 0, cost, k > 0) * c->n_sms;
+        size_t cl_smem = 0;
+        if (tc.cluster > 0 && !cluster_fits(c, jobs, s, k, tc, &cl_smem)) tc = default_cfg(c, level_pix, T);
+        const bool cl = tc.cluster > 0;
+        const size_t smem = cl ? 0 : prop_smem_bytes(tc.tw, tc.th, tc.k);
+        const int blocks = cl ? 0 : prop_blocks_per_sm(smem, tc.threads, tc.spec != 0, cost, k > 0) * c->n_sms;
         for (int t0 = 0; t0 < T; t0 += tc.k) {
             int n_iter = std::min(tc.k, T - t0);
             bool last = t0 + n_iter == T;
@@ -582,6 +610,11 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             l.prop.spec = tc.spec;
             l.prop.cost = cost;
             l.prop.grid = k > 0;
+            l.prop.cluster = tc.cluster;
+            l.prop.cl_smem = (int)cl_smem;
+            l.prop.wait_limit = c->wait_limit;
+            l.prop.withhold = c->withhold;
+            l.prop.err = c->d_err;
             size_t oq = queue.size();
             std::vector<int> pidx(nj), ntiles(nj);
             for (int j = 0; j < nj; j++) {
@@ -606,8 +639,8 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
                     pp.cost_out = B.cost[out];
                 }
                 cur_buf[j] = out;
-                pp.tiles_x = (pp.w + tc.tw - 1) / tc.tw;
-                ntiles[j] = pp.tiles_x * ((pp.h + tc.th - 1) / tc.th);
+                pp.tiles_x = cl ? 1 : (pp.w + tc.tw - 1) / tc.tw;
+                ntiles[j] = cl ? 0 : pp.tiles_x * ((pp.h + tc.th - 1) / tc.th);
                 pp.t0 = t0;
                 pp.n_iter = n_iter;
                 pp.level = s + 8 * k;  // the hash stream of this level or grid
@@ -616,6 +649,12 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
                 pp.rs_radius = jobs[j].rs_radius;
                 pidx[j] = (int)props.size();
                 props.push_back(pp);
+            }
+            if (cl) {  // cluster i of the launch runs problem pidx[0] + i
+                l.n_probs = nj;
+                l.grid = nj * tc.cluster;
+                pend.push_back({l, (size_t)pidx[0], 0, -1});
+                continue;
             }
             for (const std::vector<int>& g : groups) {
                 int most = 0;
@@ -709,6 +748,10 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
                 l.probs = tb + o_ho + pd.off_probs * sizeof(HandoverProblem);
                 break;
             case Kind::Propagate:  // queue entries hold absolute indices into the problem table
+                if (l.prop.cluster > 0) {  // the launch's problems are consecutive
+                    l.probs = tb + o_prop + pd.off_probs * sizeof(PropProblem);
+                    break;
+                }
                 l.probs = tb + o_prop;
                 l.queue = reinterpret_cast<const int2*>(tb + o_q) + pd.off_queue;
                 l.counter = reinterpret_cast<int*>(tb + o_cnt) + pd.counter;
@@ -738,11 +781,12 @@ ff_status execute_plan(ff_ctx* c, Plan& P) {
         cudaGraph_t g = nullptr;
         FF_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         ff_status s = FF_OK;
-        int nk = 0;
+        int nk = 0, nc = 0;
         for (const Launch& l : P.launches) {
             s = enqueue_launch(c, l);
             if (s != FF_OK) break;
             nk += kernels_of(l);
+            nc += clusters_of(l);
         }
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (s != FF_OK) {
@@ -757,10 +801,12 @@ ff_status execute_plan(ff_ctx* c, Plan& P) {
             return fail(c, FF_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
         }
         P.graph_nodes = nk;
+        P.cluster_nodes = nc;
     }
     FF_CUDA(c, cudaGraphLaunch(P.exec, c->stream));
     c->replays += 1;
     c->launches += P.graph_nodes;
+    c->cluster_launches += P.cluster_nodes;
     return FF_OK;
 }
 
@@ -831,6 +877,7 @@ void wave_shape(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, int k, 
 // wave-fitted variant of a configuration grows the tile (height first, then width, by at most a quarter) just
 // enough that the tiles fill one wave fewer; it returns the configuration unchanged when none does.
 TileCfg wave_fitted(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, int k, TileCfg t) {
+    if (t.cluster > 0) return t;
     int64_t tiles, slots;
     wave_shape(c, jobs, s, k, t, &tiles, &slots);
     if (slots < 1 || tiles <= slots) return t;
@@ -904,6 +951,8 @@ ff_status autotune(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
         free_plan(c, P);
         for (auto [ps, pk] : passes) {
             const int p = pass_index(ps, pk);
+            size_t sm = 0;  // a cluster-form candidate that cannot run this pass was replaced by the default there
+            if (per_pass[p].cluster > 0 && !cluster_fits(c, jobs, ps, pk, per_pass[p], &sm)) continue;
             if (pass_best[p] < best_ms[p]) {
                 best_ms[p] = pass_best[p];
                 best_cfg[p] = per_pass[p];
@@ -984,7 +1033,7 @@ bool pyr_view(const ff_pyr* p, PyrView* out) {
 TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all) {
     const int T = c->prm.iters;
     TileCfg tc;
-    if (level >= 0 && level < kMaxLevels && c->forced[level].tw > 0) {
+    if (level >= 0 && level < kMaxPasses && c->forced[level].threads > 0) {
         tc = c->forced[level];
     } else {
         // the configuration tuned for this level size with the nearest number of directions per launch
@@ -1002,6 +1051,7 @@ TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs
         }
         tc = best ? *best : default_cfg(c, level_pix_all, T);
     }
+    if (tc.cluster > 0) tc = default_cfg(c, level_pix_all, T);
     return {tc.tw, tc.th, std::min(tc.k, T), tc.threads, tc.spec};
 }
 
@@ -1408,15 +1458,23 @@ ff_status ff_autotune(ff_ctx* c, int n, const ff_pair_job* jobs, int reps) {
 
 ff_status ff_set_tuning(ff_ctx* c, int level, const ff_tuning* t) {
     if (!c) return FF_ERR_ARG;
-    if (level < 0 || level >= kMaxLevels) return fail(c, FF_ERR_ARG, "level %d outside 0..%d", level, kMaxLevels - 1);
-    TileCfg cfg{0, 0, 0, 0, 0};
+    if (level < 0 || level >= kMaxPasses)
+        return fail(c, FF_ERR_ARG, "pass %d outside 0..%d", level, kMaxPasses - 1);
+    TileCfg cfg{0, 0, 0, 0, 0, 0};
     if (t) {
-        cfg = TileCfg{t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate};
-        if (t->tile_w < 1 || t->tile_h < 1 || t->tile_w > 1024 || t->tile_h > 1024 || t->iters_per_launch < 1 ||
-            t->iters_per_launch > 255 || !prop_threads_ok(t->threads) || (t->speculate != 0 && t->speculate != 1) ||
-            !cfg_fits(cfg))
-            return fail(c, FF_ERR_ARG, "configuration %dx%d, %d iterations, %d threads, speculate %d is not valid",
-                        t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate);
+        cfg = TileCfg{t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate, t->cluster};
+        bool ok = t->iters_per_launch >= 1 && t->iters_per_launch <= 255 && (t->speculate == 0 || t->speculate == 1);
+        if (t->cluster == 0)
+            ok = ok && t->tile_w >= 1 && t->tile_h >= 1 && t->tile_w <= 1024 && t->tile_h <= 1024 &&
+                 prop_threads_ok(t->threads) && cfg_fits(cfg);
+        else  // the cluster form: the tile fields are unused, no speculation; whether a level can take it is
+              // decided per plan
+            ok = ok && t->cluster >= 1 && t->cluster <= kMaxCluster && (t->threads == 256 || t->threads == 512) &&
+                 t->tile_w == 0 && t->tile_h == 0 && t->speculate == 0;
+        if (!ok)
+            return fail(c, FF_ERR_ARG,
+                        "configuration %dx%d, %d iterations, %d threads, speculate %d, cluster %d is not valid",
+                        t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate, t->cluster);
     }
     FF_CUDA(c, cudaSetDevice(c->device));
     ff_status s = drop_plans(c);
@@ -1426,9 +1484,9 @@ ff_status ff_set_tuning(ff_ctx* c, int level, const ff_tuning* t) {
 }
 
 ff_status ff_get_tuning(ff_ctx* c, int level, ff_tuning* out) {
-    if (!c || !out || level < 0 || level >= kMaxLevels) return FF_ERR_ARG;
+    if (!c || !out || level < 0 || level >= kMaxPasses) return FF_ERR_ARG;
     const TileCfg* f = nullptr;
-    if (c->forced[level].tw > 0) {
+    if (c->forced[level].threads > 0) {
         f = &c->forced[level];
     } else {
         for (auto& kv : c->tuned)
@@ -1438,7 +1496,7 @@ ff_status ff_get_tuning(ff_ctx* c, int level, ff_tuning* out) {
             }
     }
     if (!f) return fail(c, FF_ERR_ARG, "level %d has not been tuned", level);
-    *out = ff_tuning{f->tw, f->th, f->k, f->threads, f->spec};
+    *out = ff_tuning{f->tw, f->th, f->k, f->threads, f->spec, f->cluster};
     return FF_OK;
 }
 
@@ -1523,7 +1581,9 @@ ff_status ff_sync(ff_ctx* c) {
         FF_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
         if (e != 0) {
             FF_CUDA(c, cudaMemset(c->d_err, 0, sizeof e));
-            return fail(c, FF_ERR_TIMEOUT, "a device-side wait of the tensor-core seed expired (code %d)", e);
+            return fail(c, FF_ERR_TIMEOUT, "a device-side wait expired (code %d: %s)", e,
+                        e == kErrClusterEdges ? "block edges of the cluster-form propagation"
+                                              : "copies or products of the tensor-core seed");
         }
     }
     return FF_OK;
@@ -1563,6 +1623,7 @@ ff_status ff_get_stats(ff_ctx* c, ff_stats* out) {
     out->graph_replays = c->replays;
     out->plans_built = c->plans_built;
     out->scratch_bytes = c->bytes;
+    out->cluster_launches = c->cluster_launches;
     return FF_OK;
 }
 

@@ -160,9 +160,45 @@ struct PropLaunch {
     int spec;        // 1: load the random candidate together with the neighbour candidates
     int cost;        // FF_COST_WHT_SAD or FF_COST_CENSUS
     int grid;        // 1: the problems are sub-scale grids (g > 1)
+    int cluster;     // 0: tiles from a queue; n = 1..16: cluster form, one cluster of n CTAs per problem
+    int cl_smem;     // cluster form: dynamic shared memory per CTA (the largest over the launch's problems)
+    uint32_t wait_limit;  // cluster form: polls before a wait for neighbouring block edges gives up
+    int withhold;    // cluster form, test of the bounded waits: send no block edges
+    int* err;        // cluster form: device error word (code kErrClusterEdges when a wait gave up)
 };
+constexpr int kErrClusterEdges = 3;  // error-word code of an expired cluster-form wait (1, 2: tensor-core seed)
 constexpr size_t kMaxPropSmem = 200 * 1024;
+constexpr int kMaxCluster = 16;
 size_t prop_smem_bytes(int tw, int th, int n_iter);
+
+// Cluster form of a propagation launch: the n CTAs of a cluster split a w x h problem into bx x by blocks
+// (bx * by = n), CTA r owning block (r % bx, r / bx) with columns [i*w/bx, (i+1)*w/bx) and rows
+// [j*h/by, (j+1)*h/by).  The divisor pair with the smallest total block perimeter (w*by + h*bx) is taken, among
+// those that leave every block at least one pixel wide and high; false if there is none.
+__host__ __device__ inline bool cluster_partition(int w, int h, int n, int& bx, int& by) {
+    bool found = false;
+    long long best = 0;
+    for (int a = 1; a <= n; a++) {
+        if (n % a != 0) continue;
+        const int b = n / a;
+        if (a > w || b > h) continue;
+        const long long score = (long long)w * b + (long long)h * a;
+        if (!found || score < best) {
+            found = true;
+            best = score;
+            bx = a;
+            by = b;
+        }
+    }
+    return found;
+}
+// Shared memory of a CTA of the cluster form (the same layout in every CTA of a cluster): two mbarriers; the
+// rings of neighbouring edge flows (left and right columns of mh, upper and lower rows of mw entries); the flows
+// and costs of the block (mw x mh each), where mw x mh = ceil(w / bx) x ceil(h / by) bounds every block.
+__host__ __device__ inline size_t cluster_smem_bytes(int w, int h, int bx, int by) {
+    const size_t mw = (size_t)(w + bx - 1) / bx, mh = (size_t)(h + by - 1) / by;
+    return 16 + 4 * (2 * mw + 2 * mh) + 8 * mw * mh;
+}
 cudaError_t init_kernel_attributes();  // once per device, before the first launch (also loads k_handover)
 cudaError_t seed_load_kernel();        // loads k_seed onto the current device (lazy module loading)
 // Set-up of ff_match_pair_noalloc on the current device, run by ff_create: loads its module (which reserves the
@@ -170,9 +206,13 @@ cudaError_t seed_load_kernel();        // loads k_seed onto the current device (
 cudaError_t noalloc_prepare(void** scratch);
 bool prop_threads_ok(int threads);
 int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost, bool grid = false);  // resident CTAs per SM
-// queue_dev[i] = (problem index, tile index); counter_dev must be zero when the launch starts
+// Tile form (L.cluster == 0): queue_dev[i] = (problem index, tile index); counter_dev must be zero when the launch
+// starts; `grid` CTAs.  Cluster form: problem i is probs_dev[i], `grid` = number of problems x L.cluster CTAs;
+// queue_dev and counter_dev are unused.
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st);
+// Clusters of the cluster form that can be resident at once (0: this shape cannot be launched).
+int prop_cluster_capacity(int cluster, int threads, int cost, bool grid, size_t smem);
 
 // ---------------------------------------------------------------------------------------------------------
 // consistency
@@ -214,7 +254,7 @@ struct CtxView {
     int sub_scales;
 };
 struct TileChoice {
-    int tw, th, k, threads, spec;
+    int tw, th, k, threads, spec;  // always the tile form (see ctx_level_choice)
 };
 
 // ---------------------------------------------------------------------------------------------------------
@@ -238,6 +278,39 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     x *= 0x846ca68bU;
     x ^= x >> 16;
     return x;
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// mbarrier helpers (shared memory of the executing CTA; waits are CTA-scope acquires)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false after `limit` polls; after the first `spin` polls each
+// further poll is preceded by a 256 ns sleep (so the default limit of 2^22 polls is about a second).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit, uint32_t spin = 64) {
+    for (uint32_t i = 0; i < limit; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > spin) __nanosleep(256);
+    }
+    return false;
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -315,7 +388,9 @@ namespace ff {
 bool ctx_view(const ff_ctx* c, CtxView* out);
 bool ctx_owns_live_pyr(const ff_ctx* c, const ff_pyr* p);
 bool pyr_view(const ff_pyr* p, PyrView* out);
-// the launch configuration of a pass (level s, or its sub-scale grid s + 8k) of size w x h
+// the launch configuration of a pass (level s, or its sub-scale grid s + 8k) of size w x h, in the tile form (a
+// cluster-form choice is replaced by the default tile configuration: the server and the no-allocation entry
+// point launch tiles only)
 TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all);
 // cudaMalloc on behalf of a context; fails as out of memory while the context's FF_OPT_TEST_FAIL_ALLOCS count lasts
 cudaError_t ctx_malloc(ff_ctx* c, void** p, size_t bytes);

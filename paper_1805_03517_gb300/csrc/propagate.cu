@@ -36,7 +36,8 @@ cudaError_t bounds_take_propagate(int rec[3]) {
 
 // Bounds codes of this file's checks.
 enum : int { kBoundsOwn = 1, kBoundsCand1, kBoundsCand2, kBoundsRandom, kBoundsSpec, kBoundsSmemOwn, kBoundsSmemN1,
-             kBoundsSmemN2, kBoundsTileRead, kBoundsTileSmem, kBoundsTileWrite, kBoundsParent, kBoundsHandoverDesc };
+             kBoundsSmemN2, kBoundsTileRead, kBoundsTileSmem, kBoundsTileWrite, kBoundsParent, kBoundsHandoverDesc,
+             kBoundsBlockRead, kBoundsBlockSmem, kBoundsBlockWrite, kBoundsRingN1, kBoundsRingN2 };
 
 __device__ __forceinline__ int flow_x(uint32_t f) { return (int)(int16_t)(f & 0xffffu); }
 __device__ __forceinline__ int flow_y(uint32_t f) { return ((int)f) >> 16; }
@@ -210,30 +211,105 @@ __device__ __forceinline__ bool region_pixel(int i, int HW, int rx0, int ry0, in
     return x < rx1;
 }
 
-// One half-sweep with one thread per pixel (the whole descriptor per thread: 96 B WHT, 32 B Census).  With SPEC
-// the random candidate of directions 1..3 is fetched together with the neighbour candidates, assuming the
-// neighbours will not change the pixel's flow; if one of them is taken, the random candidate is fetched again
-// from the new flow.  Either way the candidate evaluated is the one the schedule defines, so results are
-// identical.  (Fetching it early only into a buffer no neighbour needs, without SPEC, measured 16 % slower on
-// the 1242x375 pair.)
+// The candidates of one pixel (x, y) of a grid in a half-sweep of direction d, one thread per pixel (the whole
+// descriptor per thread: 96 B WHT, 32 B Census): neighbour 1 (horizontal, flow f1, valid if v1), neighbour 2
+// (vertical, f2, v2) and, for d >= 1, the hashed random offset around the flow after them.  cur / c hold the
+// pixel's flow and cost and are updated; false if there was nothing to try (they are unchanged).  With SPEC the
+// random candidate of directions 1..3 is fetched together with the neighbour candidates, assuming the neighbours
+// will not change the pixel's flow; if one of them is taken, the random candidate is fetched again from the new
+// flow.  Either way the candidate evaluated is the one the schedule defines, so results are identical.
+// (Fetching it early only into a buffer no neighbour needs, without SPEC, measured 16 % slower on the 1242x375
+// pair.)
+// Per-launch constants of update_pixel, read from the problem once per half-sweep.
+struct SweepConst {
+    int g, lw, lh;  // grid stride and level size: grid pixel (x, y) is level pixel (g*x, g*y)
+    int R;          // random-search radius
+    uint32_t span;  // 2R + 1
+};
+template <bool GRID>
+__device__ __forceinline__ SweepConst sweep_const(const PropProblem& P) {
+    const int R = P.rs_radius;
+    return {GRID ? P.g : 1, GRID ? P.lw : P.w, GRID ? P.lh : P.h, R, 2u * R + 1u};
+}
+
+template <class C, bool SPEC, bool GRID>
+__device__ __forceinline__ bool update_pixel(const PropProblem& P, const SweepConst& K, int x, int y, int d,
+                                             uint32_t k1, bool v1, uint32_t f1, bool v2, uint32_t f2, uint32_t& cur,
+                                             int& c) {
+    // flows and targets are in level pixels
+    const int g = K.g, lw = K.lw, lh = K.lh, R = K.R;
+    const uint32_t span = K.span;
+    const int n_d = lw * lh;  // descriptors of the level
+    // a candidate equal to the current flow (or to an already tried one) cannot be strictly cheaper
+    const int X = g * x, Y = g * y;  // level coordinates
+    const bool e1 = v1 && f1 != cur && in_level(X + flow_x(f1), Y + flow_y(f1), lw, lh);
+    const bool e2 = v2 && f2 != cur && !(v1 && f2 == f1) && in_level(X + flow_x(f2), Y + flow_y(f2), lw, lh);
+    if (!(e1 || e2 || d >= 1)) return false;
+    int ox = 0, oy = 0;
+    if (d >= 1) {
+        const uint32_t k2 = mix32(k1 ^ ((uint32_t)Y * 65536u + (uint32_t)X));
+        ox = (int)(mix32(k2 ^ (uint32_t)(2 * d)) % span) - R;
+        oy = (int)(mix32(k2 ^ (uint32_t)(2 * d + 1)) % span) - R;
+    }
+    const bool rnd = ox != 0 || oy != 0;
+    const uint32_t cur0 = cur;
+    // issue every independent load (own descriptor, neighbour candidates, speculative random) before compute
+    uint32_t a[C::kWords], b1[C::kWords], b2[C::kWords];
+    uint32_t b3[SPEC ? C::kWords : 1];
+    load_chk<C>(P.fa, feat_index(X, Y, lw), n_d, kBoundsOwn, a);
+    if (e1) load_chk<C>(P.fb, feat_index(X + flow_x(f1), Y + flow_y(f1), lw), n_d, kBoundsCand1, b1);
+    if (e2) load_chk<C>(P.fb, feat_index(X + flow_x(f2), Y + flow_y(f2), lw), n_d, kBoundsCand2, b2);
+    if constexpr (SPEC) {
+        const int sx = flow_x(cur) + ox, sy = flow_y(cur) + oy;
+        if (rnd && in_level(X + sx, Y + sy, lw, lh))
+            load_chk<C>(P.fb, feat_index(X + sx, Y + sy, lw), n_d, kBoundsSpec, b3);
+    }
+    C::prep(a);
+    if (e1) {
+        int s1 = C::dist(a, b1);
+        if (s1 < c) { cur = f1; c = s1; }
+    }
+    if (e2) {
+        int s2 = C::dist(a, b2);
+        if (s2 < c) { cur = f2; c = s2; }
+    }
+    if (rnd) {
+        const int fx = flow_x(cur) + ox, fy = flow_y(cur) + oy;
+        if (in_level(X + fx, Y + fy, lw, lh)) {
+            int s3;
+            if constexpr (SPEC) {
+                if (cur == cur0) {
+                    s3 = C::dist(a, b3);  // same target as speculated (which was then in the level)
+                } else {
+                    load_chk<C>(P.fb, feat_index(X + fx, Y + fy, lw), n_d, kBoundsRandom, b1);
+                    s3 = C::dist(a, b1);
+                }
+            } else {
+                load_chk<C>(P.fb, feat_index(X + fx, Y + fy, lw), n_d, kBoundsRandom, b1);
+                s3 = C::dist(a, b1);
+            }
+            if (s3 < c) { cur = pack_flow(fx, fy); c = s3; }
+        }
+    }
+    return true;
+}
+
+// One half-sweep of a tile's region (tile form).
 template <class C, bool SPEC, bool GRID>
 __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& G, uint32_t* sflow, int32_t* scost,
                                           int j, int rem, uint32_t k1) {
     const int w = P.w, h = P.h;  // the grid (the level itself unless GRID)
-    // GRID: grid pixel (x, y) is level pixel (g*x, g*y) of a lw x lh level; flows and targets are in level pixels
-    const int g = GRID ? P.g : 1, lw = GRID ? P.lw : w, lh = GRID ? P.lh : h;
     const int d = j >> 1, colour = j & 1;
     int rx0, ry0, rx1, ry1;
     halfsweep_region(G, w, h, j, rem, rx0, ry0, rx1, ry1);
     const int HW = (rx1 - rx0 + 1) >> 1;
     const int total = HW * (ry1 - ry0);
-    const int R = P.rs_radius;
-    const uint32_t span = 2u * R + 1u;
+    const SweepConst K = sweep_const<GRID>(P);
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
         int x, y;
         if (!region_pixel(i, HW, rx0, ry0, rx1, colour, x, y)) continue;
         const int sidx = (y - G.ly0) * G.RW + (x - G.lx0);
-        const int n_s = G.RW * G.RH, n_d = lw * lh;  // shared-memory entries, descriptors of the level
+        const int n_s = G.RW * G.RH;  // shared-memory entries
         if (!idx_ok(g_bounds, kBoundsSmemOwn, sidx, n_s)) continue;
         uint32_t cur = sflow[sidx];
         int c = scost[sidx];
@@ -244,57 +320,7 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
         const uint32_t f1 = v1 && idx_ok(g_bounds, kBoundsSmemN1, sidx + (n1x - x), n_s) ? sflow[sidx + (n1x - x)] : 0u;
         const uint32_t f2 =
             v2 && idx_ok(g_bounds, kBoundsSmemN2, sidx + (n2y - y) * G.RW, n_s) ? sflow[sidx + (n2y - y) * G.RW] : 0u;
-        // a candidate equal to the current flow (or to an already tried one) cannot be strictly cheaper
-        const int X = g * x, Y = g * y;  // level coordinates
-        const bool e1 = v1 && f1 != cur && in_level(X + flow_x(f1), Y + flow_y(f1), lw, lh);
-        const bool e2 = v2 && f2 != cur && !(v1 && f2 == f1) && in_level(X + flow_x(f2), Y + flow_y(f2), lw, lh);
-        if (!(e1 || e2 || d >= 1)) continue;
-        int ox = 0, oy = 0;
-        if (d >= 1) {
-            const uint32_t k2 = mix32(k1 ^ ((uint32_t)Y * 65536u + (uint32_t)X));
-            ox = (int)(mix32(k2 ^ (uint32_t)(2 * d)) % span) - R;
-            oy = (int)(mix32(k2 ^ (uint32_t)(2 * d + 1)) % span) - R;
-        }
-        const bool rnd = ox != 0 || oy != 0;
-        const uint32_t cur0 = cur;
-        // issue every independent load (own descriptor, neighbour candidates, speculative random) before compute
-        uint32_t a[C::kWords], b1[C::kWords], b2[C::kWords];
-        uint32_t b3[SPEC ? C::kWords : 1];
-        load_chk<C>(P.fa, feat_index(X, Y, lw), n_d, kBoundsOwn, a);
-        if (e1) load_chk<C>(P.fb, feat_index(X + flow_x(f1), Y + flow_y(f1), lw), n_d, kBoundsCand1, b1);
-        if (e2) load_chk<C>(P.fb, feat_index(X + flow_x(f2), Y + flow_y(f2), lw), n_d, kBoundsCand2, b2);
-        if constexpr (SPEC) {
-            const int sx = flow_x(cur) + ox, sy = flow_y(cur) + oy;
-            if (rnd && in_level(X + sx, Y + sy, lw, lh))
-                load_chk<C>(P.fb, feat_index(X + sx, Y + sy, lw), n_d, kBoundsSpec, b3);
-        }
-        C::prep(a);
-        if (e1) {
-            int s1 = C::dist(a, b1);
-            if (s1 < c) { cur = f1; c = s1; }
-        }
-        if (e2) {
-            int s2 = C::dist(a, b2);
-            if (s2 < c) { cur = f2; c = s2; }
-        }
-        if (rnd) {
-            const int fx = flow_x(cur) + ox, fy = flow_y(cur) + oy;
-            if (in_level(X + fx, Y + fy, lw, lh)) {
-                int s3;
-                if constexpr (SPEC) {
-                    if (cur == cur0) {
-                        s3 = C::dist(a, b3);  // same target as speculated (which was then in the level)
-                    } else {
-                        load_chk<C>(P.fb, feat_index(X + fx, Y + fy, lw), n_d, kBoundsRandom, b1);
-                        s3 = C::dist(a, b1);
-                    }
-                } else {
-                    load_chk<C>(P.fb, feat_index(X + fx, Y + fy, lw), n_d, kBoundsRandom, b1);
-                    s3 = C::dist(a, b1);
-                }
-                if (s3 < c) { cur = pack_flow(fx, fy); c = s3; }
-            }
-        }
+        if (!update_pixel<C, SPEC, GRID>(P, K, x, y, d, k1, v1, f1, v2, f2, cur, c)) continue;
         sflow[sidx] = cur;
         scost[sidx] = c;
     }
@@ -371,7 +397,193 @@ __global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate
     }
 }
 
+// ---------------------------------------------------------------------------------------------------------
+// Cluster form: one cluster of n CTAs per problem runs every iteration of the launch over the whole grid, with no
+// halo recomputation.  CTA r owns block r of the partition cluster_partition() gives and keeps the block's flow
+// and cost in shared memory, with a one-pixel ring of the neighbouring blocks' edge flows.  After computing an
+// edge pixel of the active colour, a CTA stores its flow straight into the ring of each CTA beside that edge
+// (st.async into the neighbour's shared memory, completing 4 bytes on the neighbour's mbarrier of that
+// half-sweep), and before the next half-sweep reads its ring it waits on its own mbarrier for the edges it
+// receives.  The waits are CTA-scope: a cluster-wide barrier per half-sweep, an acquire at cluster scope, also
+// emptied the L1 that the next half-sweep's gathers reuse (8 % L1 hits instead of 83 % at level 4 of the
+// 1242x375 pair).  A half-sweep reads exactly the state the previous one left, so the schedule is the tile
+// form's, evaluated once per pixel.  Every wait is bounded (wait_limit polls); one that expires records
+// kErrClusterEdges in the error word and the CTA stops waiting (the launch runs to its end; ff_sync then fails).
+// An alternative for small levels of a few problems, where the tile form's halo is most of the work; the
+// autotuner weighs the two forms per level.
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ int cluster_rank() {
+    uint32_t r;
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+__device__ __forceinline__ int cluster_ctas() {
+    uint32_t n;
+    asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return (int)n;
+}
+// Address, in the cluster's shared-memory window, of `p` (this CTA's shared memory) in CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, int rank) {
+    uint32_t a;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+    return a;
+}
+// 4-byte store into another CTA's shared memory that completes 4 bytes on the mbarrier `bar` (cluster window).
+__device__ __forceinline__ void st_async_u32(uint32_t addr, uint32_t v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr), "r"(v),
+                 "r"(bar)
+                 : "memory");
+}
+// Number of v in [a, b) with (k + v) of colour c ((k + v) & 1 == c).
+__device__ __forceinline__ int colour_count(int k, int a, int b, int c) {
+    const int first = a + ((c - k - a) & 1);
+    return first < b ? (b - 1 - first) / 2 + 1 : 0;
+}
+
+// (no speculative variant: measured slower at every coarse level in this form)
+template <int THREADS, class C, bool GRID = false>
+__global__ __launch_bounds__(THREADS, 1) void k_propagate_cl(const PropProblem* __restrict__ probs, PropLaunch L) {
+    grid_dependency_sync();
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int n = cluster_ctas(), r = cluster_rank();
+    const PropProblem& P = probs[blockIdx.x / n];
+    const int w = P.w, h = P.h;
+    int bx = 1, by = 1;
+    cluster_partition(w, h, n, bx, by);  // the host launches only problems that have a partition
+    const int bi = r % bx, bj = r / bx;
+    const int x0 = bi * w / bx, x1 = (bi + 1) * w / bx, y0 = bj * h / by, y1 = (bj + 1) * h / by;
+    const int bw = x1 - x0, bh = y1 - y0, nb = bw * bh;
+    const int mw = (w + bx - 1) / bx, mh = (h + by - 1) / by;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);  // [2]: the edges received in even / odd half-sweeps
+    uint32_t* ring_l = smem + 4;                         // [mh] flows of column x0 - 1
+    uint32_t* ring_r = ring_l + mh;                      // [mh] column x1
+    uint32_t* ring_u = ring_r + mh;                      // [mw] row y0 - 1
+    uint32_t* ring_d = ring_u + mw;                      // [mw] row y1
+    uint32_t* sflow = ring_d + mw;                       // [mw * mh] the block, row-major with width bw
+    int32_t* scost = reinterpret_cast<int32_t*>(sflow + mw * mh);
+    const bool has_l = bi > 0, has_r = bi + 1 < bx, has_u = bj > 0, has_d = bj + 1 < by;
+    // an edge pixel's flow goes to the opposite ring of the CTA beside it, completing on that CTA's mbarrier
+    const uint32_t to_l = has_l ? cluster_addr(ring_r, r - 1) : 0u, mb_l = has_l ? cluster_addr(mbar, r - 1) : 0u;
+    const uint32_t to_r = has_r ? cluster_addr(ring_l, r + 1) : 0u, mb_r = has_r ? cluster_addr(mbar, r + 1) : 0u;
+    const uint32_t to_u = has_u ? cluster_addr(ring_d, r - bx) : 0u, mb_u = has_u ? cluster_addr(mbar, r - bx) : 0u;
+    const uint32_t to_d = has_d ? cluster_addr(ring_u, r + bx) : 0u, mb_d = has_d ? cluster_addr(mbar, r + bx) : 0u;
+    // bytes received per half-sweep of colour c: the neighbours' edge pixels of that colour next to this block
+    uint32_t rx_bytes[2];
+#pragma unroll
+    for (int c = 0; c < 2; c++)
+        rx_bytes[c] = 4u * (uint32_t)((has_l ? colour_count(x0 - 1, y0, y1, c) : 0) +
+                                      (has_r ? colour_count(x1, y0, y1, c) : 0) +
+                                      (has_u ? colour_count(y0 - 1, x0, x1, c) : 0) +
+                                      (has_d ? colour_count(y1, x0, x1, c) : 0));
+    const bool fits = !FF_DEBUG_BOUNDS ||
+                      idx_ok(g_bounds, kBoundsBlockSmem, (long long)cluster_smem_bytes(w, h, bx, by) - 1,
+                             dyn_smem_bytes());
+    const int J = 8 * P.n_iter;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // half-sweeps 0 and 1: the first phase of each mbarrier (a colour with no edges to receive never waits)
+        if (rx_bytes[0] != 0) mbar_expect_tx(smem_u32(&mbar[0]), rx_bytes[0]);
+        if (J > 1 && rx_bytes[1] != 0) mbar_expect_tx(smem_u32(&mbar[1]), rx_bytes[1]);
+    }
+    // the block and the ring from the launch's input state
+    const long long n_in = (long long)w * h;
+    for (int i = threadIdx.x; i < nb; i += THREADS) {
+        const long long gi = (long long)(y0 + i / bw) * w + x0 + i % bw;
+        const bool ok = fits && idx_ok(g_bounds, kBoundsBlockRead, gi, n_in);
+        sflow[i] = ok ? P.flow_in[gi] : 0u;
+        scost[i] = ok ? P.cost_in[gi] : 0;
+    }
+    for (int i = threadIdx.x; i < bh; i += THREADS) {
+        const long long left = (long long)(y0 + i) * w + x0 - 1, right = (long long)(y0 + i) * w + x1;
+        if (has_l && fits && idx_ok(g_bounds, kBoundsBlockRead, left, n_in)) ring_l[i] = P.flow_in[left];
+        if (has_r && fits && idx_ok(g_bounds, kBoundsBlockRead, right, n_in)) ring_r[i] = P.flow_in[right];
+    }
+    for (int i = threadIdx.x; i < bw; i += THREADS) {
+        const long long up = (long long)(y0 - 1) * w + x0 + i, down = (long long)y1 * w + x0 + i;
+        if (has_u && fits && idx_ok(g_bounds, kBoundsBlockRead, up, n_in)) ring_u[i] = P.flow_in[up];
+        if (has_d && fits && idx_ok(g_bounds, kBoundsBlockRead, down, n_in)) ring_d[i] = P.flow_in[down];
+    }
+    cluster_sync_all();  // every CTA of the cluster running, its block loaded and its mbarriers armed
+    const int HW = (bw + 1) >> 1, total = HW * bh;
+    const SweepConst K = sweep_const<GRID>(P);
+    bool failed = false;  // a wait expired: stop waiting (CTA-uniform)
+    uint32_t k1 = 0;
+    for (int j = 0; j < J; j++) {
+        if ((j & 7) == 0) {
+            const uint32_t t = (uint32_t)(P.t0 + (j >> 3));
+            k1 = mix32(P.seed ^ mix32((uint32_t)P.dir * 65536u + (uint32_t)P.level * 256u + t));
+        }
+        const int d = (j & 7) >> 1, colour = j & 1;
+        const uint32_t slot = 8u * (uint32_t)(j & 1);  // byte offset of this half-sweep's mbarrier
+        for (int i = threadIdx.x; i < total; i += THREADS) {
+            const int row = i / HW, slot_x = i - row * HW;
+            const int y = y0 + row;
+            const int x = x0 + 2 * slot_x + ((x0 + y + colour) & 1);
+            if (x >= x1 || !fits) continue;
+            const int sidx = row * bw + (x - x0);
+            uint32_t cur = sflow[sidx];
+            int c = scost[sidx];
+            const int n1x = x + ((d & 1) ? 1 : -1);
+            const int n2y = y + ((d & 2) ? 1 : -1);
+            const bool v1 = (unsigned)n1x < (unsigned)w;
+            const bool v2 = (unsigned)n2y < (unsigned)h;
+            uint32_t f1 = 0u, f2 = 0u;
+            if (v1) {
+                if (n1x < x0)
+                    f1 = idx_ok(g_bounds, kBoundsRingN1, row, mh) ? ring_l[row] : 0u;
+                else if (n1x >= x1)
+                    f1 = idx_ok(g_bounds, kBoundsRingN1, row, mh) ? ring_r[row] : 0u;
+                else
+                    f1 = sflow[sidx + (n1x - x)];
+            }
+            if (v2) {
+                if (n2y < y0)
+                    f2 = idx_ok(g_bounds, kBoundsRingN2, x - x0, mw) ? ring_u[x - x0] : 0u;
+                else if (n2y >= y1)
+                    f2 = idx_ok(g_bounds, kBoundsRingN2, x - x0, mw) ? ring_d[x - x0] : 0u;
+                else
+                    f2 = sflow[sidx + (n2y - y) * bw];
+            }
+            if (update_pixel<C, false, GRID>(P, K, x, y, d, k1, v1, f1, v2, f2, cur, c)) {
+                sflow[sidx] = cur;
+                scost[sidx] = c;
+            }
+            if (!L.withhold) {  // every edge pixel of the colour is sent, changed or not (fixed byte counts)
+                if (has_l && x == x0) st_async_u32(to_l + 4u * row, cur, mb_l + slot);
+                if (has_r && x == x1 - 1) st_async_u32(to_r + 4u * row, cur, mb_r + slot);
+                if (has_u && y == y0) st_async_u32(to_u + 4u * (x - x0), cur, mb_u + slot);
+                if (has_d && y == y1 - 1) st_async_u32(to_d + 4u * (x - x0), cur, mb_d + slot);
+            }
+        }
+        // the neighbours' edges of this colour, read by the next half-sweep
+        const bool rx = rx_bytes[j & 1] != 0;
+        // (this wait is on the critical path of every half-sweep: spin for the first 4096 polls, then sleep)
+        const bool ok =
+            failed || !rx || mbar_wait(smem_u32(&mbar[j & 1]), (uint32_t)(j >> 1) & 1u, L.wait_limit, 4096);
+        if (!ok) atomicCAS(L.err, 0, kErrClusterEdges);
+        // the same mbarrier's next phase, half-sweep j + 2, armed before this CTA sends any edge of half-sweep
+        // j + 1 (which the neighbours' sends of j + 2 wait for); as it expects bytes, it cannot complete before
+        // every thread here has seen this phase complete, for the same reason
+        if (threadIdx.x == 0 && rx && ok && !failed && j + 2 < J)
+            mbar_expect_tx(smem_u32(&mbar[j & 1]), rx_bytes[j & 1]);
+        failed = __syncthreads_or(!ok) != 0 || failed;
+    }
+    for (int i = threadIdx.x; i < nb; i += THREADS) {
+        const long long gi = (long long)(y0 + i / bw) * w + x0 + i % bw;
+        if (!fits || !idx_ok(g_bounds, kBoundsBlockWrite, gi, n_in)) continue;
+        P.flow_out[gi] = sflow[i];
+        P.cost_out[gi] = scost[i];
+    }
+    cluster_sync_all();  // no CTA leaves while edge stores of its neighbours may still target its shared memory
+}
+
 using PropKernel = void (*)(const PropProblem*, const int2*, int, int*, PropLaunch);
+using PropClusterKernel = void (*)(const PropProblem*, PropLaunch);
 
 template <class C, bool SPEC, bool GRID>
 PropKernel prop_kernel_t(int threads) {
@@ -391,6 +603,39 @@ PropKernel prop_kernel(int threads, bool spec, int cost, bool grid = false) {
                                   : prop_kernel_c<CostSad>(threads, spec, grid);
 }
 
+// The cluster form is instantiated for 256 and 512 threads, per cost, for levels and for sub-scale grids.
+template <class C, bool GRID>
+PropClusterKernel prop_cl_kernel_t(int threads) {
+    return threads == 512 ? k_propagate_cl<512, C, GRID> : k_propagate_cl<256, C, GRID>;
+}
+
+template <class C>
+PropClusterKernel prop_cl_kernel_c(int threads, bool grid) {
+    return grid ? prop_cl_kernel_t<C, true>(threads) : prop_cl_kernel_t<C, false>(threads);
+}
+
+PropClusterKernel prop_cl_kernel(int threads, int cost, bool grid) {
+    return cost == FF_COST_CENSUS ? prop_cl_kernel_c<CostCensus>(threads, grid) : prop_cl_kernel_c<CostSad>(threads, grid);
+}
+
+cudaLaunchConfig_t cluster_config(int n_ctas, int cluster, int threads, size_t smem, cudaStream_t st,
+                                  cudaLaunchAttribute (&attr)[2]) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_ctas);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = FF_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cfg;
+}
+
 cudaError_t init_kernel_attributes() {
     cudaFuncAttributes fa;
     cudaError_t e0 = cudaFuncGetAttributes(&fa, k_handover<CostSad>);
@@ -405,6 +650,14 @@ cudaError_t init_kernel_attributes() {
                                                          (int)kMaxPropSmem);
                     if (e != cudaSuccess) return e;
                 }
+    for (int cost : {FF_COST_WHT_SAD, FF_COST_CENSUS})
+        for (int t : {256, 512})
+            for (bool grid : {false, true}) {
+                PropClusterKernel k = prop_cl_kernel(t, cost, grid);
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
+                if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+                if (e != cudaSuccess) return e;
+            }
     return cudaSuccess;
 }
 
@@ -421,8 +674,26 @@ int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost, bool grid)
     return n > 0 ? n : 1;
 }
 
+int prop_cluster_capacity(int cluster, int threads, int cost, bool grid, size_t smem) {
+    if (cluster < 1 || cluster > kMaxCluster || (threads != 256 && threads != 512) || smem > kMaxPropSmem) return 0;
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = cluster_config(cluster, cluster, threads, smem, nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, prop_cl_kernel(threads, cost, grid), &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st) {
+    if (L.cluster > 0) {
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = cluster_config(grid, L.cluster, L.threads, (size_t)L.cl_smem, st, attr);
+        cudaLaunchKernelEx(&cfg, prop_cl_kernel(L.threads, L.cost, L.grid != 0), probs_dev, L);
+        return;
+    }
     size_t smem = prop_smem_bytes(L.tw, L.th, L.max_iter);
     launch_k(prop_kernel(L.threads, L.spec != 0, L.cost, L.grid != 0), dim3(grid), dim3(L.threads),
              smem, st, probs_dev, queue_dev, n_tiles, counter_dev, L);

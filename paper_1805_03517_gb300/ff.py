@@ -59,12 +59,13 @@ class Frame(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("iters_per_launch", ctypes.c_int),
-                ("threads", ctypes.c_int), ("speculate", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("speculate", ctypes.c_int), ("cluster", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
-                ("plans_built", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64)]
+                ("plans_built", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
+                ("cluster_launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -179,19 +180,22 @@ def ff_autotune(ctx, jobs, reps: int = 3):
 
 
 def ff_set_tuning(ctx, level: int, cfg):
-    """cfg: (tile_w, tile_h, iters_per_launch, threads, speculate) or None to remove the override."""
+    """cfg: (tile_w, tile_h, iters_per_launch[, threads[, speculate[, cluster]]]) (threads 256, speculate 0 and
+    cluster 0 by default) or None to remove the override."""
     if cfg is None:
         _check(ctx, lib().ff_set_tuning(ctx, level, None))
         return
-    t = Tuning(*cfg) if len(cfg) == 5 else Tuning(*cfg, *((256, 0)[len(cfg) - 3:]))
+    t = Tuning(*cfg, *((256, 0, 0)[len(cfg) - 3:]))
     _check(ctx, lib().ff_set_tuning(ctx, level, ctypes.byref(t)))
 
 
 def ff_get_tuning(ctx, level: int):
-    """(tile_w, tile_h, iters_per_launch, threads, speculate) in force for `level`."""
+    """(tile_w, tile_h, iters_per_launch, threads, speculate) in force for `level`, with a sixth entry, the
+    cluster size, for a cluster-form configuration."""
     t = Tuning()
     _check(ctx, lib().ff_get_tuning(ctx, level, ctypes.byref(t)))
-    return t.tile_w, t.tile_h, t.iters_per_launch, t.threads, t.speculate
+    cfg = (t.tile_w, t.tile_h, t.iters_per_launch, t.threads, t.speculate)
+    return cfg + (t.cluster,) if t.cluster else cfg
 
 
 def ff_consistency(ctx, fwd: int, bwd: int, w: int, h: int, eps: int, mask_dev: int):

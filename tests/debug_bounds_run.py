@@ -1,7 +1,8 @@
 """Run by tests/test_gpu_failures.py in a child process whose FF_LIBRARY points at the debug-bounds build of
-libff: small parity cases against the oracle (plain, sub-scale grids, Census cost, two consistency checks and
-sparsification, a 1x1 and a 1-pixel-high frame), each followed by ff_sync, which fails if any index check of the
-propagation, hand-over or filter kernels recorded a violation.  Prints "debug-bounds ok" at the end."""
+libff: small parity cases against the oracle (plain, sub-scale grids, Census cost, the cluster form of the
+propagation on levels and grids, two consistency checks and sparsification, a 1x1 and a 1-pixel-high frame),
+each followed by ff_sync, which fails if any index check of the propagation, hand-over or filter kernels recorded
+a violation.  Prints "debug-bounds ok" at the end."""
 import os
 import sys
 
@@ -26,9 +27,18 @@ cases.append((configs.MatchParams(n_scales=3, iters=3, sub_scales=2), (a, b)))
 cases.append((configs.MatchParams(n_scales=3, iters=2, cost=1), (a, b)))
 cases.append((configs.MatchParams(n_scales=1, iters=2), (P.rand_img(5, 1, 1), P.rand_img(6, 1, 1))))
 cases.append((configs.MatchParams(n_scales=2, iters=2), (P.rand_img(7, 1, 37), P.rand_img(8, 1, 37))))
-for prm, (img_a, img_b) in cases:
+# the cluster form on every level and grid pass (16, 6 and 1 CTAs per problem: 4x4, 3x2 / 2x3 and 1x1 blocks)
+CLUSTER = {0: (0, 0, 3, 256, 0, 16), 1: (0, 0, 2, 512, 0, 6), 2: (0, 0, 3, 256, 0, 1), 8: (0, 0, 3, 512, 0, 6),
+           16: (0, 0, 1, 256, 0, 16), 9: (0, 0, 3, 256, 0, 16), 17: (0, 0, 3, 512, 0, 4)}
+cases.append((configs.MatchParams(n_scales=3, iters=3, sub_scales=2), (a, b), CLUSTER))
+cases.append((configs.MatchParams(n_scales=3, iters=2, cost=1), (a, b), CLUSTER))
+for prm, (img_a, img_b), *tuning in cases:
     M = ff.Matcher(prm, 0)
+    for p_, cfg in (tuning[0] if tuning else {}).items():
+        ff.ff_set_tuning(M.ctx, p_, cfg)
+    c0 = M.stats()["cluster_launches"]
     got = G.gpu_bidir(M, img_a, img_b, torch)  # ends with ff_sync: raises on a recorded violation
+    assert (M.stats()["cluster_launches"] > c0) == bool(tuning)
     G.assert_same(got, o.match_bidir(img_a, img_b, G.oracle_params(prm)))
     M.close()
 # two consistency checks and sparsification (Table 3, KITTI s)
