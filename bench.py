@@ -844,7 +844,8 @@ def main():
         # ncu's sustained wavefronts per cycle (whole GPU) x the SM clock sampled during the timed steps
         wf_peak = rec["wavefronts_peak_per_cycle"] * clocks["sm_mhz"] * 1e6
         wf_achieved = rec["wavefronts_per_launch"] / (l0_launch_ms / 1000.0)
-        roofline = {"bound": "l1", "kernel": "k_propagate (level-0 launches, 57 % of a step)",
+        share = (l0_ms / n_prof) / ms
+        roofline = {"bound": "l1", "kernel": f"k_propagate (level-0 launches, {100 * share:.0f} % of a step)",
                     "unit": "wavefronts/s", "achieved": wf_achieved, "peak": wf_peak,
                     "peak_kind": "ncu peak_sustained of l1tex__data_pipe_lsu_wavefronts x sampled SM clock",
                     "frac": wf_achieved / wf_peak, "traffic": rec["dram_bytes_per_launch"],

@@ -172,15 +172,20 @@ FF_API ff_status ff_autotune(ff_ctx* ctx, int n, const ff_pair_job* jobs, int re
 
 /* Propagation launch configuration of one level: tile interior (pixels), iterations fused per launch, threads
  * per CTA (128, 256 or 512), and whether the random candidate is fetched together with the neighbour candidates
- * (speculate = 1; refetched when a neighbour was taken).  cluster = 0 is this tile form.  cluster = n (1..16)
- * selects the cluster form instead: one thread-block cluster of n CTAs per direction of each pair covers the whole
- * level without a halo, CTAs exchanging their block edges through distributed shared memory (threads 256 or 512,
- * tile_w = tile_h = 0, speculate = 0); a plan falls back to the default tile form for a level the cluster form cannot take (a
- * level narrower or lower than the partition, blocks beyond shared memory, or clusters this device cannot
- * schedule).  The server (ff_server_*) and ff_match_pair_noalloc always launch the tile form.  None of these
- * changes any result. */
+ * (speculate = 1; refetched when a neighbour was taken).  With cluster = dataflow = 0 this is the tile form, one
+ * launch per iters_per_launch iterations.
+ * dataflow = 1 (cluster 0, iters_per_launch 1, speculate 0, tiles at least 4x4): every iteration of the level in
+ * one persistent launch of one-iteration tile tasks, a tile starting iteration t as soon as the 3x3 tiles around
+ * it have finished t - 1 (no launch boundary, hence no idle tail, between iterations).
+ * cluster = n (1..16) selects the cluster form: one thread-block cluster of n CTAs per direction of each pair
+ * covers the whole level without a halo, CTAs exchanging their block edges through distributed shared memory
+ * (threads 256 or 512, tile_w = tile_h = 0, speculate = 0); a plan falls back to the default tile form for a
+ * level the cluster form cannot take (a level narrower or lower than the partition, blocks beyond shared memory,
+ * or clusters this device cannot schedule).
+ * The server (ff_server_*) and ff_match_pair_noalloc launch the tile form only (a dataflow configuration's tiles,
+ * one iteration per launch).  None of these changes any result. */
 typedef struct {
-    int tile_w, tile_h, iters_per_launch, threads, speculate, cluster;
+    int tile_w, tile_h, iters_per_launch, threads, speculate, cluster, dataflow;
 } ff_tuning;
 
 /* Impose the configuration of one pass on every later plan of this context, overriding the autotuner; NULL

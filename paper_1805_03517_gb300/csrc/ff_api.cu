@@ -126,6 +126,7 @@ struct Plan {
 struct TileCfg {
     int tw, th, k, threads, spec;  // tile interior, iterations fused per launch, CTA size, speculative random
     int cluster = 0;               // > 0: the cluster form with this many CTAs per problem (tw, th unused)
+    int dataflow = 0;              // 1: the dataflow form (every iteration in one launch; k unused)
 };
 
 // Candidate propagation configurations (tile shape, fused iterations, CTA size) the autotuner times per level.
@@ -147,7 +148,17 @@ const TileCfg kCands[] = {
     {96, 32, 1, 128, 0}, {80, 32, 1, 128, 0}, {64, 28, 1, 128, 0}, {56, 24, 1, 128, 0}, {72, 24, 1, 128, 0},
     {64, 20, 1, 128, 0}, {24, 16, 1, 512, 0}, {32, 16, 1, 512, 0}, {20, 16, 1, 512, 0}, {26, 16, 1, 512, 0},
     // the cluster form (every iteration in one launch, no halo): small levels of a few problems
-    {0, 0, 255, 256, 0, 16}, {0, 0, 255, 512, 0, 16}, {0, 0, 255, 256, 0, 8}, {0, 0, 255, 512, 0, 8}};
+    {0, 0, 255, 256, 0, 16}, {0, 0, 255, 512, 0, 16}, {0, 0, 255, 256, 0, 8}, {0, 0, 255, 512, 0, 8},
+    // the dataflow form (every iteration in one launch, tiles start as their neighbours finish): without a last
+    // wave to fill, the fine levels can take larger tiles (a smaller share of halo pixels)
+    {50, 32, 1, 256, 0, 0, 1},  {64, 32, 1, 256, 0, 0, 1},  {80, 32, 1, 256, 0, 0, 1},  {96, 32, 1, 256, 0, 0, 1},
+    {128, 32, 1, 256, 0, 0, 1}, {64, 40, 1, 256, 0, 0, 1},  {64, 48, 1, 256, 0, 0, 1},  {96, 24, 1, 256, 0, 0, 1},
+    {128, 24, 1, 256, 0, 0, 1}, {48, 32, 1, 256, 0, 0, 1},  {64, 24, 1, 256, 0, 0, 1},  {32, 32, 1, 256, 0, 0, 1},
+    {32, 16, 1, 256, 0, 0, 1},  {16, 16, 1, 256, 0, 0, 1},  {8, 8, 1, 256, 0, 0, 1},    {48, 24, 1, 128, 0, 0, 1},
+    {64, 24, 1, 128, 0, 0, 1},  {32, 32, 1, 128, 0, 0, 1},  {32, 16, 1, 128, 0, 0, 1},  {64, 32, 1, 512, 0, 0, 1},
+    {96, 32, 1, 512, 0, 0, 1},  {128, 32, 1, 512, 0, 0, 1}, {64, 64, 1, 512, 0, 0, 1},  {64, 27, 1, 512, 0, 0, 1},
+    {32, 32, 1, 512, 0, 0, 1},  {26, 16, 1, 512, 0, 0, 1},  {16, 16, 1, 512, 0, 0, 1},  {16, 8, 1, 512, 0, 0, 1},
+    {8, 8, 1, 512, 0, 0, 1}};
 constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
 
 // Tuning key: pass index, grid size of the first job, number of directions in the launch, iterations.  A pass is
@@ -170,6 +181,7 @@ struct ff_ctx {
     std::vector<std::unique_ptr<ff_pyr>> pyrs;
     std::map<std::vector<uintptr_t>, std::unique_ptr<Plan>> plans;
     std::map<TuneKey, TileCfg> tuned;
+    std::map<TuneKey, TileCfg> tuned_queue;  // the best of the tile and dataflow forms (server, no-alloc path)
     TileCfg forced[kMaxPasses] = {};  // per-pass override (threads == 0: none)
     int seed_kernel = FF_SEED_TCGEN05;
     uint32_t wait_limit = 1u << 22;    // polls before a device-side wait gives up (~1 s)
@@ -256,7 +268,9 @@ ff_status check_params(const ff_params* p, ff_ctx* c) {
 
 // Whether a tile-form configuration's tile and halo fit in shared memory (a cluster-form configuration is
 // checked per pass by cluster_fits).
-bool cfg_fits(const TileCfg& t) { return t.cluster > 0 || prop_smem_bytes(t.tw, t.th, t.k) <= kMaxPropSmem; }
+bool cfg_fits(const TileCfg& t) {
+    return t.cluster > 0 || prop_smem_bytes(t.tw, t.th, t.dataflow ? 1 : t.k) <= kMaxPropSmem;
+}
 
 // Whether the cluster form of `t` can run pass (s, k) of these jobs: a partition of every problem, its shared
 // memory within the limit, and clusters of that shape launchable on this device.  *smem: the largest CTA's bytes.
@@ -453,6 +467,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     std::vector<PropProblem> props;
     std::vector<int2> queue;
     int n_counters = 0;
+    std::vector<std::pair<size_t, int>> progress;  // dataflow problems: (index in props, first progress counter)
     struct Pending {
         Launch l;
         size_t off_probs, off_queue;
@@ -593,9 +608,10 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         }
         size_t cl_smem = 0;
         if (tc.cluster > 0 && !cluster_fits(c, jobs, s, k, tc, &cl_smem)) tc = default_cfg(c, level_pix, T);
-        const bool cl = tc.cluster > 0;
-        const size_t smem = cl ? 0 : prop_smem_bytes(tc.tw, tc.th, tc.k);
-        const int blocks = cl ? 0 : prop_blocks_per_sm(smem, tc.threads, tc.spec != 0, cost, k > 0) * c->n_sms;
+        const bool cl = tc.cluster > 0, df = tc.dataflow > 0;
+        if (df) tc.k = T;  // one launch, one iteration per tile task
+        const size_t smem = cl ? 0 : prop_smem_bytes(tc.tw, tc.th, df ? 1 : tc.k);
+        const int blocks = cl ? 0 : prop_blocks_per_sm(smem, tc.threads, tc.spec != 0, cost, k > 0, df) * c->n_sms;
         for (int t0 = 0; t0 < T; t0 += tc.k) {
             int n_iter = std::min(tc.k, T - t0);
             bool last = t0 + n_iter == T;
@@ -605,7 +621,8 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             l.level = pass;
             l.prop.tw = tc.tw;
             l.prop.th = tc.th;
-            l.prop.max_iter = n_iter;
+            l.prop.max_iter = df ? 1 : n_iter;
+            l.prop.dataflow = df ? T : 0;
             l.prop.threads = tc.threads;
             l.prop.spec = tc.spec;
             l.prop.cost = cost;
@@ -631,6 +648,11 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
                 const LevelBufs& B = lb[j][s][k];
                 pp.flow_in = B.flow[in];
                 pp.cost_in = B.cost[in];
+                if (df) {  // iterations alternate: even ones write buffer `out` (flow_alt), odd ones `in`
+                    pp.flow_alt = B.flow[out];
+                    pp.cost_alt = B.cost[out];
+                    out = (T - 1) % 2 == 0 ? out : in;  // where the last iteration lands, apart from its source
+                }
                 if (last && s == 0 && k == 0) {  // the final launch writes the caller's buffers (cost to scratch if NULL)
                     pp.flow_out = jobs[j].flow_out;
                     pp.cost_out = jobs[j].cost_out ? jobs[j].cost_out : B.cost[out];
@@ -642,7 +664,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
                 pp.tiles_x = cl ? 1 : (pp.w + tc.tw - 1) / tc.tw;
                 ntiles[j] = cl ? 0 : pp.tiles_x * ((pp.h + tc.th - 1) / tc.th);
                 pp.t0 = t0;
-                pp.n_iter = n_iter;
+                pp.n_iter = df ? 1 : n_iter;
                 pp.level = s + 8 * k;  // the hash stream of this level or grid
                 pp.dir = jobs[j].dir;
                 pp.seed = c->prm.seed;
@@ -665,8 +687,13 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             }
             l.n_probs = nj;
             l.total = (int)(queue.size() - oq);
-            l.grid = std::min(l.total, blocks);
+            l.grid = (int)std::min<int64_t>((int64_t)l.total * (df ? T : 1), blocks);
             pend.push_back({l, 0, oq, n_counters++});
+            if (df)  // the tiles' progress counters follow the launch's queue counter in the zeroed block
+                for (int j = 0; j < nj; j++) {
+                    progress.push_back({(size_t)pidx[j], n_counters});
+                    n_counters += ntiles[j];
+                }
         }
       }
     }
@@ -717,6 +744,11 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     size_t o_cnt = o_q + align_up(queue.size() * sizeof(int2));
     size_t o_cons = o_cnt + align_up((size_t)std::max(n_counters, 1) * sizeof(int));
     size_t tbytes = o_cons + align_up(cps.size() * sizeof(ConsProblem));
+    P.bufs.emplace_back();
+    st = dev_alloc(c, P.bufs.back(), tbytes);
+    if (st != FF_OK) return st;
+    char* tb = static_cast<char*>(P.bufs.back().p);
+    for (auto [pi, first] : progress) props[pi].progress = reinterpret_cast<int*>(tb + o_cnt) + first;
     std::vector<char> host(tbytes, 0);
     memcpy(host.data() + o_seed, seeds.data(), seeds.size() * sizeof(SeedProblem));
     memcpy(host.data() + o_tc, tcseeds.data(), tcseeds.size() * sizeof(SeedTcProblem));
@@ -724,10 +756,6 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
     memcpy(host.data() + o_prop, props.data(), props.size() * sizeof(PropProblem));
     memcpy(host.data() + o_q, queue.data(), queue.size() * sizeof(int2));
     memcpy(host.data() + o_cons, cps.data(), cps.size() * sizeof(ConsProblem));
-    P.bufs.emplace_back();
-    st = dev_alloc(c, P.bufs.back(), tbytes);
-    if (st != FF_OK) return st;
-    char* tb = static_cast<char*>(P.bufs.back().p);
     FF_CUDA(c, cudaMemcpy(tb, host.data(), tbytes, cudaMemcpyHostToDevice));
     for (Pending& pd : pend) {
         Launch l = pd.l;
@@ -877,7 +905,7 @@ void wave_shape(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, int k, 
 // wave-fitted variant of a configuration grows the tile (height first, then width, by at most a quarter) just
 // enough that the tiles fill one wave fewer; it returns the configuration unchanged when none does.
 TileCfg wave_fitted(const ff_ctx* c, const std::vector<DirJob>& jobs, int s, int k, TileCfg t) {
-    if (t.cluster > 0) return t;
+    if (t.cluster > 0 || t.dataflow > 0) return t;  // no launch boundary per iteration, no last wave to fill
     int64_t tiles, slots;
     wave_shape(c, jobs, s, k, t, &tiles, &slots);
     if (slots < 1 || tiles <= slots) return t;
@@ -909,8 +937,8 @@ ff_status autotune(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
         for (int k = 0; k <= grids_of(c->prm, s); k++) passes.push_back({s, k});
     // per pass, the best time and configuration seen; each candidate is timed as given and, where it leaves a
     // short last wave in some pass, once more with its wave-fitted variant in those passes
-    std::vector<double> best_ms(kMaxPasses, 1e30);
-    std::vector<TileCfg> best_cfg(kMaxPasses);
+    std::vector<double> best_ms(kMaxPasses, 1e30), best_queue_ms(kMaxPasses, 1e30);
+    std::vector<TileCfg> best_cfg(kMaxPasses), best_queue_cfg(kMaxPasses);
     ff_status s = drop_plans(c);
     if (s != FF_OK) return s;
     bool was_profiling = c->profiling;
@@ -957,6 +985,10 @@ ff_status autotune(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
                 best_ms[p] = pass_best[p];
                 best_cfg[p] = per_pass[p];
             }
+            if (per_pass[p].cluster == 0 && pass_best[p] < best_queue_ms[p]) {
+                best_queue_ms[p] = pass_best[p];
+                best_queue_cfg[p] = per_pass[p];
+            }
         }
         return FF_OK;
     };
@@ -978,8 +1010,9 @@ ff_status autotune(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
     c->profiling = was_profiling;
     for (auto [ps, pk] : passes) {
         const int p = pass_index(ps, pk);
-        if (best_ms[p] < 1e29)
-            c->tuned[TuneKey{p, grid_dim(jobs[0].a->ws[ps], pk), grid_dim(jobs[0].a->hs[ps], pk), nj, T}] = best_cfg[p];
+        const TuneKey key{p, grid_dim(jobs[0].a->ws[ps], pk), grid_dim(jobs[0].a->hs[ps], pk), nj, T};
+        if (best_ms[p] < 1e29) c->tuned[key] = best_cfg[p];
+        if (best_queue_ms[p] < 1e29) c->tuned_queue[key] = best_queue_cfg[p];
     }
     return FF_OK;
 }
@@ -1001,6 +1034,9 @@ bool ctx_view(const ff_ctx* c, CtxView* out) {
     out->cost = c->prm.cost;
     out->noalloc_scratch = c->noalloc_scratch;
     out->sub_scales = c->prm.sub_scales;
+    out->wait_limit = c->wait_limit;
+    out->withhold = c->withhold;
+    out->err_word = c->d_err;
     return true;
 }
 
@@ -1028,18 +1064,20 @@ bool pyr_view(const ff_pyr* p, PyrView* out) {
     return true;
 }
 
-// The configuration build_plan would use for this level (override, tuned, or default).
-// `level` is a pass index: a level (0..7, where a per-level override applies) or a sub-scale grid (s + 8k).
-TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all) {
+// The configuration for pass `level` (a level s or a sub-scale grid s + 8k) of size w x h, in the tile or (if
+// dataflow_ok) the dataflow form: the override if it is of one of these forms, else the best of them the
+// autotuner timed for this size with the nearest number of directions per launch, else the default.  A dataflow
+// configuration where it is not wanted becomes its tiles with one iteration per launch.
+TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all,
+                            bool dataflow_ok) {
     const int T = c->prm.iters;
     TileCfg tc;
-    if (level >= 0 && level < kMaxPasses && c->forced[level].threads > 0) {
+    if (level >= 0 && level < kMaxPasses && c->forced[level].threads > 0 && c->forced[level].cluster == 0) {
         tc = c->forced[level];
     } else {
-        // the configuration tuned for this level size with the nearest number of directions per launch
         const TileCfg* best = nullptr;
         int best_d = 0;
-        for (const auto& kv : c->tuned) {
+        for (const auto& kv : c->tuned_queue) {
             if (std::get<0>(kv.first) != level || std::get<1>(kv.first) != w || std::get<2>(kv.first) != h ||
                 std::get<4>(kv.first) != T)
                 continue;
@@ -1051,8 +1089,14 @@ TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs
         }
         tc = best ? *best : default_cfg(c, level_pix_all, T);
     }
-    if (tc.cluster > 0) tc = default_cfg(c, level_pix_all, T);
-    return {tc.tw, tc.th, std::min(tc.k, T), tc.threads, tc.spec};
+    if (tc.dataflow > 0 && !dataflow_ok) tc = TileCfg{tc.tw, tc.th, 1, tc.threads, 0};
+    if (tc.dataflow > 0) return {tc.tw, tc.th, T, tc.threads, 0, 1};
+    return {tc.tw, tc.th, std::min(tc.k, T), tc.threads, tc.spec, 0};
+}
+
+int* ctx_err_word(ff_ctx* c) {
+    if (ensure_err_word(c) != FF_OK) return nullptr;
+    return c->d_err;
 }
 
 int ctx_set_error(ff_ctx* c, int status, const char* msg) {
@@ -1460,10 +1504,14 @@ ff_status ff_set_tuning(ff_ctx* c, int level, const ff_tuning* t) {
     if (!c) return FF_ERR_ARG;
     if (level < 0 || level >= kMaxPasses)
         return fail(c, FF_ERR_ARG, "pass %d outside 0..%d", level, kMaxPasses - 1);
-    TileCfg cfg{0, 0, 0, 0, 0, 0};
+    TileCfg cfg{0, 0, 0, 0, 0, 0, 0};
     if (t) {
-        cfg = TileCfg{t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate, t->cluster};
-        bool ok = t->iters_per_launch >= 1 && t->iters_per_launch <= 255 && (t->speculate == 0 || t->speculate == 1);
+        cfg = TileCfg{t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate, t->cluster, t->dataflow};
+        bool ok = t->iters_per_launch >= 1 && t->iters_per_launch <= 255 && (t->speculate == 0 || t->speculate == 1) &&
+                  (t->dataflow == 0 || t->dataflow == 1);
+        if (t->dataflow == 1)  // one iteration per task, its 4-pixel halo within the 3x3 tiles around it
+            ok = ok && t->cluster == 0 && t->iters_per_launch == 1 && t->speculate == 0 && t->tile_w >= 4 &&
+                 t->tile_h >= 4;
         if (t->cluster == 0)
             ok = ok && t->tile_w >= 1 && t->tile_h >= 1 && t->tile_w <= 1024 && t->tile_h <= 1024 &&
                  prop_threads_ok(t->threads) && cfg_fits(cfg);
@@ -1473,8 +1521,9 @@ ff_status ff_set_tuning(ff_ctx* c, int level, const ff_tuning* t) {
                  t->tile_w == 0 && t->tile_h == 0 && t->speculate == 0;
         if (!ok)
             return fail(c, FF_ERR_ARG,
-                        "configuration %dx%d, %d iterations, %d threads, speculate %d, cluster %d is not valid",
-                        t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate, t->cluster);
+                        "configuration %dx%d, %d iterations, %d threads, speculate %d, cluster %d, dataflow %d is not "
+                        "valid",
+                        t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate, t->cluster, t->dataflow);
     }
     FF_CUDA(c, cudaSetDevice(c->device));
     ff_status s = drop_plans(c);
@@ -1496,7 +1545,7 @@ ff_status ff_get_tuning(ff_ctx* c, int level, ff_tuning* out) {
             }
     }
     if (!f) return fail(c, FF_ERR_ARG, "level %d has not been tuned", level);
-    *out = ff_tuning{f->tw, f->th, f->k, f->threads, f->spec, f->cluster};
+    *out = ff_tuning{f->tw, f->th, f->k, f->threads, f->spec, f->cluster, f->dataflow};
     return FF_OK;
 }
 
@@ -1583,6 +1632,7 @@ ff_status ff_sync(ff_ctx* c) {
             FF_CUDA(c, cudaMemset(c->d_err, 0, sizeof e));
             return fail(c, FF_ERR_TIMEOUT, "a device-side wait expired (code %d: %s)", e,
                         e == kErrClusterEdges ? "block edges of the cluster-form propagation"
+                        : e == kErrDataflow   ? "tile progress of the dataflow-form propagation"
                                               : "copies or products of the tensor-core seed");
         }
     }

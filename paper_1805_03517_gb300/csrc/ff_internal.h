@@ -139,8 +139,8 @@ void launch_handover(const HandoverProblem* probs_dev, int n_probs, int64_t tota
 struct PropProblem {  // one (pair, direction, level) of a propagation launch
     const void* fa;  // cost descriptors of the source frame (WHT features or Census patterns)
     const void* fb;  // and of the target frame
-    const uint32_t* flow_in;
-    const int32_t* cost_in;
+    uint32_t* flow_in;  // (written too by the odd iterations of the dataflow form)
+    int32_t* cost_in;
     uint32_t* flow_out;
     int32_t* cost_out;
     int w, h;        // the grid propagated (the level itself unless g > 1)
@@ -152,6 +152,11 @@ struct PropProblem {  // one (pair, direction, level) of a propagation launch
     int dir;
     uint32_t seed;
     int rs_radius;
+    // dataflow form only: the state buffers iterations alternate with (iteration t writes flow_alt for even t,
+    // flow_in for odd t, flow_out for the last) and the tiles' progress counters (zero at the launch's start)
+    uint32_t* flow_alt;
+    int32_t* cost_alt;
+    int* progress;   // [tiles_x * tiles_y]: iterations each tile has finished
 };
 struct PropLaunch {
     int tw, th;      // tile interior
@@ -161,12 +166,15 @@ struct PropLaunch {
     int cost;        // FF_COST_WHT_SAD or FF_COST_CENSUS
     int grid;        // 1: the problems are sub-scale grids (g > 1)
     int cluster;     // 0: tiles from a queue; n = 1..16: cluster form, one cluster of n CTAs per problem
+    int dataflow;    // > 0: dataflow form, this many iterations (of one each per tile task) in the launch
     int cl_smem;     // cluster form: dynamic shared memory per CTA (the largest over the launch's problems)
-    uint32_t wait_limit;  // cluster form: polls before a wait for neighbouring block edges gives up
-    int withhold;    // cluster form, test of the bounded waits: send no block edges
-    int* err;        // cluster form: device error word (code kErrClusterEdges when a wait gave up)
+    uint32_t wait_limit;  // cluster and dataflow forms: polls before a wait gives up
+    int withhold;    // test of the bounded waits: the cluster form sends no block edges, the dataflow form
+                     // publishes no tile progress
+    int* err;        // device error word (kErrClusterEdges / kErrDataflow when a wait gave up)
 };
-constexpr int kErrClusterEdges = 3;  // error-word code of an expired cluster-form wait (1, 2: tensor-core seed)
+constexpr int kErrClusterEdges = 3;  // error-word codes of expired waits (1, 2: tensor-core seed)
+constexpr int kErrDataflow = 4;
 constexpr size_t kMaxPropSmem = 200 * 1024;
 constexpr int kMaxCluster = 16;
 size_t prop_smem_bytes(int tw, int th, int n_iter);
@@ -205,9 +213,10 @@ cudaError_t seed_load_kernel();        // loads k_seed onto the current device (
 // fixed scratch array) and the kernels it launches, and returns the array's device address.
 cudaError_t noalloc_prepare(void** scratch);
 bool prop_threads_ok(int threads);
-int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost, bool grid = false);  // resident CTAs per SM
+// resident CTAs per SM of the tile form (dataflow: of its dataflow kernel)
+int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost, bool grid = false, bool dataflow = false);
 // Tile form (L.cluster == 0): queue_dev[i] = (problem index, tile index); counter_dev must be zero when the launch
-// starts; `grid` CTAs.  Cluster form: problem i is probs_dev[i], `grid` = number of problems x L.cluster CTAs;
+// starts; `grid` CTAs.  Dataflow form (L.dataflow = T): the same queue, taken T times (iteration-major).  Cluster form: problem i is probs_dev[i], `grid` = number of problems x L.cluster CTAs;
 // queue_dev and counter_dev are unused.
 void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n_tiles, int* counter_dev, int grid,
                       const PropLaunch& L, cudaStream_t st);
@@ -252,9 +261,13 @@ struct CtxView {
     int cost;
     void* noalloc_scratch;  // device address of ff_match_pair_noalloc's scratch array on this device
     int sub_scales;
+    uint32_t wait_limit;    // FF_OPT_WAIT_LIMIT
+    int withhold;           // FF_OPT_TEST_WITHHOLD_COPIES
+    int* err_word;          // device error word of the bounded waits (null until ctx_err_word)
 };
 struct TileChoice {
-    int tw, th, k, threads, spec;  // always the tile form (see ctx_level_choice)
+    int tw, th, k, threads, spec;
+    int dataflow;  // 1: the dataflow form (k = iters: one launch per pass); 0: the tile form
 };
 
 // ---------------------------------------------------------------------------------------------------------
@@ -388,10 +401,12 @@ namespace ff {
 bool ctx_view(const ff_ctx* c, CtxView* out);
 bool ctx_owns_live_pyr(const ff_ctx* c, const ff_pyr* p);
 bool pyr_view(const ff_pyr* p, PyrView* out);
-// the launch configuration of a pass (level s, or its sub-scale grid s + 8k) of size w x h, in the tile form (a
-// cluster-form choice is replaced by the default tile configuration: the server and the no-allocation entry
-// point launch tiles only)
-TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all);
+// the launch configuration of a pass (level s, or its sub-scale grid s + 8k) of size w x h for the server and the
+// no-allocation entry point, which launch the tile form and (dataflow_ok) the dataflow form, never the cluster form
+TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs, int64_t level_pix_all,
+                            bool dataflow_ok);
+// the context's error word of the bounded device waits, allocated on first use (null if that fails)
+int* ctx_err_word(ff_ctx* c);
 // cudaMalloc on behalf of a context; fails as out of memory while the context's FF_OPT_TEST_FAIL_ALLOCS count lasts
 cudaError_t ctx_malloc(ff_ctx* c, void** p, size_t bytes);
 int ctx_set_error(ff_ctx* c, int status, const char* msg);

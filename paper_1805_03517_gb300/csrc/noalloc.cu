@@ -123,7 +123,7 @@ extern "C" ff_status ff_match_pair_noalloc(ff_ctx* c, const ff_pyr* a, const ff_
     int grid[kMaxLevels];
     int total_launches = 0;
     for (int s = L - 1; s >= 0; s--) {
-        tc[s] = ctx_level_choice(c, s, A.ws[s], A.hs[s], 1, (int64_t)A.ws[s] * A.hs[s]);
+        tc[s] = ctx_level_choice(c, s, A.ws[s], A.hs[s], 1, (int64_t)A.ws[s] * A.hs[s], false);
         sa.k[s] = tc[s].k;
         sa.n_launch[s] = (T + tc[s].k - 1) / tc[s].k;
         sa.first_launch[s] = total_launches;

@@ -326,16 +326,29 @@ __device__ __forceinline__ void halfsweep(const PropProblem& P, const TileGeom& 
     }
 }
 
+// Where a tile task reads the state of its region and writes its interior, and which iterations it runs.
+struct TileIO {
+    const uint32_t* flow_in;
+    const int32_t* cost_in;
+    uint32_t* flow_out;
+    int32_t* cost_out;
+    int t0, n_iter;
+};
+
 // One tile of one problem: load the tile and its halo, run n_iter iterations in shared memory, write the tile.
-template <class C, bool SPEC, bool GRID>
-__device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, const PropLaunch& L, uint32_t* smem) {
+// The buffers and iterations are the problem's (tile form) or, with DF, those of `io`, a dataflow task whose
+// state was written by other CTAs of the running launch and is therefore read from L2.
+template <class C, bool SPEC, bool GRID, bool DF = false>
+__device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, const PropLaunch& L, uint32_t* smem,
+                                               const TileIO* io = nullptr) {
     const int w = P.w, h = P.h;
+    const int n_iter = DF ? io->n_iter : P.n_iter;
     TileGeom G;
     G.x0 = (tile % P.tiles_x) * L.tw;
     G.y0 = (tile / P.tiles_x) * L.th;
     G.x1 = min(G.x0 + L.tw, w);
     G.y1 = min(G.y0 + L.th, h);
-    const int H = kHaloPerIter * P.n_iter;
+    const int H = kHaloPerIter * n_iter;
     G.lx0 = max(G.x0 - H, 0);
     G.ly0 = max(G.y0 - H, 0);
     G.RW = min(G.x1 + H, w) - G.lx0;
@@ -349,13 +362,18 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
         // flow and cost of the region (2 words per pixel) must fit the launch's dynamic shared memory
         const bool ok = idx_ok(g_bounds, kBoundsTileRead, (long long)g, (long long)w * h) &&
                         (!FF_DEBUG_BOUNDS || idx_ok(g_bounds, kBoundsTileSmem, 2 * G.RW * G.RH - 1, dyn_smem_bytes() / 4));
-        sflow[i] = ok ? P.flow_in[g] : 0u;
-        scost[i] = ok ? P.cost_in[g] : 0;
+        if constexpr (DF) {
+            sflow[i] = ok ? __ldcg(io->flow_in + g) : 0u;
+            scost[i] = ok ? __ldcg(io->cost_in + g) : 0;
+        } else {
+            sflow[i] = ok ? P.flow_in[g] : 0u;
+            scost[i] = ok ? P.cost_in[g] : 0;
+        }
     }
     __syncthreads();
-    for (int it = 0; it < P.n_iter; it++) {
-        const int t = P.t0 + it;
-        const int rem = kHaloPerIter * (P.n_iter - 1 - it);
+    for (int it = 0; it < n_iter; it++) {
+        const int t = (DF ? io->t0 : P.t0) + it;
+        const int rem = kHaloPerIter * (n_iter - 1 - it);
         const uint32_t k1 = mix32(P.seed ^ mix32((uint32_t)P.dir * 65536u + (uint32_t)P.level * 256u + (uint32_t)t));
         for (int j = 0; j < 8; j++) {
             halfsweep<C, SPEC, GRID>(P, G, sflow, scost, j, rem, k1);
@@ -370,8 +388,8 @@ __device__ __forceinline__ void propagate_tile(const PropProblem& P, int tile, c
         if (!idx_ok(g_bounds, kBoundsTileWrite, (long long)g, (long long)w * h) ||
             !idx_ok(g_bounds, kBoundsTileSmem, sidx, G.RW * G.RH))
             continue;
-        P.flow_out[g] = sflow[sidx];
-        P.cost_out[g] = scost[sidx];
+        (DF ? io->flow_out : P.flow_out)[g] = sflow[sidx];
+        (DF ? io->cost_out : P.cost_out)[g] = scost[sidx];
     }
 }
 
@@ -394,6 +412,75 @@ __global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate
         const int2 e = queue[q];
         propagate_tile<C, SPEC, GRID>(probs[e.x], e.y, L, smem);
         __syncthreads();
+    }
+}
+
+// Dataflow form: every iteration of a level in one persistent launch.  Task q is iteration t = q / n_tiles of
+// queue entry q % n_tiles (tasks are taken in that order); it starts once the 3x3 tiles around its tile, itself
+// included, have finished iteration t - 1, so no launch boundary separates the iterations and a CTA that
+// finishes early goes on with the next iteration's tiles.  A task of iteration t reads its region (the tile and
+// a halo of one iteration, kHaloPerIter <= tile size, so inside those nine tiles) from the buffer iteration t - 1
+// wrote and writes its tile to the next: flow_alt for even t, flow_in for odd t, flow_out for the last (a buffer
+// the host keeps apart from the one the iteration before wrote).  A tile overwrites a buffer its neighbours read
+// one iteration earlier only after they finished that iteration, by the same rule.  Progress is published with
+// a release after the tile's stores and read with an acquire; the region is then read from L2.  A task waits
+// only for tasks taken before it by running CTAs, so there is no deadlock whatever the residency; every wait is
+// bounded (wait_limit polls; on expiry kErrDataflow goes to the error word and the CTA stops waiting).
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int THREADS, bool SPEC, class C, bool GRID = false>
+__global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate_df(
+    const PropProblem* __restrict__ probs, const int2* __restrict__ queue, int n_tiles, int* __restrict__ counter,
+    PropLaunch L) {
+    grid_dependency_sync();
+    extern __shared__ uint32_t smem[];
+    __shared__ int s_next;
+    const int T = L.dataflow, n_tasks = n_tiles * T;
+    bool failed = false;  // a wait of this CTA expired: stop waiting (CTA-uniform)
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int q = s_next;
+        if (q >= n_tasks) return;
+        const int t = q / n_tiles;
+        const int2 e = queue[q - t * n_tiles];
+        const PropProblem& P = probs[e.x];
+        bool ok = true;
+        if (t > 0 && !failed && threadIdx.x < 9) {  // one waiting thread per tile of the 3x3 neighbourhood
+            const int tiles_y = (P.h + L.th - 1) / L.th;
+            const int nx = e.y % P.tiles_x + (int)threadIdx.x % 3 - 1, ny = e.y / P.tiles_x + (int)threadIdx.x / 3 - 1;
+            if (nx >= 0 && nx < P.tiles_x && ny >= 0 && ny < tiles_y) {
+                const int* f = P.progress + ny * P.tiles_x + nx;
+                ok = false;
+                for (uint32_t i = 0; i < L.wait_limit && !ok; i++) {
+                    ok = ld_acquire_gpu(f) >= t;
+                    if (!ok && i > 64) __nanosleep(128);
+                }
+                if (!ok) atomicCAS(L.err, 0, kErrDataflow);
+            }
+        }
+        failed = __syncthreads_or(!ok) != 0 || failed;
+        TileIO io;
+        io.t0 = P.t0 + t;
+        io.n_iter = 1;
+        const bool src_alt = t > 0 && ((t - 1) & 1) == 0;  // iteration t - 1 wrote flow_alt iff t - 1 is even
+        io.flow_in = t == 0 ? P.flow_in : src_alt ? P.flow_alt : P.flow_in;
+        io.cost_in = t == 0 ? P.cost_in : src_alt ? P.cost_alt : P.cost_in;
+        io.flow_out = t == T - 1 ? P.flow_out : (t & 1) == 0 ? P.flow_alt : P.flow_in;
+        io.cost_out = t == T - 1 ? P.cost_out : (t & 1) == 0 ? P.cost_alt : P.cost_in;
+        propagate_tile<C, SPEC, GRID, true>(P, e.y, L, smem, &io);
+        __syncthreads();  // every store of the tile is issued
+        if (threadIdx.x == 0 && !L.withhold) {
+            __threadfence();
+            st_release_gpu(P.progress + e.y, t + 1);
+        }
     }
 }
 
@@ -603,6 +690,20 @@ PropKernel prop_kernel(int threads, bool spec, int cost, bool grid = false) {
                                   : prop_kernel_c<CostSad>(threads, spec, grid);
 }
 
+// The dataflow form is instantiated for 128, 256 and 512 threads without speculation, per cost, for levels and
+// for sub-scale grids.
+template <class C, bool GRID>
+PropKernel prop_df_kernel_t(int threads) {
+    return threads == 128   ? k_propagate_df<128, false, C, GRID>
+           : threads == 512 ? k_propagate_df<512, false, C, GRID>
+                            : k_propagate_df<256, false, C, GRID>;
+}
+
+PropKernel prop_df_kernel(int threads, int cost, bool grid) {
+    if (cost == FF_COST_CENSUS) return grid ? prop_df_kernel_t<CostCensus, true>(threads) : prop_df_kernel_t<CostCensus, false>(threads);
+    return grid ? prop_df_kernel_t<CostSad, true>(threads) : prop_df_kernel_t<CostSad, false>(threads);
+}
+
 // The cluster form is instantiated for 256 and 512 threads, per cost, for levels and for sub-scale grids.
 template <class C, bool GRID>
 PropClusterKernel prop_cl_kernel_t(int threads) {
@@ -648,6 +749,9 @@ cudaError_t init_kernel_attributes() {
                     cudaError_t e = cudaFuncSetAttribute(prop_kernel(t, sp, cost, grid),
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          (int)kMaxPropSmem);
+                    if (e == cudaSuccess && !sp)
+                        e = cudaFuncSetAttribute(prop_df_kernel(t, cost, grid),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxPropSmem);
                     if (e != cudaSuccess) return e;
                 }
     for (int cost : {FF_COST_WHT_SAD, FF_COST_CENSUS})
@@ -663,10 +767,10 @@ cudaError_t init_kernel_attributes() {
 
 bool prop_threads_ok(int threads) { return threads == 128 || threads == 256 || threads == 512; }
 
-int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost, bool grid) {
+int prop_blocks_per_sm(size_t smem, int threads, bool spec, int cost, bool grid, bool dataflow) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prop_kernel(threads, spec, cost, grid),
-                                                      threads, smem) !=
+    PropKernel k = dataflow ? prop_df_kernel(threads, cost, grid) : prop_kernel(threads, spec, cost, grid);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -695,8 +799,9 @@ void launch_propagate(const PropProblem* probs_dev, const int2* queue_dev, int n
         return;
     }
     size_t smem = prop_smem_bytes(L.tw, L.th, L.max_iter);
-    launch_k(prop_kernel(L.threads, L.spec != 0, L.cost, L.grid != 0), dim3(grid), dim3(L.threads),
-             smem, st, probs_dev, queue_dev, n_tiles, counter_dev, L);
+    PropKernel k = L.dataflow > 0 ? prop_df_kernel(L.threads, L.cost, L.grid != 0)
+                                  : prop_kernel(L.threads, L.spec != 0, L.cost, L.grid != 0);
+    launch_k(k, dim3(grid), dim3(L.threads), smem, st, probs_dev, queue_dev, n_tiles, counter_dev, L);
 }
 
 }  // namespace ff

@@ -10,7 +10,9 @@
 // hand-over, the first chunk of every level carries that level's hand-over, and the last chunk of level 0 is
 // followed by the consistency check.  Work of all active requests of a tick is merged into one launch per
 // kernel kind (propagation: one per launch configuration and chunk position, the configurations running
-// concurrently on side streams), so requests that arrive while others are on the GPU join the next tick.
+// concurrently on side streams), so requests that arrive while others are on the GPU join the next tick.  A pass
+// whose configuration is of the dataflow form is one chunk (all its iterations in one launch); the cluster form
+// is not used here.  A bounded wait of a dataflow launch that expires is reported by the context's next ff_sync.
 // Results depend only on the request (the random-search hash is keyed by pixel, level, iteration and
 // direction), never on the mix.
 #include <cuda_runtime.h>
@@ -250,14 +252,16 @@ ff_status admit(ff_server* s) {
         for (int l = 0; l < q.L && st == FF_OK; l++)
             for (int g = 0; g <= grids_of(l, q.L, s->cv.sub_scales); g++) {  // tuning entries: pass l + 8g
                 const int gw = grid_dim(q.A.ws[l], g), gh = grid_dim(q.A.hs[l], g);
-                q.cfg[l][g] = ctx_level_choice(s->ctx, l + kMaxLevels * g, gw, gh, n_dirs, (int64_t)n_dirs * gw * gh);
+                q.cfg[l][g] =
+                    ctx_level_choice(s->ctx, l + kMaxLevels * g, gw, gh, n_dirs, (int64_t)n_dirs * gw * gh, true);
                 const TileChoice& t = q.cfg[l][g];
                 if (t.k < 1 || t.tw < 1 || t.th < 1 || !prop_threads_ok(t.threads) ||
-                    prop_smem_bytes(t.tw, t.th, t.k) > kMaxPropSmem) {
+                    prop_smem_bytes(t.tw, t.th, t.dataflow ? 1 : t.k) > kMaxPropSmem ||
+                    (t.dataflow && (t.tw < 4 || t.th < 4 || t.spec))) {
                     st = srv_fail(s, FF_ERR_CUDA, "invalid launch configuration");
                     break;
                 }
-                q.n_chunks[l][g] = (q.T + t.k - 1) / t.k;
+                q.n_chunks[l][g] = t.dataflow ? 1 : (q.T + t.k - 1) / t.k;  // dataflow: the pass in one launch
             }
         if (st != FF_OK) break;
         q.level = q.L - 1;
@@ -275,10 +279,10 @@ ff_status admit(ff_server* s) {
 // Propagation launches of a tick are grouped by phase (the position of a chunk among the chunks one request
 // runs in this tick: a request's chunk i + 1 reads what its chunk i wrote) and by launch configuration.
 struct PropGroupKey {
-    int phase, tw, th, n_iter, threads, spec, grid;
+    int phase, tw, th, n_iter, threads, spec, grid, dataflow;
     bool operator<(const PropGroupKey& o) const {
-        return std::tie(phase, tw, th, n_iter, threads, spec, grid) <
-               std::tie(o.phase, o.tw, o.th, o.n_iter, o.threads, o.spec, o.grid);
+        return std::tie(phase, tw, th, n_iter, threads, spec, grid, dataflow) <
+               std::tie(o.phase, o.tw, o.th, o.n_iter, o.threads, o.spec, o.grid, o.dataflow);
     }
 };
 
@@ -364,7 +368,7 @@ ff_status tick(ff_server* s) {
             const int chunk = q.chunk + phase;
             const int t0 = chunk * c.k, n_iter = std::min(c.k, T - t0);
             const bool last = sl == 0 && gk == 0 && chunk == q.n_chunks[sl][gk] - 1;
-            auto& grp = groups[PropGroupKey{phase, c.tw, c.th, n_iter, c.threads, c.spec, gk > 0 ? 1 : 0}];
+            auto& grp = groups[PropGroupKey{phase, c.tw, c.th, n_iter, c.threads, c.spec, gk > 0 ? 1 : 0, c.dataflow}];
             for (int d = 0; d < 2; d++) {
                 const PyrView& X = d == 0 ? q.A : q.B;
                 const PyrView& Y = d == 0 ? q.B : q.A;
@@ -376,9 +380,14 @@ ff_status tick(ff_server* s) {
                 pp.g = 1 << gk;
                 pp.lw = X.ws[sl];
                 pp.lh = X.hs[sl];
-                const int in = q.cur[d], out = in ^ 1;
+                int in = q.cur[d], out = in ^ 1;
                 pp.flow_in = q.flow[d][sl][gk][in];
                 pp.cost_in = q.cost[d][sl][gk][in];
+                if (c.dataflow) {  // iterations alternate: even ones write buffer `out`, odd ones `in`
+                    pp.flow_alt = q.flow[d][sl][gk][out];
+                    pp.cost_alt = q.cost[d][sl][gk][out];
+                    out = (T - 1) % 2 == 0 ? out : in;  // where the last iteration lands, apart from its source
+                }
                 int32_t* user_cost = d == 0 ? q.io.cost_fwd : q.io.cost_bwd;
                 if (last) {
                     pp.flow_out = reinterpret_cast<uint32_t*>(d == 0 ? q.io.flow_fwd : q.io.flow_bwd);
@@ -390,7 +399,7 @@ ff_status tick(ff_server* s) {
                 q.cur[d] = out;
                 pp.tiles_x = (pp.w + c.tw - 1) / c.tw;
                 pp.t0 = t0;
-                pp.n_iter = n_iter;
+                pp.n_iter = c.dataflow ? 1 : n_iter;
                 pp.level = sl + kMaxLevels * gk;  // the hash stream of this level or grid
                 pp.dir = d;
                 pp.seed = s->cv.seed;
@@ -424,8 +433,13 @@ ff_status tick(ff_server* s) {
     const size_t o_seed = 0, o_ho = a256(seeds.size() * sizeof(SeedProblem));
     const size_t o_prop = o_ho + a256(hos.size() * sizeof(HandoverProblem));
     const size_t o_q = o_prop + a256(n_props * sizeof(PropProblem));
+    // counters: one queue counter per launch, then the tiles' progress counters of the dataflow launches
+    size_t n_progress = 0;
+    for (auto& kv : groups)
+        if (kv.first.dataflow)
+            for (auto& pr : kv.second) n_progress += pr.second;
     const size_t o_cnt = o_q + a256(n_queue * sizeof(int2));
-    const size_t bytes = o_cnt + a256(groups.size() * sizeof(int) + 4);
+    const size_t bytes = o_cnt + a256((groups.size() + n_progress) * sizeof(int) + 4);
     RingSlot& r = s->ring[s->tick % kRing];
     ff_status st = ring_reserve(s, r, bytes);
     if (st != FF_OK) return st;
@@ -440,7 +454,9 @@ ff_status tick(ff_server* s) {
         int nq, grid, phase;
     };
     std::vector<PL> pls;
-    size_t pi = 0, qi = 0;
+    size_t pi = 0, qi = 0, prog = groups.size();  // next progress counter
+    CtxView now;  // the context's current wait limit and error word
+    ctx_view(s->ctx, &now);
     for (auto& kv : groups) {
         const PropGroupKey& k = kv.first;
         const size_t q0 = qi;
@@ -453,13 +469,26 @@ ff_status tick(ff_server* s) {
                 if (t < n1) hq[qi++] = make_int2(p0 + 1, t);
             }
         }
-        for (auto& pr : kv.second) hp[pi++] = pr.first;
-        const size_t smem = prop_smem_bytes(k.tw, k.th, k.n_iter);
+        for (auto& pr : kv.second) {
+            hp[pi] = pr.first;
+            if (k.dataflow) {
+                hp[pi].progress = reinterpret_cast<int*>(r.dev + o_cnt) + prog;
+                prog += pr.second;
+            }
+            pi++;
+        }
+        const size_t smem = prop_smem_bytes(k.tw, k.th, k.dataflow ? 1 : k.n_iter);
         const int nq = (int)(qi - q0);
-        pls.push_back({PropLaunch{k.tw, k.th, k.n_iter, k.threads, k.spec, s->cv.cost, k.grid}, q0, nq,
-                       std::min(nq, prop_blocks_per_sm(smem, k.threads, k.spec != 0, s->cv.cost, k.grid != 0) *
-                                        s->cv.n_sms),
-                       k.phase});
+        PropLaunch pl{k.tw, k.th, k.dataflow ? 1 : k.n_iter, k.threads, k.spec, s->cv.cost, k.grid};
+        const int slots =
+            prop_blocks_per_sm(smem, k.threads, k.spec != 0, s->cv.cost, k.grid != 0, k.dataflow != 0) * s->cv.n_sms;
+        if (k.dataflow) {
+            pl.dataflow = k.n_iter;
+            pl.wait_limit = now.wait_limit;
+            pl.withhold = now.withhold;
+            pl.err = now.err_word;
+        }
+        pls.push_back({pl, q0, nq, (int)std::min<int64_t>((int64_t)nq * (k.dataflow ? k.n_iter : 1), slots), k.phase});
     }
     cudaStream_t stm = s->cv.stream;
     if (cudaMemcpyAsync(r.dev, r.host, bytes, cudaMemcpyHostToDevice, stm) != cudaSuccess)
@@ -541,6 +570,8 @@ ff_status ff_server_create(ff_ctx* ctx, int64_t mem_budget_bytes, int max_active
     if (!ctx_view(ctx, &cv)) return FF_ERR_ARG;
     if (mem_budget_bytes <= 0 || max_active < 1 || max_active > 4096)
         return (ff_status)ctx_set_error(ctx, FF_ERR_ARG, "bad memory budget or max_active");
+    if (cudaSetDevice(cv.device) != cudaSuccess || !ctx_err_word(ctx))  // for the waits of dataflow launches
+        return (ff_status)ctx_set_error(ctx, FF_ERR_OOM, "no device memory for the error word");
     ff_server* s = new (std::nothrow) ff_server();
     if (!s) return FF_ERR_OOM;
     s->ctx = ctx;

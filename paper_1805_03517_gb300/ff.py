@@ -59,7 +59,8 @@ class Frame(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("iters_per_launch", ctypes.c_int),
-                ("threads", ctypes.c_int), ("speculate", ctypes.c_int), ("cluster", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("speculate", ctypes.c_int), ("cluster", ctypes.c_int),
+                ("dataflow", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -180,22 +181,24 @@ def ff_autotune(ctx, jobs, reps: int = 3):
 
 
 def ff_set_tuning(ctx, level: int, cfg):
-    """cfg: (tile_w, tile_h, iters_per_launch[, threads[, speculate[, cluster]]]) (threads 256, speculate 0 and
-    cluster 0 by default) or None to remove the override."""
+    """cfg: (tile_w, tile_h, iters_per_launch[, threads[, speculate[, cluster[, dataflow]]]]) (threads 256, the
+    others 0 by default) or None to remove the override.  `level` is a pass index (s, or s + 8k for the sub-scale
+    grid of stride 2^k of level s)."""
     if cfg is None:
         _check(ctx, lib().ff_set_tuning(ctx, level, None))
         return
-    t = Tuning(*cfg, *((256, 0, 0)[len(cfg) - 3:]))
+    t = Tuning(*cfg, *((256, 0, 0, 0)[len(cfg) - 3:]))
     _check(ctx, lib().ff_set_tuning(ctx, level, ctypes.byref(t)))
 
 
 def ff_get_tuning(ctx, level: int):
-    """(tile_w, tile_h, iters_per_launch, threads, speculate) in force for `level`, with a sixth entry, the
-    cluster size, for a cluster-form configuration."""
+    """(tile_w, tile_h, iters_per_launch, threads, speculate[, cluster[, dataflow]]) in force for pass `level`:
+    the optional entries are present up to the last non-zero one."""
     t = Tuning()
     _check(ctx, lib().ff_get_tuning(ctx, level, ctypes.byref(t)))
-    cfg = (t.tile_w, t.tile_h, t.iters_per_launch, t.threads, t.speculate)
-    return cfg + (t.cluster,) if t.cluster else cfg
+    cfg = (t.tile_w, t.tile_h, t.iters_per_launch, t.threads, t.speculate, t.cluster, t.dataflow)
+    n = 7 if t.dataflow else 6 if t.cluster else 5
+    return cfg[:n]
 
 
 def ff_consistency(ctx, fwd: int, bwd: int, w: int, h: int, eps: int, mask_dev: int):

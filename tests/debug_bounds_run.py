@@ -1,8 +1,8 @@
 """Run by tests/test_gpu_failures.py in a child process whose FF_LIBRARY points at the debug-bounds build of
-libff: small parity cases against the oracle (plain, sub-scale grids, Census cost, the cluster form of the
-propagation on levels and grids, two consistency checks and sparsification, a 1x1 and a 1-pixel-high frame),
-each followed by ff_sync, which fails if any index check of the propagation, hand-over or filter kernels recorded
-a violation.  Prints "debug-bounds ok" at the end."""
+libff: small parity cases against the oracle (plain, sub-scale grids, Census cost, the cluster and dataflow
+forms of the propagation on levels and grids, two consistency checks and sparsification, a 1x1 and a
+1-pixel-high frame), each followed by ff_sync, which fails if any index check of the propagation, hand-over or
+filter kernels recorded a violation.  Prints "debug-bounds ok" at the end."""
 import os
 import sys
 
@@ -32,13 +32,17 @@ CLUSTER = {0: (0, 0, 3, 256, 0, 16), 1: (0, 0, 2, 512, 0, 6), 2: (0, 0, 3, 256, 
            16: (0, 0, 1, 256, 0, 16), 9: (0, 0, 3, 256, 0, 16), 17: (0, 0, 3, 512, 0, 4)}
 cases.append((configs.MatchParams(n_scales=3, iters=3, sub_scales=2), (a, b), CLUSTER))
 cases.append((configs.MatchParams(n_scales=3, iters=2, cost=1), (a, b), CLUSTER))
+# the dataflow form on every level and grid pass (ragged tiles, 128 to 512 threads)
+DATAFLOW = {p_: ((7, 5), (16, 8), (4, 4))[i % 3] + (1, (128, 256, 512)[i % 3], 0, 0, 1)
+            for i, p_ in enumerate((0, 1, 2, 8, 9, 16, 17))}
+cases.append((configs.MatchParams(n_scales=3, iters=3, sub_scales=2), (a, b), DATAFLOW))
 for prm, (img_a, img_b), *tuning in cases:
     M = ff.Matcher(prm, 0)
     for p_, cfg in (tuning[0] if tuning else {}).items():
         ff.ff_set_tuning(M.ctx, p_, cfg)
     c0 = M.stats()["cluster_launches"]
     got = G.gpu_bidir(M, img_a, img_b, torch)  # ends with ff_sync: raises on a recorded violation
-    assert (M.stats()["cluster_launches"] > c0) == bool(tuning)
+    assert (M.stats()["cluster_launches"] > c0) == (bool(tuning) and tuning[0] is CLUSTER)
     G.assert_same(got, o.match_bidir(img_a, img_b, G.oracle_params(prm)))
     M.close()
 # two consistency checks and sparsification (Table 3, KITTI s)

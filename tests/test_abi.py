@@ -63,7 +63,8 @@ def test_library_is_in_tree():
 
 def test_tuned_table_is_well_formed():
     """The package table of tuned launch configurations: one valid [tile_w, tile_h, iterations per launch,
-    threads, speculate] per level of each listed workload."""
+    threads, speculate[, cluster[, dataflow]]] per level of each listed workload, in the tile, cluster or
+    dataflow form."""
     import json
 
     from paper_1805_03517_gb300 import configs
@@ -74,5 +75,12 @@ def test_tuned_table_is_well_formed():
     for name in names:
         prm = configs.workload(name).pairs[0].params
         assert len(table[name]) == prm.n_scales
-        for tw, th, k, threads, spec in table[name]:
-            assert tw >= 1 and th >= 1 and 1 <= k <= prm.iters and threads in (128, 256, 512) and spec in (0, 1)
+        for cfg in table[name]:
+            tw, th, k, threads, spec, cluster, dataflow = list(cfg) + [0] * (7 - len(cfg))
+            assert 5 <= len(cfg) <= 7 and 1 <= k <= prm.iters and threads in (128, 256, 512) and spec in (0, 1)
+            if cluster:  # the cluster form: no tiles, no speculation
+                assert tw == th == 0 and 1 <= cluster <= 16 and threads in (256, 512) and spec == 0 and not dataflow
+            elif dataflow:  # the dataflow form: one iteration per tile task, tiles of at least 4 x 4
+                assert dataflow == 1 and k == 1 and tw >= 4 and th >= 4 and spec == 0
+            else:
+                assert tw >= 1 and th >= 1

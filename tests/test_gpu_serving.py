@@ -184,3 +184,39 @@ def test_served_workload_sizes_against_the_oracle(ffm):
             raise AssertionError(f"request {i} ({w}x{h}): {e}") from None
     S.close()
     M.close()
+
+
+def test_served_mix_in_the_dataflow_form_equals_the_oracle(ffm):
+    """Passes configured in the dataflow form (levels and sub-scale grids) run through the server as one chunk
+    each, their problems merged across requests; each pair equals the oracle."""
+    import dataclasses
+
+    prm = dataclasses.replace(configs.MatchParams(n_scales=3, iters=3, eps=1), sub_scales=1)
+    sizes = [(60, 90), (97, 131), (33, 47), (60, 90), (80, 80), (45, 70)]
+    pairs = [_pair(2100 + i, h, w) for i, (h, w) in enumerate(sizes)]
+    M = ffm.Matcher(prm, 0)
+    for p in (0, 1, 2, 8, 9):
+        ffm.ff_set_tuning(M.ctx, p, (16, 8, 1, 256, 0, 0, 1))
+    dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in pairs]
+    torch.cuda.synchronize()
+    S = ffm.Server(M, mem_budget_bytes=1 << 30, max_active=12)
+    outs = {i: _outputs(M, h, w) for i, (h, w) in enumerate(sizes)}
+    done, nxt = [], 0
+    for step in range(2000):
+        if nxt < len(dev):
+            S.submit(nxt, dev[nxt][0], dev[nxt][1], outs[nxt])
+            nxt += 1
+        S.step()
+        done += S.poll()
+        if len(done) == len(dev):
+            break
+    while len(done) < len(dev):
+        S.step()
+        done += S.poll(wait=True)
+    M.sync()  # also reports an expired wait
+    got = [tuple(outs[i][k].cpu().numpy() for k in NAMES) for i in range(len(dev))]
+    want = G.oracle_bidir_many(pairs, prm)
+    for i in range(len(dev)):
+        G.assert_same(got[i], want[i])
+    S.close()
+    M.close()
