@@ -176,7 +176,9 @@ FF_API ff_status ff_autotune(ff_ctx* ctx, int n, const ff_pair_job* jobs, int re
  * launch per iters_per_launch iterations.
  * dataflow = 1 (cluster 0, iters_per_launch 1, speculate 0, tiles at least 4x4): every iteration of the level in
  * one persistent launch of one-iteration tile tasks, a tile starting iteration t as soon as the 3x3 tiles around
- * it have finished t - 1 (no launch boundary, hence no idle tail, between iterations).
+ * it have finished t - 1 (no launch boundary, hence no idle tail, between iterations); dataflow = 2 is its affine
+ * variant, each CTA keeping the same tiles for every iteration (no shared queue; their descriptors stay in that
+ * SM's L1).
  * cluster = n (1..16) selects the cluster form: one thread-block cluster of n CTAs per direction of each pair
  * covers the whole level without a halo, CTAs exchanging their block edges through distributed shared memory
  * (threads 256 or 512, tile_w = tile_h = 0, speculate = 0); a plan falls back to the default tile form for a

@@ -126,7 +126,7 @@ struct Plan {
 struct TileCfg {
     int tw, th, k, threads, spec;  // tile interior, iterations fused per launch, CTA size, speculative random
     int cluster = 0;               // > 0: the cluster form with this many CTAs per problem (tw, th unused)
-    int dataflow = 0;              // 1: the dataflow form (every iteration in one launch; k unused)
+    int dataflow = 0;              // 1: the dataflow form (every iteration in one launch; k unused), 2: affine
 };
 
 // Candidate propagation configurations (tile shape, fused iterations, CTA size) the autotuner times per level.
@@ -158,7 +158,11 @@ const TileCfg kCands[] = {
     {64, 24, 1, 128, 0, 0, 1},  {32, 32, 1, 128, 0, 0, 1},  {32, 16, 1, 128, 0, 0, 1},  {64, 32, 1, 512, 0, 0, 1},
     {96, 32, 1, 512, 0, 0, 1},  {128, 32, 1, 512, 0, 0, 1}, {64, 64, 1, 512, 0, 0, 1},  {64, 27, 1, 512, 0, 0, 1},
     {32, 32, 1, 512, 0, 0, 1},  {26, 16, 1, 512, 0, 0, 1},  {16, 16, 1, 512, 0, 0, 1},  {16, 8, 1, 512, 0, 0, 1},
-    {8, 8, 1, 512, 0, 0, 1}};
+    {8, 8, 1, 512, 0, 0, 1},
+    // its affine variant (fixed tiles per CTA, warm L1 across iterations): coarse levels, few tiles per CTA
+    {26, 16, 1, 512, 0, 0, 2},  {32, 16, 1, 512, 0, 0, 2},  {16, 16, 1, 512, 0, 0, 2},  {16, 8, 1, 512, 0, 0, 2},
+    {8, 8, 1, 512, 0, 0, 2},    {16, 8, 1, 256, 0, 0, 2},   {8, 8, 1, 256, 0, 0, 2},    {32, 16, 1, 256, 0, 0, 2},
+    {32, 32, 1, 256, 0, 0, 2},  {64, 32, 1, 256, 0, 0, 2},  {64, 24, 1, 512, 0, 0, 2}};
 constexpr int kNCands = sizeof(kCands) / sizeof(kCands[0]);
 
 // Tuning key: pass index, grid size of the first job, number of directions in the launch, iterations.  A pass is
@@ -623,6 +627,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             l.prop.th = tc.th;
             l.prop.max_iter = df ? 1 : n_iter;
             l.prop.dataflow = df ? T : 0;
+            l.prop.affine = tc.dataflow == 2;
             l.prop.threads = tc.threads;
             l.prop.spec = tc.spec;
             l.prop.cost = cost;
@@ -687,7 +692,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             }
             l.n_probs = nj;
             l.total = (int)(queue.size() - oq);
-            l.grid = (int)std::min<int64_t>((int64_t)l.total * (df ? T : 1), blocks);
+            l.grid = (int)std::min<int64_t>((int64_t)l.total * (df && tc.dataflow != 2 ? T : 1), blocks);
             pend.push_back({l, 0, oq, n_counters++});
             if (df)  // the tiles' progress counters follow the launch's queue counter in the zeroed block
                 for (int j = 0; j < nj; j++) {
@@ -1090,7 +1095,7 @@ TileChoice ctx_level_choice(const ff_ctx* c, int level, int w, int h, int n_dirs
         tc = best ? *best : default_cfg(c, level_pix_all, T);
     }
     if (tc.dataflow > 0 && !dataflow_ok) tc = TileCfg{tc.tw, tc.th, 1, tc.threads, 0};
-    if (tc.dataflow > 0) return {tc.tw, tc.th, T, tc.threads, 0, 1};
+    if (tc.dataflow > 0) return {tc.tw, tc.th, T, tc.threads, 0, tc.dataflow};
     return {tc.tw, tc.th, std::min(tc.k, T), tc.threads, tc.spec, 0};
 }
 
@@ -1508,8 +1513,8 @@ ff_status ff_set_tuning(ff_ctx* c, int level, const ff_tuning* t) {
     if (t) {
         cfg = TileCfg{t->tile_w, t->tile_h, t->iters_per_launch, t->threads, t->speculate, t->cluster, t->dataflow};
         bool ok = t->iters_per_launch >= 1 && t->iters_per_launch <= 255 && (t->speculate == 0 || t->speculate == 1) &&
-                  (t->dataflow == 0 || t->dataflow == 1);
-        if (t->dataflow == 1)  // one iteration per task, its 4-pixel halo within the 3x3 tiles around it
+                  t->dataflow >= 0 && t->dataflow <= 2;
+        if (t->dataflow > 0)  // one iteration per task, its 4-pixel halo within the 3x3 tiles around it
             ok = ok && t->cluster == 0 && t->iters_per_launch == 1 && t->speculate == 0 && t->tile_w >= 4 &&
                  t->tile_h >= 4;
         if (t->cluster == 0)

@@ -167,6 +167,7 @@ struct PropLaunch {
     int grid;        // 1: the problems are sub-scale grids (g > 1)
     int cluster;     // 0: tiles from a queue; n = 1..16: cluster form, one cluster of n CTAs per problem
     int dataflow;    // > 0: dataflow form, this many iterations (of one each per tile task) in the launch
+    int affine;      // dataflow form: 1 = each CTA keeps fixed tiles (no queue counter), 0 = tiles from the queue
     int cl_smem;     // cluster form: dynamic shared memory per CTA (the largest over the launch's problems)
     uint32_t wait_limit;  // cluster and dataflow forms: polls before a wait gives up
     int withhold;    // test of the bounded waits: the cluster form sends no block edges, the dataflow form
@@ -267,7 +268,7 @@ struct CtxView {
 };
 struct TileChoice {
     int tw, th, k, threads, spec;
-    int dataflow;  // 1: the dataflow form (k = iters: one launch per pass); 0: the tile form
+    int dataflow;  // 1: the dataflow form (k = iters: one launch per pass), 2: its affine variant; 0: tile form
 };
 
 // ---------------------------------------------------------------------------------------------------------

@@ -426,6 +426,10 @@ __global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate
 // a release after the tile's stores and read with an acquire; the region is then read from L2.  A task waits
 // only for tasks taken before it by running CTAs, so there is no deadlock whatever the residency; every wait is
 // bounded (wait_limit polls; on expiry kErrDataflow goes to the error word and the CTA stops waiting).
+// Affine variant (L.affine): no queue counter; CTA b owns entries b, b + G, ... of every iteration (G CTAs, at
+// most the resident ones) and runs them iteration by iteration, keeping its tiles' descriptors in its L1.  Its
+// waits are for iteration t - 1 of tiles other CTAs own, which wait only for earlier iterations, so every CTA
+// makes progress once the grid is resident (with the grid sized to the resident CTAs, it is).
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -444,11 +448,21 @@ __global__ __launch_bounds__(THREADS, SPEC ? 1 : 512 / THREADS) void k_propagate
     __shared__ int s_next;
     const int T = L.dataflow, n_tasks = n_tiles * T;
     bool failed = false;  // a wait of this CTA expired: stop waiting (CTA-uniform)
-    for (;;) {
-        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
-        __syncthreads();
-        const int q = s_next;
-        if (q >= n_tasks) return;
+    // affine: CTA b owns queue entries b, b + G, b + 2G, ... (G CTAs) for every iteration and runs them
+    // iteration by iteration, so a tile's region stays in the same SM's L1 from one iteration to the next
+    const int G = (int)gridDim.x, per_iter = (n_tiles - (int)blockIdx.x + G - 1) / G;  // entries this CTA owns
+    for (int k = 0;; k++) {
+        int q;
+        if (L.affine) {
+            if (k >= per_iter * T) return;
+            const int ti = k / per_iter;
+            q = ti * n_tiles + (int)blockIdx.x + (k - ti * per_iter) * G;
+        } else {
+            if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+            __syncthreads();
+            q = s_next;
+            if (q >= n_tasks) return;
+        }
         const int t = q / n_tiles;
         const int2 e = queue[q - t * n_tiles];
         const PropProblem& P = probs[e.x];

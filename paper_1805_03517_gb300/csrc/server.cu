@@ -484,11 +484,13 @@ ff_status tick(ff_server* s) {
             prop_blocks_per_sm(smem, k.threads, k.spec != 0, s->cv.cost, k.grid != 0, k.dataflow != 0) * s->cv.n_sms;
         if (k.dataflow) {
             pl.dataflow = k.n_iter;
+            pl.affine = k.dataflow == 2;
             pl.wait_limit = now.wait_limit;
             pl.withhold = now.withhold;
             pl.err = now.err_word;
         }
-        pls.push_back({pl, q0, nq, (int)std::min<int64_t>((int64_t)nq * (k.dataflow ? k.n_iter : 1), slots), k.phase});
+        const int64_t tasks = (int64_t)nq * (k.dataflow == 1 ? k.n_iter : 1);  // affine: one CTA per tile at most
+        pls.push_back({pl, q0, nq, (int)std::min<int64_t>(tasks, slots), k.phase});
     }
     cudaStream_t stm = s->cv.stream;
     if (cudaMemcpyAsync(r.dev, r.host, bytes, cudaMemcpyHostToDevice, stm) != cudaSuccess)

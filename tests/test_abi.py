@@ -81,6 +81,6 @@ def test_tuned_table_is_well_formed():
             if cluster:  # the cluster form: no tiles, no speculation
                 assert tw == th == 0 and 1 <= cluster <= 16 and threads in (256, 512) and spec == 0 and not dataflow
             elif dataflow:  # the dataflow form: one iteration per tile task, tiles of at least 4 x 4
-                assert dataflow == 1 and k == 1 and tw >= 4 and th >= 4 and spec == 0
+                assert dataflow in (1, 2) and k == 1 and tw >= 4 and th >= 4 and spec == 0
             else:
                 assert tw >= 1 and th >= 1

@@ -195,8 +195,8 @@ def test_served_mix_in_the_dataflow_form_equals_the_oracle(ffm):
     sizes = [(60, 90), (97, 131), (33, 47), (60, 90), (80, 80), (45, 70)]
     pairs = [_pair(2100 + i, h, w) for i, (h, w) in enumerate(sizes)]
     M = ffm.Matcher(prm, 0)
-    for p in (0, 1, 2, 8, 9):
-        ffm.ff_set_tuning(M.ctx, p, (16, 8, 1, 256, 0, 0, 1))
+    for p in (0, 1, 2, 8, 9):  # the dataflow form, its affine variant at levels 1 and 2
+        ffm.ff_set_tuning(M.ctx, p, (16, 8, 1, 256, 0, 0, 2 if p in (1, 2) else 1))
     dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in pairs]
     torch.cuda.synchronize()
     S = ffm.Server(M, mem_budget_bytes=1 << 30, max_active=12)

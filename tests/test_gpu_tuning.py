@@ -63,7 +63,8 @@ def test_autotune_then_bit_exact(ffm):
     for cfg in chosen:
         tw, th, k, n, spec = cfg[:5]
         if len(cfg) == 7:  # the dataflow form
-            assert tw >= 4 and th >= 4 and k == 1 and n in (128, 256, 512) and spec == 0 and cfg[5:] == (0, 1)
+            assert tw >= 4 and th >= 4 and k == 1 and n in (128, 256, 512) and spec == 0 and cfg[5] == 0
+            assert cfg[6] in (1, 2)
         elif len(cfg) == 6:  # the cluster form
             assert tw == th == 0 and 1 <= cfg[5] <= 16 and n in (256, 512) and k >= 1 and spec == 0
         else:
@@ -90,7 +91,7 @@ def test_set_tuning_rejects_bad_configurations(ffm):
                        (0, (0, 0, 3, 128, 0, 16)), (0, (0, 0, 3, 256, 0, 17)), (0, (8, 8, 3, 256, 0, 16)),
                        (0, (0, 0, 3, 256, 0, -1)), (0, (0, 0, 0, 256, 0, 8)), (0, (0, 0, 3, 256, 1, 8)),
                        (0, (16, 16, 2, 256, 0, 0, 1)), (0, (16, 16, 1, 256, 1, 0, 1)), (0, (3, 16, 1, 256, 0, 0, 1)),
-                       (0, (16, 16, 1, 256, 0, 8, 1)), (0, (16, 16, 1, 256, 0, 0, 2))):
+                       (0, (16, 16, 1, 256, 0, 8, 1)), (0, (16, 16, 1, 256, 0, 0, 3))):
         with pytest.raises(ffm.FFError) as e:
             ffm.ff_set_tuning(M.ctx, level, cfg)
         assert e.value.status == ffm.FF_ERR_ARG
@@ -222,7 +223,9 @@ def test_cluster_form_bounded_wait_reports_expiry_and_context_recovers(ffm):
 
 @pytest.mark.parametrize("cfg,T", [((50, 32, 1, 256, 0, 0, 1), 5), ((16, 16, 1, 128, 0, 0, 1), 4),
                                    ((7, 5, 1, 512, 0, 0, 1), 3), ((64, 27, 1, 512, 0, 0, 1), 6),
-                                   ((4, 4, 1, 256, 0, 0, 1), 2), ((33, 9, 1, 256, 0, 0, 1), 1)])
+                                   ((4, 4, 1, 256, 0, 0, 1), 2), ((33, 9, 1, 256, 0, 0, 1), 1),
+                                   ((16, 8, 1, 512, 0, 0, 2), 6), ((4, 4, 1, 128, 0, 0, 2), 3),
+                                   ((50, 32, 1, 256, 0, 0, 2), 4), ((13, 7, 1, 256, 0, 0, 2), 1)])
 def test_dataflow_form_is_bit_exact(ffm, cfg, T):
     """The dataflow form (every iteration of a level in one persistent launch, a tile starting iteration t once the
     3x3 tiles around it have finished t - 1) on every level, with odd and even iteration counts (the buffer the
@@ -247,7 +250,7 @@ def test_dataflow_form_on_sub_scale_grids_and_census(ffm, cost):
     a, b = _pair_70x133()
     M = ffm.Matcher(prm, 0)
     for i, p in enumerate([0, 1, 2, 8, 9, 16, 17]):
-        ffm.ff_set_tuning(M.ctx, p, ((16, 8), (8, 8), (32, 16))[i % 3] + (1, (128, 256, 512)[i % 3], 0, 0, 1))
+        ffm.ff_set_tuning(M.ctx, p, ((16, 8), (8, 8), (32, 16))[i % 3] + (1, (128, 256, 512)[i % 3], 0, 0, 1 + i % 2))
     got = G.gpu_bidir(M, a, b, torch)
     G.assert_same(got, oracle.default().match_bidir(a, b, G.oracle_params(prm)))
     M.close()
@@ -263,8 +266,8 @@ def test_dataflow_form_in_a_batch_of_mixed_sizes_and_replayed(ffm):
         a = P.smooth_texture(460 + i, h, w)
         pairs.append((a, P.shifted(a, 3 - i, i - 1, 470 + i)))
     M = ffm.Matcher(prm, 0)
-    for lvl in range(3):
-        ffm.ff_set_tuning(M.ctx, lvl, (16, 16, 1, 256, 0, 0, 1))
+    for lvl in range(3):  # level 1 in the affine variant
+        ffm.ff_set_tuning(M.ctx, lvl, (16, 16, 1, 256, 0, 0, 2 if lvl == 1 else 1))
     dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in pairs]
     torch.cuda.synchronize()
     pyrs = [(M.features(x), M.features(y)) for x, y in dev]
@@ -281,7 +284,8 @@ def test_dataflow_form_in_a_batch_of_mixed_sizes_and_replayed(ffm):
     M.close()
 
 
-def test_dataflow_form_bounded_wait_reports_expiry_and_context_recovers(ffm):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_dataflow_form_bounded_wait_reports_expiry_and_context_recovers(ffm, variant):
     """With the tiles' progress withheld, every wait of the dataflow form expires after its poll limit: ff_sync
     reports FF_ERR_TIMEOUT, nothing hangs, and the same context then matches bit-exactly again."""
     prm = mp(3, 3)
@@ -289,7 +293,7 @@ def test_dataflow_form_bounded_wait_reports_expiry_and_context_recovers(ffm):
     M = ffm.Matcher(prm, 0)
     ffm.ff_set_option(M.ctx, ffm.FF_OPT_SEED_KERNEL, ffm.FF_SEED_MMA_SYNC)  # only the propagation waits
     for lvl in range(3):
-        ffm.ff_set_tuning(M.ctx, lvl, (16, 16, 1, 256, 0, 0, 1))
+        ffm.ff_set_tuning(M.ctx, lvl, (16, 16, 1, 256, 0, 0, variant))
     ffm.ff_set_option(M.ctx, ffm.FF_OPT_WAIT_LIMIT, 2000)
     ffm.ff_set_option(M.ctx, ffm.FF_OPT_TEST_WITHHOLD_COPIES, 1)  # no tile publishes its progress
     ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
