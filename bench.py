@@ -538,10 +538,10 @@ def measure_served(torch, ff, configs, stream, local_rank, n_req):
     stream.synchronize()
     gen_s = time.perf_counter() - t_gen
     for (w, h, _) in configs.SERVE_SIZES:  # per-size launch configurations, as a deployment would tune once:
-        same = [f for f, p in zip(frames, specs) if (p.w, p.h) == (w, h)][:8]
+        same = [f for f, p in zip(frames, specs) if (p.w, p.h) == (w, h)][:32]
         pyrs = [(M.features(a), M.features(b)) for a, b in same]
         M.autotune(pyrs[:1], reps=2)  # for one pair in flight (light load)
-        M.autotune(pyrs, reps=2)      # for launches shared by many pairs (under load)
+        M.autotune(pyrs, reps=2)      # for launches shared by many pairs (under load: 64 directions per size)
         for pa, pb in pyrs:
             M.release(pa)
             M.release(pb)

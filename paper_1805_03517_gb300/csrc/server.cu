@@ -36,7 +36,7 @@ namespace {
 constexpr int kRing = 4;         // ticks in flight before the host waits
 constexpr int kSideStreams = 3;  // extra streams for the concurrent propagation launches of a tick
 constexpr int kWholeLevelMaxActive = 8;  // up to this many requests in flight, a tick runs a whole level
-constexpr int kLoadedDirs = 16;          // directions per launch the configurations under load are looked up for
+constexpr int kLoadedDirs = 64;          // directions per launch the configurations under load are looked up for
 
 size_t a256(size_t v) { return (v + 255) / 256 * 256; }
 
