@@ -73,8 +73,19 @@ def aggregate_ranks(torch, dist, dev, ms_local, px_per_step, world):
     return ms, px_per_step * world / (ms / 1000.0) / 1e6
 
 
+def prop_kernel(cfg):
+    """The propagation kernel a level's configuration [tile w, tile h, iterations/launch, threads, speculate,
+    cluster, dataflow] launches: the dataflow form, the cluster form or the tile form."""
+    cfg = list(cfg)
+    if len(cfg) > 6 and cfg[6]:
+        return "k_propagate_df"
+    if len(cfg) > 5 and cfg[5]:
+        return "k_propagate_cl"
+    return "k_propagate"
+
+
 def propagate_l1_record(tuning):
-    """The committed ncu capture of a level-0 k_propagate launch of the 1242x375 pair (L1 LSU data-pipe wavefronts,
+    """The committed ncu capture of a level-0 propagation launch of the 1242x375 pair (L1 LSU data-pipe wavefronts,
     their peak per cycle, DRAM bytes), if the kernel source and the launch configuration are the ones it was
     captured with."""
     import hashlib
@@ -277,7 +288,7 @@ def measure_batched(torch, ff, configs, stream, local_rank, steps):
     l0_launch_ms = l0_ms / l0_n
     l0_alg = sum(p.w * p.h for p in wl.pairs) * wl.pairs[0].params.iters * 2 * ALG_BYTES_PER_PIXEL_ITER / (l0_n / n_prof)
     alg_gbs = l0_alg / (l0_launch_ms / 1000.0) / 1e9
-    roof = {"kernel": "k_propagate (level-0 launches)", "avg_launch_ms": l0_launch_ms, "alg_bytes_per_launch": l0_alg,
+    roof = {"kernel": f"{prop_kernel(tuning[0])} (level-0 launches)", "avg_launch_ms": l0_launch_ms, "alg_bytes_per_launch": l0_alg,
             "alg_gbs": alg_gbs, "launches_per_step": l0_n / n_prof}
     rec = batch_traffic()
     if rec:
@@ -833,7 +844,8 @@ def main():
     l0_launch_ms = l0_ms / l0_launches if l0_launches else None
     l0_alg = l0_px_iters * (ALG_BYTES_PER_PIXEL_ITER_CENSUS if cost_id else ALG_BYTES_PER_PIXEL_ITER) / (
         l0_launches / n_prof) if l0_launches else None
-    hbm_roof = {"bound": "hbm", "kernel": "k_propagate", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+    hbm_roof = {"bound": "hbm", "kernel": "propagation, all levels: " + ", ".join(
+                    sorted({prop_kernel(c) for c in tuning})), "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": achieved / peak,
                 "traffic": propagate_traffic(tuning) if cost_id == 0 else None,
                 "alg_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
@@ -845,7 +857,7 @@ def main():
         wf_peak = rec["wavefronts_peak_per_cycle"] * clocks["sm_mhz"] * 1e6
         wf_achieved = rec["wavefronts_per_launch"] / (l0_launch_ms / 1000.0)
         share = (l0_ms / n_prof) / ms
-        roofline = {"bound": "l1", "kernel": f"k_propagate (level-0 launches, {100 * share:.0f} % of a step)",
+        roofline = {"bound": "l1", "kernel": f"{prop_kernel(tuning[0])} (level-0 launches, {100 * share:.0f} % of a step)",
                     "unit": "wavefronts/s", "achieved": wf_achieved, "peak": wf_peak,
                     "peak_kind": "ncu peak_sustained of l1tex__data_pipe_lsu_wavefronts x sampled SM clock",
                     "frac": wf_achieved / wf_peak, "traffic": rec["dram_bytes_per_launch"],
