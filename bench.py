@@ -55,8 +55,12 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="run the autotuner instead of the package's table of tuned configurations")
     ap.add_argument("--serve-requests", type=int, default=2000)
-    ap.add_argument("--features", default="batch", choices=["frame", "batch"],
-                    help="features of the step's frames: one ff_features call per frame, or ff_features_batch")
+    ap.add_argument("--features", default="frames", choices=["frame", "batch", "frames"],
+                    help="features of the step's frames: one ff_features call per frame, ff_features_batch, or "
+                         "ff_match_frames (features and matching in one call, the fine levels' descriptors beside "
+                         "the coarse levels' matching)")
+    ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2],
+                    help="with --features frames: where the fine levels' descriptors fork off (FF_OPT_OVERLAP)")
     ap.add_argument("--tuning", default=None,
                     help="JSON list of per-level [tile_w, tile_h, iters_per_launch, threads, speculate] instead of "
                          "autotuning (for reproducible profiler captures)")
@@ -677,13 +681,22 @@ def main():
             return list(zip(fp[0::2], fp[1::2]))
         return [(m.features(a), m.features(b)) for a, b in imgs]
 
+    def match_step(m, imgs, outs):
+        """One step's features and matching through the public API; returns the outputs."""
+        if args.features == "frames":
+            return m.match_frames(imgs, outs=outs, with_cost=False)
+        pyrs = features(m, imgs)
+        outs = m.match_batch(pyrs, outs=outs, with_cost=False)
+        for pa, pb in pyrs:
+            m.release(pa)
+            m.release(pb)
+        return outs
+
+    ff.ff_set_option(M.ctx, ff.FF_OPT_OVERLAP, args.overlap)
+
     def step():
         nonlocal outs
-        pyrs = features(M, dev_imgs)
-        outs = M.match_batch(pyrs, outs=outs, with_cost=False)
-        for pa, pb in pyrs:
-            M.release(pa)
-            M.release(pb)
+        outs = match_step(M, dev_imgs, outs)
 
     def timed(n, body, pre=None):
         ms = []
@@ -785,11 +798,7 @@ def main():
     def e2e_step():
         with torch.cuda.stream(stream):
             d_in.copy_(h_in, non_blocking=True)
-        pyrs = features(M, e2e_imgs)
-        M.match_batch(pyrs, outs=e2e_outs, with_cost=False)
-        for pa, pb in pyrs:
-            M.release(pa)
-            M.release(pb)
+        match_step(M, e2e_imgs, e2e_outs)
         with torch.cuda.stream(stream):
             h_out.copy_(d_out, non_blocking=True)
 
@@ -811,11 +820,7 @@ def main():
 
     def prof_step():
         nonlocal prof_outs
-        pyrs = features(P, dev_imgs)
-        prof_outs = P.match_batch(pyrs, outs=prof_outs, with_cost=False)
-        for pa, pb in pyrs:
-            P.release(pa)
-            P.release(pb)
+        prof_outs = match_step(P, dev_imgs, prof_outs)
 
     for _ in range(3):
         prof_step()
@@ -884,8 +889,11 @@ def main():
                        "tiles_per_level": {str(l): list(c) for l, c in enumerate(tuning)},
                        "tiles_from": tuning_source,
                        "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write, outside the events)",
-                       "features": "ff_features_batch (one launch per kernel for all frames)" if args.features == "batch"
-                                   else "ff_features per frame",
+                       "features": {"batch": "ff_features_batch (one launch per kernel for all frames)",
+                                    "frame": "ff_features per frame",
+                                    "frames": "ff_match_frames (features and matching in one call; levels 0-1 "
+                                              f"descriptors on a branch of the matching graph, FF_OPT_OVERLAP {args.overlap})"
+                                    }[args.features],
                        "settle_s": args.settle_s},
             "gpu_launches": launches,
             "clocks": clocks,

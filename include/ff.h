@@ -163,6 +163,28 @@ typedef struct {
  * pyramids and output buffers) are matched again. */
 FF_API ff_status ff_match_batch(ff_ctx* ctx, int n, const ff_pair_job* jobs);
 
+/* One frame pair of ff_match_frames: a and b index its frame list; the outputs are those of ff_pair_job. */
+typedef struct {
+    int a, b;
+    int16_t* flow_fwd;
+    int16_t* flow_bwd;
+    int32_t* cost_fwd;
+    int32_t* cost_bwd;
+    uint8_t* mask;
+    int16_t* flow_bwd2;
+} ff_frame_job;
+
+/* ff_features_batch on n_frames frames followed by ff_match_batch on n_jobs pairs of them (Sec. 3 and 3.1), in
+ * one call, with results identical to those two calls.  The descriptors of pyramid levels 0 and 1 are needed
+ * only once the matching reaches level 1.  So when the context has a stream of its own, is not profiling and
+ * matches more than two levels, their launch runs on a branch of the matching's CUDA graph, beside the coarse
+ * levels' matching, whose kernels have the higher priority (FF_OPT_OVERLAP); level 1 waits for it.  All work is
+ * ordered on the context's stream when the call returns.  If out is not NULL it receives the n_frames
+ * pyramids (released by the caller); otherwise they are released at the end of the call and their memory is
+ * recycled by later calls.  Argument errors are found before anything is launched. */
+FF_API ff_status ff_match_frames(ff_ctx* ctx, int n_frames, const ff_frame* frames, int n_jobs,
+                                 const ff_frame_job* jobs, ff_pyr** out);
+
 /* Choose, per pyramid level, the propagation tile shape, CTA size and the number of iterations fused into one launch for
  * batches shaped like `jobs` (same level sizes and number of pairs): every candidate configuration is run
  * `reps` (1..100) times on these jobs and the fastest is kept for each level.  Results never depend on the
@@ -347,8 +369,19 @@ FF_API ff_status ff_match_pair_noalloc(ff_ctx* ctx, const ff_pyr* a, const ff_py
  *                                server's scratch and tables) fail as on an exhausted device, without calling the
  *                                allocator, so the calls that need them return FF_ERR_OOM and launch nothing (a test
  *                                of the out-of-memory paths); 0 (default) normal operation.  Unlike the other
- *                                options it keeps the cached plans. */
-enum { FF_OPT_SEED_KERNEL = 1, FF_OPT_WAIT_LIMIT = 2, FF_OPT_TEST_WITHHOLD_COPIES = 3, FF_OPT_TEST_FAIL_ALLOCS = 4 };
+ *                                options it keeps the cached plans.
+ *   FF_OPT_OVERLAP               where the branch of ff_match_frames that writes the fine levels' descriptors
+ *                                starts: 0, nowhere (they are written before the matching, on the context's
+ *                                stream); 1, at the start of the matching; 2 (default), at the coarsest level's
+ *                                first propagation launch.  Results never depend on it; it keeps the cached
+ *                                plans. */
+enum {
+    FF_OPT_SEED_KERNEL = 1,
+    FF_OPT_WAIT_LIMIT = 2,
+    FF_OPT_TEST_WITHHOLD_COPIES = 3,
+    FF_OPT_TEST_FAIL_ALLOCS = 4,
+    FF_OPT_OVERLAP = 5
+};
 enum { FF_SEED_MMA_SYNC = 0, FF_SEED_TCGEN05 = 1 };
 FF_API ff_status ff_set_option(ff_ctx* ctx, int option, int64_t value);
 

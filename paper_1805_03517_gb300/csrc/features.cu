@@ -344,8 +344,13 @@ void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st) {
     launch_k(k_wht, dim3(total_tiles), dim3(256), 0, st, a);
 }
 
-void launch_wht_tab(const WhtLevel* tab_dev, int n, int total_tiles, cudaStream_t st) {
-    launch_k(k_wht_tab, dim3(total_tiles), dim3(256), 0, st, tab_dev, n);
+const void* wht_tab_kernel() { return reinterpret_cast<const void*>(k_wht_tab); }
+
+void launch_wht_tab(const WhtLevel* tab_dev, int n, int total_tiles, cudaStream_t st, bool after_kernel) {
+    if (after_kernel)
+        launch_k(k_wht_tab, dim3(total_tiles), dim3(256), 0, st, tab_dev, n);
+    else  // after an event wait: an ordinary launch (no programmatic dependency on an earlier kernel)
+        k_wht_tab<<<total_tiles, 256, 0, st>>>(tab_dev, n);
 }
 
 }  // namespace ff

@@ -72,6 +72,7 @@ struct Launch {
     Kind kind;
     int phase;
     int level = -1;
+    int desc_level = -1;     // the finest pyramid level whose descriptors the launch reads (-1: none)
     // seed / handover / propagate: problem arrays in the plan's device table
     const void* probs = nullptr;
     int n_probs = 0;
@@ -121,6 +122,20 @@ struct Plan {
     cudaGraphExec_t exec = nullptr;
     int graph_nodes = 0;
     int cluster_nodes = 0;  // of graph_nodes: propagation launches of the cluster form
+    // ff_match_frames: the same launches in one graph with the fine levels' descriptor launch on a branch from
+    // launch split_at[0] to launch split_at[1], for the descriptor table split_tab (split_n entries, split_tiles CTAs)
+    cudaGraphExec_t split_exec = nullptr;
+    size_t split_at[2] = {0, 0};
+    const void* split_tab = nullptr;
+    int split_n = 0, split_tiles = 0;
+    int split_nodes = 0, split_clusters = 0;
+};
+
+// The descriptor launch of the fine pyramid levels that ff_match_frames runs beside the coarse levels' matching.
+struct FineWht {
+    const WhtLevel* tab = nullptr;  // device table of the fine levels (in the context's feature table)
+    int n = 0;                      // entries
+    int tiles = 0;                  // CTAs
 };
 
 struct TileCfg {
@@ -194,6 +209,9 @@ struct ff_ctx {
     void* noalloc_scratch = nullptr;   // device address of ff_match_pair_noalloc's fixed scratch array
     int64_t fail_allocs = 0;           // test of the out-of-memory paths: device allocations still to fail
     DevBuf feat_tab;                   // device table of ff_features_batch (frames' pyramid and WHT launch entries)
+    int overlap = 2;                   // ff_match_frames: where the fine levels' descriptors fork off (FF_OPT_OVERLAP)
+    cudaStream_t side = nullptr;       // ff_match_frames: carries the descriptor branch while a graph is captured
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     int64_t launches = 0, replays = 0, plans_built = 0, bytes = 0;
     int64_t cluster_launches = 0;      // of `launches`: propagation launches of the cluster form
@@ -494,6 +512,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         Launch l{};
         l.kind = Kind::SeedTc;
         l.phase = FF_PHASE_SEED;
+        l.desc_level = L - 1;
         int ctas = 0;
         int64_t pix = 0;
         for (int j = 0; j < nj; j++) {
@@ -528,6 +547,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
         Launch l{};
         l.kind = Kind::Seed;
         l.phase = FF_PHASE_SEED;
+        l.desc_level = L - 1;
         int tiles = 0;
         size_t o = seeds.size();
         for (int j = 0; j < nj; j++) {
@@ -559,6 +579,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             Launch l{};
             l.kind = Kind::Handover;
             l.phase = s == L - 1 ? FF_PHASE_SEED : FF_PHASE_HANDOVER;
+            l.desc_level = s;
             size_t o = hos.size();
             int64_t pix = 0;
             for (int j = 0; j < nj; j++) {
@@ -623,6 +644,7 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
             l.kind = Kind::Propagate;
             l.phase = FF_PHASE_PROPAGATE;
             l.level = pass;
+            l.desc_level = s;
             l.prop.tw = tc.tw;
             l.prop.th = tc.th;
             l.prop.max_iter = df ? 1 : n_iter;
@@ -803,7 +825,38 @@ ff_status build_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vect
 void free_plan(ff_ctx* c, Plan& P) {
     if (P.exec) cudaGraphExecDestroy(P.exec);
     P.exec = nullptr;
+    if (P.split_exec) cudaGraphExecDestroy(P.split_exec);
+    P.split_exec = nullptr;
     for (DevBuf& b : P.bufs) dev_free(c, b);
+}
+
+// Record launches [i0, i1) of the plan into one executable graph (none when the range is empty).
+ff_status capture_range(ff_ctx* c, const Plan& P, size_t i0, size_t i1, cudaGraphExec_t* out, int* nk, int* nc) {
+    *out = nullptr;
+    *nk = *nc = 0;
+    if (i0 >= i1) return FF_OK;
+    cudaGraph_t g = nullptr;
+    FF_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    ff_status s = FF_OK;
+    for (size_t i = i0; i < i1; i++) {
+        s = enqueue_launch(c, P.launches[i]);
+        if (s != FF_OK) break;
+        *nk += kernels_of(P.launches[i]);
+        *nc += clusters_of(P.launches[i]);
+    }
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (s != FF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return fail(c, FF_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return fail(c, FF_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    return FF_OK;
 }
 
 ff_status execute_plan(ff_ctx* c, Plan& P) {
@@ -811,35 +864,128 @@ ff_status execute_plan(ff_ctx* c, Plan& P) {
     bool use_graph = !c->profiling && c->stream != nullptr;
     if (!use_graph) return run_launches(c, P.launches, c->profiling);
     if (!P.exec) {
-        cudaGraph_t g = nullptr;
-        FF_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        ff_status s = FF_OK;
-        int nk = 0, nc = 0;
-        for (const Launch& l : P.launches) {
-            s = enqueue_launch(c, l);
-            if (s != FF_OK) break;
-            nk += kernels_of(l);
-            nc += clusters_of(l);
-        }
-        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-        if (s != FF_OK) {
-            if (g) cudaGraphDestroy(g);
-            return s;
-        }
-        if (e != cudaSuccess) return fail(c, FF_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&P.exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            P.exec = nullptr;
-            return fail(c, FF_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
-        }
-        P.graph_nodes = nk;
-        P.cluster_nodes = nc;
+        ff_status s = capture_range(c, P, 0, P.launches.size(), &P.exec, &P.graph_nodes, &P.cluster_nodes);
+        if (s != FF_OK) return s;
     }
     FF_CUDA(c, cudaGraphLaunch(P.exec, c->stream));
     c->replays += 1;
     c->launches += P.graph_nodes;
     c->cluster_launches += P.cluster_nodes;
+    return FF_OK;
+}
+
+// The side stream and the two events of ff_match_frames, created on first use.
+ff_status ensure_side(ff_ctx* c) {
+    if (!c->side) FF_CUDA(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    if (!c->ev_fork) FF_CUDA(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    if (!c->ev_join) FF_CUDA(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    return FF_OK;
+}
+
+// Record the plan's launches into one graph with the fine levels' descriptor launch on a branch: it starts after
+// launch `fork` - 1 and joins before launch `join`, the first that reads a level below the split.  The side stream
+// only carries the branch during the capture.  Every kernel node but the descriptor launch gets the highest
+// priority, so that the block scheduler serves the latency-bound coarse levels' launches first and the descriptor
+// launch takes the SMs they leave idle.
+ff_status capture_split(ff_ctx* c, Plan& P, size_t fork, size_t join, const FineWht& fine) {
+    int least = 0, greatest = 0;
+    FF_CUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    cudaGraph_t g = nullptr;
+    FF_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    ff_status s = FF_OK;
+    cudaError_t e = cudaSuccess;
+    bool forked = false;
+    int nk = 1, nc = 0;  // the descriptor launch, then the plan's
+    for (size_t i = 0; i < P.launches.size() && s == FF_OK && e == cudaSuccess; i++) {
+        if (i == fork) {
+            e = cudaEventRecord(c->ev_fork, c->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+            if (e != cudaSuccess) break;
+            forked = true;
+            launch_wht_tab(fine.tab, fine.n, fine.tiles, c->side, false);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+            if (e != cudaSuccess) break;
+        }
+        if (i == join) {
+            e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+            forked = false;
+            if (e != cudaSuccess) break;
+        }
+        s = enqueue_launch(c, P.launches[i]);
+        nk += kernels_of(P.launches[i]);
+        nc += clusters_of(P.launches[i]);
+    }
+    if (forked) {  // the branch rejoins the capture in every case
+        cudaError_t ej = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+        if (e == cudaSuccess) e = ej;
+    }
+    cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    if (s != FF_OK || e != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (s != FF_OK) return s;
+        return fail(c, FF_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    size_t nn = 0;
+    e = cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (size_t i = 0; i < nn && e == cudaSuccess; i++) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[i], &t);
+        if (e != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        e = cudaGraphKernelNodeGetParams(nodes[i], &kp);
+        if (e != cudaSuccess || kp.func == wht_tab_kernel()) continue;
+        cudaLaunchAttributeValue v{};
+        v.priority = greatest;
+        e = cudaGraphKernelNodeSetAttribute(nodes[i], cudaLaunchAttributePriority, &v);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiateWithFlags(&P.split_exec, g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        P.split_exec = nullptr;
+        return fail(c, FF_ERR_CUDA, "split graph failed: %s", cudaGetErrorString(e));
+    }
+    P.split_at[0] = fork;
+    P.split_at[1] = join;
+    P.split_tab = fine.tab;
+    P.split_n = fine.n;
+    P.split_tiles = fine.tiles;
+    P.split_nodes = nk;
+    P.split_clusters = nc;
+    return FF_OK;
+}
+
+// Run the plan with the fine levels' descriptor launch beside the coarse levels' matching (ff_match_frames).
+// Fork point: FF_OPT_OVERLAP 1, the start of the matching; 2, the first propagation launch (the coarsest level's,
+// once its initial matches and their costs are done).  Join: the first launch that reads a level below
+// `fine_below`.
+ff_status execute_plan_split(ff_ctx* c, Plan& P, const FineWht& fine, int fine_below) {
+    const size_t n = P.launches.size();
+    size_t join = n, fork = 0;
+    for (size_t i = 0; i < n; i++)
+        if (P.launches[i].desc_level >= 0 && P.launches[i].desc_level < fine_below) {
+            join = i;
+            break;
+        }
+    if (c->overlap == 2)
+        for (size_t i = 0; i < join; i++)
+            if (P.launches[i].kind == Kind::Propagate) {
+                fork = i;
+                break;
+            }
+    if (!P.split_exec || P.split_at[0] != fork || P.split_at[1] != join || P.split_tab != fine.tab ||
+        P.split_n != fine.n || P.split_tiles != fine.tiles) {
+        if (P.split_exec) cudaGraphExecDestroy(P.split_exec);
+        P.split_exec = nullptr;
+        ff_status s = capture_split(c, P, fork, join, fine);
+        if (s != FF_OK) return s;
+    }
+    FF_CUDA(c, cudaGraphLaunch(P.split_exec, c->stream));
+    c->replays += 1;
+    c->launches += P.split_nodes;
+    c->cluster_launches += P.split_clusters;
     return FF_OK;
 }
 
@@ -871,7 +1017,8 @@ ff_status drop_plans(ff_ctx* c) {
     return FF_OK;
 }
 
-ff_status run_jobs(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons) {
+// The cached plan of these jobs, built on first use.
+ff_status find_plan(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons, Plan** out) {
     std::vector<uintptr_t> key = plan_key(jobs, cons);
     auto it = c->plans.find(key);
     if (it == c->plans.end()) {
@@ -889,7 +1036,15 @@ ff_status run_jobs(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector
         c->plans_built += 1;
         it = c->plans.emplace(key, std::move(P)).first;
     }
-    return execute_plan(c, *it->second);
+    *out = it->second.get();
+    return FF_OK;
+}
+
+ff_status run_jobs(ff_ctx* c, const std::vector<DirJob>& jobs, const std::vector<ConsJob>& cons) {
+    Plan* P = nullptr;
+    ff_status s = find_plan(c, jobs, cons, &P);
+    if (s != FF_OK) return s;
+    return execute_plan(c, *P);
 }
 
 // Time every candidate configuration on the given jobs and keep, per level, the fastest.  Runs the real
@@ -1349,9 +1504,13 @@ ff_status ff_features(ff_ctx* c, const uint8_t* rgb_dev, int w, int h, int pitch
     return FF_OK;
 }
 
-ff_status ff_features_batch(ff_ctx* c, int n, const ff_frame* frames, ff_pyr** out) {
+// ff_features_batch; with fine_below > 0 the levels below it are left out of the launches and their table entries
+// returned in *fine, for the caller to launch.
+static ff_status features_batch_impl(ff_ctx* c, int n, const ff_frame* frames, ff_pyr** out, int fine_below,
+                                     FineWht* fine) {
     if (!c) return FF_ERR_ARG;
     if (n < 0 || (n > 0 && (!frames || !out))) return fail(c, FF_ERR_ARG, "bad frame list");
+    if (fine) *fine = FineWht{};
     for (int i = 0; i < n; i++) out[i] = nullptr;
     if (n == 0) return FF_OK;
     for (int i = 0; i < n; i++) {
@@ -1367,8 +1526,8 @@ ff_status ff_features_batch(ff_ctx* c, int n, const ff_frame* frames, ff_pyr** o
     // tables: one pyramid entry per frame with more than one level; the WHT levels of all frames, coarsest levels
     // first (their CTAs also write the seed rows, the longest tiles)
     std::vector<PyrArgs> pyr_tab;
-    std::vector<WhtLevel> wht_tab;
-    int ctas = 0, tiles = 0, max_L = 0;
+    std::vector<WhtLevel> wht_tab, wht_fine;
+    int ctas = 0, tiles = 0, fine_tiles = 0, max_L = 0;
     for (int i = 0; i < n; i++) {
         max_L = std::max(max_L, out[i]->L);
         if (out[i]->L > 1) {
@@ -1382,10 +1541,16 @@ ff_status ff_features_batch(ff_ctx* c, int n, const ff_frame* frames, ff_pyr** o
     for (int up = 0; up < max_L; up++)  // up = levels above the finest: 0 is each frame's coarsest level
         for (int i = 0; i < n; i++) {
             const int L = out[i]->L;
-            if (up < L) wht_tab.push_back(wht_level(out[i], L - 1 - up, frames[i].rgb_dev, frames[i].pitch_bytes, &tiles));
+            if (up >= L) continue;
+            if (L - 1 - up < fine_below)
+                wht_fine.push_back(wht_level(out[i], L - 1 - up, frames[i].rgb_dev, frames[i].pitch_bytes, &fine_tiles));
+            else
+                wht_tab.push_back(wht_level(out[i], L - 1 - up, frames[i].rgb_dev, frames[i].pitch_bytes, &tiles));
         }
     const size_t o_wht = align_up(pyr_tab.size() * sizeof(PyrArgs));
-    const size_t bytes = o_wht + wht_tab.size() * sizeof(WhtLevel);
+    const size_t o_fine = o_wht + align_up(wht_tab.size() * sizeof(WhtLevel));
+    const size_t bytes = wht_fine.empty() ? o_wht + wht_tab.size() * sizeof(WhtLevel)
+                                          : o_fine + wht_fine.size() * sizeof(WhtLevel);
     auto give_back = [&]() {
         for (int i = 0; i < n; i++) {
             out[i]->in_use = false;
@@ -1408,6 +1573,7 @@ ff_status ff_features_batch(ff_ctx* c, int n, const ff_frame* frames, ff_pyr** o
     std::vector<char> host(bytes);
     memcpy(host.data(), pyr_tab.data(), pyr_tab.size() * sizeof(PyrArgs));
     memcpy(host.data() + o_wht, wht_tab.data(), wht_tab.size() * sizeof(WhtLevel));
+    if (!wht_fine.empty()) memcpy(host.data() + o_fine, wht_fine.data(), wht_fine.size() * sizeof(WhtLevel));
     char* dev = static_cast<char*>(c->feat_tab.p);
 
     cudaEvent_t ea = nullptr, eb = nullptr;
@@ -1425,7 +1591,7 @@ ff_status ff_features_batch(ff_ctx* c, int n, const ff_frame* frames, ff_pyr** o
         nl++;
         for (int i = 0; i < n; i++) nl += deep_levels(out[i], c->stream);
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !wht_tab.empty()) {
         launch_wht_tab(reinterpret_cast<const WhtLevel*>(dev + o_wht), (int)wht_tab.size(), tiles, c->stream);
         nl++;
         e = cudaGetLastError();
@@ -1439,7 +1605,16 @@ ff_status ff_features_batch(ff_ctx* c, int n, const ff_frame* frames, ff_pyr** o
         FF_CUDA(c, cudaEventRecord(eb, c->stream));
         c->events.push_back({FF_PHASE_FEATURES, -1, ea, eb, nl});
     }
+    if (fine && !wht_fine.empty()) {
+        fine->tab = reinterpret_cast<const WhtLevel*>(dev + o_fine);
+        fine->n = (int)wht_fine.size();
+        fine->tiles = fine_tiles;
+    }
     return FF_OK;
+}
+
+ff_status ff_features_batch(ff_ctx* c, int n, const ff_frame* frames, ff_pyr** out) {
+    return features_batch_impl(c, n, frames, out, 0, nullptr);
 }
 
 ff_status ff_match_pair(ff_ctx* c, const ff_pyr* a, const ff_pyr* b, int dir, int16_t* flow_dev, int32_t* cost_dev) {
@@ -1492,6 +1667,61 @@ ff_status ff_match_batch(ff_ctx* c, int n, const ff_pair_job* jobs) {
     if (s != FF_OK) return s;
     FF_CUDA(c, cudaSetDevice(c->device));
     return run_jobs(c, dj, cj);
+}
+
+ff_status ff_match_frames(ff_ctx* c, int n_frames, const ff_frame* frames, int n_jobs, const ff_frame_job* jobs,
+                          ff_pyr** out) {
+    if (!c) return FF_ERR_ARG;
+    if (n_frames < 1 || !frames || n_jobs < 1 || !jobs) return fail(c, FF_ERR_ARG, "bad frame or job list");
+    if (out)
+        for (int i = 0; i < n_frames; i++) out[i] = nullptr;
+    for (int i = 0; i < n_jobs; i++) {  // everything the jobs can get wrong, before anything is launched
+        const ff_frame_job& J = jobs[i];
+        if (J.a < 0 || J.a >= n_frames || J.b < 0 || J.b >= n_frames)
+            return fail(c, FF_ERR_ARG, "job %d: frame index outside 0..%d", i, n_frames - 1);
+        if (frames[J.a].w != frames[J.b].w || frames[J.a].h != frames[J.b].h)
+            return fail(c, FF_ERR_ARG, "job %d: frames differ in size", i);
+        if (!J.flow_fwd || !J.flow_bwd || !J.mask) return fail(c, FF_ERR_ARG, "job %d: NULL output", i);
+        if (!aligned4(J.flow_fwd) || !aligned4(J.flow_bwd) || (J.cost_fwd && !aligned4(J.cost_fwd)) ||
+            (J.cost_bwd && !aligned4(J.cost_bwd)) || (J.flow_bwd2 && !aligned4(J.flow_bwd2)))
+            return fail(c, FF_ERR_ARG, "job %d: outputs must be 4-byte aligned", i);
+    }
+    FF_CUDA(c, cudaSetDevice(c->device));
+    // the fine levels' descriptors go beside the coarse levels' matching when the matching runs as graphs on a
+    // stream of its own and the coarsest level is above them
+    const int fine_below = 2;
+    const bool overlap = c->overlap > 0 && !c->profiling && c->stream != nullptr && c->prm.n_scales > fine_below;
+    if (overlap) {
+        ff_status s = ensure_side(c);
+        if (s != FF_OK) return s;
+    }
+    std::vector<ff_pyr*> pyrs(n_frames, nullptr);
+    FineWht fine;
+    ff_status s = features_batch_impl(c, n_frames, frames, pyrs.data(), overlap ? fine_below : 0, &fine);
+    if (s != FF_OK) return s;
+    std::vector<ff_pair_job> pj(n_jobs);
+    for (int i = 0; i < n_jobs; i++) {
+        const ff_frame_job& J = jobs[i];
+        pj[i] = ff_pair_job{pyrs[J.a], pyrs[J.b], J.flow_fwd, J.flow_bwd, J.cost_fwd, J.cost_bwd, J.mask, J.flow_bwd2};
+    }
+    std::vector<DirJob> dj;
+    std::vector<ConsJob> cj;
+    s = collect_batch(c, n_jobs, pj.data(), dj, cj);
+    Plan* P = nullptr;
+    if (s == FF_OK) s = find_plan(c, dj, cj, &P);
+    if (s == FF_OK) {
+        s = fine.n > 0 ? execute_plan_split(c, *P, fine, fine_below) : execute_plan(c, *P);
+    } else if (fine.n > 0) {  // no matching: the pyramids are still completed, on the context's stream
+        launch_wht_tab(fine.tab, fine.n, fine.tiles, c->stream);
+        c->launches += 1;
+    }
+    for (int i = 0; i < n_frames; i++) {
+        if (out)
+            out[i] = pyrs[i];
+        else
+            pyrs[i]->in_use = false;  // recycled by later calls, after this call's work on the stream
+    }
+    return s;
 }
 
 ff_status ff_autotune(ff_ctx* c, int n, const ff_pair_job* jobs, int reps) {
@@ -1660,6 +1890,10 @@ ff_status ff_set_option(ff_ctx* c, int option, int64_t value) {
             if (value < 0 || value > (1ll << 30)) return fail(c, FF_ERR_ARG, "allocation failures must be 0..2^30");
             c->fail_allocs = value;  // takes effect at once and keeps the cached plans
             return FF_OK;
+        case FF_OPT_OVERLAP:
+            if (value < 0 || value > 2) return fail(c, FF_ERR_ARG, "overlap must be 0, 1 or 2");
+            c->overlap = (int)value;  // the plans' split graphs are recaptured when the fork point moves
+            return FF_OK;
         default:
             return fail(c, FF_ERR_ARG, "unknown option %d", option);
     }
@@ -1751,9 +1985,13 @@ ff_status ff_destroy(ff_ctx* c) {
     if (!c) return FF_ERR_ARG;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->side) cudaStreamSynchronize(c->side);
     for (auto& kv : c->plans) free_plan(c, *kv.second);
     for (auto& p : c->pyrs) dev_free(c, p->mem);
     dev_free(c, c->feat_tab);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->d_err) cudaFree(c->d_err);
     for (auto& e : c->events) {
         cudaEventDestroy(e.a);

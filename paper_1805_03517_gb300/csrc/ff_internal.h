@@ -72,7 +72,8 @@ int wht_tiles_x(int w);
 int wht_tiles(int w, int h);
 void launch_wht(const WhtArgs& a, int total_tiles, cudaStream_t st);
 // the levels of many frames in one launch (tab_dev: n entries in device memory, tile_base ascending)
-void launch_wht_tab(const WhtLevel* tab_dev, int n, int total_tiles, cudaStream_t st);
+void launch_wht_tab(const WhtLevel* tab_dev, int n, int total_tiles, cudaStream_t st, bool after_kernel = true);
+const void* wht_tab_kernel();  // the kernel of launch_wht_tab (to find its node in a captured graph)
 
 // ---------------------------------------------------------------------------------------------------------
 // initial matches (exact nearest neighbour at the coarsest level)

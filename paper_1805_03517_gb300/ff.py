@@ -21,7 +21,7 @@ LIB_PATH = os.environ.get("FF_LIBRARY", LIB_PATH)
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "ff.h")
 
 FF_OK, FF_ERR_ARG, FF_ERR_OOM, FF_ERR_CUDA, FF_ERR_TIMEOUT, FF_ERR_BUSY = range(6)
-FF_OPT_SEED_KERNEL, FF_OPT_WAIT_LIMIT, FF_OPT_TEST_WITHHOLD_COPIES, FF_OPT_TEST_FAIL_ALLOCS = 1, 2, 3, 4
+FF_OPT_SEED_KERNEL, FF_OPT_WAIT_LIMIT, FF_OPT_TEST_WITHHOLD_COPIES, FF_OPT_TEST_FAIL_ALLOCS, FF_OPT_OVERLAP = 1, 2, 3, 4, 5
 FF_SEED_MMA_SYNC, FF_SEED_TCGEN05 = 0, 1
 FF_COST_WHT_SAD, FF_COST_CENSUS = 0, 1
 STATUS_NAMES = {0: "FF_OK", 1: "FF_ERR_ARG", 2: "FF_ERR_OOM", 3: "FF_ERR_CUDA", 4: "FF_ERR_TIMEOUT", 5: "FF_ERR_BUSY"}
@@ -55,6 +55,12 @@ class Request(ctypes.Structure):
 
 class Frame(ctypes.Structure):
     _fields_ = [("rgb_dev", ctypes.c_void_p), ("w", ctypes.c_int), ("h", ctypes.c_int), ("pitch_bytes", ctypes.c_int)]
+
+
+class FrameJob(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int), ("b", ctypes.c_int), ("flow_fwd", ctypes.c_void_p),
+                ("flow_bwd", ctypes.c_void_p), ("cost_fwd", ctypes.c_void_p), ("cost_bwd", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("flow_bwd2", ctypes.c_void_p)]
 
 
 class Tuning(ctypes.Structure):
@@ -95,6 +101,7 @@ def lib():
         "ff_features_batch": (S, [vp, i, ctypes.POINTER(Frame), ctypes.POINTER(vp)]),
         "ff_match_pair": (S, [vp, vp, vp, i, vp, vp]),
         "ff_match_batch": (S, [vp, i, ctypes.POINTER(PairJob)]),
+        "ff_match_frames": (S, [vp, i, ctypes.POINTER(Frame), i, ctypes.POINTER(FrameJob), ctypes.POINTER(vp)]),
         "ff_autotune": (S, [vp, i, ctypes.POINTER(PairJob), i]),
         "ff_set_tuning": (S, [vp, i, ctypes.POINTER(Tuning)]),
         "ff_get_tuning": (S, [vp, i, ctypes.POINTER(Tuning)]),
@@ -173,6 +180,16 @@ def ff_match_pair(ctx, a, b, dir: int, flow_dev: int, cost_dev: int | None):
 def ff_match_batch(ctx, jobs):
     arr = (PairJob * len(jobs))(*jobs)
     _check(ctx, lib().ff_match_batch(ctx, len(jobs), arr))
+
+
+def ff_match_frames(ctx, frames, jobs, keep: bool = False):
+    """frames: list of (rgb_dev, w, h, pitch_bytes); jobs: list of FrameJob.  Returns the pyramid handles with
+    keep, else None (the pyramids are released by the call)."""
+    arr = (Frame * len(frames))(*[Frame(*f) for f in frames])
+    jarr = (FrameJob * len(jobs))(*jobs)
+    out = (ctypes.c_void_p * len(frames))() if keep else None
+    _check(ctx, lib().ff_match_frames(ctx, len(frames), arr, len(jobs), jarr, out))
+    return [ctypes.c_void_p(p) for p in out] if keep else None
 
 
 def ff_autotune(ctx, jobs, reps: int = 3):
@@ -384,14 +401,18 @@ class Matcher:
         self._uses(img)
         return Pyramid(ff_features(self.ctx, img.data_ptr(), w, h, img.stride(0)), w, h)
 
-    def features_batch(self, imgs) -> list:
-        """Pyramids of many frames (uint8 [h][w][3] CUDA tensors of any sizes) in one launch per kernel."""
+    def _frames(self, imgs):
         frames = []
         for img in imgs:
             assert img.dtype == self.torch.uint8 and img.is_cuda and img.dim() == 3 and img.shape[2] == 3
             assert img.stride(2) == 1 and img.stride(1) == 3
             frames.append((img.data_ptr(), int(img.shape[1]), int(img.shape[0]), img.stride(0)))
         self._uses(*imgs)
+        return frames
+
+    def features_batch(self, imgs) -> list:
+        """Pyramids of many frames (uint8 [h][w][3] CUDA tensors of any sizes) in one launch per kernel."""
+        frames = self._frames(imgs)
         hs = ff_features_batch(self.ctx, frames)
         return [Pyramid(hd, f[1], f[2]) for hd, f in zip(hs, frames)]
 
@@ -468,6 +489,24 @@ class Matcher:
             outs = self.alloc_outputs(pairs, with_cost, second_check)
         ff_match_batch(self.ctx, self._jobs(pairs, outs))
         return outs
+
+    def match_frames(self, img_pairs, outs=None, with_cost=True, second_check=False, keep_pyramids=False):
+        """Features and matching of image pairs [(a, b), ...] (uint8 [h][w][3] CUDA tensors) in one call, the fine
+        levels' descriptors written beside the coarse levels' matching.  Returns (or fills) the outputs of
+        match_batch; with keep_pyramids, (outputs, [(Pyramid a, Pyramid b), ...]), released by the caller."""
+        frames = self._frames([x for pr in img_pairs for x in pr])
+        if outs is None:
+            outs = self.alloc_outputs([(Pyramid(None, f[1], f[2]), None) for f in frames[0::2]], with_cost,
+                                      second_check)
+        jobs = [FrameJob(2 * k, 2 * k + 1, o["flow_fwd"].data_ptr(), o["flow_bwd"].data_ptr(),
+                         o["cost_fwd"].data_ptr() if "cost_fwd" in o else None,
+                         o["cost_bwd"].data_ptr() if "cost_bwd" in o else None, o["mask"].data_ptr(),
+                         o["flow_bwd2"].data_ptr() if "flow_bwd2" in o else None) for k, o in enumerate(outs)]
+        hs = ff_match_frames(self.ctx, frames, jobs, keep_pyramids)
+        if not keep_pyramids:
+            return outs
+        pyrs = [Pyramid(hd, f[1], f[2]) for hd, f in zip(hs, frames)]
+        return outs, list(zip(pyrs[0::2], pyrs[1::2]))
 
     def autotune(self, pairs, outs=None, reps=3):
         """Tune the per-level propagation configuration for batches shaped like `pairs` (outputs overwritten)."""
