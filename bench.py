@@ -230,8 +230,9 @@ def flow_accuracy(flow, mask, gt):
             "outliers_kept": float(out[k].mean()) if k.any() else None}
 
 
-def measure_batched(torch, ff, configs, stream, local_rank, steps):
-    """48 pairs of three sizes per step in merged launches (graph replay), inputs larger than L2."""
+def measure_batched(torch, ff, configs, stream, local_rank, steps, frames_call=True):
+    """48 pairs of three sizes per step in merged launches (graph replay), inputs larger than L2; with frames_call,
+    each step is one ff_match_frames call, else ff_features_batch + ff_match_batch."""
     wl = configs.workload("batch48_mixed")
     imgs = make_inputs(wl)
     dev = torch.device("cuda", local_rank)
@@ -250,6 +251,9 @@ def measure_batched(torch, ff, configs, stream, local_rank, steps):
 
     def step():  # features of all 96 frames in one launch per kernel, then the merged matching launches
         nonlocal outs
+        if frames_call:
+            outs = M.match_frames(d, outs=outs, with_cost=False)
+            return
         fp = M.features_batch(frames)
         pyrs = list(zip(fp[0::2], fp[1::2]))
         outs = M.match_batch(pyrs, outs=outs, with_cost=False)
@@ -315,7 +319,8 @@ def measure_batched(torch, ff, configs, stream, local_rank, steps):
     return {"workload": wl.name, "pairs_per_step": len(wl.pairs), "px_per_step": wl.pixels,
             "value": wl.pixels / (ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "gpu_launches_per_step": launches / steps, "tiles_per_level": [list(c) for c in tuning],
-            "l2": "not flushed: 5 GB of features per step exceed L2", "roofline": roof}
+            "l2": "not flushed: 5 GB of features per step exceed L2", "roofline": roof,
+            "features": "ff_match_frames" if frames_call else "ff_features_batch + ff_match_batch"}
 
 
 def measure_census(torch, ff, configs, stream, local_rank, steps, flush):
@@ -928,7 +933,8 @@ def main():
         if rank == 0:
             line["census_cost"] = census
     if not args.no_batched:
-        batched = measure_batched(torch, ff, configs, stream, local_rank, steps=max(5, min(30, args.steps // 10)))
+        batched = measure_batched(torch, ff, configs, stream, local_rank, steps=max(5, min(30, args.steps // 10)),
+                                  frames_call=args.features == "frames")
         if rank == 0:
             line["batched"] = batched
     if not args.no_served:
