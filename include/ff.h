@@ -181,7 +181,8 @@ typedef struct {
  * levels' matching, whose kernels have the higher priority (FF_OPT_OVERLAP); level 1 waits for it.  All work is
  * ordered on the context's stream when the call returns.  If out is not NULL it receives the n_frames
  * pyramids (released by the caller); otherwise they are released at the end of the call and their memory is
- * recycled by later calls.  Argument errors are found before anything is launched. */
+ * recycled by later calls.  Argument errors are found before anything is launched; on any error out[] is all
+ * NULL and the call keeps no pyramid. */
 FF_API ff_status ff_match_frames(ff_ctx* ctx, int n_frames, const ff_frame* frames, int n_jobs,
                                  const ff_frame_job* jobs, ff_pyr** out);
 

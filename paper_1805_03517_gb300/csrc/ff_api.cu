@@ -1709,14 +1709,13 @@ ff_status ff_match_frames(ff_ctx* c, int n_frames, const ff_frame* frames, int n
     s = collect_batch(c, n_jobs, pj.data(), dj, cj);
     Plan* P = nullptr;
     if (s == FF_OK) s = find_plan(c, dj, cj, &P);
-    if (s == FF_OK) {
-        s = fine.n > 0 ? execute_plan_split(c, *P, fine, fine_below) : execute_plan(c, *P);
-    } else if (fine.n > 0) {  // no matching: the pyramids are still completed, on the context's stream
+    if (s == FF_OK) s = fine.n > 0 ? execute_plan_split(c, *P, fine, fine_below) : execute_plan(c, *P);
+    if (s != FF_OK && fine.n > 0) {  // no (or a failed) matching: the pyramids are still completed on the stream
         launch_wht_tab(fine.tab, fine.n, fine.tiles, c->stream);
         c->launches += 1;
     }
     for (int i = 0; i < n_frames; i++) {
-        if (out)
+        if (out && s == FF_OK)
             out[i] = pyrs[i];
         else
             pyrs[i]->in_use = false;  // recycled by later calls, after this call's work on the stream

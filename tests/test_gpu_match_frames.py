@@ -226,3 +226,31 @@ def test_argument_errors_launch_nothing(ffm):
     M.sync()
     assert M.stats()["kernel_launches"] > s0["kernel_launches"]
     M.close()
+
+
+def test_out_of_memory_keeps_no_pyramid(ffm):
+    """An allocation failure while the matching is prepared returns FF_ERR_OOM; the call's pyramids go back to the
+    pool (the next call gets the same ones) and the next call matches as before."""
+    prm = configs.MatchParams(n_scales=4, iters=2, eps=1)
+    dev = to_dev(small_pairs([(90, 140)], 2010))
+    M = ffm.Matcher(prm, 0)
+    outs, pyrs = M.match_frames(dev, keep_pyramids=True)
+    M.sync()
+    ref = host(outs)
+    handles = {p.handle.value for pr in pyrs for p in pr}
+    for pa, pb in pyrs:
+        M.release(pa)
+        M.release(pb)
+    ffm.ff_set_option(M.ctx, ffm.FF_OPT_TEST_FAIL_ALLOCS, 1)
+    with pytest.raises(ffm.FFError) as e:
+        M.match_frames(dev, keep_pyramids=True)  # new outputs: a new plan, whose scratch allocation fails
+    assert e.value.status == ffm.FF_ERR_OOM
+    ffm.ff_set_option(M.ctx, ffm.FF_OPT_TEST_FAIL_ALLOCS, 0)
+    outs2, pyrs2 = M.match_frames(dev, keep_pyramids=True)
+    M.sync()
+    assert {p.handle.value for pr in pyrs2 for p in pr} == handles
+    G.assert_same(host(outs2)[0], ref[0])
+    for pa, pb in pyrs2:
+        M.release(pa)
+        M.release(pb)
+    M.close()
